@@ -1,0 +1,618 @@
+/*
+ * oracle.c -- FP64 CPU oracle (test infrastructure only; see oracle.h).
+ *
+ * Written to be read against the paper, not to be fast:
+ *   Eq. 1 ............ oracle_direct, kernel_term
+ *   Sect. 1 (tree) ... oracle_tree_build (recursive subdivision), node moments
+ *   Eq. 2 (MAC) ...... mac_accept
+ *   Sect. 1 (list) ... walk_group / walk_particle (one shared list per group)
+ * Readings where the paper is silent are marked READING and repeated in the
+ * design notes.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1: one softened pair term, accumulated into s[0..2] (acceleration) and
+ * s[3] (potential).  (dx,dy,dz) = r_j - r_i. */
+static inline void kernel_term(double dx, double dy, double dz, double mj, double e2, double *s)
+{
+    double r2 = dx * dx + dy * dy + dz * dz + e2;
+    double rinv = 1.0 / sqrt(r2);
+    double w = mj * rinv * rinv * rinv; /* m_j / (|r|^2 + eps^2)^{3/2} */
+    s[0] += w * dx;
+    s[1] += w * dy;
+    s[2] += w * dz;
+    s[3] -= mj * rinv;
+}
+
+static void direct_one(int64_t n, const double *x, const double *y, const double *z,
+                       const double *m, int64_t i, double G, double e2, double *out)
+{
+    double s[4] = {0, 0, 0, 0};
+    for (int64_t j = 0; j < n; j++) {
+        if (j == i) continue; /* j != i in Eq. 1 */
+        kernel_term(x[j] - x[i], y[j] - y[i], z[j] - z[i], m[j], e2, s);
+    }
+    for (int k = 0; k < 4; k++) out[k] = G * s[k];
+}
+
+void oracle_direct(int64_t n, const double *x, const double *y, const double *z,
+                   const double *m, double G, double eps,
+                   double *ax, double *ay, double *az, double *phi)
+{
+    double e2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        double o[4];
+        direct_one(n, x, y, z, m, i, G, e2, o);
+        ax[i] = o[0]; ay[i] = o[1]; az[i] = o[2];
+        if (phi) phi[i] = o[3];
+    }
+}
+
+void oracle_direct_targets(int64_t n, const double *x, const double *y, const double *z,
+                           const double *m, int64_t nt, const int64_t *tgt,
+                           double G, double eps,
+                           double *ax, double *ay, double *az, double *phi)
+{
+    double e2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < nt; k++) {
+        double o[4];
+        direct_one(n, x, y, z, m, tgt[k], G, e2, o);
+        ax[k] = o[0]; ay[k] = o[1]; az[k] = o[2];
+        if (phi) phi[k] = o[3];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bounding cube and FP32 cell quantisation.  READING: the paper sorts
+ * space-filling-curve keys (Sect. 4.1) but gives no formula; the cube is the
+ * axis-aligned box of the particles, widened by 2^-20 so the maximum maps
+ * inside, and cell indices are taken in FP32 so that both implementations
+ * quantise identically. */
+void oracle_cube(int64_t n, const float *x, const float *y, const float *z, float cube[4])
+{
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const float *p[3] = {x, y, z};
+    for (int64_t i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++) {
+            float v = p[a][i];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+    if (n <= 0) {
+        lo[0] = lo[1] = lo[2] = 0.0f;
+        hi[0] = hi[1] = hi[2] = 0.0f;
+    }
+    float ext = hi[0] - lo[0];
+    float ey = hi[1] - lo[1], ez = hi[2] - lo[2];
+    if (ey > ext) ext = ey;
+    if (ez > ext) ext = ez;
+    volatile float L = ext * (1.0f + 0x1p-20f);
+    cube[0] = lo[0];
+    cube[1] = lo[1];
+    cube[2] = lo[2];
+    cube[3] = (L > 0.0f) ? L : 1.0f;
+}
+
+void oracle_cells(int64_t n, const float *x, const float *y, const float *z,
+                  const float cube[4], int levels,
+                  uint32_t *qx, uint32_t *qy, uint32_t *qz)
+{
+    const float *p[3] = {x, y, z};
+    uint32_t *q[3] = {qx, qy, qz};
+    uint32_t top = (1u << levels) - 1u;
+    volatile float scale = (float)(1u << levels) / cube[3];
+    for (int64_t i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++) {
+            volatile float d = p[a][i] - cube[a];
+            volatile float t = d * scale;
+            float f = floorf(t);
+            uint32_t c = (f <= 0.0f) ? 0u : (uint32_t)f;
+            q[a][i] = c > top ? top : c;
+        }
+}
+
+uint64_t oracle_interleave(uint32_t qx, uint32_t qy, uint32_t qz, int levels)
+{
+    uint64_t key = 0;
+    for (int l = levels - 1; l >= 0; l--) {
+        key = (key << 3) | ((uint64_t)((qx >> l) & 1u) << 2)
+                         | ((uint64_t)((qy >> l) & 1u) << 1)
+                         | (uint64_t)((qz >> l) & 1u);
+    }
+    return key;
+}
+
+static const uint64_t *g_sort_keys;
+static int cmp_key_index(const void *a, const void *b)
+{
+    int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+    uint64_t ki = g_sort_keys[i], kj = g_sort_keys[j];
+    if (ki < kj) return -1;
+    if (ki > kj) return 1;
+    return (i > j) - (i < j);
+}
+
+void oracle_sort(int64_t n, const uint64_t *keys, int64_t *order)
+{
+    for (int64_t i = 0; i < n; i++) order[i] = i;
+    g_sort_keys = keys;
+    qsort(order, (size_t)n, sizeof(int64_t), cmp_key_index);
+    g_sort_keys = NULL;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Octree (Sect. 1, Barnes & Hut), built by recursive subdivision. */
+struct oracle_tree {
+    int64_t n;
+    int levels, leaf_cap;
+    float cube[4];
+    double *x, *y, *z, *m;
+    uint32_t *q[3];
+    uint64_t *key;
+    int64_t *order; /* particle ids in tree order */
+    /* nodes */
+    int64_t nn, capn;
+    int32_t *lev, *nchild;
+    int64_t *first, *count, *child;
+    uint64_t *prefix;
+    double *cx, *cy, *cz, *M, *b;
+};
+
+static int grow_nodes(oracle_tree *t)
+{
+    int64_t nc = t->capn ? 2 * t->capn : 1024;
+#define GROW(f, T) do { void *p_ = realloc(t->f, (size_t)nc * sizeof(T)); if (!p_) return 0; t->f = (T *)p_; } while (0)
+    GROW(lev, int32_t); GROW(nchild, int32_t);
+    GROW(first, int64_t); GROW(count, int64_t); GROW(child, int64_t);
+    GROW(prefix, uint64_t);
+    GROW(cx, double); GROW(cy, double); GROW(cz, double); GROW(M, double); GROW(b, double);
+#undef GROW
+    t->capn = nc;
+    return 1;
+}
+
+static int64_t new_node(oracle_tree *t)
+{
+    if (t->nn == t->capn && !grow_nodes(t)) return -1;
+    return t->nn++;
+}
+
+static const oracle_tree *g_leaf_tree;
+static int cmp_leaf(const void *a, const void *b)
+{
+    int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+    uint64_t ki = g_leaf_tree->key[i], kj = g_leaf_tree->key[j];
+    if (ki < kj) return -1;
+    if (ki > kj) return 1;
+    return (i > j) - (i < j);
+}
+
+/* Node `id` holds order[lo..hi).  Split into the 8 octants of its cell while
+ * it holds more than leaf_cap particles and is above the finest level. */
+static int build_rec(oracle_tree *t, int64_t id, int level, uint64_t prefix,
+                     int64_t lo, int64_t hi, int64_t *tmp)
+{
+    t->lev[id] = level;
+    t->prefix[id] = prefix;
+    t->first[id] = lo;
+    t->count[id] = hi - lo;
+    t->nchild[id] = 0;
+    t->child[id] = -1;
+    if (hi - lo <= t->leaf_cap || level == t->levels) {
+        g_leaf_tree = t;
+        qsort(t->order + lo, (size_t)(hi - lo), sizeof(int64_t), cmp_leaf);
+        return 1;
+    }
+    int shift = t->levels - 1 - level;
+    int64_t cnt[8] = {0}, pos[8];
+    for (int64_t k = lo; k < hi; k++) {
+        int64_t p = t->order[k];
+        int o = (int)((((t->q[0][p] >> shift) & 1u) << 2) | (((t->q[1][p] >> shift) & 1u) << 1) |
+                      ((t->q[2][p] >> shift) & 1u));
+        cnt[o]++;
+    }
+    pos[0] = lo;
+    for (int o = 1; o < 8; o++) pos[o] = pos[o - 1] + cnt[o - 1];
+    int64_t start[8];
+    memcpy(start, pos, sizeof start);
+    for (int64_t k = lo; k < hi; k++) {
+        int64_t p = t->order[k];
+        int o = (int)((((t->q[0][p] >> shift) & 1u) << 2) | (((t->q[1][p] >> shift) & 1u) << 1) |
+                      ((t->q[2][p] >> shift) & 1u));
+        tmp[pos[o]++] = p;
+    }
+    memcpy(t->order + lo, tmp + lo, (size_t)(hi - lo) * sizeof(int64_t));
+    /* allocate the non-empty children contiguously, then recurse */
+    int64_t ids[8];
+    int nc = 0;
+    for (int o = 0; o < 8; o++) {
+        if (!cnt[o]) continue;
+        int64_t c = new_node(t);
+        if (c < 0) return 0;
+        ids[o] = c;
+        if (!nc) t->child[id] = c;
+        nc++;
+    }
+    t->nchild[id] = nc;
+    for (int o = 0; o < 8; o++) {
+        if (!cnt[o]) continue;
+        if (!build_rec(t, ids[o], level + 1, (prefix << 3) | (uint64_t)o, start[o],
+                       start[o] + cnt[o], tmp))
+            return 0;
+    }
+    return 1;
+}
+
+/* Integer cell coordinates of node id at its level (from its prefix). */
+static void node_cell(const oracle_tree *t, int64_t id, uint32_t c[3])
+{
+    c[0] = c[1] = c[2] = 0;
+    uint64_t p = t->prefix[id];
+    for (int l = 0; l < t->lev[id]; l++) {
+        uint32_t o = (uint32_t)((p >> (3 * l)) & 7u);
+        c[0] |= ((o >> 2) & 1u) << l;
+        c[1] |= ((o >> 1) & 1u) << l;
+        c[2] |= (o & 1u) << l;
+    }
+}
+
+/* Monopole (Sect. 2.2: centre of mass and total mass of each node) and size
+ * b_J for the MAC (Eq. 2).  READING for b_J: an upper bound on the distance
+ * from the centre of mass to any member particle -- exact (the maximum) for
+ * leaves, for internal nodes the smaller of max_c(|com_c - com| + b_c) and
+ * the distance from com to the farthest corner of the node's cell, the cell
+ * being widened by one finest-level cell width on every side to cover the
+ * FP32 quantisation. */
+static void node_moments(oracle_tree *t)
+{
+    for (int64_t id = t->nn - 1; id >= 0; id--) {
+        double M = 0, sx = 0, sy = 0, sz = 0;
+        for (int64_t k = t->first[id]; k < t->first[id] + t->count[id]; k++) {
+            int64_t p = t->order[k];
+            M += t->m[p];
+            sx += t->m[p] * t->x[p];
+            sy += t->m[p] * t->y[p];
+            sz += t->m[p] * t->z[p];
+        }
+        uint32_t c[3];
+        node_cell(t, id, c);
+        double side = (double)t->cube[3] / (double)(1u << t->lev[id]);
+        double pad = (double)t->cube[3] / (double)(1u << t->levels);
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; a++) {
+            lo[a] = (double)t->cube[a] + (double)c[a] * side - pad;
+            hi[a] = (double)t->cube[a] + (double)(c[a] + 1) * side + pad;
+        }
+        double com[3];
+        if (M > 0) {
+            com[0] = sx / M; com[1] = sy / M; com[2] = sz / M;
+        } else { /* massless node: use the cell centre */
+            for (int a = 0; a < 3; a++) com[a] = 0.5 * (lo[a] + hi[a]);
+        }
+        t->M[id] = M;
+        t->cx[id] = com[0]; t->cy[id] = com[1]; t->cz[id] = com[2];
+        double bb;
+        if (t->nchild[id] == 0) {
+            bb = 0;
+            for (int64_t k = t->first[id]; k < t->first[id] + t->count[id]; k++) {
+                int64_t p = t->order[k];
+                double dx = t->x[p] - com[0], dy = t->y[p] - com[1], dz = t->z[p] - com[2];
+                double d = sqrt(dx * dx + dy * dy + dz * dz);
+                if (d > bb) bb = d;
+            }
+        } else {
+            double rec = 0;
+            for (int64_t ch = t->child[id]; ch < t->child[id] + t->nchild[id]; ch++) {
+                double dx = t->cx[ch] - com[0], dy = t->cy[ch] - com[1], dz = t->cz[ch] - com[2];
+                double d = sqrt(dx * dx + dy * dy + dz * dz) + t->b[ch];
+                if (d > rec) rec = d;
+            }
+            double c2 = 0;
+            for (int a = 0; a < 3; a++) {
+                double e = fmax(com[a] - lo[a], hi[a] - com[a]);
+                c2 += e * e;
+            }
+            double corner = sqrt(c2);
+            bb = rec < corner ? rec : corner;
+        }
+        t->b[id] = bb;
+    }
+}
+
+oracle_tree *oracle_tree_build(int64_t n, const double *x, const double *y, const double *z,
+                               const double *m, int levels, int leaf_cap)
+{
+    if (n <= 0 || levels < 1 || levels > 21 || leaf_cap < 1) return NULL;
+    oracle_tree *t = (oracle_tree *)calloc(1, sizeof *t);
+    if (!t) return NULL;
+    t->n = n;
+    t->levels = levels;
+    t->leaf_cap = leaf_cap;
+    size_t nd = (size_t)n * sizeof(double);
+    t->x = malloc(nd); t->y = malloc(nd); t->z = malloc(nd); t->m = malloc(nd);
+    float *fx = malloc((size_t)n * sizeof(float)), *fy = malloc((size_t)n * sizeof(float)),
+          *fz = malloc((size_t)n * sizeof(float));
+    for (int a = 0; a < 3; a++) t->q[a] = malloc((size_t)n * sizeof(uint32_t));
+    t->key = malloc((size_t)n * sizeof(uint64_t));
+    t->order = malloc((size_t)n * sizeof(int64_t));
+    int64_t *tmp = malloc((size_t)n * sizeof(int64_t));
+    int ok = t->x && t->y && t->z && t->m && fx && fy && fz && t->q[0] && t->q[1] && t->q[2] &&
+             t->key && t->order && tmp;
+    if (ok) {
+        memcpy(t->x, x, nd); memcpy(t->y, y, nd); memcpy(t->z, z, nd); memcpy(t->m, m, nd);
+        for (int64_t i = 0; i < n; i++) {
+            fx[i] = (float)x[i]; fy[i] = (float)y[i]; fz[i] = (float)z[i];
+            t->order[i] = i;
+        }
+        oracle_cube(n, fx, fy, fz, t->cube);
+        oracle_cells(n, fx, fy, fz, t->cube, levels, t->q[0], t->q[1], t->q[2]);
+        for (int64_t i = 0; i < n; i++)
+            t->key[i] = oracle_interleave(t->q[0][i], t->q[1][i], t->q[2][i], levels);
+        int64_t root = new_node(t);
+        ok = root == 0 && build_rec(t, root, 0, 0, 0, n, tmp);
+        if (ok) node_moments(t);
+    }
+    free(fx); free(fy); free(fz); free(tmp);
+    if (!ok) {
+        oracle_tree_free(t);
+        return NULL;
+    }
+    return t;
+}
+
+void oracle_tree_free(oracle_tree *t)
+{
+    if (!t) return;
+    free(t->x); free(t->y); free(t->z); free(t->m);
+    free(t->q[0]); free(t->q[1]); free(t->q[2]);
+    free(t->key); free(t->order);
+    free(t->lev); free(t->nchild); free(t->first); free(t->count); free(t->child);
+    free(t->prefix); free(t->cx); free(t->cy); free(t->cz); free(t->M); free(t->b);
+    free(t);
+}
+
+int64_t oracle_tree_nnodes(const oracle_tree *t) { return t->nn; }
+
+void oracle_tree_cube(const oracle_tree *t, float cube[4]) { memcpy(cube, t->cube, sizeof t->cube); }
+
+void oracle_tree_nodes(const oracle_tree *t, int32_t *level, uint64_t *prefix,
+                       int64_t *first, int64_t *count, int32_t *nchild, int64_t *child,
+                       double *cx, double *cy, double *cz, double *M, double *b)
+{
+    for (int64_t i = 0; i < t->nn; i++) {
+        if (level) level[i] = t->lev[i];
+        if (prefix) prefix[i] = t->prefix[i];
+        if (first) first[i] = t->first[i];
+        if (count) count[i] = t->count[i];
+        if (nchild) nchild[i] = t->nchild[i];
+        if (child) child[i] = t->child[i];
+        if (cx) cx[i] = t->cx[i];
+        if (cy) cy[i] = t->cy[i];
+        if (cz) cz[i] = t->cz[i];
+        if (M) M[i] = t->M[i];
+        if (b) b[i] = t->b[i];
+    }
+}
+
+void oracle_tree_order(const oracle_tree *t, int64_t *order)
+{
+    memcpy(order, t->order, (size_t)t->n * sizeof(int64_t));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Groups of particles sharing one interaction list (Sect. 1: 32 threads of a
+ * warp share a list).  READING: a group is the largest node holding at most
+ * group_size particles; a finest-level leaf holding more is cut into chunks. */
+static int64_t groups_rec(const oracle_tree *t, int64_t id, int G, int64_t ng,
+                          int64_t *first, int64_t *count)
+{
+    if (t->count[id] <= G) {
+        if (first) { first[ng] = t->first[id]; count[ng] = t->count[id]; }
+        return ng + 1;
+    }
+    if (t->nchild[id] == 0) {
+        for (int64_t s = 0; s < t->count[id]; s += G) {
+            if (first) {
+                first[ng] = t->first[id] + s;
+                count[ng] = (t->count[id] - s < G) ? t->count[id] - s : G;
+            }
+            ng++;
+        }
+        return ng;
+    }
+    for (int64_t c = t->child[id]; c < t->child[id] + t->nchild[id]; c++)
+        ng = groups_rec(t, c, G, ng, first, count);
+    return ng;
+}
+
+int64_t oracle_tree_groups(const oracle_tree *t, int group_size, int64_t *first, int64_t *count)
+{
+    return groups_rec(t, 0, group_size, 0, first, count);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 2, the acceleration MAC:  G M_J / d^2 (b_J / d)^2 <= dacc |a_old|,
+ * evaluated as G M_J b_J^2 <= dacc |a_old| d^4 (accept on equality), plus the
+ * READING that a node is accepted only if d > b_J (it cannot contain the
+ * target).  Geometric variant: b_J <= theta d, also with d > b_J. */
+static inline int mac_accept(int geometric, double d, double bJ, double MJ, double G,
+                             double dacc, double amin, double theta)
+{
+    if (!(d > bJ)) return 0;
+    if (geometric) return bJ <= theta * d;
+    double d2 = d * d;
+    return G * MJ * bJ * bJ <= dacc * amin * d2 * d2;
+}
+
+typedef struct {
+    const oracle_tree *t;
+    int geometric;
+    double G, e2, dacc, theta;
+} walk_ctx;
+
+/* Walk for the particles tree-order[k0 .. k0+cnt) sharing one list.  The MAC
+ * uses the group sphere (c, r) and amin; for particle mode cnt = 1, r = 0. */
+static void walk_list(const walk_ctx *w, int64_t k0, int64_t cnt, const double c[3], double r,
+                      double amin, double *acc /* 4*cnt */, int64_t *nint /* cnt */,
+                      int64_t *stack)
+{
+    const oracle_tree *t = w->t;
+    int64_t sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        int64_t J = stack[--sp];
+        double dx = t->cx[J] - c[0], dy = t->cy[J] - c[1], dz = t->cz[J] - c[2];
+        double d = sqrt(dx * dx + dy * dy + dz * dz) - r;
+        if (mac_accept(w->geometric, d, t->b[J], t->M[J], w->G, w->dacc, amin, w->theta)) {
+            /* the node's pseudo particle enters every member's list */
+            for (int64_t k = 0; k < cnt; k++) {
+                int64_t i = t->order[k0 + k];
+                kernel_term(t->cx[J] - t->x[i], t->cy[J] - t->y[i], t->cz[J] - t->z[i], t->M[J],
+                            w->e2, acc + 4 * k);
+                nint[k]++;
+            }
+        } else if (t->nchild[J] == 0) {
+            for (int64_t k = 0; k < cnt; k++) {
+                int64_t i = t->order[k0 + k];
+                for (int64_t q = t->first[J]; q < t->first[J] + t->count[J]; q++) {
+                    int64_t j = t->order[q];
+                    nint[k]++;
+                    if (j == i) continue; /* j != i in Eq. 1 */
+                    kernel_term(t->x[j] - t->x[i], t->y[j] - t->y[i], t->z[j] - t->z[i], t->m[j],
+                                w->e2, acc + 4 * k);
+                }
+            }
+        } else {
+            /* push children in reverse so they are visited in octant order */
+            for (int64_t ch = t->child[J] + t->nchild[J] - 1; ch >= t->child[J]; ch--)
+                stack[sp++] = ch;
+        }
+    }
+}
+
+void oracle_tree_walk(const oracle_tree *t, int mode, double G, double eps,
+                      double delta_acc, double theta, int group_size, const double *a_old,
+                      double *ax, double *ay, double *az, double *phi, int64_t *ninter)
+{
+    walk_ctx w = {t, mode == ORACLE_MAC_PARTICLE_GEO || mode == ORACLE_MAC_GROUP_GEO, G,
+                  eps * eps, delta_acc, theta};
+    int group_mode = (mode == ORACLE_MAC_GROUP_ACC || mode == ORACLE_MAC_GROUP_GEO);
+    int64_t ng;
+    int64_t *gf = NULL, *gc = NULL;
+    if (group_mode) {
+        gf = malloc((size_t)t->n * sizeof(int64_t));
+        gc = malloc((size_t)t->n * sizeof(int64_t));
+        ng = oracle_tree_groups(t, group_size, gf, gc);
+    } else {
+        ng = t->n;
+    }
+    int64_t stack_cap = 8 * (int64_t)(t->levels + 2) + 8;
+#pragma omp parallel
+    {
+        int64_t cmax = group_mode ? group_size : 1;
+        double *acc = malloc((size_t)(4 * cmax) * sizeof(double));
+        int64_t *nint = malloc((size_t)cmax * sizeof(int64_t));
+        int64_t *stack = malloc((size_t)stack_cap * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t g = 0; g < ng; g++) {
+            int64_t k0 = group_mode ? gf[g] : g, cnt = group_mode ? gc[g] : 1;
+            double c[3], r = 0, amin = INFINITY;
+            if (group_mode) {
+                double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                for (int64_t k = 0; k < cnt; k++) {
+                    int64_t i = t->order[k0 + k];
+                    double p[3] = {t->x[i], t->y[i], t->z[i]};
+                    for (int a = 0; a < 3; a++) {
+                        if (p[a] < lo[a]) lo[a] = p[a];
+                        if (p[a] > hi[a]) hi[a] = p[a];
+                    }
+                }
+                for (int a = 0; a < 3; a++) c[a] = 0.5 * (lo[a] + hi[a]);
+                for (int64_t k = 0; k < cnt; k++) {
+                    int64_t i = t->order[k0 + k];
+                    double dx = t->x[i] - c[0], dy = t->y[i] - c[1], dz = t->z[i] - c[2];
+                    double d = sqrt(dx * dx + dy * dy + dz * dz);
+                    if (d > r) r = d;
+                    if (a_old && a_old[i] < amin) amin = a_old[i];
+                }
+            } else {
+                int64_t i = t->order[g];
+                c[0] = t->x[i]; c[1] = t->y[i]; c[2] = t->z[i];
+                amin = a_old ? a_old[i] : 0.0;
+            }
+            if (!a_old) amin = 0.0;
+            memset(acc, 0, (size_t)(4 * cnt) * sizeof(double));
+            memset(nint, 0, (size_t)cnt * sizeof(int64_t));
+            walk_list(&w, k0, cnt, c, r, amin, acc, nint, stack);
+            for (int64_t k = 0; k < cnt; k++) {
+                int64_t i = t->order[k0 + k];
+                ax[i] = G * acc[4 * k + 0];
+                ay[i] = G * acc[4 * k + 1];
+                az[i] = G * acc[4 * k + 2];
+                if (phi) phi[i] = G * acc[4 * k + 3];
+                if (ninter) ninter[i] = nint[k];
+            }
+        }
+        free(acc); free(nint); free(stack);
+    }
+    free(gf);
+    free(gc);
+}
+
+/* ------------------------------------------------------------------------ */
+void oracle_kick(int64_t n, double *vx, double *vy, double *vz,
+                 const double *ax, const double *ay, const double *az, double h)
+{
+    for (int64_t i = 0; i < n; i++) {
+        vx[i] += ax[i] * h;
+        vy[i] += ay[i] * h;
+        vz[i] += az[i] * h;
+    }
+}
+
+void oracle_drift(int64_t n, double *x, double *y, double *z,
+                  const double *vx, const double *vy, const double *vz, double h)
+{
+    for (int64_t i = 0; i < n; i++) {
+        x[i] += vx[i] * h;
+        y[i] += vy[i] * h;
+        z[i] += vz[i] * h;
+    }
+}
+
+void oracle_diagnostics(int64_t n, const double *x, const double *y, const double *z,
+                        const double *vx, const double *vy, const double *vz,
+                        const double *m, const double *phi, double out[8])
+{
+    double s[8] = {0};
+    for (int64_t i = 0; i < n; i++) {
+        s[0] += 0.5 * m[i] * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]);
+        if (phi) s[1] += 0.5 * m[i] * phi[i];
+        s[2] += m[i] * vx[i];
+        s[3] += m[i] * vy[i];
+        s[4] += m[i] * vz[i];
+        s[5] += m[i] * (y[i] * vz[i] - z[i] * vy[i]);
+        s[6] += m[i] * (z[i] * vx[i] - x[i] * vz[i]);
+        s[7] += m[i] * (x[i] * vy[i] - y[i] * vx[i]);
+    }
+    memcpy(out, s, sizeof s);
+}

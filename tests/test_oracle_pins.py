@@ -1,0 +1,415 @@
+"""Pins of the FP64 CPU oracle against things other than itself.
+
+Every check here is fixed by the paper or by mathematics: hand-derived closed
+forms (tests/golden/closed_forms.json), symmetry, Newton's third law,
+analytic density profiles, a library stable sort, higher-precision brute
+force on tiny inputs, special cases where the tree must reduce to the direct
+sum, and conservation properties of the leapfrog.  A plausible mistake in
+the oracle (a dropped term, a wrong sign or index, a transposed operand)
+fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import ics
+import oracle
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
+def _rel(a, b):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b)) / np.maximum(np.abs(np.asarray(b)), 1e-300))
+
+
+# --------------------------------------------------------------------------- Eq. 1
+@pytest.mark.parametrize("case", ["two_body_pythagorean", "two_body_unsoftened"])
+def test_direct_two_body_closed_form(case):
+    c = GOLD[case]
+    ax, ay, az, phi = oracle.direct(c["x"], c["y"], c["z"], c["m"], c["G"], c["eps"])
+    for got, want in ((ax, c["ax"]), (ay, c["ay"]), (phi, c["phi"])):
+        assert np.allclose(got, want, rtol=1e-14, atol=0)
+    assert np.all(az == 0.0)
+
+
+def _cube():
+    v = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)], float)
+    return v
+
+
+def test_direct_cube_vertices():
+    v = _cube()
+    m = np.ones(8)
+    ax, ay, az, _ = oracle.direct(v[:, 0], v[:, 1], v[:, 2], m, 1.0, 0.0)
+    want = GOLD["cube_vertices"]["component_magnitude"]
+    a = np.stack([ax, ay, az], 1)
+    # every component has the closed-form magnitude and points to the centre
+    assert np.allclose(np.abs(a), want, rtol=1e-14)
+    assert np.all(np.sign(a) == -np.sign(v))
+
+
+def test_direct_cube_plus_centre_symmetry():
+    v = np.vstack([_cube(), [[0, 0, 0]]])
+    m = np.ones(9)
+    ax, ay, az, _ = oracle.direct(v[:, 0], v[:, 1], v[:, 2], m, 1.0, 0.0)
+    assert abs(ax[8]) < 1e-15 and abs(ay[8]) < 1e-15 and abs(az[8]) < 1e-15
+    want = GOLD["cube_vertices_plus_centre"]["component_magnitude"]
+    assert np.allclose(np.abs(ax[:8]), want, rtol=1e-14)
+
+
+def test_direct_octahedron_centre_zero():
+    v = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1], [0, 0, 0]], float)
+    ax, ay, az, _ = oracle.direct(v[:, 0], v[:, 1], v[:, 2], np.ones(7), 1.0, 0.1)
+    assert max(abs(ax[6]), abs(ay[6]), abs(az[6])) < 1e-15
+    mags = np.sqrt(ax[:6] ** 2 + ay[:6] ** 2 + az[:6] ** 2)
+    assert np.allclose(mags, mags[0], rtol=1e-14)
+
+
+def test_direct_longdouble_bruteforce():
+    """Brute force in extended precision for N <= 64."""
+    g = ics.rng(7)
+    n = 48
+    x, y, z = (g.normal(size=n) for _ in range(3))
+    m = g.uniform(0.5, 2.0, n)
+    eps = 0.05
+    ax, ay, az, phi = oracle.direct(x, y, z, m, 1.0, eps)
+    L = np.longdouble
+    X, Y, Z, Mm = (np.asarray(a, dtype=L) for a in (x, y, z, m))
+    for i in range(n):
+        dx, dy, dz = X - X[i], Y - Y[i], Z - Z[i]
+        r2 = dx * dx + dy * dy + dz * dz + L(eps) * L(eps)
+        w = Mm / (r2 * np.sqrt(r2))
+        w[i] = 0
+        pw = Mm / np.sqrt(r2)
+        pw[i] = 0
+        assert abs(float((w * dx).sum()) - ax[i]) <= 1e-14 * float(np.abs(w * dx).sum())
+        assert abs(float((w * dy).sum()) - ay[i]) <= 1e-14 * float(np.abs(w * dy).sum())
+        assert abs(float((w * dz).sum()) - az[i]) <= 1e-14 * float(np.abs(w * dz).sum())
+        assert abs(-float(pw.sum()) - phi[i]) <= 1e-14 * float(pw.sum())
+
+
+def test_direct_third_law():
+    p = ics.plummer(2000, 3)
+    ax, ay, az, _ = oracle.direct(p["x"], p["y"], p["z"], p["m"], 1.0, 1 / 128)
+    m = p["m"].astype(float)
+    for a in (ax, ay, az):
+        assert abs((m * a).sum()) <= 1e-13 * np.abs(m * a).sum()
+
+
+def test_direct_G_scaling_and_softened_point_mass():
+    # a test particle of negligible mass at distance r from a mass M
+    M, r, eps, G = 3.0, 2.5, 0.7, 4.0
+    ax, ay, az, phi = oracle.direct([0.0, r], [0.0, 0.0], [0.0, 0.0], [M, 1e-30], G, eps)
+    assert np.isclose(ax[1], -G * M * r / (r * r + eps * eps) ** 1.5, rtol=1e-15)
+    assert np.isclose(phi[1], -G * M / np.sqrt(r * r + eps * eps), rtol=1e-15)
+
+
+def _shell_checks(p, seed, eps):
+    """Per target: direct-sum radial acceleration over -G M_enc(r)/r^2 and the
+    potential over -G M_enc(r)/r - G sum_{r_j > r} m_j/r_j, both from the
+    sample's own radial mass profile (Newton's shell theorem)."""
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    n = x.size
+    tg = ics.rng(seed, 5).choice(n, 3000, replace=False)
+    ax, ay, az, phi = oracle.direct_targets(x, y, z, m, tg, 1.0, eps, want_phi=True)
+    R = np.sqrt(x * x + y * y + z * z)
+    o = np.argsort(R)
+    Rs = R[o]
+    cm = np.cumsum(m[o])
+    outer = np.cumsum((m[o] / Rs)[::-1])[::-1]
+    r = R[tg]
+    k = np.searchsorted(Rs, r, side="left")
+    menc = np.where(k > 0, cm[np.maximum(k - 1, 0)], 0.0)
+    out = np.where(k + 1 < n, outer[np.minimum(k + 1, n - 1)], 0.0)
+    ar = (ax * x[tg] + ay * y[tg] + az * z[tg]) / r
+    return r, ar / (-menc / r ** 2), phi / (-menc / r - out)
+
+
+@pytest.mark.parametrize("gen,seed", [(ics.plummer, 11), (ics.hernquist, 12)])
+def test_direct_shell_theorem_profiles(gen, seed):
+    """Plummer and Hernquist spheres: shell-averaged radial acceleration and
+    potential of the direct sum match the monopole of the sample's own
+    spherical mass profile, away from the softening scale."""
+    r, ra, rp = _shell_checks(gen(1 << 15, seed), seed, 1 / 256)
+    edges = [0.15, 0.4, 0.8, 1.5, 3.0, 8.0]
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (r >= lo) & (r < hi)
+        assert sel.sum() > 100
+        for q in (ra[sel], rp[sel]):
+            sem = q.std() / np.sqrt(sel.sum())
+            assert abs(q.mean() - 1) < 4 * sem + 1e-3, (lo, hi, q.mean(), sem)
+
+
+def test_ic_profiles_follow_analytic_mass():
+    """The samplers draw from the stated profiles: enclosed-mass fractions
+    agree with M(<r) within binomial noise (Plummer r^3/(1+r^2)^{3/2};
+    truncated Hernquist (r/(r+1))^2 / (100/101)^2)."""
+    n = 1 << 15
+    for gen, seed, M in ((ics.plummer, 11, lambda r: r ** 3 / (1 + r * r) ** 1.5),
+                         (ics.hernquist, 12, lambda r: (r / (r + 1)) ** 2 / (100 / 101) ** 2)):
+        p = gen(n, seed)
+        R = np.sqrt(p["x"].astype(float) ** 2 + p["y"] ** 2 + p["z"] ** 2)
+        for r in (0.3, 1.0, 3.0):
+            f = (R < r).mean()
+            assert abs(f - M(r)) < 5 * np.sqrt(M(r) * (1 - M(r)) / n) + 1e-4
+
+
+# --------------------------------------------------------------------------- keys and order
+def test_interleave_golden():
+    for c in GOLD["morton_keys"]["cases"]:
+        got = oracle.interleave([c["q"][0]], [c["q"][1]], [c["q"][2]], c["levels"])[0]
+        assert int(got) == c["key"], c
+
+
+def test_cells_fp32_quantisation_bounds():
+    p = ics.galaxy(5000, 4)
+    cube = oracle.cube(p["x"], p["y"], p["z"])
+    lo = np.array([p["x"].min(), p["y"].min(), p["z"].min()], np.float32)
+    assert np.array_equal(cube[:3], lo)
+    ext = max(np.float32(p["x"].max() - lo[0]), np.float32(p["y"].max() - lo[1]),
+              np.float32(p["z"].max() - lo[2]))
+    assert cube[3] == np.float32(ext * np.float32(1 + 2.0 ** -20))
+    q = oracle.cells(p["x"], p["y"], p["z"], cube, 21)
+    for a, c in zip(q, (p["x"], p["y"], p["z"])):
+        assert a.max() <= (1 << 21) - 1
+        # the cell index is the FP32 floor of the scaled offset (monotone in x)
+        o = np.argsort(c, kind="stable")
+        assert np.all(np.diff(a[o].astype(np.int64)) >= 0)
+
+
+def test_sort_matches_library_stable_sort():
+    p = ics.galaxy(20000, 5)
+    k, _ = oracle.keys(p["x"], p["y"], p["z"], 21)
+    k[::7] = k[3]  # force many ties
+    assert np.array_equal(oracle.sort_order(k), np.argsort(k, kind="stable"))
+
+
+# --------------------------------------------------------------------------- tree
+@pytest.fixture(scope="module")
+def gal_tree():
+    n = 1 << 14
+    p = ics.galaxy(n, 6)
+    t = oracle.Tree(p["x"], p["y"], p["z"], p["m"], levels=21, leaf_cap=16)
+    return p, t
+
+
+def test_tree_order_is_sorted_morton_order(gal_tree):
+    """The recursive subdivision visits particles in (key, index) order, the
+    order a stable radix sort of the keys produces."""
+    p, t = gal_tree
+    k, _ = oracle.keys(p["x"], p["y"], p["z"], 21)
+    assert np.array_equal(t.order(), np.argsort(k, kind="stable"))
+
+
+def test_tree_invariants(gal_tree):
+    p, t = gal_tree
+    nd = t.nodes()
+    n, cap = t.n, t.leaf_cap
+    order = t.order()
+    leaf = nd["nchild"] == 0
+    # every particle in exactly one leaf
+    cover = np.zeros(n, np.int64)
+    for f, c in zip(nd["first"][leaf], nd["count"][leaf]):
+        cover[f:f + c] += 1
+    assert np.all(cover == 1)
+    # leaf sizes, internal sizes
+    assert np.all((nd["count"][leaf] <= cap) | (nd["level"][leaf] == 21))
+    assert np.all(nd["count"][~leaf] > cap)
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    for i in np.flatnonzero(~leaf):
+        ch = np.arange(nd["child"][i], nd["child"][i] + nd["nchild"][i])
+        assert nd["count"][ch].sum() == nd["count"][i]
+        assert np.all(nd["level"][ch] == nd["level"][i] + 1)
+        assert np.all(nd["prefix"][ch] >> np.uint64(3) == nd["prefix"][i])
+        assert np.isclose(nd["M"][ch].sum(), nd["M"][i], rtol=1e-14)
+        assert nd["first"][ch[0]] == nd["first"][i]
+    # moments against the definition, and b >= the exact member radius
+    for i in range(0, nd["M"].size, 7):
+        mem = order[nd["first"][i]:nd["first"][i] + nd["count"][i]]
+        M = m[mem].sum()
+        com = np.array([(m[mem] * q[mem]).sum() / M for q in (x, y, z)])
+        assert np.isclose(nd["M"][i], M, rtol=1e-14)
+        assert np.allclose([nd["cx"][i], nd["cy"][i], nd["cz"][i]], com, rtol=1e-14, atol=1e-14)
+        rmax = np.sqrt((x[mem] - com[0]) ** 2 + (y[mem] - com[1]) ** 2 + (z[mem] - com[2]) ** 2).max()
+        if leaf[i]:
+            assert np.isclose(nd["b"][i], rmax, rtol=1e-14, atol=1e-15)
+        else:
+            assert nd["b"][i] >= rmax * (1 - 1e-14)
+
+
+def test_tree_groups_partition(gal_tree):
+    p, t = gal_tree
+    nd = t.nodes()
+    for G in (16, 32, 64):
+        f, c = t.groups(G)
+        assert np.all(c <= G) and np.all(c >= 1)
+        assert f[0] == 0 and np.all(f[1:] == f[:-1] + c[:-1]) and f[-1] + c[-1] == t.n
+        # each group is a node whose parent holds more than G particles
+        key = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(nd["first"], nd["count"]))}
+        parent = np.full(nd["M"].size, -1)
+        for i in np.flatnonzero(nd["nchild"] > 0):
+            parent[nd["child"][i]:nd["child"][i] + nd["nchild"][i]] = i
+        for a, b in zip(f, c):
+            i = key[(int(a), int(b))]
+            assert parent[i] < 0 or nd["count"][parent[i]] > G
+
+
+@pytest.mark.parametrize("mode", [oracle.MAC_PARTICLE_ACC, oracle.MAC_GROUP_ACC])
+def test_tree_dacc_zero_is_direct(mode):
+    """With delta_acc = 0 Eq. 2 accepts only single-particle nodes, so the
+    tree sum reduces to the direct sum of Eq. 1."""
+    p = ics.plummer(3000, 8)
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    ax, ay, az, phi = oracle.direct(x, y, z, m, 1.0, 1 / 64)
+    t = oracle.Tree(x, y, z, m, 21, 8)
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    bx, by, bz, bphi, nint = t.walk(mode, 1.0, 1 / 64, 0.0, 0.5, 32, amag)
+    assert np.max(oracle.rel_err(bx, by, bz, ax, ay, az)) < 1e-13
+    assert np.allclose(bphi, phi, rtol=1e-13)
+    assert np.all(nint == 3000)
+
+
+def test_tree_tiny_theta_is_direct():
+    p = ics.plummer(2000, 9)
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 0.01)
+    t = oracle.Tree(x, y, z, m, 21, 16)
+    bx, by, bz, _, _ = t.walk(oracle.MAC_GROUP_GEO, 1.0, 0.01, 0.0, 1e-9, 32, None)
+    assert np.max(oracle.rel_err(bx, by, bz, ax, ay, az)) < 1e-12
+
+
+def test_tree_distant_cluster_is_its_monopole():
+    """A compact cluster far from the target is accepted as one node and
+    contributes exactly its monopole: G M (com - r)/(d^2 + eps^2)^{3/2}."""
+    g = ics.rng(10)
+    k = 12
+    cl = g.normal(scale=0.01, size=(k, 3)) + np.array([100.0, 50.0, -20.0])
+    mc = g.uniform(1.0, 2.0, k)
+    x = np.concatenate([cl[:, 0], [0.0]])
+    y = np.concatenate([cl[:, 1], [0.0]])
+    z = np.concatenate([cl[:, 2], [0.0]])
+    m = np.concatenate([mc, [1e-6]])
+    t = oracle.Tree(x, y, z, m, 21, 8)
+    aold = np.full(k + 1, 1e3)
+    eps = 0.3
+    ax, ay, az, phi, nint = t.walk(oracle.MAC_PARTICLE_ACC, 1.0, eps, 2 ** -9, 0.5, 1, aold)
+    M = mc.sum()
+    com = (mc[:, None] * cl).sum(0) / M
+    d = com  # target at the origin
+    r2 = (d * d).sum() + eps * eps
+    want = M * d / r2 ** 1.5
+    assert nint[k] < k  # the cluster was not opened particle by particle
+    assert np.allclose([ax[k], ay[k], az[k]], want, rtol=1e-12)
+
+
+def test_tree_error_decreases_with_dacc():
+    n = 1 << 13
+    p = ics.plummer(n, 1)
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 1 / 128, want_phi=False)
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    t = oracle.Tree(x, y, z, m, 21, 16)
+    prev = np.inf
+    prev_n = 0
+    for k in (2, 5, 8, 11, 14):
+        bx, by, bz, _, nint = t.walk(oracle.MAC_GROUP_ACC, 1.0, 1 / 128, 2.0 ** -k, 0.5, 32, amag,
+                                     want_phi=False)
+        e50 = np.percentile(oracle.rel_err(bx, by, bz, ax, ay, az), 50)
+        assert e50 < prev
+        assert nint.sum() > prev_n
+        prev, prev_n = e50, nint.sum()
+
+
+def test_tree_group_mac_not_looser_than_particle_mac():
+    """The group distance |com - c_g| - r_g is a lower bound of every member's
+    distance and amin <= |a_i|, so a group accepts a node only if every member
+    would: group-mode lists are at least as long as particle-mode lists."""
+    n = 1 << 12
+    p = ics.plummer(n, 2)
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 1 / 128, want_phi=False)
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    t = oracle.Tree(x, y, z, m, 21, 16)
+    _, _, _, _, ng = t.walk(oracle.MAC_GROUP_ACC, 1.0, 1 / 128, 2 ** -9, 0.5, 32, amag)
+    _, _, _, _, npart = t.walk(oracle.MAC_PARTICLE_ACC, 1.0, 1 / 128, 2 ** -9, 0.5, 32, amag)
+    assert np.all(ng >= npart)
+
+
+def test_tree_coincident_particles():
+    """More coincident particles than a leaf holds: the finest-level leaf keeps
+    them all, groups are chunked, and with eps > 0 the sum stays the direct one."""
+    p = ics.plummer(500, 13)
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    x[:100], y[:100], z[:100] = 0.25, -0.5, 0.125
+    t = oracle.Tree(x, y, z, m, 21, 8)
+    nd = t.nodes()
+    assert nd["count"][(nd["nchild"] == 0)].max() == 100
+    f, c = t.groups(32)
+    assert c.max() <= 32 and c.sum() == 500
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 0.05)
+    bx, by, bz, _, _ = t.walk(oracle.MAC_GROUP_ACC, 1.0, 0.05, 0.0, 0.5, 32,
+                              np.sqrt(ax ** 2 + ay ** 2 + az ** 2))
+    assert np.max(oracle.rel_err(bx, by, bz, ax, ay, az)) < 1e-12
+
+
+# --------------------------------------------------------------------------- leapfrog, diagnostics
+def _kdk(x, v, m, eps, dt, steps):
+    a = oracle.direct(*x, m, 1.0, eps, want_phi=False)[:3]
+    for _ in range(steps):
+        oracle.kick(v, a, dt / 2)
+        oracle.drift(x, v, dt)
+        a = oracle.direct(*x, m, 1.0, eps, want_phi=False)[:3]
+        oracle.kick(v, a, dt / 2)
+    return x, v
+
+
+def test_leapfrog_time_reversible():
+    p = ics.plummer(64, 14)
+    x = [p[k].astype(float) for k in ("x", "y", "z")]
+    v = [p[k].astype(float) for k in ("vx", "vy", "vz")]
+    m = p["m"].astype(float)
+    x0 = [a.copy() for a in x]
+    v0 = [a.copy() for a in v]
+    _kdk(x, v, m, 0.05, 1 / 256, 20)
+    _kdk(x, v, m, 0.05, -1 / 256, 20)
+    for a, b in zip(x + v, x0 + v0):
+        assert np.max(np.abs(a - b)) < 1e-11
+
+
+def test_leapfrog_kepler_energy_second_order():
+    """Two-body circular orbit: the energy error of KDK falls as dt^2."""
+    def run(dt):
+        x = [np.array([0.5, -0.5]), np.array([0.0, 0.0]), np.array([0.0, 0.0])]
+        vc = np.sqrt(1.0 / 2.0 / 2.0)  # m = 1 each, separation 1
+        v = [np.array([0.0, 0.0]), np.array([vc, -vc]), np.array([0.0, 0.0])]
+        m = np.array([1.0, 1.0])
+        phi = oracle.direct(*x, m, 1.0, 0.0)[3]
+        e0 = oracle.diagnostics(*x, *v, m, phi)
+        emax = 0.0
+        T = 2 * np.pi / np.sqrt(2.0)
+        steps = int(round(T / dt))
+        for _ in range(steps // 8):
+            _kdk(x, v, m, 0.0, dt, 8)
+            phi = oracle.direct(*x, m, 1.0, 0.0)[3]
+            e = oracle.diagnostics(*x, *v, m, phi)
+            emax = max(emax, abs((e[0] + e[1]) - (e0[0] + e0[1])))
+        return emax
+
+    e1, e2 = run(2 ** -6), run(2 ** -7)
+    assert 3.0 < e1 / e2 < 5.0
+
+
+def test_diagnostics_two_body_closed_form():
+    x, y, z = np.array([0.0, 3.0]), np.array([0.0, 4.0]), np.zeros(2)
+    vx, vy, vz = np.array([1.0, -0.5]), np.array([0.0, 2.0]), np.array([0.5, 0.0])
+    m = np.array([1.0, 2.0])
+    phi = oracle.direct(x, y, z, m, 1.0, 12.0)[3]
+    d = oracle.diagnostics(x, y, z, vx, vy, vz, m, phi)
+    ek = 0.5 * 1.0 * (1 + 0.25) + 0.5 * 2.0 * (0.25 + 4)
+    ep = -1.0 * 2.0 / 13.0
+    assert np.isclose(d[0], ek, rtol=1e-15) and np.isclose(d[1], ep, rtol=1e-15)
+    assert np.allclose(d[2:5], [1.0 - 1.0, 0.0 + 4.0, 0.5], rtol=1e-15)
+    # L = sum m r x v ; particle 1: r = (3,4,0), v = (-0.5, 2, 0) -> (0, 0, 3*2 - 4*-0.5) = 8, times 2
+    assert np.allclose(d[5:], [0.0, 0.0, 16.0], rtol=1e-15)
