@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark of the gravitational octree step on a GB300.
+
+Workload (default): the three-component galaxy with N = 2^23 equal-mass
+particles (Hernquist bulge 15 %, exponential disk 10 %, NFW halo 75 %),
+eps = 1/64, delta_acc = 2^-9, leapfrog dt = 1/256, the tree rebuilt every
+step.  One step = kick-drift, bounding cube, Morton keys, radix sort, octree,
+monopoles, groups, tree walk (Eq. 1 under the MAC of Eq. 2), kick.
+
+Prints ONE JSON line (rank 0).  `value` is whole-job Ginteractions/s
+(interactions = Eq. 1 kernel evaluations in the walk, 22 flops each);
+`s_per_step` and the FP32 fraction of peak sit beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the deliberately plain
+reference implementation) on the host cores, on a bounded sample.
+Multi-GPU (torchrun): every rank runs its own replica of the workload; the
+single large system does not shard (replicas only), so there is no
+collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "s/step & Ginteractions/s at N=2^23, % GB300 FP32 peak, at stated force error"
+UNIT = "Ginteractions/s"
+FLOPS_PER_INTERACTION = 22  # 3 sub, 3 FMA (r^2+eps^2), rsqrt = 4, 3 mul, 3 FMA
+EPS, DACC, DT = 1.0 / 64, 2.0 ** -9, 1.0 / 256
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=1 << 23)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--error-sample", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-group-stride", type=int, default=32,
+                    help="CPU baseline walks every k-th group of the full tree")
+    return ap.parse_args()
+
+
+def workload_config(n):
+    return {
+        "workload": f"three-component galaxy N={n} (Hernquist bulge 15% a=0.6, exponential disk "
+                    f"10% Rd=5.4 z0=0.6, NFW halo 75% rs=12 cut 10rs), eps=1/64, "
+                    f"delta_acc=2^-9, shared-step leapfrog dt=1/256, tree rebuilt every step",
+        "n": n,
+        "flops_per_interaction": FLOPS_PER_INTERACTION,
+        "l2": "inputs larger than L2 (particle state ~0.45 GB, tree ~0.4 GB > 129 MB)",
+    }
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9 or (self.uuid and self.uuid not in f[0]):
+                continue
+            rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9]) if "Active" == v})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(rows),
+                "reasons": reasons}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------- oracle (CPU)
+def cpu_oracle_sample(p, group_stride, a_old=None):
+    """FP64 oracle: full tree build + walk of every group_stride-th group.
+    Returns (interactions, walk_seconds, build_seconds, threads, ngroups_walked)."""
+    import oracle
+    x, y, z, m = (np.asarray(p[k], np.float64) for k in ("x", "y", "z", "m"))
+    t0 = time.perf_counter()
+    tree = oracle.Tree(x, y, z, m, 21, 16)
+    t1 = time.perf_counter()
+    f, c = tree.groups(64)
+    sel = np.arange(0, f.size, group_stride)
+    if a_old is None:  # bootstrap for the sampled groups, as the library does
+        gx, gy, gz, _ = tree.walk_groups(sel, oracle.MAC_GROUP_GEO, 1.0, EPS, 0.0, 0.5, 64, None)
+        a_old = np.nan_to_num(np.sqrt(gx ** 2 + gy ** 2 + gz ** 2), nan=1.0)
+    t2 = time.perf_counter()
+    _, _, _, nint = tree.walk_groups(sel, oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, 64, a_old)
+    t3 = time.perf_counter()
+    return int(nint[nint > 0].sum()), t3 - t2, t1 - t0, oracle.threads(), int(sel.size), int(f.size)
+
+
+# ---------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import ics
+    import paper_1811_02761_gb300 as nb
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    nsm = props.multi_processor_count
+    uuid = str(getattr(props, "uuid", "") or "")
+    p = ics.galaxy(args.n, args.seed)
+    n = args.n
+
+    def D(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    X64 = [D(p[k]) for k in ("x64", "y64", "z64")]
+    V = [D(p[k]) for k in ("vx", "vy", "vz")]
+    M = D(p["m"])
+    A = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    stream = torch.cuda.current_stream(dev)
+    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC)
+    ctx = nb.nbody_create(cfg, stream)
+    try:
+        # accelerations at t = 0 (bootstrap MAC), then warm-up steps
+        nb.nbody_build(ctx, *[D(p[k]) for k in ("x", "y", "z")], M)
+        nb.nbody_walk(ctx, None, *A)
+        nb.nbody_step(ctx, *X64, *V, M, *A, DT, args.warmup)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        sampler = ClockSampler(uuid)
+        sampler.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        st = nb.nbody_step(ctx, *X64, *V, M, *A, DT, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop()
+        if world > 1:
+            dist.barrier()
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+        inter = st.interactions
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        it = torch.tensor([inter], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        elapsed_max, inter_all = float(t.item()), float(it.item())
+
+        # end-to-end through the C ABI with pinned host buffers
+        hx = [a.cpu().pin_memory() for a in X64]
+        hv = [a.cpu().pin_memory() for a in V]
+        hm = M.cpu().pin_memory()
+        ha = [a.cpu().pin_memory() for a in A]
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_inter = 0
+        e0.record(stream)
+        w0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            s2 = nb.nbody_step(ctx, *hx, *hv, hm, *ha, DT, 1)
+            e2e_inter += s2.interactions
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_wall = time.perf_counter() - w0
+        e2e_s = max(e0.elapsed_time(e1) / 1e3, e2e_wall)
+
+        # force error of the final accelerations on a seeded sample (FP64 direct)
+        err = None
+        if rank == 0 and args.error_sample > 0:
+            import oracle
+            xs = [a.cpu().numpy().astype(np.float32).astype(np.float64) for a in X64]
+            ms = M.cpu().numpy().astype(np.float64)
+            tg = np.random.default_rng(args.seed).choice(n, args.error_sample, replace=False)
+            bx, by, bz, _ = oracle.direct_targets(*xs, ms, tg, 1.0, EPS)
+            ga = [a.cpu().numpy()[tg].astype(np.float64) for a in A]
+            e = oracle.rel_err(*ga, bx, by, bz)
+            err = {"p50": oracle.percentile_nearest_rank(e, 50),
+                   "p99": oracle.percentile_nearest_rank(e, 99), "max": float(e.max()),
+                   "sample": int(args.error_sample),
+                   "vs": "FP64 direct summation at the final positions"}
+    finally:
+        nb.nbody_destroy(ctx)
+
+    if rank != 0:
+        return None
+    steps = args.steps
+    s_per_step = elapsed_max / steps
+    value = inter_all / elapsed_max / 1e9
+    inter_per_step = inter / steps
+    walk_avg_s = (st.ms_walk_kernel / max(st.walk_launches, 1)) / 1e3
+    walk_tflops = FLOPS_PER_INTERACTION * inter_per_step / walk_avg_s / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = 2 * FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12
+    med = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else None
+    peak_med = 2 * FP32_LANES_PER_SM * nsm * med * 1e6 / 1e12 if med else None
+    whole_tflops = FLOPS_PER_INTERACTION * inter_per_step / s_per_step / 1e12
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        ni, walk_s, build_s, thr, nsel, ng = cpu_oracle_sample(p, args.cpu_group_stride)
+        cpu = {"value": ni / walk_s / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"FP64 oracle tree walk (group-mode acceleration MAC) of every "
+                         f"{args.cpu_group_stride}th group ({nsel} of {ng} groups, {ni} "
+                         f"interactions) of the same N={n} galaxy; full oracle tree build "
+                         f"{build_s:.2f} s timed separately",
+               "build_s": build_s, "walk_s": walk_s}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": s_per_step * 1e3, "s_per_step": s_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded three-component galaxy; stands in for the paper's M31 model)",
+        "config": dict(workload_config(n), parallelism=f"replicas x{world}",
+                       walk=cfg.as_dict()),
+        "interactions_per_step": inter_per_step,
+        "whole_step_tflops": whole_tflops,
+        "whole_step_fp32_peak_frac": whole_tflops / peak_tflops,
+        "walk_ms_per_step": st.ms_walk_kernel / max(st.walk_launches, 1),
+        "build_ms_per_step": st.ms_build / steps,
+        "walk_phase_ms_per_step": st.ms_walk / steps,
+        "nodes": st.n_nodes, "groups": st.n_groups, "max_stack": st.max_stack,
+        "roofline": {"bound": "alu", "achieved": walk_tflops, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": walk_tflops / peak_tflops, "traffic": None,
+                     "kernel": "walk_kernel",
+                     "peak_note": f"FP32 2 x {FP32_LANES_PER_SM} lanes x {nsm} SMs x {sm_max:.0f} MHz "
+                                  f"(max clock, MEASURED_PEAKS sm_max_mhz)",
+                     "frac_at_median_clock": (walk_tflops / peak_med) if peak_med else None},
+        "force_error": err,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_inter / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": n * (3 * 8 + 7 * 4),
+                "d2h_bytes_per_step": n * (3 * 8 + 6 * 4),
+                "steps": args.e2e_steps,
+                "note": "nbody_step(nsteps=1) per step on pinned host arrays; the library "
+                        "copies state in and out every call"},
+        "clocks": clocks,
+        "gpu_launches": int(st.kernels),
+    }
+    return out
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import ics
+    import oracle
+    p = ics.galaxy(args.n, args.seed)
+    x, y, z, m = (np.asarray(p[k], np.float64) for k in ("x", "y", "z", "m"))
+    t0 = time.perf_counter()
+    tree = oracle.Tree(x, y, z, m, 21, 16)
+    build_s = time.perf_counter() - t0
+    f, c = tree.groups(64)
+    stride = 1024
+    warm = np.arange(0, f.size, stride)
+    gx, gy, gz, _ = tree.walk_groups(warm, oracle.MAC_GROUP_GEO, 1.0, EPS, 0.0, 0.5, 64, None)
+    a_old = np.nan_to_num(np.sqrt(gx ** 2 + gy ** 2 + gz ** 2), nan=1.0)
+    for _ in range(args.warmup):
+        tree.walk_groups(warm, oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, 64, a_old)
+    total_i, total_s = 0, 0.0
+    for k in range(args.steps):
+        sel = np.arange(k % stride, f.size, stride)
+        gx, gy, gz, _ = tree.walk_groups(sel, oracle.MAC_GROUP_GEO, 1.0, EPS, 0.0, 0.5, 64, None)
+        ao = np.nan_to_num(np.sqrt(gx ** 2 + gy ** 2 + gz ** 2), nan=1.0)
+        t1 = time.perf_counter()
+        _, _, _, nint = tree.walk_groups(sel, oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, 64, ao)
+        total_s += time.perf_counter() - t1
+        total_i += int(nint[nint > 0].sum())
+    value = total_i / total_s / 1e9
+    sample = (f"FP64 oracle tree walk of 1/{stride} of the groups of the N={args.n} galaxy per "
+              f"step (a different slice each step); oracle tree built once ({build_s:.2f} s)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded three-component galaxy)",
+            "config": workload_config(args.n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "oracle_build_s": build_s}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

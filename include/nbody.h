@@ -1,0 +1,227 @@
+/*
+ * nbody.h -- C ABI of libnbody.so, a GB300 (sm_103a) implementation of the
+ * gravitational octree force calculation of Y. Miki, "Gravitational octree
+ * code performance evaluation on Volta GPU" (arXiv:1811.02761).
+ *
+ * The library computes, per step:
+ *   - the softened Newtonian acceleration of Eq. 1
+ *       a_i = sum_{j != i} G m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^{3/2}
+ *     either by direct summation or by the Barnes-Hut tree method (Sect. 1);
+ *   - the tree from radix-sorted space-filling-curve (Morton) keys (Sect. 4.1,
+ *     "makeTree"), node centres of mass and masses ("calcNode", Sect. 2.2),
+ *   - a tree walk in which groups of particles share one interaction list
+ *     (Sect. 1) and distant nodes are accepted by the acceleration MAC of Eq. 2
+ *       G m_J / d^2 (b_J / d)^2 <= delta_acc |a_i^old|,
+ *   - leapfrog kick-drift-kick orbit integration (the paper's code uses a
+ *     second-order Runge-Kutta scheme; this library integrates with leapfrog).
+ *
+ * Conventions for every entry point
+ *   - Pointers may be device pointers or host pointers (pageable or pinned);
+ *     the library inspects each with cudaPointerGetAttributes and stages host
+ *     data through its own device buffers.  Device pointers are used in place.
+ *   - Arrays are structure-of-arrays, length n, in the caller's particle
+ *     order; the library's internal Morton order never leaks out.
+ *   - Every call returns an nbody_status; no C++ exception crosses the ABI.
+ *     Argument errors are detected before any launch.  Device-side errors
+ *     (traversal stack overflow) are reported through a device status word
+ *     that the call reads after synchronising its stream.
+ *   - All work of a context is enqueued on the stream given at creation
+ *     (NULL = the legacy default stream).  A context is not thread-safe.
+ *   - Calls that return results synchronise the context's stream before
+ *     returning, so outputs are complete when the call returns.
+ *   - Ownership: the caller owns every array it passes.  The context owns all
+ *     scratch (keys, tree, groups, interaction lists); it grows on demand with
+ *     cudaMalloc and is released by nbody_destroy.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NBODY_ABI_VERSION 1
+
+typedef enum {
+    NBODY_OK = 0,
+    NBODY_EINVAL = 1,    /* bad argument (n < 0, NULL, eps < 0, bad config)  */
+    NBODY_ENOMEM = 2,    /* device or host allocation failed                 */
+    NBODY_EOVERFLOW = 3, /* a traversal stack overflowed; results invalid    */
+    NBODY_ETIMEOUT = 4,  /* reserved: a bounded device wait ran out          */
+    NBODY_ECUDA = 5,     /* a CUDA runtime call failed (see nbody_last_error)*/
+    NBODY_ENOTBUILT = 6  /* nbody_walk before nbody_build                    */
+} nbody_status;
+
+/* Scheduling of the persistent walk's group queue. */
+typedef enum {
+    NBODY_SCHED_MORTON = 0,   /* groups in Morton order                       */
+    NBODY_SCHED_MLP = 1,      /* descending cost predicted by the MLP         */
+    NBODY_SCHED_LASTCOST = 2  /* descending cost measured in the previous walk*/
+} nbody_schedule;
+
+/* Parameters.  Fill with nbody_config_default() and then override. */
+typedef struct {
+    float G;             /* gravitational constant of Eq. 1 (default 1)             */
+    float eps;           /* Plummer softening eps of Eq. 1, >= 0 (default 1/64)       */
+    float delta_acc;     /* delta_acc of Eq. 2, >= 0 (default 2^-9)                  */
+    float theta;         /* opening angle of the bootstrap geometric MAC used when
+                            no |a_old| is given, 0 < theta < 1 (default 0.5)        */
+    int32_t leaf_cap;    /* max particles in a leaf, 1..32 (default 16)             */
+    int32_t group_size;  /* max particles sharing one list, leaf_cap..32*ipl (64)   */
+    int32_t ipl;         /* i-particles per lane of a walking warp: 1, 2 or 4 (2)   */
+    int32_t list_depth;  /* interaction-list entries per warp, 64..1024, multiple
+                            of 32 (default 256)                                    */
+    int32_t stack_depth; /* traversal stack entries per warp, 64..4096 (1024)       */
+    int32_t warps_per_block; /* walk warps per CTA, 1..16 (default 4)             */
+    int32_t compensated; /* 1: per-flush partial sums added with Neumaier
+                            compensation; 0: plain FP32 sums (default 0)          */
+    int32_t want_potential; /* 1: also accumulate phi (default 0)                 */
+    int32_t schedule;    /* nbody_schedule (default NBODY_SCHED_MORTON)             */
+} nbody_config;
+
+typedef struct {
+    int64_t n_nodes;       /* nodes of the last build                        */
+    int64_t n_groups;      /* i-groups of the last walk                      */
+    int64_t interactions;  /* kernel evaluations of the last walk (the zero
+                              self term of each particle included)            */
+    int64_t list_entries;  /* interaction-list entries flushed (sum over groups) */
+    int32_t max_stack;     /* deepest traversal stack seen                   */
+    int32_t levels;        /* tree levels below the root                     */
+    int64_t kernels;       /* kernels this library launched in the last call  */
+    float ms_build;        /* device time of the build phase(s) (CUDA events)  */
+    float ms_walk;         /* device time of the walk phase(s) (CUDA events)   */
+    float ms_walk_kernel;  /* device time of the walk kernel launches alone    */
+    int32_t walk_launches; /* walk kernel launches behind ms_walk_kernel       */
+} nbody_stats;
+
+typedef struct nbody_ctx nbody_ctx;
+
+/* Version of this ABI (NBODY_ABI_VERSION). */
+int32_t nbody_abi_version(void);
+
+/* Default parameters (values listed in nbody_config). */
+void nbody_config_default(nbody_config *cfg);
+
+/* Create a context on the current device.  cuda_stream is a cudaStream_t
+ * (NULL for the default stream); the caller keeps it alive until destroy.
+ * Errors: EINVAL (cfg invalid or out NULL), ECUDA. */
+nbody_status nbody_create(nbody_ctx **out, const nbody_config *cfg, void *cuda_stream);
+
+/* Release every buffer of the context.  NULL is accepted. */
+nbody_status nbody_destroy(nbody_ctx *ctx);
+
+/* Replace the parameters (e.g. after autotuning); the next build or walk
+ * uses them.  Errors: EINVAL. */
+nbody_status nbody_set_config(nbody_ctx *ctx, const nbody_config *cfg);
+nbody_status nbody_get_config(const nbody_ctx *ctx, nbody_config *cfg);
+
+/* Build the octree of one system (Sect. 4.1 "makeTree" + Sect. 2.2
+ * "calcNode"): bounding cube, 63-bit Morton keys (21 bits per axis, FP32
+ * quantisation), stable LSD radix sort, level-ordered octree with leaves of
+ * at most leaf_cap particles, bottom-up monopoles and node sizes b_J.
+ * x, y, z, m: FP32 [n], n >= 1.  The context keeps its own sorted copy.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+nbody_status nbody_build(nbody_ctx *ctx, int64_t n, const float *x, const float *y,
+                         const float *z, const float *m);
+
+/* Build a forest of nsys independent systems in one pass: system s holds
+ * particles offsets[s] .. offsets[s+1]-1 (offsets: HOST int64 [nsys+1],
+ * offsets[0] = 0, non-decreasing).  eps_sys: HOST float [nsys], the
+ * softening of each system (NULL: cfg.eps for all).  Keys carry the system id
+ * above the Morton bits, so one sort orders all systems; each system has its
+ * own cube and root.  1 <= nsys <= 2^20.  Errors: EINVAL, ENOMEM, ECUDA. */
+nbody_status nbody_build_batched(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
+                                 const float *eps_sys, const float *x, const float *y,
+                                 const float *z, const float *m);
+
+/* Tree accelerations for every particle of the last build (Eq. 1 evaluated
+ * over the interaction lists of Sect. 1, nodes accepted by Eq. 2).
+ * a_old: FP32 [n], |a_i^old| in caller order, or NULL: then one walk with the
+ * geometric criterion b_J <= theta d provides |a| for the acceleration-MAC
+ * walk.  Outputs ax, ay, az: FP32 [n]; phi: FP32 [n] or NULL (requires
+ * want_potential = 1 in the config).  stats: nullable.
+ * Errors: ENOTBUILT, EINVAL, EOVERFLOW (stack_depth too small), ECUDA. */
+nbody_status nbody_walk(nbody_ctx *ctx, const float *a_old, float *ax, float *ay, float *az,
+                        float *phi, nbody_stats *stats);
+
+/* Eq. 1 by direct O(n^2) summation on the GPU (FP32, rsqrt; compensated = 1
+ * adds per-tile partial sums with Neumaier compensation).  Stateless: uses
+ * cuda_stream (NULL = default stream) and synchronises it.  phi nullable.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+nbody_status nbody_direct(int64_t n, const float *x, const float *y, const float *z,
+                          const float *m, float G, float eps, int32_t compensated,
+                          float *ax, float *ay, float *az, float *phi, void *cuda_stream);
+
+/* nsteps leapfrog kick-drift-kick steps of length dt with the tree force,
+ * the tree rebuilt every step:
+ *   v += a dt/2;  x += v dt (FP64 positions);  rebuild;  walk with |a|;
+ *   v += a dt/2.
+ * x, y, z: FP64 [n]; vx, vy, vz: FP32 [n]; m: FP32 [n];
+ * ax, ay, az: FP32 [n], on entry the acceleration at the entry positions (from
+ * nbody_walk), on return the acceleration at the final positions.  All arrays
+ * are updated in place, in caller order.  Errors: EINVAL, ENOMEM, EOVERFLOW,
+ * ECUDA. */
+nbody_status nbody_step(nbody_ctx *ctx, int64_t n, double *x, double *y, double *z,
+                        float *vx, float *vy, float *vz, const float *m,
+                        float *ax, float *ay, float *az, float dt, int32_t nsteps,
+                        nbody_stats *stats);
+
+/* nbody_step for nsys independent systems (offsets, eps_sys as in
+ * nbody_build_batched): one sort, one forest, one persistent walk over all
+ * groups of all systems per step. */
+nbody_status nbody_step_batched(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
+                                const float *eps_sys, double *x, double *y, double *z,
+                                float *vx, float *vy, float *vz, const float *m,
+                                float *ax, float *ay, float *az, float dt, int32_t nsteps,
+                                nbody_stats *stats);
+
+/* FP64 diagnostics over n particles: out (HOST double [8]) = {E_kin, E_pot,
+ * Px, Py, Pz, Lx, Ly, Lz} with E_kin = 1/2 sum m v^2, E_pot = 1/2 sum m phi
+ * (phi NULL: 0), P = sum m v, L = sum m r x v; FP64 reductions on the device.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+nbody_status nbody_diagnostics(nbody_ctx *ctx, int64_t n, const double *x, const double *y,
+                               const double *z, const float *vx, const float *vy,
+                               const float *vz, const float *m, const float *phi,
+                               double *out);
+
+/* Per-group cost log of the last walk: counts[g] = interaction-list entries
+ * group g processed, groups in Morton order.  counts: int32 [cap] (host or
+ * device); *n_groups receives the number of groups (may exceed cap: then
+ * only cap entries are written).  Errors: ENOTBUILT, EINVAL, ECUDA. */
+nbody_status nbody_get_group_costs(nbody_ctx *ctx, int32_t *counts, int64_t cap,
+                                   int64_t *n_groups);
+
+/* Internal arrays of the last build, for inspection and testing. */
+typedef enum {
+    NBODY_EXPORT_PERM = 0,         /* int32 [n]: caller index of sorted particle k  */
+    NBODY_EXPORT_KEYS = 1,         /* uint64 [n]: sorted Morton keys (system id on
+                                      top of 3*levels Morton bits)                  */
+    NBODY_EXPORT_NODE_LEVEL = 2,   /* int8 [nodes]                                  */
+    NBODY_EXPORT_NODE_START = 3,   /* int32 [nodes]: first sorted particle          */
+    NBODY_EXPORT_NODE_COUNT = 4,   /* int32 [nodes]: particles in the node          */
+    NBODY_EXPORT_NODE_PARENT = 5,  /* int32 [nodes]: parent, -1 for roots           */
+    NBODY_EXPORT_NODE_A = 6,       /* float4 [nodes]: com.x, com.y, com.z, M        */
+    NBODY_EXPORT_NODE_B = 7,       /* float4 [nodes]: b_J, G M b_J^2, link, meta    */
+    NBODY_EXPORT_GROUP_FIRST = 8,  /* int32 [groups]: first sorted particle         */
+    NBODY_EXPORT_GROUP_COUNT = 9,  /* int32 [groups]                                */
+    NBODY_EXPORT_GROUP_SPHERE = 10,/* float4 [groups]: centre, radius               */
+    NBODY_EXPORT_SYS_BOX = 11      /* float4 [nsys]: x0, y0, z0, L of each cube     */
+} nbody_export_what;
+
+/* Copy internal array `what` of the last build into dst (host or device),
+ * at most cap elements; *count receives the array's length.  Nodes are in
+ * level-major order (children of a node contiguous).  Errors: ENOTBUILT,
+ * EINVAL, ECUDA. */
+nbody_status nbody_export(nbody_ctx *ctx, int32_t what, void *dst, int64_t cap, int64_t *count);
+
+/* Message of the last error of this context (or of the last stateless call
+ * on this thread if ctx is NULL), NUL-terminated, truncated to len. */
+nbody_status nbody_last_error(const nbody_ctx *ctx, char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBODY_H */

@@ -70,6 +70,9 @@ def _load():
         lib.oracle_tree_groups.restype = C.c_int64
         lib.oracle_tree_walk.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double,
                                          C.c_double, C.c_int, d, d, d, d, d, i64]
+        lib.oracle_tree_walk_groups.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                                C.c_double, C.c_double, C.c_int, d, C.c_int64,
+                                                i64, d, d, d, d, i64]
         lib.oracle_kick.argtypes = [C.c_int64, d, d, d, d, d, d, C.c_double]
         lib.oracle_drift.argtypes = [C.c_int64, d, d, d, d, d, d, C.c_double]
         lib.oracle_diagnostics.argtypes = [C.c_int64, d, d, d, d, d, d, d, d, d]
@@ -231,6 +234,22 @@ class Tree:
                                    _p(ao, C.c_double), _p(ax, C.c_double), _p(ay, C.c_double),
                                    _p(az, C.c_double), _p(phi, C.c_double), _p(nint, C.c_int64))
         return ax, ay, az, phi, nint
+
+
+    def walk_groups(self, groups, mode=MAC_GROUP_ACC, G=1.0, eps=0.0, delta_acc=2.0 ** -9,
+                    theta=0.5, group_size=32, a_old=None):
+        """Walk only the listed groups.  Returns (ax, ay, az, ninter) with NaN /
+        -1 for particles outside them (caller order)."""
+        n = self.n
+        ax, ay, az = np.full(n, np.nan), np.full(n, np.nan), np.full(n, np.nan)
+        nint = np.full(n, -1, np.int64)
+        sel = np.ascontiguousarray(groups, dtype=np.int64)
+        ao = _f64(a_old) if a_old is not None else None
+        self._lib.oracle_tree_walk_groups(self._h, mode, G, eps, delta_acc, theta, group_size,
+                                          _p(ao, C.c_double), sel.size, _p(sel, C.c_int64),
+                                          _p(ax, C.c_double), _p(ay, C.c_double),
+                                          _p(az, C.c_double), None, _p(nint, C.c_int64))
+        return ax, ay, az, nint
 
 
 def kick(v, a, h):

@@ -509,9 +509,10 @@ static void walk_list(const walk_ctx *w, int64_t k0, int64_t cnt, const double c
     }
 }
 
-void oracle_tree_walk(const oracle_tree *t, int mode, double G, double eps,
-                      double delta_acc, double theta, int group_size, const double *a_old,
-                      double *ax, double *ay, double *az, double *phi, int64_t *ninter)
+static void tree_walk_impl(const oracle_tree *t, int mode, double G, double eps,
+                           double delta_acc, double theta, int group_size, const double *a_old,
+                           int64_t nsel, const int64_t *sel,
+                           double *ax, double *ay, double *az, double *phi, int64_t *ninter)
 {
     walk_ctx w = {t, mode == ORACLE_MAC_PARTICLE_GEO || mode == ORACLE_MAC_GROUP_GEO, G,
                   eps * eps, delta_acc, theta};
@@ -526,6 +527,7 @@ void oracle_tree_walk(const oracle_tree *t, int mode, double G, double eps,
         ng = t->n;
     }
     int64_t stack_cap = 8 * (int64_t)(t->levels + 2) + 8;
+    int64_t nwork = sel ? nsel : ng;
 #pragma omp parallel
     {
         int64_t cmax = group_mode ? group_size : 1;
@@ -533,7 +535,9 @@ void oracle_tree_walk(const oracle_tree *t, int mode, double G, double eps,
         int64_t *nint = malloc((size_t)cmax * sizeof(int64_t));
         int64_t *stack = malloc((size_t)stack_cap * sizeof(int64_t));
 #pragma omp for schedule(dynamic, 16)
-        for (int64_t g = 0; g < ng; g++) {
+        for (int64_t w_ = 0; w_ < nwork; w_++) {
+            int64_t g = sel ? sel[w_] : w_;
+            if (g < 0 || g >= ng) continue;
             int64_t k0 = group_mode ? gf[g] : g, cnt = group_mode ? gc[g] : 1;
             double c[3], r = 0, amin = INFINITY;
             if (group_mode) {
@@ -576,6 +580,23 @@ void oracle_tree_walk(const oracle_tree *t, int mode, double G, double eps,
     }
     free(gf);
     free(gc);
+}
+
+void oracle_tree_walk(const oracle_tree *t, int mode, double G, double eps,
+                      double delta_acc, double theta, int group_size, const double *a_old,
+                      double *ax, double *ay, double *az, double *phi, int64_t *ninter)
+{
+    tree_walk_impl(t, mode, G, eps, delta_acc, theta, group_size, a_old, 0, NULL,
+                   ax, ay, az, phi, ninter);
+}
+
+void oracle_tree_walk_groups(const oracle_tree *t, int mode, double G, double eps,
+                             double delta_acc, double theta, int group_size, const double *a_old,
+                             int64_t nsel, const int64_t *sel,
+                             double *ax, double *ay, double *az, double *phi, int64_t *ninter)
+{
+    tree_walk_impl(t, mode, G, eps, delta_acc, theta, group_size, a_old, nsel, sel,
+                   ax, ay, az, phi, ninter);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -100,6 +100,14 @@ void oracle_tree_walk(const oracle_tree *t, int mode, double G, double eps,
                       double delta_acc, double theta, int group_size, const double *a_old,
                       double *ax, double *ay, double *az, double *phi, int64_t *ninter);
 
+/* As oracle_tree_walk, but only for the groups (group mode) or tree-order
+ * particles (particle mode) listed in sel[0..nsel); outputs of other
+ * particles are left untouched. */
+void oracle_tree_walk_groups(const oracle_tree *t, int mode, double G, double eps,
+                             double delta_acc, double theta, int group_size, const double *a_old,
+                             int64_t nsel, const int64_t *sel,
+                             double *ax, double *ay, double *az, double *phi, int64_t *ninter);
+
 /* ------------------------------------------------------------------------ */
 /* Leapfrog pieces: v += a * h ; x += v * h. */
 void oracle_kick(int64_t n, double *vx, double *vy, double *vz,

@@ -1,0 +1,947 @@
+// api.cu -- the C ABI of libnbody (declared in include/nbody.h): argument
+// checks, the context and its device buffers, host/device staging, and the
+// order of kernel launches for build, walk, direct, step and diagnostics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace nb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct nbody_ctx {
+    nbody_config cfg;
+    cudaStream_t stream = nullptr;
+    int device = 0, nsm = 0;
+    std::string err;
+
+    // capacities
+    int64_t cap_n = 0, cap_nodes = 0;
+    int cap_sys = 0;
+    std::vector<DevBuf *> owned;
+
+    DevState *ds = nullptr;
+    DevState *h_ds = nullptr;  // pinned
+    // particles (sorted)
+    DevBuf keys, keys_alt, vals, vals_alt, pos4, delta, leaflev;
+    DevBuf rs_temp, tree_temp, grp_temp, diag_temp, diag_out;
+    // nodes
+    DevBuf node_start, node_level, node_parent, node_link, node_count, node_nchild, node_arrive;
+    DevBuf nodeA, nodeB, mom64;
+    // groups
+    DevBuf gflag, grp_first, grp_count, grp_sphere, grp_sys, grp_alpha, grp_cost, grp_order;
+    // systems
+    DevBuf sys_off, sys_box, sys_boxord, sys_eps2, sys_root;
+    // walk / step
+    DevBuf acc_s, aold_s;
+    DevBuf st_buf[2][9];
+    // staging of host arrays
+    DevBuf stage[12];
+    double *h_diag = nullptr;  // pinned
+
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> wev;  // (start, end) pairs around walk-kernel launches
+    int wev_used = 0;
+    std::vector<cudaEvent_t> evpool;  // phase boundaries of asynchronous multi-step calls
+    int evused = 0;
+    int64_t kernels = 0;           // kernels launched by the current call
+    bool built = false;
+    bool eps_zero = false;  // some system of the last build has eps == 0
+    Layout L{};
+    float last_ms_build = 0.0f;
+    nbody_stats last{};
+
+    nbody_ctx() {
+        DevBuf *all[] = {&keys, &keys_alt, &vals, &vals_alt, &pos4, &delta, &leaflev, &rs_temp,
+                         &tree_temp, &grp_temp, &diag_temp, &diag_out, &node_start, &node_level,
+                         &node_parent, &node_link, &node_count, &node_nchild, &node_arrive,
+                         &nodeA, &nodeB, &mom64, &gflag, &grp_first, &grp_count, &grp_sphere,
+                         &grp_sys, &grp_alpha, &grp_cost, &grp_order, &sys_off, &sys_box,
+                         &sys_boxord, &sys_eps2, &sys_root, &acc_s, &aold_s};
+        for (DevBuf *b : all) owned.push_back(b);
+        for (auto &a : st_buf)
+            for (auto &b : a) owned.push_back(&b);
+        for (auto &b : stage) owned.push_back(&b);
+    }
+};
+
+namespace {
+
+nbody_status fail(nbody_ctx *ctx, nbody_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    g_last_error = msg;
+    return st;
+}
+
+nbody_status cuda_fail(nbody_ctx *ctx, cudaError_t e, const char *where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(ctx, NBODY_ECUDA, msg);
+}
+
+#define NB_CUDA(ctx, call)                                             \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);     \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t ensure(DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return cudaSuccess;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return e;
+    }
+    size_t want = bytes ? bytes : 16;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.bytes = want;
+    return cudaSuccess;
+}
+
+template <typename T>
+T *P(DevBuf &b) {
+    return reinterpret_cast<T *>(b.p);
+}
+
+bool config_ok(const nbody_config *c, std::string &why) {
+    char buf[160];
+    auto bad = [&](const char *m) {
+        why = m;
+        return false;
+    };
+    if (!(c->eps >= 0.0f) || !std::isfinite(c->eps)) return bad("eps must be finite and >= 0");
+    if (!(c->delta_acc >= 0.0f) || !std::isfinite(c->delta_acc)) return bad("delta_acc must be finite and >= 0");
+    if (!(c->theta > 0.0f && c->theta < 1.0f)) return bad("theta must be in (0, 1)");
+    if (!std::isfinite(c->G)) return bad("G must be finite");
+    if (c->ipl != 1 && c->ipl != 2 && c->ipl != 4) return bad("ipl must be 1, 2 or 4");
+    if (c->leaf_cap < 1 || c->leaf_cap > 32) return bad("leaf_cap must be in 1..32");
+    if (c->group_size < c->leaf_cap || c->group_size > 32 * c->ipl) {
+        snprintf(buf, sizeof buf, "group_size must be in leaf_cap..32*ipl (%d..%d)", c->leaf_cap,
+                 32 * c->ipl);
+        why = buf;
+        return false;
+    }
+    if (c->list_depth < 64 || c->list_depth > 1024 || c->list_depth % 32)
+        return bad("list_depth must be a multiple of 32 in 64..1024");
+    if (c->stack_depth < 64 || c->stack_depth > 4096) return bad("stack_depth must be in 64..4096");
+    if (c->warps_per_block < 1 || c->warps_per_block > 16) return bad("warps_per_block must be in 1..16");
+    if (c->schedule < 0 || c->schedule > 2) return bad("schedule must be 0, 1 or 2");
+    size_t smem = (size_t)c->warps_per_block *
+                  ((size_t)c->list_depth * 16 + (size_t)c->stack_depth * 4);
+    if (smem > 227 * 1024) return bad("warps_per_block * (16 list_depth + 4 stack_depth) exceeds 227 KB");
+    return true;
+}
+
+// Stage a caller array: device pointers pass through, host arrays are copied
+// into staging slot `slot`.
+cudaError_t stage_in(nbody_ctx *c, int slot, const void *p, size_t bytes, const void **out) {
+    if (!p) {
+        *out = nullptr;
+        return cudaSuccess;
+    }
+    if (is_device_ptr(p)) {
+        *out = p;
+        return cudaSuccess;
+    }
+    cudaError_t e = ensure(c->stage[slot], bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(c->stage[slot].p, p, bytes, cudaMemcpyHostToDevice, c->stream);
+    *out = c->stage[slot].p;
+    return e;
+}
+
+// Output array: device pointers pass through; host arrays get a staging slot
+// and are copied back by stage_out_finish.
+cudaError_t stage_out(nbody_ctx *c, int slot, void *p, size_t bytes, void **out) {
+    if (!p) {
+        *out = nullptr;
+        return cudaSuccess;
+    }
+    if (is_device_ptr(p)) {
+        *out = p;
+        return cudaSuccess;
+    }
+    cudaError_t e = ensure(c->stage[slot], bytes);
+    *out = c->stage[slot].p;
+    return e;
+}
+
+cudaError_t stage_out_finish(nbody_ctx *c, void *host, const void *dev, size_t bytes) {
+    if (!host || host == dev) return cudaSuccess;
+    return cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream);
+}
+
+int64_t node_capacity(int64_t n, int levels, int leaf_cap, int nsys) {
+    // internal nodes of one level are disjoint and hold > leaf_cap particles;
+    // leaves are disjoint and non-empty.
+    return n + (int64_t)levels * (n / (leaf_cap + 1)) + nsys + 8;
+}
+
+cudaError_t ensure_capacity(nbody_ctx *c, int64_t n, int nsys, int levels) {
+    cudaError_t e;
+#define NB_E(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+    if (n > c->cap_n) {
+        NB_E(ensure(c->keys, n * 8)); NB_E(ensure(c->keys_alt, n * 8));
+        NB_E(ensure(c->vals, n * 4)); NB_E(ensure(c->vals_alt, n * 4));
+        NB_E(ensure(c->pos4, n * 16)); NB_E(ensure(c->delta, n + 1)); NB_E(ensure(c->leaflev, n));
+        NB_E(ensure(c->rs_temp, radix_temp_bytes(n)));
+        NB_E(ensure(c->tree_temp, tree_temp_bytes(n, kMaxLevels)));
+        NB_E(ensure(c->grp_temp, (size_t)((n + 4095) / 4096 + 64) * 4));
+        NB_E(ensure(c->gflag, n));
+        NB_E(ensure(c->grp_first, n * 4)); NB_E(ensure(c->grp_count, n * 4));
+        NB_E(ensure(c->grp_sphere, n * 16)); NB_E(ensure(c->grp_sys, n * 4));
+        NB_E(ensure(c->grp_alpha, n * 4)); NB_E(ensure(c->grp_cost, n * 4));
+        NB_E(ensure(c->grp_order, n * 4));
+        NB_E(ensure(c->acc_s, n * 16)); NB_E(ensure(c->aold_s, n * 4));
+        c->cap_n = n;
+    }
+    int64_t cn = node_capacity(n, levels, c->cfg.leaf_cap, nsys);
+    if (cn > c->cap_nodes) {
+        NB_E(ensure(c->node_start, cn * 4)); NB_E(ensure(c->node_level, cn));
+        NB_E(ensure(c->node_parent, cn * 4)); NB_E(ensure(c->node_link, cn * 4));
+        NB_E(ensure(c->node_count, cn * 4)); NB_E(ensure(c->node_nchild, cn * 4));
+        NB_E(ensure(c->node_arrive, cn * 4));
+        NB_E(ensure(c->nodeA, cn * 16)); NB_E(ensure(c->nodeB, cn * 16));
+        NB_E(ensure(c->mom64, cn * 32));
+        c->cap_nodes = cn;
+    }
+    if (nsys > c->cap_sys) {
+        NB_E(ensure(c->sys_off, (size_t)(nsys + 1) * 8)); NB_E(ensure(c->sys_box, (size_t)nsys * sizeof(SysBox)));
+        NB_E(ensure(c->sys_boxord, (size_t)nsys * 24)); NB_E(ensure(c->sys_eps2, (size_t)nsys * 4));
+        NB_E(ensure(c->sys_root, (size_t)nsys * 4));
+        c->cap_sys = nsys;
+    }
+#undef NB_E
+    return cudaSuccess;
+}
+
+Layout make_layout(int64_t n, int nsys) {
+    Layout L;
+    L.n = n;
+    L.nsys = nsys;
+    int sb = 0;
+    while ((1 << sb) < nsys) sb++;
+    L.sysbits = nsys > 1 ? sb : 0;
+    L.levels = std::min(kMaxLevels, (63 - L.sysbits) / 3);
+    L.keybits = L.sysbits + 3 * L.levels;
+    return L;
+}
+
+// Keys, sort and tree of n particles whose positions are x, y, z (FP32, or
+// FP64 when dbl); pos4 must be filled by the caller-specific gather given
+// the permutation in vals (fill_pos4 == true: gather from x, y, z, m here).
+nbody_status build_core(nbody_ctx *c, const Layout &L, const void *x, const void *y,
+                        const void *z, bool dbl, const float *m, bool fill_pos4) {
+    cudaStream_t s = c->stream;
+    launch_bbox(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<uint32_t>(c->sys_boxord),
+                P<SysBox>(c->sys_box), c->nsm);
+    c->kernels += 3;
+    launch_keys(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<SysBox>(c->sys_box),
+                P<uint64_t>(c->keys), P<uint32_t>(c->vals));
+    c->kernels += 1 + 4 * ((L.keybits + 8) / 9);
+    if (radix_sort(s, P<uint64_t>(c->keys), P<uint32_t>(c->vals), P<uint64_t>(c->keys_alt),
+                   P<uint32_t>(c->vals_alt), L.n, L.keybits, c->rs_temp.p)) {
+        std::swap(c->keys, c->keys_alt);
+        std::swap(c->vals, c->vals_alt);
+    }
+    if (fill_pos4) {
+        launch_gather_pos4(s, L.n, P<uint32_t>(c->vals), x, y, z, dbl, m, P<float4>(c->pos4));
+        c->kernels += 1;
+    }
+    NB_CUDA(c, cudaGetLastError());
+    return NBODY_OK;
+}
+
+nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
+    cudaStream_t s = c->stream;
+    build_tree(s, L, P<uint64_t>(c->keys), P<float4>(c->pos4), P<SysBox>(c->sys_box),
+               P<int64_t>(c->sys_off), c->cfg.leaf_cap, c->cfg.G, c->cap_nodes, P<int8_t>(c->delta),
+               P<int8_t>(c->leaflev), c->tree_temp.p, c->ds, P<int32_t>(c->node_start),
+               P<int8_t>(c->node_level), P<int32_t>(c->node_parent), P<int32_t>(c->node_link),
+               P<int32_t>(c->node_count), P<int32_t>(c->node_nchild), P<int32_t>(c->node_arrive),
+               P<float4>(c->nodeA), P<float4>(c->nodeB), P<Mom64>(c->mom64),
+               P<int32_t>(c->sys_root), c->nsm);
+    build_groups(s, L, c->cfg.group_size, P<float4>(c->pos4), P<int64_t>(c->sys_off),
+                 P<int32_t>(c->node_start), P<int32_t>(c->node_parent), P<int32_t>(c->node_count),
+                 P<int32_t>(c->node_nchild), P<int8_t>(c->node_level), c->ds,
+                 P<uint8_t>(c->gflag), c->grp_temp.p, P<int32_t>(c->grp_first),
+                 P<int32_t>(c->grp_count), P<float4>(c->grp_sphere), P<int32_t>(c->grp_sys),
+                 c->nsm);
+    c->kernels += 6 + 5;
+    NB_CUDA(c, cudaGetLastError());
+    return NBODY_OK;
+}
+
+// Upload the CSR offsets and per-system eps^2.
+nbody_status upload_systems(nbody_ctx *c, int nsys, const int64_t *offsets, const float *eps_sys) {
+    std::vector<int64_t> off(nsys + 1);
+    std::vector<float> e2(nsys);
+    if (offsets) {
+        std::memcpy(off.data(), offsets, sizeof(int64_t) * (nsys + 1));
+    } else {
+        off[0] = 0;
+    }
+    for (int s = 0; s < nsys; s++) {
+        float e = eps_sys ? eps_sys[s] : c->cfg.eps;
+        e2[s] = e * e;
+    }
+    NB_CUDA(c, cudaMemcpyAsync(c->sys_off.p, off.data(), sizeof(int64_t) * (nsys + 1),
+                               cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(c->sys_eps2.p, e2.data(), sizeof(float) * nsys,
+                               cudaMemcpyHostToDevice, c->stream));
+    // the copies read pageable host vectors: make sure they have completed
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return NBODY_OK;
+}
+
+bool any_zero_eps(nbody_ctx *c, int nsys, const float *eps_sys) {
+    if (!eps_sys) return !(c->cfg.eps > 0.0f);
+    for (int s = 0; s < nsys; s++)
+        if (!(eps_sys[s] > 0.0f)) return true;
+    return false;
+}
+
+nbody_status check_systems(nbody_ctx *c, int32_t nsys, const int64_t *offsets,
+                           const float *eps_sys) {
+    if (nsys < 1 || nsys > (1 << 20)) return fail(c, NBODY_EINVAL, "nsys must be in 1..2^20");
+    if (!offsets) return fail(c, NBODY_EINVAL, "offsets is NULL");
+    if (offsets[0] != 0) return fail(c, NBODY_EINVAL, "offsets[0] must be 0");
+    for (int s = 0; s < nsys; s++)
+        if (offsets[s + 1] < offsets[s]) return fail(c, NBODY_EINVAL, "offsets must be non-decreasing");
+    if (offsets[nsys] < 1) return fail(c, NBODY_EINVAL, "no particles");
+    if (offsets[nsys] >= (int64_t)1 << 31) return fail(c, NBODY_EINVAL, "n must be < 2^31");
+    if (eps_sys)
+        for (int s = 0; s < nsys; s++)
+            if (!(eps_sys[s] >= 0.0f) || !std::isfinite(eps_sys[s]))
+                return fail(c, NBODY_EINVAL, "eps_sys must be finite and >= 0");
+    return NBODY_OK;
+}
+
+nbody_status read_status(nbody_ctx *c) {
+    NB_CUDA(c, cudaMemcpyAsync(c->h_ds, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->h_ds->status & kStatusBadTree)
+        return fail(c, NBODY_ECUDA, "internal error: a tree index failed its bounds check");
+    if (c->h_ds->status & kStatusStackOverflow)
+        return fail(c, NBODY_EOVERFLOW,
+                    "traversal stack or node capacity overflowed; increase stack_depth");
+    return NBODY_OK;
+}
+
+nbody_status do_build(nbody_ctx *c, int64_t n, int nsys, const int64_t *offsets,
+                      const float *eps_sys, const float *x, const float *y, const float *z,
+                      const float *m) {
+    Layout L = make_layout(n, nsys);
+    cudaError_t e = ensure_capacity(c, n, nsys, L.levels);
+    if (e != cudaSuccess) return fail(c, NBODY_ENOMEM, std::string("allocation: ") + cudaGetErrorString(e));
+    std::vector<int64_t> off1 = {0, n};
+    nbody_status st = upload_systems(c, nsys, offsets ? offsets : off1.data(), eps_sys);
+    if (st != NBODY_OK) return st;
+    c->kernels = 0;
+    c->wev_used = 0;
+    NB_CUDA(c, cudaMemsetAsync(c->ds, 0, sizeof(DevState), c->stream));
+    const void *dx, *dy, *dz, *dm;
+    size_t fb = (size_t)n * 4;
+    NB_CUDA(c, stage_in(c, 0, x, fb, &dx));
+    NB_CUDA(c, stage_in(c, 1, y, fb, &dy));
+    NB_CUDA(c, stage_in(c, 2, z, fb, &dz));
+    NB_CUDA(c, stage_in(c, 3, m, fb, &dm));
+    NB_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    st = build_core(c, L, dx, dy, dz, false, (const float *)dm, true);
+    if (st != NBODY_OK) return st;
+    st = build_tree_groups(c, L);
+    if (st != NBODY_OK) return st;
+    NB_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    st = read_status(c);
+    if (st != NBODY_OK) return st;
+    NB_CUDA(c, cudaEventElapsedTime(&c->last_ms_build, c->ev[0], c->ev[1]));
+    c->L = L;
+    c->built = true;
+    c->eps_zero = any_zero_eps(c, nsys, eps_sys);
+    c->last.n_nodes = c->h_ds->nnodes;
+    c->last.n_groups = c->h_ds->ngroups;
+    c->last.levels = L.levels;
+    c->last.ms_build = c->last_ms_build;
+    c->last.kernels = c->kernels;
+    return NBODY_OK;
+}
+
+WalkShape walk_shape(nbody_ctx *c, bool geometric, bool phi, bool safe) {
+    WalkShape sh;
+    sh.ipl = c->cfg.ipl;
+    sh.geometric = geometric;
+    sh.potential = phi;
+    sh.compensated = c->cfg.compensated != 0;
+    sh.safe = safe;
+    sh.warps_per_block = c->cfg.warps_per_block;
+    return sh;
+}
+
+WalkArgs walk_args(nbody_ctx *c) {
+    WalkArgs a{};
+    a.pos4 = P<float4>(c->pos4);
+    a.nodeA = P<float4>(c->nodeA);
+    a.nodeB = P<float4>(c->nodeB);
+    a.grp_first = P<int32_t>(c->grp_first);
+    a.grp_count = P<int32_t>(c->grp_count);
+    a.grp_sphere = P<float4>(c->grp_sphere);
+    a.grp_alpha = P<float>(c->grp_alpha);
+    a.grp_sys = P<int32_t>(c->grp_sys);
+    a.order = nullptr;
+    a.sys_eps2 = P<float>(c->sys_eps2);
+    a.sys_root = P<int32_t>(c->sys_root);
+    a.ds = c->ds;
+    a.grp_cost = P<int32_t>(c->grp_cost);
+    a.n = c->L.n;
+    a.G = c->cfg.G;
+    a.theta = c->cfg.theta;
+    a.list_depth = c->cfg.list_depth;
+    a.stack_depth = c->cfg.stack_depth;
+    return a;
+}
+
+// Reset the walk's queue head and counters (status is kept).
+nbody_status reset_walk_counters(nbody_ctx *c, bool accumulators) {
+    char *base = reinterpret_cast<char *>(c->ds);
+    NB_CUDA(c, cudaMemsetAsync(base + offsetof(DevState, queue_head), 0, sizeof(int32_t), c->stream));
+    if (accumulators) {
+        NB_CUDA(c, cudaMemsetAsync(base + offsetof(DevState, max_stack), 0, sizeof(int32_t), c->stream));
+        NB_CUDA(c, cudaMemsetAsync(base + offsetof(DevState, list_entries), 0,
+                                   2 * sizeof(unsigned long long), c->stream));
+    }
+    return NBODY_OK;
+}
+
+// Events from a pool that grows on demand (timing of asynchronous phases).
+cudaError_t pool_event(nbody_ctx *c, cudaEvent_t *out);
+
+cudaError_t pool_event(nbody_ctx *c, cudaEvent_t *out) {
+    if ((int)c->evpool.size() <= c->evused) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        c->evpool.push_back(ev);
+    }
+    *out = c->evpool[c->evused++];
+    return cudaSuccess;
+}
+
+// Walk over the current groups; aold_s (sorted) must hold |a_old|.
+nbody_status run_walk(nbody_ctx *c, bool geometric, bool phi, bool safe, const int32_t *perm,
+                      float *ax, float *ay, float *az, float *ph, float4 *acc_sorted,
+                      bool reset_accumulators = true) {
+    nbody_status st = reset_walk_counters(c, reset_accumulators);
+    if (st != NBODY_OK) return st;
+    if (!geometric) {
+        launch_group_alpha(c->stream, c->L.n, c->ds, P<int32_t>(c->grp_first),
+                           P<int32_t>(c->grp_count), P<float>(c->aold_s), c->cfg.delta_acc,
+                           P<float>(c->grp_alpha), c->nsm);
+        c->kernels += 1;
+    }
+    while ((int)c->wev.size() < c->wev_used + 2) {
+        cudaEvent_t ev;
+        NB_CUDA(c, cudaEventCreate(&ev));
+        c->wev.push_back(ev);
+    }
+    WalkArgs a = walk_args(c);
+    a.perm = perm;
+    a.ax = ax;
+    a.ay = ay;
+    a.az = az;
+    a.phi = ph;
+    a.acc_sorted = acc_sorted;
+    NB_CUDA(c, cudaEventRecord(c->wev[c->wev_used], c->stream));
+    cudaError_t e = launch_walk(c->stream, a, walk_shape(c, geometric, phi, safe), c->nsm);
+    if (e != cudaSuccess) return cuda_fail(c, e, "walk launch");
+    NB_CUDA(c, cudaEventRecord(c->wev[c->wev_used + 1], c->stream));
+    c->wev_used += 2;
+    c->kernels += 1;
+    return NBODY_OK;
+}
+
+// After a synchronisation: total walk-kernel time of the recorded pairs.
+float collect_walk_ms(nbody_ctx *c, int *launches) {
+    float t = 0.0f;
+    for (int k = 0; k + 1 < c->wev_used; k += 2) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c->wev[k], c->wev[k + 1]) == cudaSuccess) t += ms;
+    }
+    *launches = c->wev_used / 2;
+    c->wev_used = 0;
+    return t;
+}
+
+
+}  // namespace
+
+// ============================================================================ ABI
+extern "C" {
+
+int32_t nbody_abi_version(void) { return NBODY_ABI_VERSION; }
+
+void nbody_config_default(nbody_config *c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->G = 1.0f;
+    c->eps = 1.0f / 64.0f;
+    c->delta_acc = 1.0f / 512.0f;
+    c->theta = 0.5f;
+    c->leaf_cap = 16;
+    c->group_size = 64;
+    c->ipl = 2;
+    c->list_depth = 256;
+    c->stack_depth = 1024;
+    c->warps_per_block = 4;
+    c->compensated = 0;
+    c->want_potential = 0;
+    c->schedule = NBODY_SCHED_MORTON;
+}
+
+nbody_status nbody_create(nbody_ctx **out, const nbody_config *cfg, void *cuda_stream) {
+    if (!out) return fail(nullptr, NBODY_EINVAL, "out is NULL");
+    *out = nullptr;
+    nbody_config c;
+    if (cfg) c = *cfg; else nbody_config_default(&c);
+    std::string why;
+    if (!config_ok(&c, why)) return fail(nullptr, NBODY_EINVAL, why);
+    nbody_ctx *ctx = new (std::nothrow) nbody_ctx();
+    if (!ctx) return fail(nullptr, NBODY_ENOMEM, "host allocation");
+    ctx->cfg = c;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->ds, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_ds, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_diag, 8 * sizeof(double));
+    for (int k = 0; k < 4 && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->ev[k]);
+    if (e == cudaSuccess) e = cudaMemset(ctx->ds, 0, sizeof(DevState));
+    if (e != cudaSuccess) {
+        nbody_status st = cuda_fail(nullptr, e, "nbody_create");
+        nbody_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return NBODY_OK;
+}
+
+nbody_status nbody_destroy(nbody_ctx *ctx) {
+    if (!ctx) return NBODY_OK;
+    cudaStreamSynchronize(ctx->stream);
+    for (DevBuf *b : ctx->owned)
+        if (b->p) cudaFree(b->p);
+    if (ctx->ds) cudaFree(ctx->ds);
+    if (ctx->h_ds) cudaFreeHost(ctx->h_ds);
+    if (ctx->h_diag) cudaFreeHost(ctx->h_diag);
+    for (auto &ev : ctx->ev)
+        if (ev) cudaEventDestroy(ev);
+    for (auto ev : ctx->wev) cudaEventDestroy(ev);
+    for (auto ev : ctx->evpool) cudaEventDestroy(ev);
+    delete ctx;
+    return NBODY_OK;
+}
+
+nbody_status nbody_set_config(nbody_ctx *ctx, const nbody_config *cfg) {
+    if (!ctx || !cfg) return fail(ctx, NBODY_EINVAL, "NULL argument");
+    std::string why;
+    if (!config_ok(cfg, why)) return fail(ctx, NBODY_EINVAL, why);
+    bool rebuild = cfg->leaf_cap != ctx->cfg.leaf_cap || cfg->group_size != ctx->cfg.group_size ||
+                   cfg->G != ctx->cfg.G || cfg->eps != ctx->cfg.eps;
+    ctx->cfg = *cfg;
+    if (rebuild) ctx->built = false;
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_config(const nbody_ctx *ctx, nbody_config *cfg) {
+    if (!ctx || !cfg) return NBODY_EINVAL;
+    *cfg = ctx->cfg;
+    return NBODY_OK;
+}
+
+nbody_status nbody_build(nbody_ctx *ctx, int64_t n, const float *x, const float *y,
+                         const float *z, const float *m) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    if (n < 1 || n >= ((int64_t)1 << 31)) return fail(ctx, NBODY_EINVAL, "n must be in 1..2^31-1");
+    if (!x || !y || !z || !m) return fail(ctx, NBODY_EINVAL, "NULL array");
+    ctx->built = false;
+    return do_build(ctx, n, 1, nullptr, nullptr, x, y, z, m);
+}
+
+nbody_status nbody_build_batched(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
+                                 const float *eps_sys, const float *x, const float *y,
+                                 const float *z, const float *m) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    nbody_status st = check_systems(ctx, nsys, offsets, eps_sys);
+    if (st != NBODY_OK) return st;
+    if (!x || !y || !z || !m) return fail(ctx, NBODY_EINVAL, "NULL array");
+    ctx->built = false;
+    return do_build(ctx, offsets[nsys], nsys, offsets, eps_sys, x, y, z, m);
+}
+
+nbody_status nbody_walk(nbody_ctx *ctx, const float *a_old, float *ax, float *ay, float *az,
+                        float *phi, nbody_stats *stats) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    if (!ctx->built) return fail(ctx, NBODY_ENOTBUILT, "nbody_walk before nbody_build");
+    if (!ax || !ay || !az) return fail(ctx, NBODY_EINVAL, "NULL output array");
+    if (phi && !ctx->cfg.want_potential) return fail(ctx, NBODY_EINVAL, "phi requested but want_potential = 0");
+    const int64_t n = ctx->L.n;
+    const size_t fb = (size_t)n * 4;
+    cudaStream_t s = ctx->stream;
+    void *dax, *day, *daz, *dph;
+    NB_CUDA(ctx, stage_out(ctx, 4, ax, fb, &dax));
+    NB_CUDA(ctx, stage_out(ctx, 5, ay, fb, &day));
+    NB_CUDA(ctx, stage_out(ctx, 6, az, fb, &daz));
+    NB_CUDA(ctx, stage_out(ctx, 7, phi, fb, &dph));
+    const bool safe = ctx->eps_zero;
+    const bool want_phi = phi != nullptr;
+    ctx->kernels = 0;
+    ctx->wev_used = 0;
+    char *dsb = reinterpret_cast<char *>(ctx->ds);
+    NB_CUDA(ctx, cudaMemsetAsync(dsb + offsetof(DevState, status), 0, sizeof(int32_t), s));
+    NB_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+    nbody_status st;
+    if (a_old) {
+        const void *dao;
+        NB_CUDA(ctx, stage_in(ctx, 8, a_old, fb, &dao));
+        launch_gather_f32(s, n, P<uint32_t>(ctx->vals), (const float *)dao, P<float>(ctx->aold_s));
+        ctx->kernels += 1;
+    } else {
+        // bootstrap: geometric criterion first, its |a| feeds Eq. 2
+        st = run_walk(ctx, true, false, safe, nullptr, nullptr, nullptr, nullptr, nullptr,
+                      P<float4>(ctx->acc_s));
+        if (st != NBODY_OK) return st;
+        launch_acc_mag(s, n, P<float4>(ctx->acc_s), P<float>(ctx->aold_s));
+        ctx->kernels += 1;
+    }
+    st = run_walk(ctx, false, want_phi, safe, (const int32_t *)P<uint32_t>(ctx->vals),
+                  (float *)dax, (float *)day, (float *)daz, (float *)dph, nullptr);
+    if (st != NBODY_OK) return st;
+    NB_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
+    NB_CUDA(ctx, stage_out_finish(ctx, ax, dax, fb));
+    NB_CUDA(ctx, stage_out_finish(ctx, ay, day, fb));
+    NB_CUDA(ctx, stage_out_finish(ctx, az, daz, fb));
+    NB_CUDA(ctx, stage_out_finish(ctx, phi, dph, fb));
+    st = read_status(ctx);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    ctx->last.n_groups = ctx->h_ds->ngroups;
+    ctx->last.interactions = (int64_t)ctx->h_ds->interactions;
+    ctx->last.list_entries = (int64_t)ctx->h_ds->list_entries;
+    ctx->last.max_stack = ctx->h_ds->max_stack;
+    ctx->last.ms_walk = ms;
+    ctx->last.ms_walk_kernel = collect_walk_ms(ctx, &ctx->last.walk_launches);
+    ctx->last.kernels = ctx->kernels;
+    if (stats) *stats = ctx->last;
+    return st;
+}
+
+nbody_status nbody_direct(int64_t n, const float *x, const float *y, const float *z,
+                          const float *m, float G, float eps, int32_t compensated, float *ax,
+                          float *ay, float *az, float *phi, void *cuda_stream) {
+    if (n < 1 || n >= ((int64_t)1 << 31)) return fail(nullptr, NBODY_EINVAL, "n must be in 1..2^31-1");
+    if (!x || !y || !z || !m || !ax || !ay || !az) return fail(nullptr, NBODY_EINVAL, "NULL array");
+    if (!(eps >= 0.0f) || !std::isfinite(eps) || !std::isfinite(G))
+        return fail(nullptr, NBODY_EINVAL, "eps must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t fb = (size_t)n * 4;
+    const float *in[4] = {x, y, z, m};
+    float *out[4] = {ax, ay, az, phi};
+    const float *din[4];
+    float *dout[4];
+    std::vector<void *> tmp;
+    auto cleanup = [&]() {
+        for (void *p : tmp) cudaFree(p);
+    };
+    for (int k = 0; k < 4; k++) {
+        if (is_device_ptr(in[k])) {
+            din[k] = in[k];
+        } else {
+            void *p = nullptr;
+            cudaError_t e = cudaMalloc(&p, fb);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(p, in[k], fb, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) { if (p) cudaFree(p); cleanup(); return cuda_fail(nullptr, e, "nbody_direct staging"); }
+            tmp.push_back(p);
+            din[k] = (const float *)p;
+        }
+        if (!out[k] || is_device_ptr(out[k])) {
+            dout[k] = out[k];
+        } else {
+            void *p = nullptr;
+            cudaError_t e = cudaMalloc(&p, fb);
+            if (e != cudaSuccess) { cleanup(); return cuda_fail(nullptr, e, "nbody_direct staging"); }
+            tmp.push_back(p);
+            dout[k] = (float *)p;
+        }
+    }
+    cudaError_t e = launch_direct(s, n, din[0], din[1], din[2], din[3], G, eps, compensated != 0,
+                                  dout[0], dout[1], dout[2], dout[3]);
+    for (int k = 0; k < 4 && e == cudaSuccess; k++)
+        if (out[k] && dout[k] != out[k]) e = cudaMemcpyAsync(out[k], dout[k], fb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "nbody_direct");
+    return NBODY_OK;
+}
+
+static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
+                              const float *eps_sys, int64_t n, double *x, double *y, double *z,
+                              float *vx, float *vy, float *vz, const float *m, float *ax,
+                              float *ay, float *az, float dt, int32_t nsteps, nbody_stats *stats) {
+    if (!x || !y || !z || !vx || !vy || !vz || !m || !ax || !ay || !az)
+        return fail(ctx, NBODY_EINVAL, "NULL array");
+    if (nsteps < 0) return fail(ctx, NBODY_EINVAL, "nsteps must be >= 0");
+    if (!std::isfinite(dt)) return fail(ctx, NBODY_EINVAL, "dt must be finite");
+    ctx->built = false;
+    cudaStream_t s = ctx->stream;
+    Layout L = make_layout(n, nsys);
+    cudaError_t e = ensure_capacity(ctx, n, nsys, L.levels);
+    for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+        for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure(ctx->st_buf[b][k], (size_t)n * 8);
+        for (int k = 3; k < 9 && e == cudaSuccess; k++) e = ensure(ctx->st_buf[b][k], (size_t)n * 4);
+    }
+    if (e != cudaSuccess) return fail(ctx, NBODY_ENOMEM, std::string("allocation: ") + cudaGetErrorString(e));
+    std::vector<int64_t> off1 = {0, n};
+    nbody_status st = upload_systems(ctx, nsys, offsets ? offsets : off1.data(), eps_sys);
+    if (st != NBODY_OK) return st;
+    const bool safe = any_zero_eps(ctx, nsys, eps_sys);
+    StepState S[2];
+    for (int b = 0; b < 2; b++) {
+        S[b].x = P<double>(ctx->st_buf[b][0]);
+        S[b].y = P<double>(ctx->st_buf[b][1]);
+        S[b].z = P<double>(ctx->st_buf[b][2]);
+        S[b].vx = P<float>(ctx->st_buf[b][3]);
+        S[b].vy = P<float>(ctx->st_buf[b][4]);
+        S[b].vz = P<float>(ctx->st_buf[b][5]);
+        S[b].m = P<float>(ctx->st_buf[b][6]);
+        S[b].aold = P<float>(ctx->st_buf[b][7]);
+        S[b].id = P<uint32_t>(ctx->st_buf[b][8]);
+    }
+    const size_t db = (size_t)n * 8, fb = (size_t)n * 4;
+    const void *in[10];
+    void *arr[10] = {x, y, z, vx, vy, vz, (void *)m, ax, ay, az};
+    size_t sz[10] = {db, db, db, fb, fb, fb, fb, fb, fb, fb};
+    for (int k = 0; k < 10; k++) NB_CUDA(ctx, stage_in(ctx, k, arr[k], sz[k], &in[k]));
+    float4 *acc = P<float4>(ctx->acc_s);
+    ctx->kernels = 0;
+    ctx->wev_used = 0;
+    ctx->evused = 0;
+    NB_CUDA(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevState), s));
+    launch_load_state(s, n, (const double *)in[0], (const double *)in[1], (const double *)in[2],
+                      (const float *)in[3], (const float *)in[4], (const float *)in[5],
+                      (const float *)in[6], (const float *)in[7], (const float *)in[8],
+                      (const float *)in[9], S[0], acc);
+    ctx->kernels += 1;
+    int cur = 0;
+    std::vector<int> marks;  // per step: event indices (build start, build end, walk end)
+    for (int it = 0; it < nsteps; it++) {
+        launch_kick_drift(s, n, S[cur], acc, 0.5f * dt, dt);
+        ctx->kernels += 1;
+        cudaEvent_t e0, e1, e2;
+        NB_CUDA(ctx, pool_event(ctx, &e0));
+        NB_CUDA(ctx, cudaEventRecord(e0, s));
+        st = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
+        if (st != NBODY_OK) return st;
+        launch_permute_state(s, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur], P<float4>(ctx->pos4));
+        ctx->kernels += 1;
+        cur = 1 - cur;
+        st = build_tree_groups(ctx, L);
+        if (st != NBODY_OK) return st;
+        NB_CUDA(ctx, pool_event(ctx, &e1));
+        NB_CUDA(ctx, cudaEventRecord(e1, s));
+        NB_CUDA(ctx, cudaMemcpyAsync(ctx->aold_s.p, S[cur].aold, fb, cudaMemcpyDeviceToDevice, s));
+        st = run_walk(ctx, false, false, safe, nullptr, nullptr, nullptr, nullptr, nullptr, acc,
+                      false);
+        if (st != NBODY_OK) return st;
+        NB_CUDA(ctx, pool_event(ctx, &e2));
+        NB_CUDA(ctx, cudaEventRecord(e2, s));
+        launch_kick(s, n, S[cur], acc, 0.5f * dt);
+        ctx->kernels += 1;
+        marks.push_back(ctx->evused - 3);
+    }
+    // in[] are the device copies (the caller's arrays themselves when on the device)
+    launch_store_state(s, n, S[cur], acc, (double *)in[0], (double *)in[1], (double *)in[2],
+                       (float *)in[3], (float *)in[4], (float *)in[5], (float *)in[7],
+                       (float *)in[8], (float *)in[9]);
+    ctx->kernels += 1;
+    for (int k = 0; k < 10; k++) {
+        if (k == 6) continue;
+        if (in[k] != arr[k])
+            NB_CUDA(ctx, cudaMemcpyAsync(arr[k], in[k], sz[k], cudaMemcpyDeviceToHost, s));
+    }
+    st = read_status(ctx);
+    float ms_build = 0.0f, ms_walk = 0.0f;
+    for (int k : marks) {
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, ctx->evpool[k], ctx->evpool[k + 1]);
+        cudaEventElapsedTime(&b, ctx->evpool[k + 1], ctx->evpool[k + 2]);
+        ms_build += a;
+        ms_walk += b;
+    }
+    ctx->L = L;
+    ctx->last.n_nodes = ctx->h_ds->nnodes;
+    ctx->last.n_groups = ctx->h_ds->ngroups;
+    ctx->last.levels = L.levels;
+    ctx->last.interactions = (int64_t)ctx->h_ds->interactions;
+    ctx->last.list_entries = (int64_t)ctx->h_ds->list_entries;
+    ctx->last.max_stack = ctx->h_ds->max_stack;
+    ctx->last.ms_build = ms_build;
+    ctx->last.ms_walk = ms_walk;
+    ctx->last.ms_walk_kernel = collect_walk_ms(ctx, &ctx->last.walk_launches);
+    ctx->last.kernels = ctx->kernels;
+    if (stats) *stats = ctx->last;
+    // the sorted state no longer matches a caller-order build
+    ctx->built = false;
+    return st;
+}
+
+nbody_status nbody_step(nbody_ctx *ctx, int64_t n, double *x, double *y, double *z, float *vx,
+                        float *vy, float *vz, const float *m, float *ax, float *ay, float *az,
+                        float dt, int32_t nsteps, nbody_stats *stats) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    if (n < 1 || n >= ((int64_t)1 << 31)) return fail(ctx, NBODY_EINVAL, "n must be in 1..2^31-1");
+    return step_impl(ctx, 1, nullptr, nullptr, n, x, y, z, vx, vy, vz, m, ax, ay, az, dt, nsteps,
+                     stats);
+}
+
+nbody_status nbody_step_batched(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
+                                const float *eps_sys, double *x, double *y, double *z,
+                                float *vx, float *vy, float *vz, const float *m, float *ax,
+                                float *ay, float *az, float dt, int32_t nsteps,
+                                nbody_stats *stats) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    nbody_status st = check_systems(ctx, nsys, offsets, eps_sys);
+    if (st != NBODY_OK) return st;
+    return step_impl(ctx, nsys, offsets, eps_sys, offsets[nsys], x, y, z, vx, vy, vz, m, ax, ay,
+                     az, dt, nsteps, stats);
+}
+
+nbody_status nbody_diagnostics(nbody_ctx *ctx, int64_t n, const double *x, const double *y,
+                               const double *z, const float *vx, const float *vy,
+                               const float *vz, const float *m, const float *phi, double *out) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    if (n < 1 || n >= ((int64_t)1 << 31)) return fail(ctx, NBODY_EINVAL, "n must be in 1..2^31-1");
+    if (!x || !y || !z || !vx || !vy || !vz || !m || !out) return fail(ctx, NBODY_EINVAL, "NULL array");
+    const size_t db = (size_t)n * 8, fb = (size_t)n * 4;
+    const void *in[8];
+    const void *arr[8] = {x, y, z, vx, vy, vz, m, phi};
+    size_t sz[8] = {db, db, db, fb, fb, fb, fb, fb};
+    for (int k = 0; k < 8; k++) NB_CUDA(ctx, stage_in(ctx, k, arr[k], sz[k], &in[k]));
+    cudaError_t e = ensure(ctx->diag_temp, diag_temp_bytes());
+    if (e == cudaSuccess) e = ensure(ctx->diag_out, 8 * sizeof(double));
+    if (e != cudaSuccess) return fail(ctx, NBODY_ENOMEM, "allocation");
+    launch_diagnostics(ctx->stream, n, (const double *)in[0], (const double *)in[1],
+                       (const double *)in[2], (const float *)in[3], (const float *)in[4],
+                       (const float *)in[5], (const float *)in[6], (const float *)in[7],
+                       ctx->diag_temp.p, P<double>(ctx->diag_out));
+    NB_CUDA(ctx, cudaGetLastError());
+    NB_CUDA(ctx, cudaMemcpyAsync(ctx->h_diag, ctx->diag_out.p, 8 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::memcpy(out, ctx->h_diag, 8 * sizeof(double));
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_group_costs(nbody_ctx *ctx, int32_t *counts, int64_t cap,
+                                   int64_t *n_groups) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    if (!counts || cap < 0 || !n_groups) return fail(ctx, NBODY_EINVAL, "bad argument");
+    if (!ctx->grp_cost.p) return fail(ctx, NBODY_ENOTBUILT, "no walk yet");
+    NB_CUDA(ctx, cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+    NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int64_t ng = ctx->h_ds->ngroups;
+    *n_groups = ng;
+    int64_t k = std::min(ng, cap);
+    if (k > 0) {
+        cudaMemcpyKind kind = is_device_ptr(counts) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        NB_CUDA(ctx, cudaMemcpyAsync(counts, ctx->grp_cost.p, (size_t)k * 4, kind, ctx->stream));
+        NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return NBODY_OK;
+}
+
+nbody_status nbody_export(nbody_ctx *ctx, int32_t what, void *dst, int64_t cap, int64_t *count) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    if (!count || cap < 0 || (cap > 0 && !dst)) return fail(ctx, NBODY_EINVAL, "bad argument");
+    if (!ctx->built) return fail(ctx, NBODY_ENOTBUILT, "no build to export");
+    NB_CUDA(ctx, cudaMemcpyAsync(ctx->h_ds, ctx->ds, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+    NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t n = ctx->L.n, nn = ctx->h_ds->nnodes, ng = ctx->h_ds->ngroups;
+    const void *src = nullptr;
+    int64_t len = 0;
+    size_t esz = 4;
+    switch (what) {
+        case NBODY_EXPORT_PERM: src = ctx->vals.p; len = n; break;
+        case NBODY_EXPORT_KEYS: src = ctx->keys.p; len = n; esz = 8; break;
+        case NBODY_EXPORT_NODE_LEVEL: src = ctx->node_level.p; len = nn; esz = 1; break;
+        case NBODY_EXPORT_NODE_START: src = ctx->node_start.p; len = nn; break;
+        case NBODY_EXPORT_NODE_COUNT: src = ctx->node_count.p; len = nn; break;
+        case NBODY_EXPORT_NODE_PARENT: src = ctx->node_parent.p; len = nn; break;
+        case NBODY_EXPORT_NODE_A: src = ctx->nodeA.p; len = nn; esz = 16; break;
+        case NBODY_EXPORT_NODE_B: src = ctx->nodeB.p; len = nn; esz = 16; break;
+        case NBODY_EXPORT_GROUP_FIRST: src = ctx->grp_first.p; len = ng; break;
+        case NBODY_EXPORT_GROUP_COUNT: src = ctx->grp_count.p; len = ng; break;
+        case NBODY_EXPORT_GROUP_SPHERE: src = ctx->grp_sphere.p; len = ng; esz = 16; break;
+        case NBODY_EXPORT_SYS_BOX: {
+            // SysBox is 32 bytes; export the first 16 (x0, y0, z0, L) of each
+            *count = ctx->L.nsys;
+            int64_t k = std::min<int64_t>(cap, ctx->L.nsys);
+            if (k > 0) {
+                cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+                NB_CUDA(ctx, cudaMemcpy2DAsync(dst, 16, ctx->sys_box.p, sizeof(SysBox), 16, (size_t)k,
+                                               kind, ctx->stream));
+                NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            }
+            return NBODY_OK;
+        }
+        default: return fail(ctx, NBODY_EINVAL, "unknown export");
+    }
+    *count = len;
+    int64_t k = std::min(cap, len);
+    if (k > 0) {
+        cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        NB_CUDA(ctx, cudaMemcpyAsync(dst, src, (size_t)k * esz, kind, ctx->stream));
+        NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return NBODY_OK;
+}
+
+nbody_status nbody_last_error(const nbody_ctx *ctx, char *buf, size_t len) {
+    if (!buf || len == 0) return NBODY_EINVAL;
+    const std::string &m = ctx ? ctx->err : g_last_error;
+    size_t k = std::min(len - 1, m.size());
+    std::memcpy(buf, m.data(), k);
+    buf[k] = '\0';
+    return NBODY_OK;
+}
+
+}  // extern "C"

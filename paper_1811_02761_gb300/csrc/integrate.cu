@@ -1,0 +1,188 @@
+// integrate.cu -- leapfrog kick-drift-kick on the sorted particle state, state
+// permutation after each re-sort, and FP64 energy/momentum diagnostics.
+//
+// The paper's code integrates with a second-order Runge-Kutta predictor /
+// corrector under block time steps (Sect. 1, Table 2 "predict"/"correct");
+// this library uses the (also second-order) leapfrog with a shared step.
+// Positions are FP64 so that x += v dt keeps its low bits at large N;
+// velocities and accelerations are FP32.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace nb {
+
+static inline int grid_for(int64_t n, int threads = 256) {
+    int64_t b = (n + threads - 1) / threads;
+    return (int)(b > 65535 * 8 ? 65535 * 8 : (b < 1 ? 1 : b));
+}
+
+#define NB_GRID_LOOP(i, n) \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void kick_drift_kernel(int64_t n, StepState st, const float4 *__restrict__ acc,
+                                  float hdt, double dt) {
+    NB_GRID_LOOP(i, n) {
+        float4 a = acc[i];
+        float vx = fmaf(a.x, hdt, st.vx[i]);
+        float vy = fmaf(a.y, hdt, st.vy[i]);
+        float vz = fmaf(a.z, hdt, st.vz[i]);
+        st.vx[i] = vx;
+        st.vy[i] = vy;
+        st.vz[i] = vz;
+        st.x[i] += (double)vx * dt;
+        st.y[i] += (double)vy * dt;
+        st.z[i] += (double)vz * dt;
+    }
+}
+
+__global__ void kick_kernel(int64_t n, StepState st, const float4 *__restrict__ acc, float hdt) {
+    NB_GRID_LOOP(i, n) {
+        float4 a = acc[i];
+        st.vx[i] = fmaf(a.x, hdt, st.vx[i]);
+        st.vy[i] = fmaf(a.y, hdt, st.vy[i]);
+        st.vz[i] = fmaf(a.z, hdt, st.vz[i]);
+        st.aold[i] = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+    }
+}
+
+void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
+                       float dt) {
+    kick_drift_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, hdt, (double)dt);
+}
+
+void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt) {
+    kick_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, hdt);
+}
+
+// Gather the state into the new Morton order and refresh the FP32 walk copy.
+__global__ void permute_state_kernel(int64_t n, const uint32_t *__restrict__ perm, StepState src,
+                                     StepState dst, float4 *__restrict__ pos4) {
+    NB_GRID_LOOP(i, n) {
+        uint32_t j = perm[i];
+        double px = src.x[j], py = src.y[j], pz = src.z[j];
+        float mj = src.m[j];
+        dst.x[i] = px;
+        dst.y[i] = py;
+        dst.z[i] = pz;
+        pos4[i] = make_float4((float)px, (float)py, (float)pz, mj);
+        dst.vx[i] = src.vx[j];
+        dst.vy[i] = src.vy[j];
+        dst.vz[i] = src.vz[j];
+        dst.m[i] = mj;
+        dst.aold[i] = src.aold[j];
+        dst.id[i] = src.id[j];
+    }
+}
+
+void launch_permute_state(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
+                          StepState dst, float4 *pos4) {
+    permute_state_kernel<<<grid_for(n), 256, 0, s>>>(n, perm, src, dst, pos4);
+}
+
+__global__ void load_state_kernel(int64_t n, const double *x, const double *y, const double *z,
+                                  const float *vx, const float *vy, const float *vz,
+                                  const float *m, const float *ax, const float *ay,
+                                  const float *az, StepState st, float4 *acc) {
+    NB_GRID_LOOP(i, n) {
+        st.x[i] = x[i];
+        st.y[i] = y[i];
+        st.z[i] = z[i];
+        st.vx[i] = vx[i];
+        st.vy[i] = vy[i];
+        st.vz[i] = vz[i];
+        st.m[i] = m[i];
+        float a0 = ax[i], a1 = ay[i], a2 = az[i];
+        acc[i] = make_float4(a0, a1, a2, 0.0f);
+        st.aold[i] = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+        st.id[i] = (uint32_t)i;
+    }
+}
+
+void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double *y,
+                       const double *z, const float *vx, const float *vy, const float *vz,
+                       const float *m, const float *ax, const float *ay, const float *az,
+                       StepState st, float4 *acc) {
+    load_state_kernel<<<grid_for(n), 256, 0, s>>>(n, x, y, z, vx, vy, vz, m, ax, ay, az, st, acc);
+}
+
+__global__ void store_state_kernel(int64_t n, StepState st, const float4 *__restrict__ acc,
+                                   double *x, double *y, double *z, float *vx, float *vy,
+                                   float *vz, float *ax, float *ay, float *az) {
+    NB_GRID_LOOP(i, n) {
+        uint32_t o = st.id[i];
+        x[o] = st.x[i];
+        y[o] = st.y[i];
+        z[o] = st.z[i];
+        vx[o] = st.vx[i];
+        vy[o] = st.vy[i];
+        vz[o] = st.vz[i];
+        float4 a = acc[i];
+        ax[o] = a.x;
+        ay[o] = a.y;
+        az[o] = a.z;
+    }
+}
+
+void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
+                        double *y, double *z, float *vx, float *vy, float *vz, float *ax,
+                        float *ay, float *az) {
+    store_state_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, x, y, z, vx, vy, vz, ax, ay, az);
+}
+
+// ---------------------------------------------------------------- diagnostics
+constexpr int DG_T = 256;
+constexpr int DG_BLOCKS = 1024;
+
+// Per block: FP64 partial sums of {E_kin, E_pot, P, L}; then one block adds
+// the partials in a fixed order, so the result is deterministic.
+__global__ void __launch_bounds__(DG_T) diag_partial_kernel(int64_t n, const double *x,
+                                                            const double *y, const double *z,
+                                                            const float *vx, const float *vy,
+                                                            const float *vz, const float *m,
+                                                            const float *phi, double *part) {
+    __shared__ double sh[8][DG_T];
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    NB_GRID_LOOP(i, n) {
+        double mi = m[i], u = vx[i], v = vy[i], w = vz[i];
+        double px = x[i], py = y[i], pz = z[i];
+        s[0] += 0.5 * mi * (u * u + v * v + w * w);
+        if (phi) s[1] += 0.5 * mi * (double)phi[i];
+        s[2] += mi * u;
+        s[3] += mi * v;
+        s[4] += mi * w;
+        s[5] += mi * (py * w - pz * v);
+        s[6] += mi * (pz * u - px * w);
+        s[7] += mi * (px * v - py * u);
+    }
+    for (int k = 0; k < 8; k++) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int h = DG_T / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int k = 0; k < 8; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) part[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void diag_final_kernel(int nb, const double *part, double *out) {
+    if (threadIdx.x < 8) {
+        double t = 0;
+        for (int b = 0; b < nb; b++) t += part[b * 8 + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+}
+
+size_t diag_temp_bytes() { return (size_t)DG_BLOCKS * 8 * sizeof(double); }
+
+void launch_diagnostics(cudaStream_t s, int64_t n, const double *x, const double *y,
+                        const double *z, const float *vx, const float *vy, const float *vz,
+                        const float *m, const float *phi, void *temp, double *d_out) {
+    int nb = grid_for(n, DG_T);
+    if (nb > DG_BLOCKS) nb = DG_BLOCKS;
+    double *part = (double *)temp;
+    diag_partial_kernel<<<nb, DG_T, 0, s>>>(n, x, y, z, vx, vy, vz, m, phi, part);
+    diag_final_kernel<<<1, 32, 0, s>>>(nb, part, d_out);
+}
+
+}  // namespace nb

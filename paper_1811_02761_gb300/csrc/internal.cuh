@@ -1,0 +1,214 @@
+// internal.cuh -- shared declarations of libnbody (not part of the public ABI).
+//
+// Data layout in device memory (sorted = Morton order of the last build):
+//   particles  pos4[n]   float4 (x, y, z, m), sorted
+//              perm[n]   int32, sorted index -> caller index
+//              keys[n]   uint64 Morton keys (system id above the Morton bits)
+//   boundaries delta[n+1] int8: deepest shared level of particles i-1 and i
+//              (-1 at 0, n and where the system changes); leaflev[n] int8
+//   nodes      level-major order (all level-0 nodes, then level 1, ...);
+//              the children of a node are contiguous.
+//              nodeA[k] float4 (com.x, com.y, com.z, M)          -- walk data
+//              nodeB[k] float4 (b_J, G M b_J^2, link, meta)      -- walk data
+//                link = first child (internal) or first particle (leaf)
+//                meta = (nchild << 1) | 0 (internal), (count << 1) | 1 (leaf)
+//              mom64[k] Mom64 (com.x, com.y, com.z, M)        -- FP64 moments
+//   groups     Morton order: first, count, sphere (centre, radius), alpha =
+//              delta_acc * min |a_old|, system id, cost log
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "nbody.h"
+
+#define NB_FULL 0xffffffffu
+
+namespace nb {
+
+constexpr int kMaxLevels = 21;              // 21 bits per axis -> 63-bit keys
+constexpr int kMaxNL = kMaxLevels + 1;      // levels 0..21
+constexpr int kStatusStackOverflow = 1;
+constexpr int kStatusBadTree = 2;  // an index failed a bounds check (skipped)
+
+// Device-resident counters and small per-build values.
+struct DevState {
+    int32_t nnodes;
+    int32_t ngroups;
+    int32_t queue_head;
+    int32_t status;
+    int32_t max_stack;
+    int32_t pad0;
+    unsigned long long list_entries;
+    unsigned long long interactions;
+    int32_t lvl_off[kMaxNL + 1];
+};
+
+// FP64 monopole of a node: centre of mass and mass.
+struct __align__(32) Mom64 {
+    double x, y, z, w;
+};
+__host__ __device__ __forceinline__ Mom64 make_Mom64(double x, double y, double z, double w) {
+    Mom64 r;
+    r.x = x; r.y = y; r.z = z; r.w = w;
+    return r;
+}
+// L2-coherent load (bypasses L1), for data another thread just published.
+__device__ __forceinline__ Mom64 ldcg_mom(const Mom64 *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = __ldcg(q), b = __ldcg(q + 1);
+    return make_Mom64(a.x, a.y, b.x, b.y);
+}
+
+// Geometry of one system: cube corner, side and the FP32 quantisation scale.
+struct SysBox {
+    float x0, y0, z0, L;
+    float scale;  // 2^levels / L (FP32, correctly rounded)
+    float pad[3];
+};
+
+// Problem layout shared by the build kernels.
+struct Layout {
+    int64_t n;
+    int32_t nsys;
+    int32_t sysbits;
+    int32_t levels;   // Morton levels below the root (21 for one system)
+    int32_t keybits;  // sysbits + 3 * levels
+};
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(NB_FULL, v, o);
+        if ((int)lane_id() >= o) v += t;
+    }
+    return v;
+}
+
+// Order-preserving map of a float onto uint32 (for atomic min/max).
+__device__ __forceinline__ uint32_t f2ord(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// System of sorted/caller particle i from the CSR offsets (nsys small).
+__device__ __forceinline__ int sys_of(const int64_t *off, int nsys, int64_t i) {
+    if (nsys <= 1) return 0;
+    int lo = 0, hi = nsys;  // invariant: off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- launchers
+// sort.cu
+void launch_bbox(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
+                 bool dbl, const int64_t *d_off, uint32_t *d_boxord, SysBox *d_box, int nsm);
+void launch_keys(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
+                 bool dbl, const int64_t *d_off, const SysBox *d_box, uint64_t *keys,
+                 uint32_t *vals);
+size_t radix_temp_bytes(int64_t n);
+// Sorts (keys, vals) by the low `bits` bits of keys, stably (ties keep their
+// input order).  Returns 1 if the result ended in the alt buffers, else 0.
+int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+               uint32_t *vals_alt, int64_t n, int bits, void *temp);
+// Single-block exclusive scan of sums[0..nb) in place (total to *total_out).
+void launch_scan_sums(cudaStream_t s, uint32_t *sums, int nb, int32_t *total_out);
+void launch_gather_pos4(cudaStream_t s, int64_t n, const uint32_t *perm, const void *x,
+                        const void *y, const void *z, bool dbl, const float *m, float4 *pos4);
+
+// tree.cu
+size_t tree_temp_bytes(int64_t n, int levels);
+void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const float4 *pos4,
+                const SysBox *d_box, const int64_t *d_off, int leaf_cap, float G,
+                int64_t cap_nodes, int8_t *delta, int8_t *leaflev, void *temp, DevState *ds,
+                int32_t *node_start, int8_t *node_level, int32_t *node_parent,
+                int32_t *node_link, int32_t *node_count, int32_t *node_nchild,
+                int32_t *node_arrive, float4 *nodeA, float4 *nodeB, Mom64 *mom64,
+                int32_t *sys_root, int nsm);
+void build_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
+                  const int64_t *d_off, const int32_t *node_start, const int32_t *node_parent,
+                  const int32_t *node_count, const int32_t *node_nchild, const int8_t *node_level,
+                  DevState *ds, uint8_t *gflag, void *temp, int32_t *grp_first,
+                  int32_t *grp_count, float4 *grp_sphere, int32_t *grp_sys, int nsm);
+void launch_group_alpha(cudaStream_t s, int64_t n, const DevState *ds, const int32_t *grp_first,
+                        const int32_t *grp_count, const float *aold_sorted, float delta_acc,
+                        float *grp_alpha, int nsm);
+
+// walk.cu
+struct WalkArgs {
+    const float4 *pos4;
+    const float4 *nodeA;
+    const float4 *nodeB;
+    const int32_t *grp_first;
+    const int32_t *grp_count;
+    const float4 *grp_sphere;
+    const float *grp_alpha;
+    const int32_t *grp_sys;
+    const int32_t *order;      // schedule permutation (NULL: Morton order)
+    const float *sys_eps2;
+    const int32_t *sys_root;
+    DevState *ds;
+    int32_t *grp_cost;         // list entries per group (NULL: not logged)
+    int64_t n;                 // particles (bounds of pos4)
+    float G;
+    float theta;
+    int list_depth;
+    int stack_depth;
+    // outputs: scatter mode (perm != NULL) or sorted mode
+    const int32_t *perm;
+    float *ax, *ay, *az, *phi;
+    float4 *acc_sorted;        // (ax, ay, az, phi)
+};
+struct WalkShape {
+    int ipl;
+    bool geometric;
+    bool potential;
+    bool compensated;
+    bool safe;                  // some eps == 0: guard the self term
+    int warps_per_block;
+};
+cudaError_t launch_walk(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm);
+cudaError_t launch_direct(cudaStream_t s, int64_t n, const float *x, const float *y,
+                          const float *z, const float *m, float G, float eps, bool compensated,
+                          float *ax, float *ay, float *az, float *phi);
+void launch_acc_mag(cudaStream_t s, int64_t n, const float4 *acc_sorted, float *aold_sorted);
+void launch_gather_f32(cudaStream_t s, int64_t n, const uint32_t *perm, const float *src,
+                       float *dst);
+
+// integrate.cu
+struct StepState {
+    double *x, *y, *z;
+    float *vx, *vy, *vz, *m;
+    float *aold;
+    uint32_t *id;    // caller index of each sorted particle
+};
+void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
+                       float dt);
+void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt);
+void launch_permute_state(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
+                          StepState dst, float4 *pos4);
+void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double *y,
+                       const double *z, const float *vx, const float *vy, const float *vz,
+                       const float *m, const float *ax, const float *ay, const float *az,
+                       StepState st, float4 *acc);
+void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
+                        double *y, double *z, float *vx, float *vy, float *vz, float *ax,
+                        float *ay, float *az);
+size_t diag_temp_bytes();
+void launch_diagnostics(cudaStream_t s, int64_t n, const double *x, const double *y,
+                        const double *z, const float *vx, const float *vy, const float *vz,
+                        const float *m, const float *phi, void *temp, double *d_out);
+
+}  // namespace nb

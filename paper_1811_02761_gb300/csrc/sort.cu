@@ -1,0 +1,437 @@
+// sort.cu -- bounding cube, Morton keys and the LSD radix sort of the tree
+// build ("makeTree", Sect. 2.2; its time is dominated by the radix sort of
+// the space-filling-curve keys, Sect. 4.1).
+//
+// All passes are HBM-bound.  The radix sort is reduce-then-scan: per pass a
+// tile histogram, a device-wide exclusive scan of the digit-major counts, and
+// a stable scatter that ranks keys inside a tile with warp match/popc and
+// stages the tile in shared memory so global writes are runs of one digit.
+// There is no inter-CTA waiting anywhere.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace nb {
+
+// ---------------------------------------------------------------- bounding cube
+template <typename T>
+__global__ void bbox_kernel(int64_t n, const T *__restrict__ x, const T *__restrict__ y,
+                            const T *__restrict__ z, const int64_t *__restrict__ off, int nsys,
+                            uint32_t *boxord) {
+    const unsigned lane = lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const T *p[3] = {x, y, z};
+    for (int64_t base = warp * 256; base < n; base += nwarps * 256) {
+        int64_t last = (base + 256 < n ? base + 256 : n) - 1;
+        int s0 = sys_of(off, nsys, base), s1 = sys_of(off, nsys, last);
+        if (s0 == s1) {
+            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                int64_t i = base + k * 32 + lane;
+                if (i < n) {
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        float v = (float)p[a][i];
+                        lo[a] = fminf(lo[a], v);
+                        hi[a] = fmaxf(hi[a], v);
+                    }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    lo[a] = fminf(lo[a], __shfl_xor_sync(NB_FULL, lo[a], o));
+                    hi[a] = fmaxf(hi[a], __shfl_xor_sync(NB_FULL, hi[a], o));
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    atomicMin(&boxord[s0 * 6 + a], f2ord(lo[a]));
+                    atomicMax(&boxord[s0 * 6 + 3 + a], f2ord(hi[a]));
+                }
+            }
+        } else {
+            for (int k = 0; k < 8; k++) {
+                int64_t i = base + k * 32 + lane;
+                if (i < n) {
+                    int s = sys_of(off, nsys, i);
+                    for (int a = 0; a < 3; a++) {
+                        uint32_t v = f2ord((float)p[a][i]);
+                        atomicMin(&boxord[s * 6 + a], v);
+                        atomicMax(&boxord[s * 6 + 3 + a], v);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void bbox_init_kernel(int nsys, uint32_t *boxord) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsys * 6; i += gridDim.x * blockDim.x)
+        boxord[i] = (i % 6) < 3 ? 0xffffffffu : 0u;
+}
+
+// Cube of each system, in FP32 with the stated operation order:
+// corner = per-axis minimum; L = (max extent) * (1 + 2^-20); L = 1 if 0;
+// scale = 2^levels / L.
+__global__ void bbox_finalize_kernel(int nsys, int levels, const uint32_t *boxord, SysBox *box) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+        SysBox b;
+        if (boxord[s * 6] == 0xffffffffu) {  // empty system
+            b.x0 = b.y0 = b.z0 = 0.0f;
+            b.L = 1.0f;
+        } else {
+            float lo[3], hi[3];
+            for (int a = 0; a < 3; a++) {
+                lo[a] = ord2f(boxord[s * 6 + a]);
+                hi[a] = ord2f(boxord[s * 6 + 3 + a]);
+            }
+            float ext = __fsub_rn(hi[0], lo[0]);
+            float ey = __fsub_rn(hi[1], lo[1]), ez = __fsub_rn(hi[2], lo[2]);
+            if (ey > ext) ext = ey;
+            if (ez > ext) ext = ez;
+            float L = __fmul_rn(ext, 1.0f + 0x1p-20f);
+            b.x0 = lo[0];
+            b.y0 = lo[1];
+            b.z0 = lo[2];
+            b.L = (L > 0.0f) ? L : 1.0f;
+        }
+        b.scale = __fdiv_rn((float)(1u << levels), b.L);
+        b.pad[0] = b.pad[1] = b.pad[2] = 0.0f;
+        box[s] = b;
+    }
+}
+
+void launch_bbox(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
+                 bool dbl, const int64_t *d_off, uint32_t *d_boxord, SysBox *d_box, int nsm) {
+    bbox_init_kernel<<<(L.nsys * 6 + 255) / 256, 256, 0, s>>>(L.nsys, d_boxord);
+    int64_t warps = (L.n + 255) / 256;
+    int blocks = (int)((warps + 7) / 8);
+    int maxb = nsm * 8;
+    if (blocks > maxb) blocks = maxb;
+    if (blocks < 1) blocks = 1;
+    if (dbl)
+        bbox_kernel<double><<<blocks, 256, 0, s>>>(L.n, (const double *)x, (const double *)y,
+                                                   (const double *)z, d_off, L.nsys, d_boxord);
+    else
+        bbox_kernel<float><<<blocks, 256, 0, s>>>(L.n, (const float *)x, (const float *)y,
+                                                  (const float *)z, d_off, L.nsys, d_boxord);
+    bbox_finalize_kernel<<<(L.nsys + 127) / 128, 128, 0, s>>>(L.nsys, L.levels, d_boxord, d_box);
+}
+
+// ---------------------------------------------------------------- Morton keys
+// Spread the low 21 bits of v so that bit k lands on bit 3k.
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Cell index along one axis: floor((v - v0) * scale) in FP32, clamped.
+__device__ __forceinline__ uint32_t quantise(float v, float v0, float scale, uint32_t top) {
+    float d = __fsub_rn(v, v0);
+    float t = __fmul_rn(d, scale);
+    float f = floorf(t);
+    uint32_t c = (f <= 0.0f) ? 0u : (uint32_t)f;
+    return c > top ? top : c;
+}
+
+template <typename T>
+__global__ void keys_kernel(Layout L, const T *__restrict__ x, const T *__restrict__ y,
+                            const T *__restrict__ z, const int64_t *__restrict__ off,
+                            const SysBox *__restrict__ box, uint64_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals) {
+    const uint32_t top = (1u << L.levels) - 1u;
+    const int mbits = 3 * L.levels;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int s = sys_of(off, L.nsys, i);
+        SysBox b = box[s];
+        uint32_t qx = quantise((float)x[i], b.x0, b.scale, top);
+        uint32_t qy = quantise((float)y[i], b.y0, b.scale, top);
+        uint32_t qz = quantise((float)z[i], b.z0, b.scale, top);
+        uint64_t k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+        if (L.sysbits) k |= (uint64_t)s << mbits;
+        keys[i] = k;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+void launch_keys(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
+                 bool dbl, const int64_t *d_off, const SysBox *d_box, uint64_t *keys,
+                 uint32_t *vals) {
+    int blocks = (int)((L.n + 255) / 256);
+    if (blocks > 65535 * 8) blocks = 65535 * 8;
+    if (dbl)
+        keys_kernel<double><<<blocks, 256, 0, s>>>(L, (const double *)x, (const double *)y,
+                                                   (const double *)z, d_off, d_box, keys, vals);
+    else
+        keys_kernel<float><<<blocks, 256, 0, s>>>(L, (const float *)x, (const float *)y,
+                                                  (const float *)z, d_off, d_box, keys, vals);
+}
+
+// ---------------------------------------------------------------- radix sort
+constexpr int RS_BITS = 9;
+constexpr int RS_BINS = 1 << RS_BITS;
+constexpr int RS_THREADS = 512;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_IPT = 8;
+constexpr int RS_TILE = RS_THREADS * RS_IPT;
+constexpr int SCAN_T = 1024;
+constexpr int SCAN_IPT = 4;
+constexpr int SCAN_CH = SCAN_T * SCAN_IPT;
+
+// Exclusive scan of one value per thread over a block of NT threads.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh /* NT/32 */,
+                                                    uint32_t *total) {
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    uint32_t incl = (uint32_t)warp_incl_scan((int)v);
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < NT / 32 ? sh[lane] : 0u;
+        t = (uint32_t)warp_incl_scan((int)t);
+        if (lane < NT / 32) sh[lane] = t;
+    }
+    __syncthreads();
+    uint32_t r = incl - v + (w ? sh[w - 1] : 0u);
+    if (total) *total = sh[NT / 32 - 1];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const uint64_t *__restrict__ keys,
+                                                             int64_t n, int shift,
+                                                             uint32_t *__restrict__ counts,
+                                                             int ntiles) {
+    __shared__ uint32_t h[RS_BINS];
+    for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) h[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int k = 0; k < RS_IPT; k++) {
+        int64_t i = base + k * RS_THREADS + threadIdx.x;
+        bool ok = i < n;
+        unsigned act = __ballot_sync(NB_FULL, ok);
+        if (ok) {
+            uint32_t d = (uint32_t)(keys[i] >> shift) & (RS_BINS - 1);
+            unsigned peers = __match_any_sync(act, d);
+            if (lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS)
+        counts[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+// In-place exclusive scan of a[0..len) in chunks of SCAN_CH; chunk totals go
+// to sums[] (scanned later by scan_sums_kernel).
+__global__ void __launch_bounds__(SCAN_T) scan_chunks_kernel(uint32_t *a, int64_t len,
+                                                             uint32_t *sums) {
+    __shared__ uint32_t sh[SCAN_T / 32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_CH + threadIdx.x * SCAN_IPT;
+    uint32_t v[SCAN_IPT], t = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; k++) {
+        v[k] = (base + k < len) ? a[base + k] : 0u;
+        t += v[k];
+    }
+    uint32_t total;
+    uint32_t ex = block_excl_scan<SCAN_T>(t, sh, &total);
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; k++) {
+        if (base + k < len) a[base + k] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// Single-block exclusive scan of sums[0..nb) in place; the grand total goes
+// to *total_out when given.
+__global__ void __launch_bounds__(SCAN_T) scan_sums_kernel(uint32_t *sums, int nb,
+                                                           int32_t *total_out) {
+    __shared__ uint32_t sh[SCAN_T / 32];
+    uint32_t carry = 0;
+    for (int base = 0; base < nb; base += SCAN_T) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < nb ? sums[i] : 0u;
+        uint32_t total;
+        uint32_t ex = block_excl_scan<SCAN_T>(v, sh, &total);
+        if (i < nb) sums[i] = carry + ex;
+        carry += total;
+    }
+    if (total_out && threadIdx.x == 0) *total_out = (int32_t)carry;
+}
+
+void launch_scan_sums(cudaStream_t s, uint32_t *sums, int nb, int32_t *total_out) {
+    scan_sums_kernel<<<1, SCAN_T, 0, s>>>(sums, nb, total_out);
+}
+
+struct RsShared {
+    uint32_t whist[RS_WARPS][RS_BINS];
+    uint32_t tdoff[RS_BINS];
+    uint32_t goff[RS_BINS];
+    uint32_t wsum[RS_THREADS / 32];
+    uint64_t sk[RS_TILE];
+    uint32_t sv[RS_TILE];
+};
+
+template <bool FIRST>
+__global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(
+    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ counts,
+    const uint32_t *__restrict__ sums, int ntiles) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    RsShared &S = *reinterpret_cast<RsShared *>(rs_smem);
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    const int tile = blockIdx.x;
+    const int64_t base = (int64_t)tile * RS_TILE;
+    const int valid = (int)((n - base) < RS_TILE ? (n - base) : RS_TILE);
+
+    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS)
+        (&S.whist[0][0])[i] = 0;
+    __syncthreads();
+
+    uint64_t key[RS_IPT];
+    uint32_t val[RS_IPT], dg[RS_IPT], rk[RS_IPT];
+    // warp-striped: warp w owns the contiguous run [w*32*IPT, (w+1)*32*IPT)
+#pragma unroll
+    for (int k = 0; k < RS_IPT; k++) {
+        int64_t i = base + (int64_t)w * 32 * RS_IPT + k * 32 + lane;
+        if (i < n) {
+            key[k] = kin[i];
+            val[k] = FIRST ? (uint32_t)i : vin[i];
+        } else {
+            key[k] = ~0ull;
+            val[k] = 0;
+        }
+        dg[k] = (uint32_t)(key[k] >> shift) & (RS_BINS - 1);
+    }
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < RS_IPT; k++) {
+        unsigned peers = __match_any_sync(NB_FULL, dg[k]);
+        uint32_t b = S.whist[w][dg[k]];
+        __syncwarp();
+        if ((peers & lt) == 0) S.whist[w][dg[k]] = b + (uint32_t)__popc(peers);
+        __syncwarp();
+        rk[k] = b + (uint32_t)__popc(peers & lt);
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, then over digits
+    for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int q = 0; q < RS_WARPS; q++) {
+            uint32_t c = S.whist[q][d];
+            S.whist[q][d] = run;
+            run += c;
+        }
+        S.tdoff[d] = run;
+    }
+    __syncthreads();
+    static_assert(RS_BINS == RS_THREADS, "one digit per thread");
+    {
+        uint32_t tot = S.tdoff[threadIdx.x];
+        uint32_t ex = block_excl_scan<RS_THREADS>(tot, S.wsum, nullptr);
+        S.tdoff[threadIdx.x] = ex;
+        int64_t ci = (int64_t)threadIdx.x * ntiles + tile;
+        S.goff[threadIdx.x] = counts[ci] + sums[ci / SCAN_CH] - ex;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RS_IPT; k++) {
+        uint32_t pos = S.tdoff[dg[k]] + S.whist[w][dg[k]] + rk[k];
+        S.sk[pos] = key[k];
+        S.sv[pos] = val[k];
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < valid; p += RS_THREADS) {
+        uint64_t kk = S.sk[p];
+        uint32_t d = (uint32_t)(kk >> shift) & (RS_BINS - 1);
+        uint32_t dst = S.goff[d] + (uint32_t)p;
+        kout[dst] = kk;
+        vout[dst] = S.sv[p];
+    }
+}
+
+size_t radix_temp_bytes(int64_t n) {
+    int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    int64_t len = ntiles * RS_BINS;
+    int64_t nch = (len + SCAN_CH - 1) / SCAN_CH;
+    return (size_t)(len + nch + 64) * sizeof(uint32_t);
+}
+
+int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+               uint32_t *vals_alt, int64_t n, int bits, void *temp) {
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(rs_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(RsShared));
+        cudaFuncSetAttribute(rs_scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(RsShared));
+        attr_done = true;
+    }
+    int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    int64_t len = (int64_t)ntiles * RS_BINS;
+    int nch = (int)((len + SCAN_CH - 1) / SCAN_CH);
+    uint32_t *counts = (uint32_t *)temp;
+    uint32_t *sums = counts + len;
+    int passes = (bits + RS_BITS - 1) / RS_BITS;
+    uint64_t *kin = keys, *kout = keys_alt;
+    uint32_t *vin = vals, *vout = vals_alt;
+    for (int p = 0; p < passes; p++) {
+        int shift = p * RS_BITS;
+        rs_hist_kernel<<<ntiles, RS_THREADS, 0, s>>>(kin, n, shift, counts, ntiles);
+        scan_chunks_kernel<<<nch, SCAN_T, 0, s>>>(counts, len, sums);
+        scan_sums_kernel<<<1, SCAN_T, 0, s>>>(sums, nch, nullptr);
+        if (p == 0)
+            rs_scatter_kernel<true><<<ntiles, RS_THREADS, sizeof(RsShared), s>>>(
+                kin, vin, kout, vout, n, shift, counts, sums, ntiles);
+        else
+            rs_scatter_kernel<false><<<ntiles, RS_THREADS, sizeof(RsShared), s>>>(
+                kin, vin, kout, vout, n, shift, counts, sums, ntiles);
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        uint32_t *tv = vin; vin = vout; vout = tv;
+    }
+    return kin != keys;  // 1: the sorted result is in the alt buffers
+}
+
+// ---------------------------------------------------------------- gather
+template <typename T>
+__global__ void gather_pos4_kernel(int64_t n, const uint32_t *__restrict__ perm,
+                                   const T *__restrict__ x, const T *__restrict__ y,
+                                   const T *__restrict__ z, const float *__restrict__ m,
+                                   float4 *__restrict__ pos4) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t j = perm[i];
+        pos4[i] = make_float4((float)x[j], (float)y[j], (float)z[j], m[j]);
+    }
+}
+
+void launch_gather_pos4(cudaStream_t s, int64_t n, const uint32_t *perm, const void *x,
+                        const void *y, const void *z, bool dbl, const float *m, float4 *pos4) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 65535 * 8) blocks = 65535 * 8;
+    if (dbl)
+        gather_pos4_kernel<double><<<blocks, 256, 0, s>>>(n, perm, (const double *)x,
+                                                          (const double *)y, (const double *)z,
+                                                          m, pos4);
+    else
+        gather_pos4_kernel<float><<<blocks, 256, 0, s>>>(n, perm, (const float *)x,
+                                                         (const float *)y, (const float *)z, m,
+                                                         pos4);
+}
+
+}  // namespace nb

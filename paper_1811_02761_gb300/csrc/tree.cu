@@ -1,0 +1,556 @@
+// tree.cu -- octree from sorted Morton keys ("makeTree"), bottom-up monopoles
+// and node sizes ("calcNode", Sect. 2.2), and the i-groups that share one
+// interaction list in the walk (Sect. 1).
+//
+// Octree definition.  A node at level l is a maximal run of sorted particles
+// sharing the top 3l Morton bits (plus the system id).  A node is split into
+// its non-empty octants while it holds more than leaf_cap particles and
+// l < levels.  Writing delta_i for the deepest level shared by particles i-1
+// and i (-1 at 0, n and at system changes), and L_i for the level of the leaf
+// that holds particle i, the nodes that start at particle i are exactly the
+// levels delta_i < l <= L_i, and
+//     L_i = min(levels, 1 + min over boundary pairs (left <= i < right,
+//               right - left <= leaf_cap) of max(delta_left, delta_right)),
+// because a run bounded by two boundaries whose shared levels are both below
+// l+1 is cut at level l+1.  So the whole tree comes from per-particle work in
+// a window of 2*leaf_cap boundaries plus one scan per level -- no level-by-
+// level launches and no global synchronisation (the paper's calcNode needs
+// 21 grid-wide barriers per step, App. A).
+//
+// Monopoles are accumulated bottom-up in FP64 with "last child arrives"
+// atomic counters: the thread that finishes the last child of a node computes
+// the node.  Nothing spins.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace nb {
+
+constexpr int TB = 256;  // particles per block in the per-particle tree kernels
+
+__device__ __forceinline__ int delta_of(uint64_t a, uint64_t b, int mbits, int levels) {
+    uint64_t x = a ^ b;
+    if (x >> mbits) return -1;  // different systems
+    if (x == 0) return levels;
+    int h = 63 - __clzll((long long)x);
+    return (mbits - 1 - h) / 3;
+}
+
+__device__ __forceinline__ uint32_t level_mask(int d, int L) {
+    if (L <= d) return 0u;
+    uint32_t hi = (2u << L) - 1u;
+    uint32_t lo = d < 0 ? 0u : ((2u << d) - 1u);
+    return hi & ~lo;
+}
+
+// delta, leaf level and per-level node counts of each block of TB particles.
+constexpr int kMaxCap = 32;
+__global__ void __launch_bounds__(TB) leaflevel_kernel(Layout L, int cap,
+                                                       const uint64_t *__restrict__ keys,
+                                                       int8_t *__restrict__ delta,
+                                                       int8_t *__restrict__ leaflev,
+                                                       uint32_t *__restrict__ blockcnt, int nblk) {
+    __shared__ uint64_t sk[TB + 2 * kMaxCap + 1];
+    __shared__ int sd[TB + 2 * kMaxCap];
+    __shared__ uint32_t wc[kMaxNL][TB / 32];
+    const int64_t n = L.n;
+    const int64_t lo = (int64_t)blockIdx.x * TB - cap;  // global boundary index of sd[0]
+    for (int t = threadIdx.x; t < TB + 2 * cap + 1; t += TB) {
+        int64_t g = lo - 1 + t;
+        sk[t] = (g >= 0 && g < n) ? keys[g] : 0ull;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < TB + 2 * cap; t += TB) {
+        int64_t g = lo + t;
+        sd[t] = (g <= 0 || g >= n) ? -1 : delta_of(sk[t], sk[t + 1], 3 * L.levels, L.levels);
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    uint32_t mask = 0;
+    if (i < n) {
+        const int ti = threadIdx.x + cap;
+        int R = 127, best = 127;
+        // R = min delta over boundaries i+1..i+k; a run [i-cap+k, right) with
+        // right <= i-cap+k+cap is cut at level max(delta_left, R) + 1.
+        for (int k = 1; k <= cap; k++) {
+            if (i + k <= n) R = min(R, sd[ti + k]);
+            if (i - cap + k >= 0) best = min(best, max(sd[ti - cap + k], R));
+        }
+        int Li = min(L.levels, best + 1);
+        int di = sd[ti];
+        delta[i] = (int8_t)di;
+        leaflev[i] = (int8_t)Li;
+        if (i == n - 1) delta[n] = -1;
+        mask = level_mask(di, Li);
+    }
+    const int NL = L.levels + 1;
+    const unsigned w = threadIdx.x >> 5;
+    for (int l = 0; l < NL; l++) {
+        unsigned b = __ballot_sync(NB_FULL, (mask >> l) & 1u);
+        if (lane_id() == 0) wc[l][w] = (uint32_t)__popc(b);
+    }
+    __syncthreads();
+    if (threadIdx.x < NL) {
+        uint32_t t = 0;
+        for (int q = 0; q < TB / 32; q++) t += wc[threadIdx.x][q];
+        blockcnt[(int64_t)threadIdx.x * nblk + blockIdx.x] = t;
+    }
+}
+
+// One block: exclusive scan of each level's block counts; level offsets.
+__global__ void __launch_bounds__(1024) level_scan_kernel(int NL, uint32_t *blockcnt, int nblk,
+                                                          DevState *ds, int64_t cap_nodes) {
+    __shared__ uint32_t sh[32];
+    __shared__ int32_t off;
+    if (threadIdx.x == 0) {
+        off = 0;
+        ds->lvl_off[0] = 0;
+    }
+    __syncthreads();
+    for (int l = 0; l < NL; l++) {
+        uint32_t carry = 0;
+        uint32_t *row = blockcnt + (int64_t)l * nblk;
+        for (int base = 0; base < nblk; base += 1024) {
+            int i = base + threadIdx.x;
+            uint32_t v = i < nblk ? row[i] : 0u;
+            uint32_t incl = (uint32_t)warp_incl_scan((int)v);
+            if (lane_id() == 31) sh[threadIdx.x >> 5] = incl;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                uint32_t t = sh[threadIdx.x];
+                t = (uint32_t)warp_incl_scan((int)t);
+                sh[threadIdx.x] = t;
+            }
+            __syncthreads();
+            uint32_t ex = incl - v + ((threadIdx.x >> 5) ? sh[(threadIdx.x >> 5) - 1] : 0u);
+            if (i < nblk) row[i] = carry + ex;
+            carry += sh[31];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            off += (int32_t)carry;
+            ds->lvl_off[l + 1] = off;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ds->nnodes = off;
+        if (off > cap_nodes) atomicOr(&ds->status, kStatusStackOverflow);
+    }
+}
+
+// Writes every node: start, level, parent, first child / first particle and,
+// for leaves, the particle count.  Children bump their parent's child count.
+__global__ void __launch_bounds__(TB) nodes_kernel(Layout L, const int8_t *__restrict__ delta,
+                                                   const int8_t *__restrict__ leaflev,
+                                                   const uint32_t *__restrict__ blockcnt, int nblk,
+                                                   const DevState *__restrict__ ds,
+                                                   int64_t cap_nodes, int32_t *node_start,
+                                                   int8_t *node_level, int32_t *node_parent,
+                                                   int32_t *node_link, int32_t *node_count,
+                                                   int32_t *node_nchild, int32_t *node_arrive) {
+    __shared__ uint32_t wc[kMaxNL][TB / 32];
+    const int64_t n = L.n;
+    const int NL = L.levels + 1;
+    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    const unsigned w = threadIdx.x >> 5;
+    int di = -1, Li = -1;
+    uint32_t mask = 0;
+    if (i < n) {
+        di = delta[i];
+        Li = leaflev[i];
+        mask = level_mask(di, Li);
+    }
+    for (int l = 0; l < NL; l++) {
+        unsigned b = __ballot_sync(NB_FULL, (mask >> l) & 1u);
+        if (lane_id() == 0) wc[l][w] = (uint32_t)__popc(b);
+    }
+    __syncthreads();
+    if (threadIdx.x < NL) {
+        uint32_t run = 0;
+        for (int q = 0; q < TB / 32; q++) {
+            uint32_t c = wc[threadIdx.x][q];
+            wc[threadIdx.x][q] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned lt = lanemask_lt();
+    int prev_excl = 0, prev_bit = 0, prev_id = -1;
+    bool prev_internal = false;
+    for (int l = 0; l < NL; l++) {
+        int bit = (mask >> l) & 1u;
+        unsigned b = __ballot_sync(NB_FULL, bit);
+        int excl = ds->lvl_off[l] + (int)blockcnt[(int64_t)l * nblk + blockIdx.x] + (int)wc[l][w] +
+                   __popc(b & lt);
+        if (prev_internal) node_link[prev_id] = excl;  // first child starts at i too
+        if (bit && excl < cap_nodes) {
+            int id = excl;
+            node_start[id] = (int32_t)i;
+            node_level[id] = (int8_t)l;
+            node_arrive[id] = 0;
+            if (l > 0) {
+                int par = prev_excl + prev_bit - 1;
+                node_parent[id] = par;
+                atomicAdd(&node_nchild[par], 1);
+            } else {
+                node_parent[id] = -1;
+            }
+            if (l == Li) {  // leaf: particles until the next boundary above level l
+                int64_t j = i + 1;
+                while (j < n && delta[j] >= l) j++;
+                node_link[id] = (int32_t)i;
+                node_count[id] = (int32_t)(j - i);
+                prev_internal = false;
+            } else {
+                prev_internal = true;
+                prev_id = id;
+            }
+        } else {
+            prev_internal = false;
+        }
+        prev_excl = excl;
+        prev_bit = bit;
+    }
+}
+
+__global__ void sys_root_kernel(const DevState *ds, const int32_t *node_start, const int64_t *off,
+                                int nsys, int32_t *sys_root) {
+    int nroot = ds->lvl_off[1];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nroot; r += gridDim.x * blockDim.x)
+        sys_root[sys_of(off, nsys, node_start[r])] = r;
+}
+
+__global__ void sys_root_init_kernel(int nsys, int32_t *sys_root) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x)
+        sys_root[s] = -1;
+}
+
+// ---------------------------------------------------------------- moments
+__device__ __forceinline__ int &ds_status(DevState *ds) { return ds->status; }
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x001f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x001f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x00000000001fffffull;
+    return (uint32_t)x;
+}
+
+// Cell of a node, widened by one finest cell on every side (covers the FP32
+// quantisation of member positions).
+struct Cell {
+    double lo[3], hi[3];
+};
+
+__device__ __forceinline__ Cell node_cell(const Layout &L, uint64_t key, int level,
+                                          const SysBox *box) {
+    const int mbits = 3 * L.levels;
+    int s = L.sysbits ? (int)(key >> mbits) : 0;
+    SysBox b = box[s];
+    uint64_t morton = mbits >= 64 ? key : (key & ((1ull << mbits) - 1ull));
+    uint64_t prefix = morton >> (3 * (L.levels - level));
+    uint32_t c[3] = {compact3(prefix >> 2), compact3(prefix >> 1), compact3(prefix)};
+    double side = (double)b.L / (double)(1u << level);
+    double pad = (double)b.L / (double)(1u << L.levels);
+    double o[3] = {(double)b.x0, (double)b.y0, (double)b.z0};
+    Cell cell;
+    for (int a = 0; a < 3; a++) {
+        cell.lo[a] = o[a] + (double)c[a] * side - pad;
+        cell.hi[a] = o[a] + (double)(c[a] + 1) * side + pad;
+    }
+    return cell;
+}
+
+__device__ __forceinline__ void write_node(int id, double cx, double cy, double cz, double M,
+                                           double b, float G, int link, int meta, float4 *nodeA,
+                                           float4 *nodeB, Mom64 *mom64) {
+    float bf = __double2float_ru(b);
+    float q = __double2float_ru((double)G * M * (double)bf * (double)bf);
+    nodeA[id] = make_float4((float)cx, (float)cy, (float)cz, (float)M);
+    nodeB[id] = make_float4(bf, q, __int_as_float(link), __int_as_float(meta));
+    mom64[id] = make_Mom64(cx, cy, cz, M);
+}
+
+__global__ void __launch_bounds__(256) moments_kernel(
+    Layout L, const uint64_t *__restrict__ keys, const float4 *__restrict__ pos4,
+    const SysBox *__restrict__ box, float G, DevState *ds,
+    const int32_t *__restrict__ node_start, const int8_t *__restrict__ node_level,
+    const int32_t *__restrict__ node_parent, const int32_t *__restrict__ node_link,
+    int32_t *node_count, const int32_t *__restrict__ node_nchild, int32_t *node_arrive,
+    float4 *nodeA, float4 *nodeB, Mom64 *mom64) {
+    const int nn = ds->nnodes;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
+        if (node_nchild[id] != 0) continue;
+        // leaf: FP64 sums over its particles
+        const int first = node_link[id], cnt = node_count[id];
+        if (first < 0 || cnt < 1 || (int64_t)first + cnt > L.n) {
+            atomicOr(&ds_status(ds), kStatusBadTree);
+            continue;
+        }
+        double M = 0, sx = 0, sy = 0, sz = 0;
+        for (int k = first; k < first + cnt; k++) {
+            float4 p = pos4[k];
+            M += (double)p.w;
+            sx += (double)p.w * (double)p.x;
+            sy += (double)p.w * (double)p.y;
+            sz += (double)p.w * (double)p.z;
+        }
+        double c[3];
+        if (M > 0) {
+            c[0] = sx / M; c[1] = sy / M; c[2] = sz / M;
+        } else {
+            Cell cell = node_cell(L, keys[node_start[id]], node_level[id], box);
+            for (int a = 0; a < 3; a++) c[a] = 0.5 * (cell.lo[a] + cell.hi[a]);
+        }
+        double b2 = 0;
+        for (int k = first; k < first + cnt; k++) {
+            float4 p = pos4[k];
+            double dx = (double)p.x - c[0], dy = (double)p.y - c[1], dz = (double)p.z - c[2];
+            b2 = fmax(b2, dx * dx + dy * dy + dz * dz);
+        }
+        write_node(id, c[0], c[1], c[2], M, sqrt(b2), G, first, (cnt << 1) | 1, nodeA, nodeB,
+                   mom64);
+        // climb while this thread completes the last child of the parent
+        int nd = id;
+        for (;;) {
+            int par = node_parent[nd];
+            if (par < 0) break;
+            __threadfence();
+            int old = atomicAdd(&node_arrive[par], 1);
+            if (old != node_nchild[par] - 1) break;
+            __threadfence();
+            const int c0 = node_link[par], nc = node_nchild[par];
+            if (c0 <= par || c0 + nc > nn) {
+                atomicOr(&ds_status(ds), kStatusBadTree);
+                break;
+            }
+            double Mp = 0, px = 0, py = 0, pz = 0;
+            int count = 0;
+            for (int ch = c0; ch < c0 + nc; ch++) {
+                Mom64 mc = ldcg_mom(&mom64[ch]);
+                Mp += mc.w;
+                px += mc.w * mc.x;
+                py += mc.w * mc.y;
+                pz += mc.w * mc.z;
+                count += __ldcg(&node_count[ch]);
+            }
+            Cell cell = node_cell(L, keys[node_start[par]], node_level[par], box);
+            double cp[3];
+            if (Mp > 0) {
+                cp[0] = px / Mp; cp[1] = py / Mp; cp[2] = pz / Mp;
+            } else {
+                for (int a = 0; a < 3; a++) cp[a] = 0.5 * (cell.lo[a] + cell.hi[a]);
+            }
+            double rec = 0;
+            for (int ch = c0; ch < c0 + nc; ch++) {
+                Mom64 mc = ldcg_mom(&mom64[ch]);
+                float bc = __ldcg(&nodeB[ch].x);
+                double dx = mc.x - cp[0], dy = mc.y - cp[1], dz = mc.z - cp[2];
+                rec = fmax(rec, sqrt(dx * dx + dy * dy + dz * dz) + (double)bc);
+            }
+            double c2 = 0;
+            for (int a = 0; a < 3; a++) {
+                double e = fmax(cp[a] - cell.lo[a], cell.hi[a] - cp[a]);
+                c2 += e * e;
+            }
+            double bp = fmin(rec, sqrt(c2));
+            node_count[par] = count;
+            write_node(par, cp[0], cp[1], cp[2], Mp, bp, G, c0, nc << 1, nodeA, nodeB, mom64);
+            nd = par;
+        }
+    }
+}
+
+size_t tree_temp_bytes(int64_t n, int levels) {
+    int64_t nblk = (n + TB - 1) / TB;
+    return (size_t)(levels + 1) * (size_t)nblk * sizeof(uint32_t) + 256;
+}
+
+void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const float4 *pos4,
+                const SysBox *d_box, const int64_t *d_off, int leaf_cap, float G,
+                int64_t cap_nodes, int8_t *delta, int8_t *leaflev, void *temp, DevState *ds,
+                int32_t *node_start, int8_t *node_level, int32_t *node_parent,
+                int32_t *node_link, int32_t *node_count, int32_t *node_nchild,
+                int32_t *node_arrive, float4 *nodeA, float4 *nodeB, Mom64 *mom64,
+                int32_t *sys_root, int nsm) {
+    const int nblk = (int)((L.n + TB - 1) / TB);
+    uint32_t *blockcnt = (uint32_t *)temp;
+    leaflevel_kernel<<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
+    level_scan_kernel<<<1, 1024, 0, s>>>(L.levels + 1, blockcnt, nblk, ds, cap_nodes);
+    cudaMemsetAsync(node_nchild, 0, (size_t)cap_nodes * sizeof(int32_t), s);
+    nodes_kernel<<<nblk, TB, 0, s>>>(L, delta, leaflev, blockcnt, nblk, ds, cap_nodes, node_start,
+                                     node_level, node_parent, node_link, node_count, node_nchild,
+                                     node_arrive);
+    sys_root_init_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(L.nsys, sys_root);
+    sys_root_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(ds, node_start, d_off, L.nsys, sys_root);
+    int mb = (int)((L.n + 255) / 256);
+    if (mb > nsm * 16) mb = nsm * 16;
+    moments_kernel<<<mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start, node_level,
+                                      node_parent, node_link, node_count, node_nchild, node_arrive,
+                                      nodeA, nodeB, mom64);
+}
+
+// ---------------------------------------------------------------- groups
+constexpr int FL_T = 1024, FL_IPT = 4, FL_CH = FL_T * FL_IPT;
+
+// A group is the largest node holding at most G particles; a finest-level
+// leaf holding more is cut into chunks of G.  Mark each group's first particle.
+__global__ void group_mark_kernel(const DevState *__restrict__ ds, int G,
+                                  const int32_t *__restrict__ node_start,
+                                  const int32_t *__restrict__ node_parent,
+                                  const int32_t *__restrict__ node_count,
+                                  const int32_t *__restrict__ node_nchild, uint8_t *gflag) {
+    const int nn = ds->nnodes;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
+        int cnt = node_count[id], par = node_parent[id];
+        if (cnt <= G) {
+            if (par < 0 || node_count[par] > G) gflag[node_start[id]] = 1;
+        } else if (node_nchild[id] == 0) {
+            for (int k = 0; k < cnt; k += G) gflag[node_start[id] + k] = 1;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *sh) {
+    uint32_t incl = (uint32_t)warp_incl_scan((int)v);
+    if (lane_id() == 31) sh[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    if (threadIdx.x < 32) sh[threadIdx.x] = (uint32_t)warp_incl_scan((int)sh[threadIdx.x]);
+    __syncthreads();
+    uint32_t r = incl - v + ((threadIdx.x >> 5) ? sh[(threadIdx.x >> 5) - 1] : 0u);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(FL_T) flag_count_kernel(const uint8_t *__restrict__ f, int64_t n,
+                                                          uint32_t *bsum) {
+    __shared__ uint32_t sh[32];
+    int64_t base = (int64_t)blockIdx.x * FL_CH + threadIdx.x * FL_IPT;
+    uint32_t t = 0;
+    for (int k = 0; k < FL_IPT; k++)
+        if (base + k < n) t += f[base + k];
+    uint32_t incl = (uint32_t)warp_incl_scan((int)t);
+    if (lane_id() == 31) sh[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int q = 0; q < 32; q++) s += sh[q];
+        bsum[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(FL_T) flag_write_kernel(const uint8_t *__restrict__ f, int64_t n,
+                                                          const uint32_t *__restrict__ bsum,
+                                                          int32_t *__restrict__ out) {
+    __shared__ uint32_t sh[32];
+    int64_t base = (int64_t)blockIdx.x * FL_CH + threadIdx.x * FL_IPT;
+    uint32_t v[FL_IPT], t = 0;
+    for (int k = 0; k < FL_IPT; k++) {
+        v[k] = (base + k < n) ? f[base + k] : 0u;
+        t += v[k];
+    }
+    uint32_t ex = block_excl_scan_1024(t, sh) + bsum[blockIdx.x];
+    for (int k = 0; k < FL_IPT; k++) {
+        if (v[k]) out[ex] = (int32_t)(base + k);
+        ex += v[k];
+    }
+}
+
+// Warp per group: count, bounding-box centre and enclosing radius, system.
+__global__ void __launch_bounds__(256) group_info_kernel(Layout L, int G,
+                                                         const float4 *__restrict__ pos4,
+                                                         const int64_t *__restrict__ off,
+                                                         const DevState *__restrict__ ds,
+                                                         const int32_t *__restrict__ grp_first,
+                                                         int32_t *grp_count, float4 *grp_sphere,
+                                                         int32_t *grp_sys) {
+    const int ng = ds->ngroups;
+    const unsigned lane = lane_id();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int g = warp; g < ng; g += nw) {
+        int first = grp_first[g];
+        int end = (g + 1 < ng) ? grp_first[g + 1] : (int)L.n;
+        int cnt = end - first;
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int k = lane; k < cnt; k += 32) {
+            float4 p = pos4[first + k];
+            lo[0] = fminf(lo[0], p.x); hi[0] = fmaxf(hi[0], p.x);
+            lo[1] = fminf(lo[1], p.y); hi[1] = fmaxf(hi[1], p.y);
+            lo[2] = fminf(lo[2], p.z); hi[2] = fmaxf(hi[2], p.z);
+        }
+        for (int a = 0; a < 3; a++)
+            for (int o = 16; o; o >>= 1) {
+                lo[a] = fminf(lo[a], __shfl_xor_sync(NB_FULL, lo[a], o));
+                hi[a] = fmaxf(hi[a], __shfl_xor_sync(NB_FULL, hi[a], o));
+            }
+        float c[3];
+        for (int a = 0; a < 3; a++) c[a] = 0.5f * (lo[a] + hi[a]);
+        float r2 = 0.0f;
+        for (int k = lane; k < cnt; k += 32) {
+            float4 p = pos4[first + k];
+            float dx = p.x - c[0], dy = p.y - c[1], dz = p.z - c[2];
+            r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+        }
+        for (int o = 16; o; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(NB_FULL, r2, o));
+        if (lane == 0) {
+            // rounded up so the sphere encloses every member despite FP32 error
+            float r = __fsqrt_ru(r2) * (1.0f + 0x1p-20f);
+            grp_count[g] = cnt;
+            grp_sphere[g] = make_float4(c[0], c[1], c[2], r);
+            grp_sys[g] = sys_of(off, L.nsys, first);
+        }
+    }
+}
+
+void build_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
+                  const int64_t *d_off, const int32_t *node_start, const int32_t *node_parent,
+                  const int32_t *node_count, const int32_t *node_nchild, const int8_t *node_level,
+                  DevState *ds, uint8_t *gflag, void *temp, int32_t *grp_first,
+                  int32_t *grp_count, float4 *grp_sphere, int32_t *grp_sys, int nsm) {
+    (void)node_level;
+    cudaMemsetAsync(gflag, 0, (size_t)L.n, s);
+    int mb = (int)((L.n + 255) / 256);
+    if (mb > nsm * 16) mb = nsm * 16;
+    group_mark_kernel<<<mb, 256, 0, s>>>(ds, group_size, node_start, node_parent, node_count,
+                                         node_nchild, gflag);
+    int nb = (int)((L.n + FL_CH - 1) / FL_CH);
+    uint32_t *bsum = (uint32_t *)temp;
+    flag_count_kernel<<<nb, FL_T, 0, s>>>(gflag, L.n, bsum);
+    launch_scan_sums(s, bsum, nb, &ds->ngroups);
+    flag_write_kernel<<<nb, FL_T, 0, s>>>(gflag, L.n, bsum, grp_first);
+    int gb = nsm * 8;
+    group_info_kernel<<<gb, 256, 0, s>>>(L, group_size, pos4, d_off, ds, grp_first, grp_count,
+                                         grp_sphere, grp_sys);
+}
+
+// alpha_g = delta_acc * min over members of |a_old| (Eq. 2 per group).
+__global__ void group_alpha_kernel(const DevState *__restrict__ ds,
+                                   const int32_t *__restrict__ grp_first,
+                                   const int32_t *__restrict__ grp_count,
+                                   const float *__restrict__ aold, float dacc, float *grp_alpha) {
+    const int ng = ds->ngroups;
+    const unsigned lane = lane_id();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int g = warp; g < ng; g += nw) {
+        int first = grp_first[g], cnt = grp_count[g];
+        float m = INFINITY;
+        for (int k = lane; k < cnt; k += 32) m = fminf(m, aold[first + k]);
+        for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(NB_FULL, m, o));
+        if (lane == 0) grp_alpha[g] = dacc * m;
+    }
+}
+
+void launch_group_alpha(cudaStream_t s, int64_t n, const DevState *ds, const int32_t *grp_first,
+                        const int32_t *grp_count, const float *aold_sorted, float delta_acc,
+                        float *grp_alpha, int nsm) {
+    (void)n;
+    group_alpha_kernel<<<nsm * 8, 256, 0, s>>>(ds, grp_first, grp_count, aold_sorted, delta_acc,
+                                                grp_alpha);
+}
+
+}  // namespace nb

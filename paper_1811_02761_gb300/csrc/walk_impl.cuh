@@ -1,0 +1,301 @@
+// walk_impl.cuh -- the tree walk ("walkTree", the dominant kernel of the
+// paper, Sect. 3 and Table 2).
+//
+// Design (GB300 re-think of Sect. 1's shared interaction list):
+//   * persistent grid, one warp per i-group, groups popped from a device queue
+//     (one atomicAdd per group); the queue order is Morton order or a cost
+//     order chosen by the scheduler;
+//   * each lane holds IPL i-particles (group <= 32*IPL particles);
+//   * traversal: a per-warp stack in shared memory whose entries are child
+//     ranges (first node, count <= 8).  Each round the warp pops up to 32
+//     nodes (one per lane), evaluates the MAC of Eq. 2 against the group's
+//     bounding sphere, and compacts the outcomes with ballot/popc:
+//       accepted node       -> its pseudo particle (com, M) joins the list,
+//       opened internal node -> its child range is pushed,
+//       opened leaf          -> its particles join the list;
+//   * the list (float4 x, y, z, m in shared memory) is flushed whenever the
+//     next append would overflow it: every lane evaluates Eq. 1 for its IPL
+//     particles against every entry, reading each entry as one broadcast
+//     LDS.128 -- 12 FP32-pipe instructions + 1 MUFU.RSQ per interaction;
+//   * optional Neumaier compensation of the per-flush partial sums.
+// No warp ever waits on another warp or CTA.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace nb {
+
+__device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
+    float t = s + x;
+    if (fabsf(s) >= fabsf(x))
+        c += (s - t) + x;
+    else
+        c += (x - t) + s;
+    s = t;
+}
+
+template <int IPL, bool PHI, bool COMP, bool SAFE>
+__device__ __forceinline__ void flush_list(const float4 *list, int nl, float eps2,
+                                           const float (&xi)[IPL], const float (&yi)[IPL],
+                                           const float (&zi)[IPL], float (&acc)[IPL][4],
+                                           float (&cmp)[IPL][4]) {
+    float part[IPL][4];
+    if constexpr (COMP) {
+#pragma unroll
+        for (int q = 0; q < IPL; q++) part[q][0] = part[q][1] = part[q][2] = part[q][3] = 0.0f;
+    }
+    float(&T)[IPL][4] = COMP ? part : acc;
+#pragma unroll 4
+    for (int k = 0; k < nl; k++) {
+        const float4 p = list[k];
+#pragma unroll
+        for (int q = 0; q < IPL; q++) {
+            const float dx = p.x - xi[q], dy = p.y - yi[q], dz = p.z - zi[q];
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+            float rinv = rsqrtf(r2);
+            if constexpr (SAFE) rinv = r2 > 0.0f ? rinv : 0.0f;
+            const float mr = p.w * rinv;
+            const float w3 = mr * rinv * rinv;
+            T[q][0] = fmaf(w3, dx, T[q][0]);
+            T[q][1] = fmaf(w3, dy, T[q][1]);
+            T[q][2] = fmaf(w3, dz, T[q][2]);
+            if constexpr (PHI) T[q][3] -= mr;
+        }
+    }
+    if constexpr (COMP) {
+#pragma unroll
+        for (int q = 0; q < IPL; q++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) neumaier_add(acc[q][c], cmp[q][c], part[q][c]);
+    }
+}
+
+template <int IPL, bool PHI, bool COMP, bool SAFE>
+__global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
+    extern __shared__ __align__(16) unsigned char walk_smem[];
+    const int D = a.list_depth, S = a.stack_depth;
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    const size_t per_warp = (size_t)D * sizeof(float4) + (size_t)S * sizeof(uint32_t);
+    float4 *list = reinterpret_cast<float4 *>(walk_smem + w * per_warp);
+    uint32_t *stk = reinterpret_cast<uint32_t *>(walk_smem + w * per_warp + (size_t)D * sizeof(float4));
+    DevState *ds = a.ds;
+    const int ng = ds->ngroups;
+    const int nnodes = ds->nnodes;
+    const int npart = (int)a.n;
+    const unsigned lt = lanemask_lt();
+    int max_sp = 0;
+    unsigned long long warp_entries = 0, warp_inter = 0;
+    bool overflow = false, bad = false;
+
+    for (;;) {
+        int qi = 0;
+        if (lane == 0) qi = atomicAdd(&ds->queue_head, 1);
+        qi = __shfl_sync(NB_FULL, qi, 0);
+        if (qi >= ng) break;
+        const int g = a.order ? a.order[qi] : qi;
+        const int first = a.grp_first[g], cnt = a.grp_count[g];
+        const float4 sph = a.grp_sphere[g];
+        const float alpha = geometric ? 0.0f : a.grp_alpha[g];
+        const int sys = a.grp_sys[g];
+        const float eps2 = a.sys_eps2[sys];
+        const int root = a.sys_root[sys];
+
+        float xi[IPL], yi[IPL], zi[IPL], mi[IPL];
+        float acc[IPL][4], cmp[IPL][4];
+#pragma unroll
+        for (int q = 0; q < IPL; q++) {
+            const int k = lane + 32 * q;
+            float4 p = k < cnt ? a.pos4[first + k] : make_float4(sph.x, sph.y, sph.z, 0.0f);
+            xi[q] = p.x; yi[q] = p.y; zi[q] = p.z; mi[q] = p.w;
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[q][c] = cmp[q][c] = 0.0f;
+        }
+
+        if (lane == 0) stk[0] = (uint32_t)root << 3;  // one node: the system's root
+        int sp = 1, nl = 0;
+        long long entries = 0;
+        __syncwarp();
+        while (sp > 0) {
+            // ---- pop up to 32 nodes (one per lane) from the top ranges
+            const int take = sp < 32 ? sp : 32;
+            uint32_t e = 0;
+            int ne = 0;
+            if ((int)lane < take) {
+                e = stk[sp - 1 - lane];
+                ne = (int)(e & 7u) + 1;
+            }
+            const int incl = warp_incl_scan(ne);
+            const int excl = incl - ne;
+            const bool cons = (int)lane < take && excl < 32;
+            const unsigned cm = __ballot_sync(NB_FULL, cons);
+            const int ncons = __popc(cm);
+            const int last = ncons - 1;
+            const int last_incl = __shfl_sync(NB_FULL, incl, last);
+            const uint32_t last_e = __shfl_sync(NB_FULL, e, last);
+            const int last_ex = __shfl_sync(NB_FULL, excl, last);
+            const int nn = last_incl < 32 ? last_incl : 32;
+            const unsigned smap = __reduce_or_sync(NB_FULL, cons ? (1u << excl) : 0u);
+            const int owner = __popc(smap & (0xffffffffu >> (31 - lane))) - 1;
+            const uint32_t oe = __shfl_sync(NB_FULL, e, owner);
+            const int oex = __shfl_sync(NB_FULL, excl, owner);
+            const int node = (int)(oe >> 3) + ((int)lane - oex);
+            const bool in_range = node >= 0 && node < nnodes;
+            if ((int)lane < nn && !in_range) bad = true;
+            const bool has = (int)lane < nn && in_range;
+            sp -= ncons;
+            __syncwarp();
+            if (last_incl > 32) {  // put back the unconsumed tail of the last range
+                if (lane == 0)
+                    stk[sp] = ((last_e >> 3) + (uint32_t)(32 - last_ex)) << 3 |
+                              (uint32_t)(last_incl - 32 - 1);
+                sp += 1;
+            }
+
+            // ---- MAC (Eq. 2) against the group's bounding sphere
+            float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (has) {
+                A = __ldg(&a.nodeA[node]);
+                B = __ldg(&a.nodeB[node]);
+            }
+            const float dx = A.x - sph.x, dy = A.y - sph.y, dz = A.z - sph.z;
+            const float d = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) - sph.w;
+            bool accept;
+            if (geometric) {
+                accept = has && d > B.x && B.x <= a.theta * d;
+            } else {
+                const float d2 = d * d;
+                accept = has && d > B.x && B.y <= alpha * (d2 * d2);
+            }
+            const int link = __float_as_int(B.z), meta = __float_as_int(B.w);
+            const bool leaf = (meta & 1) != 0;
+            const int mcount = meta >> 1;
+            const bool open_leaf = has && !accept && leaf;
+            const bool open_node = has && !accept && !leaf;
+
+            // ---- push the child ranges of opened internal nodes
+            const unsigned om = __ballot_sync(NB_FULL, open_node);
+            const int npush = __popc(om);
+            if (open_node) {
+                const int pos = sp + __popc(om & lt);
+                if (pos < S) stk[pos] = ((uint32_t)link << 3) | (uint32_t)(mcount - 1);
+            }
+            sp += npush;
+            if (sp > S) {
+                overflow = true;
+                sp = S;
+            }
+            if (sp > max_sp) max_sp = sp;
+
+            // ---- accepted nodes join the list
+            const unsigned am = __ballot_sync(NB_FULL, accept);
+            const int na = __popc(am);
+            if (nl + na > D) {
+                __syncwarp();
+                flush_list<IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+                entries += nl;
+                nl = 0;
+                __syncwarp();
+            }
+            if (accept) list[nl + __popc(am & lt)] = A;
+            nl += na;
+
+            // ---- particles of opened leaves join the list
+            unsigned lm = __ballot_sync(NB_FULL, open_leaf);
+            while (lm) {
+                const int src = __ffs(lm) - 1;
+                lm &= lm - 1;
+                const int pf = __shfl_sync(NB_FULL, link, src);
+                int pc = __shfl_sync(NB_FULL, mcount, src);
+                if (pf < 0 || pc < 0 || pf + pc > npart) {
+                    bad = true;
+                    pc = 0;
+                }
+                for (int off = 0; off < pc; off += 32) {
+                    const int c = (pc - off) < 32 ? (pc - off) : 32;
+                    if (nl + c > D) {
+                        __syncwarp();
+                        flush_list<IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+                        entries += nl;
+                        nl = 0;
+                        __syncwarp();
+                    }
+                    if ((int)lane < c) list[nl + lane] = __ldg(&a.pos4[pf + off + lane]);
+                    nl += c;
+                }
+            }
+            __syncwarp();
+        }
+        if (nl > 0) {
+            __syncwarp();
+            flush_list<IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+            entries += nl;
+            nl = 0;
+        }
+        __syncwarp();
+
+        // ---- results (G applied once; the potential's self term removed)
+        const float G = a.G;
+        const float self = SAFE ? 0.0f : rsqrtf(eps2);
+#pragma unroll
+        for (int q = 0; q < IPL; q++) {
+            const int k = lane + 32 * q;
+            if (k < cnt) {
+                float r[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) r[c] = COMP ? acc[q][c] + cmp[q][c] : acc[q][c];
+                const float ph = PHI ? G * (r[3] + mi[q] * self) : 0.0f;
+                const int i = first + k;
+                if (a.perm) {
+                    const int o = a.perm[i];
+                    a.ax[o] = G * r[0];
+                    a.ay[o] = G * r[1];
+                    a.az[o] = G * r[2];
+                    if (PHI && a.phi) a.phi[o] = ph;
+                } else {
+                    a.acc_sorted[i] = make_float4(G * r[0], G * r[1], G * r[2], ph);
+                }
+            }
+        }
+        if (lane == 0 && a.grp_cost) a.grp_cost[g] = (int32_t)entries;
+        warp_entries += (unsigned long long)entries;
+        warp_inter += (unsigned long long)entries * (unsigned long long)cnt;
+    }
+    if (lane == 0) {
+        atomicMax(&ds->max_stack, max_sp);
+        if (warp_entries) {
+            atomicAdd(&ds->list_entries, warp_entries);
+            atomicAdd(&ds->interactions, warp_inter);
+        }
+        if (overflow) atomicOr(&ds->status, kStatusStackOverflow);
+    }
+    if (bad) atomicOr(&ds->status, kStatusBadTree);
+    if (lane == 0) {
+    }
+}
+
+template <int IPL>
+cudaError_t launch_walk_ipl(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm) {
+    const int threads = 32 * sh.warps_per_block;
+    const size_t smem = (size_t)sh.warps_per_block *
+                        ((size_t)a.list_depth * sizeof(float4) + (size_t)a.stack_depth * sizeof(uint32_t));
+    void (*k)(WalkArgs, int);
+    if (sh.potential) {
+        if (sh.compensated) k = sh.safe ? walk_kernel<IPL, true, true, true> : walk_kernel<IPL, true, true, false>;
+        else k = sh.safe ? walk_kernel<IPL, true, false, true> : walk_kernel<IPL, true, false, false>;
+    } else {
+        if (sh.compensated) k = sh.safe ? walk_kernel<IPL, false, true, true> : walk_kernel<IPL, false, true, false>;
+        else k = sh.safe ? walk_kernel<IPL, false, false, true> : walk_kernel<IPL, false, false, false>;
+    }
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    k<<<nsm * per_sm, threads, smem, s>>>(a, sh.geometric ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

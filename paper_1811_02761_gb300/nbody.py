@@ -1,0 +1,302 @@
+"""Thin ctypes binding of libnbody.so (C ABI in include/nbody.h).
+
+Argument marshalling only: every function here checks dtypes/sizes, turns
+torch tensors (device or host) or numpy arrays into raw pointers, calls the C
+entry point of the same name and raises NbodyError on a non-OK status.  No
+step of the computation runs in Python, and there is no CPU fallback: if the
+CUDA library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+NBODY_OK, NBODY_EINVAL, NBODY_ENOMEM, NBODY_EOVERFLOW, NBODY_ETIMEOUT, NBODY_ECUDA, \
+    NBODY_ENOTBUILT = range(7)
+SCHED_MORTON, SCHED_MLP, SCHED_LASTCOST = 0, 1, 2
+_STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EOVERFLOW", 4: "ETIMEOUT", 5: "ECUDA",
+                 6: "ENOTBUILT"}
+
+
+class NbodyError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("G", C.c_float), ("eps", C.c_float), ("delta_acc", C.c_float),
+                ("theta", C.c_float), ("leaf_cap", C.c_int32), ("group_size", C.c_int32),
+                ("ipl", C.c_int32), ("list_depth", C.c_int32), ("stack_depth", C.c_int32),
+                ("warps_per_block", C.c_int32), ("compensated", C.c_int32),
+                ("want_potential", C.c_int32), ("schedule", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_groups", C.c_int64), ("interactions", C.c_int64),
+                ("list_entries", C.c_int64), ("max_stack", C.c_int32), ("levels", C.c_int32),
+                ("kernels", C.c_int64), ("ms_build", C.c_float), ("ms_walk", C.c_float),
+                ("ms_walk_kernel", C.c_float), ("walk_launches", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+EXPORTS = ("nbody_abi_version", "nbody_config_default", "nbody_create", "nbody_destroy",
+           "nbody_set_config", "nbody_get_config", "nbody_build", "nbody_build_batched",
+           "nbody_walk", "nbody_direct", "nbody_step", "nbody_step_batched", "nbody_diagnostics",
+           "nbody_get_group_costs", "nbody_export", "nbody_last_error")
+EXPORT_PERM, EXPORT_KEYS, EXPORT_NODE_LEVEL, EXPORT_NODE_START, EXPORT_NODE_COUNT, \
+    EXPORT_NODE_PARENT, EXPORT_NODE_A, EXPORT_NODE_B, EXPORT_GROUP_FIRST, EXPORT_GROUP_COUNT, \
+    EXPORT_GROUP_SPHERE, EXPORT_SYS_BOX = range(12)
+_EXPORT_DTYPE = {0: (np.int32, 1), 1: (np.uint64, 1), 2: (np.int8, 1), 3: (np.int32, 1),
+                 4: (np.int32, 1), 5: (np.int32, 1), 6: (np.float32, 4), 7: (np.float32, 4),
+                 8: (np.int32, 1), 9: (np.int32, 1), 10: (np.float32, 4), 11: (np.float32, 4)}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libnbody.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and _build.stale():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise NbodyError(NBODY_ECUDA, f"CUDA library not found at {_build.LIB}")
+        lib = C.CDLL(_build.LIB)
+        vp, i64, i32, f32 = C.c_void_p, C.c_int64, C.c_int32, C.c_float
+        st = C.c_int
+        sig = {
+            "nbody_abi_version": (C.c_int32, []),
+            "nbody_config_default": (None, [C.POINTER(Config)]),
+            "nbody_create": (st, [C.POINTER(vp), C.POINTER(Config), vp]),
+            "nbody_destroy": (st, [vp]),
+            "nbody_set_config": (st, [vp, C.POINTER(Config)]),
+            "nbody_get_config": (st, [vp, C.POINTER(Config)]),
+            "nbody_build": (st, [vp, i64, vp, vp, vp, vp]),
+            "nbody_build_batched": (st, [vp, i32, vp, vp, vp, vp, vp, vp]),
+            "nbody_walk": (st, [vp, vp, vp, vp, vp, vp, C.POINTER(Stats)]),
+            "nbody_direct": (st, [i64, vp, vp, vp, vp, f32, f32, i32, vp, vp, vp, vp, vp]),
+            "nbody_step": (st, [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, f32, i32,
+                                C.POINTER(Stats)]),
+            "nbody_step_batched": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                        f32, i32, C.POINTER(Stats)]),
+            "nbody_diagnostics": (st, [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "nbody_get_group_costs": (st, [vp, vp, i64, C.POINTER(i64)]),
+            "nbody_export": (st, [vp, i32, vp, i64, C.POINTER(i64)]),
+            "nbody_last_error": (st, [vp, C.c_char_p, C.c_size_t]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ---------------------------------------------------------------- marshalling
+def _ptr(a, dtype: str, n=None, name="array", allow_none=False):
+    """Raw pointer of a contiguous torch tensor or numpy array of `dtype`."""
+    if a is None:
+        if allow_none:
+            return None
+        raise NbodyError(NBODY_EINVAL, f"{name} is None")
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"]:
+            raise NbodyError(NBODY_EINVAL, f"{name} must be a contiguous {dtype} array")
+        if n is not None and a.size != n:
+            raise NbodyError(NBODY_EINVAL, f"{name} has {a.size} elements, expected {n}")
+        return a.ctypes.data
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise NbodyError(NBODY_EINVAL, f"{name} must be a torch tensor or numpy array")
+    want = {"float32": torch.float32, "float64": torch.float64, "int64": torch.int64,
+            "int32": torch.int32}[dtype]
+    if a.dtype != want or not a.is_contiguous():
+        raise NbodyError(NBODY_EINVAL, f"{name} must be a contiguous {dtype} tensor")
+    if n is not None and a.numel() != n:
+        raise NbodyError(NBODY_EINVAL, f"{name} has {a.numel()} elements, expected {n}")
+    return a.data_ptr()
+
+
+def _size(a):
+    return int(a.size if isinstance(a, np.ndarray) else a.numel())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _check(lib, ctx, status):
+    if status != NBODY_OK:
+        buf = C.create_string_buffer(512)
+        lib.nbody_last_error(ctx, buf, 512)
+        raise NbodyError(status, buf.value.decode(errors="replace"))
+
+
+# ---------------------------------------------------------------- entry points
+def nbody_abi_version() -> int:
+    return int(load().nbody_abi_version())
+
+
+def nbody_config_default(**overrides) -> Config:
+    cfg = Config()
+    load().nbody_config_default(C.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise NbodyError(NBODY_EINVAL, f"unknown config field {k}")
+        setattr(cfg, k, v)
+    return cfg
+
+
+def nbody_create(cfg: Config | None = None, stream=None):
+    """Returns an opaque context handle (c_void_p)."""
+    lib = load()
+    h = C.c_void_p()
+    _check(lib, None, lib.nbody_create(C.byref(h), C.byref(cfg) if cfg is not None else None,
+                                       _stream_ptr(stream)))
+    return h
+
+
+def nbody_destroy(ctx):
+    lib = load()
+    _check(lib, None, lib.nbody_destroy(ctx))
+
+
+def nbody_set_config(ctx, cfg: Config):
+    lib = load()
+    _check(lib, ctx, lib.nbody_set_config(ctx, C.byref(cfg)))
+
+
+def nbody_get_config(ctx) -> Config:
+    lib = load()
+    cfg = Config()
+    _check(lib, ctx, lib.nbody_get_config(ctx, C.byref(cfg)))
+    return cfg
+
+
+def nbody_build(ctx, x, y, z, m):
+    lib = load()
+    n = _size(x)
+    ps = [_ptr(a, "float32", n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (m, "m"))]
+    _check(lib, ctx, lib.nbody_build(ctx, n, *ps))
+
+
+def nbody_build_batched(ctx, offsets, eps_sys, x, y, z, m):
+    """offsets: host int64 [nsys+1]; eps_sys: host float32 [nsys] or None."""
+    lib = load()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nsys = off.size - 1
+    eps = None if eps_sys is None else np.ascontiguousarray(eps_sys, dtype=np.float32)
+    if eps is not None and eps.size != nsys:
+        raise NbodyError(NBODY_EINVAL, "eps_sys must have nsys entries")
+    n = int(off[-1])
+    ps = [_ptr(a, "float32", n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (m, "m"))]
+    _check(lib, ctx, lib.nbody_build_batched(ctx, nsys, off.ctypes.data,
+                                             None if eps is None else eps.ctypes.data, *ps))
+
+
+def nbody_walk(ctx, a_old, ax, ay, az, phi=None) -> Stats:
+    lib = load()
+    n = _size(ax)
+    st = Stats()
+    _check(lib, ctx, lib.nbody_walk(ctx, _ptr(a_old, "float32", n, "a_old", True),
+                                    _ptr(ax, "float32", n, "ax"), _ptr(ay, "float32", n, "ay"),
+                                    _ptr(az, "float32", n, "az"),
+                                    _ptr(phi, "float32", n, "phi", True), C.byref(st)))
+    return st
+
+
+def nbody_direct(x, y, z, m, G, eps, compensated, ax, ay, az, phi=None, stream=None):
+    lib = load()
+    n = _size(x)
+    ps = [_ptr(a, "float32", n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (m, "m"))]
+    _check(lib, None, lib.nbody_direct(n, *ps, float(G), float(eps), int(compensated),
+                                       _ptr(ax, "float32", n, "ax"), _ptr(ay, "float32", n, "ay"),
+                                       _ptr(az, "float32", n, "az"),
+                                       _ptr(phi, "float32", n, "phi", True), _stream_ptr(stream)))
+
+
+def nbody_step(ctx, x, y, z, vx, vy, vz, m, ax, ay, az, dt, nsteps) -> Stats:
+    lib = load()
+    n = _size(x)
+    st = Stats()
+    d = [_ptr(a, "float64", n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"))]
+    f = [_ptr(a, "float32", n, nm) for a, nm in ((vx, "vx"), (vy, "vy"), (vz, "vz"), (m, "m"),
+                                                 (ax, "ax"), (ay, "ay"), (az, "az"))]
+    _check(lib, ctx, lib.nbody_step(ctx, n, *d, *f, float(dt), int(nsteps), C.byref(st)))
+    return st
+
+
+def nbody_step_batched(ctx, offsets, eps_sys, x, y, z, vx, vy, vz, m, ax, ay, az, dt,
+                       nsteps) -> Stats:
+    lib = load()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nsys = off.size - 1
+    eps = None if eps_sys is None else np.ascontiguousarray(eps_sys, dtype=np.float32)
+    n = int(off[-1])
+    st = Stats()
+    d = [_ptr(a, "float64", n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"))]
+    f = [_ptr(a, "float32", n, nm) for a, nm in ((vx, "vx"), (vy, "vy"), (vz, "vz"), (m, "m"),
+                                                 (ax, "ax"), (ay, "ay"), (az, "az"))]
+    _check(lib, ctx, lib.nbody_step_batched(ctx, nsys, off.ctypes.data,
+                                            None if eps is None else eps.ctypes.data, *d, *f,
+                                            float(dt), int(nsteps), C.byref(st)))
+    return st
+
+
+def nbody_diagnostics(ctx, x, y, z, vx, vy, vz, m, phi=None) -> np.ndarray:
+    lib = load()
+    n = _size(x)
+    out = np.zeros(8, np.float64)
+    d = [_ptr(a, "float64", n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"))]
+    f = [_ptr(a, "float32", n, nm) for a, nm in ((vx, "vx"), (vy, "vy"), (vz, "vz"), (m, "m"))]
+    _check(lib, ctx, lib.nbody_diagnostics(ctx, n, *d, *f, _ptr(phi, "float32", n, "phi", True),
+                                           out.ctypes.data))
+    return out
+
+
+def nbody_get_group_costs(ctx, counts) -> int:
+    lib = load()
+    ng = C.c_int64()
+    _check(lib, ctx, lib.nbody_get_group_costs(ctx, _ptr(counts, "int32", None, "counts"),
+                                               _size(counts), C.byref(ng)))
+    return int(ng.value)
+
+
+def nbody_export(ctx, what: int) -> np.ndarray:
+    """Host copy of an internal array of the last build (see nbody_export_what)."""
+    lib = load()
+    cnt = C.c_int64()
+    _check(lib, ctx, lib.nbody_export(ctx, int(what), None, 0, C.byref(cnt)))
+    dt, width = _EXPORT_DTYPE[int(what)]
+    out = np.empty(cnt.value * width, dt)
+    _check(lib, ctx, lib.nbody_export(ctx, int(what), out.ctypes.data if out.size else None,
+                                      cnt.value, C.byref(cnt)))
+    return out.reshape(-1, width) if width > 1 else out
+
+
+def nbody_last_error(ctx=None) -> str:
+    lib = load()
+    buf = C.create_string_buffer(512)
+    lib.nbody_last_error(ctx, buf, 512)
+    return buf.value.decode(errors="replace")

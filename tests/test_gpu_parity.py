@@ -1,0 +1,355 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Integer work (keys, sort, tree structure, groups) must match bit for bit;
+floating-point results within the tolerances stated in each test:
+  * GPU direct vs FP64 direct: max relative error <= 1e-5 (compensated);
+  * GPU tree error percentiles (p50, p99) vs FP64 direct within 1.1x the
+    oracle tree's percentiles + 1e-6 (same MAC reading, group mode).
+"""
+import numpy as np
+import pytest
+
+import ics
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1811_02761_gb300 as nb  # noqa: E402
+
+EPS = 1.0 / 128
+DACC = 2.0 ** -9
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def f64(p):
+    return [p[k].astype(np.float64) for k in ("x", "y", "z", "m")]
+
+
+@pytest.fixture(scope="module")
+def plummer8k():
+    p = ics.plummer(8192, 1)
+    x, y, z, m = f64(p)
+    ax, ay, az, phi = oracle.direct(x, y, z, m, 1.0, EPS)
+    return p, (ax, ay, az, phi)
+
+
+def gpu_walk(p, cfg, a_old=None, want_phi=False, offsets=None, eps_sys=None):
+    ctx = nb.nbody_create(cfg)
+    try:
+        X = [dev(p[k]) for k in ("x", "y", "z", "m")]
+        if offsets is None:
+            nb.nbody_build(ctx, *X)
+        else:
+            nb.nbody_build_batched(ctx, offsets, eps_sys, *X)
+        n = X[0].numel()
+        out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(4)]
+        st = nb.nbody_walk(ctx, None if a_old is None else dev(a_old.astype(np.float32)),
+                           out[0], out[1], out[2], out[3] if want_phi else None)
+        exports = {w: nb.nbody_export(ctx, w) for w in range(12)}
+        return [host(o) for o in out], st, exports
+    finally:
+        nb.nbody_destroy(ctx)
+
+
+# --------------------------------------------------------------------------- direct
+@pytest.mark.parametrize("compensated", [1, 0])
+def test_direct_vs_fp64(plummer8k, compensated):
+    p, (ax, ay, az, phi) = plummer8k
+    n = p["x"].size
+    out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(4)]
+    X = [dev(p[k]) for k in ("x", "y", "z", "m")]
+    nb.nbody_direct(*X, 1.0, EPS, compensated, *out)
+    gx, gy, gz, gphi = (host(o).astype(np.float64) for o in out)
+    e = oracle.rel_err(gx, gy, gz, ax, ay, az)
+    if compensated:
+        assert e.max() <= 1e-5, e.max()
+    else:
+        assert e.max() <= 1e-4, e.max()
+    assert np.max(np.abs(gphi - phi) / np.abs(phi)) < 1e-5
+
+
+def test_direct_host_buffers_match_device(plummer8k):
+    p, _ = plummer8k
+    n = 2000
+    q = {k: np.ascontiguousarray(p[k][:n]) for k in ("x", "y", "z", "m")}
+    hout = [np.empty(n, np.float32) for _ in range(3)]
+    nb.nbody_direct(q["x"], q["y"], q["z"], q["m"], 1.0, EPS, 1, *hout)
+    dout = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    nb.nbody_direct(*[dev(q[k]) for k in ("x", "y", "z", "m")], 1.0, EPS, 1, *dout)
+    for a, b in zip(hout, dout):
+        assert np.array_equal(a, host(b))
+
+
+# --------------------------------------------------------------------------- keys, sort, tree
+def test_keys_and_sort_bit_exact(plummer8k):
+    p, (ax, ay, az, _) = plummer8k
+    cfg = nb.nbody_config_default(eps=EPS)
+    _, _, ex = gpu_walk(p, cfg, a_old=np.sqrt(ax ** 2 + ay ** 2 + az ** 2))
+    k, cube = oracle.keys(p["x"], p["y"], p["z"], 21)
+    order = oracle.sort_order(k)
+    assert np.array_equal(ex[nb.nbody.EXPORT_SYS_BOX][0], cube)
+    assert np.array_equal(ex[nb.nbody.EXPORT_PERM], order.astype(np.int32))
+    assert np.array_equal(ex[nb.nbody.EXPORT_KEYS], k[order])
+
+
+def _gpu_nodes(ex):
+    lev = ex[nb.nbody.EXPORT_NODE_LEVEL].astype(np.int64)
+    start = ex[nb.nbody.EXPORT_NODE_START].astype(np.int64)
+    cnt = ex[nb.nbody.EXPORT_NODE_COUNT].astype(np.int64)
+    B = ex[nb.nbody.EXPORT_NODE_B]
+    leaf = (B[:, 3].view(np.int32) & 1).astype(bool)
+    return lev, start, cnt, leaf, ex[nb.nbody.EXPORT_NODE_A], B
+
+
+@pytest.mark.parametrize("gen,n,cap", [(ics.plummer, 8192, 16), (ics.galaxy, 20000, 8),
+                                       (ics.hernquist, 5000, 32)])
+def test_tree_structure_and_moments(gen, n, cap):
+    p = gen(n, 3)
+    cfg = nb.nbody_config_default(eps=EPS, leaf_cap=cap, group_size=max(cap, 32))
+    _, _, ex = gpu_walk(p, cfg, a_old=np.ones(n))
+    t = oracle.Tree(*f64(p), levels=21, leaf_cap=cap)
+    on = t.nodes()
+    lev, start, cnt, leaf, A, B = _gpu_nodes(ex)
+    # identical node sets (the oracle's tree order equals the sorted order)
+    g = sorted(zip(lev, start, cnt, leaf))
+    o = sorted(zip(on["level"].astype(np.int64), on["first"], on["count"], on["nchild"] == 0))
+    assert g == o
+    # level-major order with contiguous children
+    assert np.all(np.diff(lev) >= 0)
+    # moments: match nodes by (level, start)
+    key_o = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(on["level"], on["first"]))}
+    idx = np.array([key_o[(int(a), int(b))] for a, b in zip(lev, start)])
+    assert np.allclose(A[:, 3], on["M"][idx], rtol=2e-6)
+    for c, k in ((0, "cx"), (1, "cy"), (2, "cz")):
+        scale = np.maximum(np.abs(on[k][idx]), on["b"][idx] + 1e-3)
+        assert np.all(np.abs(A[:, c] - on[k][idx]) <= 2e-6 * scale)
+    b_o = on["b"][idx]
+    assert np.all(B[:, 0] >= b_o * (1 - 1e-6))
+    assert np.all(B[:, 0] <= b_o * (1 + 1e-5) + 1e-6)
+
+
+def test_groups_bit_exact(plummer8k):
+    p, _ = plummer8k
+    for G, ipl in ((32, 1), (64, 2), (128, 4)):
+        cfg = nb.nbody_config_default(eps=EPS, group_size=G, ipl=ipl)
+        _, _, ex = gpu_walk(p, cfg, a_old=np.ones(p["x"].size))
+        t = oracle.Tree(*f64(p), levels=21, leaf_cap=16)
+        f, c = t.groups(G)
+        assert np.array_equal(ex[nb.nbody.EXPORT_GROUP_FIRST], f.astype(np.int32))
+        assert np.array_equal(ex[nb.nbody.EXPORT_GROUP_COUNT], c.astype(np.int32))
+
+
+# --------------------------------------------------------------------------- walk
+def _pcts(e):
+    return oracle.percentile_nearest_rank(e, 50), oracle.percentile_nearest_rank(e, 99)
+
+
+@pytest.mark.parametrize("ipl,G", [(1, 32), (2, 64), (4, 128), (2, 32)])
+def test_walk_error_vs_oracle_tree(plummer8k, ipl, G):
+    p, (ax, ay, az, phi) = plummer8k
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    aold32 = amag.astype(np.float32)
+    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, ipl=ipl, group_size=G)
+    (gx, gy, gz, _), st, _ = gpu_walk(p, cfg, a_old=aold32)
+    t = oracle.Tree(*f64(p), levels=21, leaf_cap=16)
+    ox, oy, oz, _, nint = t.walk(oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, G,
+                                 aold32.astype(np.float64))
+    eg = oracle.rel_err(gx.astype(float), gy.astype(float), gz.astype(float), ax, ay, az)
+    eo = oracle.rel_err(ox, oy, oz, ax, ay, az)
+    g50, g99 = _pcts(eg)
+    o50, o99 = _pcts(eo)
+    assert g50 <= 1.1 * o50 + 1e-6, (g50, o50)
+    assert g99 <= 1.1 * o99 + 1e-6, (g99, o99)
+    # same tree, same groups, same MAC: per-particle agreement with the oracle tree
+    d = oracle.rel_err(gx.astype(float), gy.astype(float), gz.astype(float), ox, oy, oz)
+    assert np.median(d) < 5e-6
+    assert abs(st.interactions - nint.sum()) <= 0.01 * nint.sum()
+
+
+def test_walk_bootstrap_without_a_old(plummer8k):
+    p, (ax, ay, az, _) = plummer8k
+    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC)
+    (gx, gy, gz, _), st, _ = gpu_walk(p, cfg, a_old=None)
+    t = oracle.Tree(*f64(p), levels=21, leaf_cap=16)
+    bx, by, bz, _, _ = t.walk(oracle.MAC_GROUP_GEO, 1.0, EPS, 0.0, 0.5, 64, None, want_phi=False)
+    a0 = np.sqrt(bx ** 2 + by ** 2 + bz ** 2).astype(np.float32).astype(np.float64)
+    ox, oy, oz, _, _ = t.walk(oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, 64, a0, want_phi=False)
+    eg = oracle.rel_err(gx.astype(float), gy.astype(float), gz.astype(float), ax, ay, az)
+    eo = oracle.rel_err(ox, oy, oz, ax, ay, az)
+    (g50, g99), (o50, o99) = _pcts(eg), _pcts(eo)
+    assert g50 <= 1.1 * o50 + 1e-6 and g99 <= 1.1 * o99 + 1e-6
+
+
+def test_walk_potential_and_compensation(plummer8k):
+    p, (ax, ay, az, phi) = plummer8k
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2).astype(np.float32)
+    t = oracle.Tree(*f64(p), levels=21, leaf_cap=16)
+    ox, oy, oz, ophi, _ = t.walk(oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, 64, amag.astype(float))
+    res = {}
+    for comp in (0, 1):
+        cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, want_potential=1, compensated=comp)
+        (gx, gy, gz, gphi), _, _ = gpu_walk(p, cfg, a_old=amag, want_phi=True)
+        assert np.median(np.abs(gphi - ophi) / np.abs(ophi)) < 2e-6
+        res[comp] = oracle.rel_err(gx.astype(float), gy.astype(float), gz.astype(float), ox, oy, oz)
+    # compensation cannot make the agreement with the FP64 tree worse on average
+    assert np.mean(res[1]) <= np.mean(res[0]) * 1.05 + 1e-9
+
+
+def test_walk_deterministic(plummer8k):
+    p, (ax, ay, az, _) = plummer8k
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2).astype(np.float32)
+    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC)
+    (a1, _, _, _), _, _ = gpu_walk(p, cfg, a_old=amag)
+    (a2, _, _, _), _, _ = gpu_walk(p, cfg, a_old=amag)
+    assert np.array_equal(a1, a2)
+
+
+# --------------------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("n", [1, 2, 15, 16, 17, 100, 8192 + 13])
+def test_walk_small_and_ragged_n(n):
+    p = ics.plummer(n, 5)
+    x, y, z, m = f64(p)
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 0.05)
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    cfg = nb.nbody_config_default(eps=0.05, delta_acc=DACC)
+    (gx, gy, gz, _), _, _ = gpu_walk(p, cfg, a_old=amag)
+    if n == 1:
+        assert gx[0] == 0 and gy[0] == 0 and gz[0] == 0
+        return
+    t = oracle.Tree(x, y, z, m, 21, 16)
+    ox, oy, oz, _, _ = t.walk(oracle.MAC_GROUP_ACC, 1.0, 0.05, DACC, 0.5, 64,
+                              amag.astype(np.float32).astype(float))
+    d = oracle.rel_err(gx.astype(float), gy.astype(float), gz.astype(float), ox, oy, oz)
+    assert np.median(d) < 1e-5 and np.percentile(d, 99) < 1e-2
+
+
+def test_walk_coincident_particles():
+    p = ics.plummer(3000, 6)
+    for k in ("x", "y", "z"):
+        p[k][:200] = p[k][0]
+    x, y, z, m = f64(p)
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 0.05)
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    cfg = nb.nbody_config_default(eps=0.05, delta_acc=0.0)
+    (gx, gy, gz, _), _, ex = gpu_walk(p, cfg, a_old=amag)
+    assert ex[nb.nbody.EXPORT_GROUP_COUNT].max() <= 64
+    e = oracle.rel_err(gx.astype(float), gy.astype(float), gz.astype(float), ax, ay, az)
+    assert e.max() < 1e-4
+
+
+def test_walk_zero_softening():
+    g = ics.rng(9)
+    n = 2000
+    p = {k: g.normal(size=n).astype(np.float32) for k in ("x", "y", "z")}
+    p["m"] = np.full(n, 1.0 / n, np.float32)
+    x, y, z, m = f64(p)
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 0.0)
+    cfg = nb.nbody_config_default(eps=0.0, delta_acc=0.0)
+    (gx, gy, gz, _), _, _ = gpu_walk(p, cfg, a_old=np.sqrt(ax ** 2 + ay ** 2 + az ** 2))
+    e = oracle.rel_err(gx.astype(float), gy.astype(float), gz.astype(float), ax, ay, az)
+    assert np.all(np.isfinite(gx)) and np.median(e) < 1e-5
+
+
+# --------------------------------------------------------------------------- batched
+def test_batched_forest_matches_per_system_oracle():
+    sizes = [1, 20, 700, 3000, 65, 1, 0, 4096]
+    b = ics.batched(len(sizes), 7, sizes=sizes)
+    off, eps = b["offsets"], b["eps"]
+    n = int(off[-1])
+    cfg = nb.nbody_config_default(delta_acc=DACC)
+    # |a_old| from each system's own direct sum
+    aold = np.zeros(n)
+    for s in range(len(sizes)):
+        sl = slice(off[s], off[s + 1])
+        if off[s + 1] - off[s] < 2:
+            continue
+        ax, ay, az, _ = oracle.direct(*[b[k][sl].astype(float) for k in ("x", "y", "z", "m")],
+                                      1.0, float(eps[s]), want_phi=False)
+        aold[sl] = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    (gx, gy, gz, _), _, ex = gpu_walk(b, cfg, a_old=aold, offsets=off, eps_sys=eps)
+    levels = 63 // 3 if len(sizes) == 1 else (63 - int(np.ceil(np.log2(len(sizes))))) // 3
+    for s in range(len(sizes)):
+        sl = slice(off[s], off[s + 1])
+        ns = off[s + 1] - off[s]
+        if ns == 0:
+            continue
+        if ns == 1:
+            assert gx[sl][0] == 0
+            continue
+        t = oracle.Tree(*[b[k][sl].astype(float) for k in ("x", "y", "z", "m")], levels=levels,
+                        leaf_cap=16)
+        ox, oy, oz, _, _ = t.walk(oracle.MAC_GROUP_ACC, 1.0, float(eps[s]), DACC, 0.5, 64,
+                                  aold[sl].astype(np.float32).astype(float), want_phi=False)
+        d = oracle.rel_err(gx[sl].astype(float), gy[sl].astype(float), gz[sl].astype(float),
+                           ox, oy, oz)
+        assert np.median(d) < 5e-6, (s, np.median(d))
+
+
+# --------------------------------------------------------------------------- step, diagnostics
+def test_step_one_kdk_vs_oracle():
+    p = ics.plummer(4096, 8)
+    n = p["x"].size
+    x, y, z, m = f64(p)
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, EPS)
+    a0 = [a.astype(np.float32) for a in (ax, ay, az)]
+    dt = 1.0 / 256
+    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC)
+    ctx = nb.nbody_create(cfg)
+    try:
+        X = [dev(a) for a in (x, y, z)]
+        V = [dev(p[k]) for k in ("vx", "vy", "vz")]
+        A = [dev(a) for a in a0]
+        nb.nbody_step(ctx, *X, *V, dev(p["m"]), *A, dt, 1)
+        gx, gy, gz = (host(t) for t in X)
+        gv = [host(t) for t in V]
+        ga = [host(t) for t in A]
+    finally:
+        nb.nbody_destroy(ctx)
+    # oracle leapfrog with the same entry accelerations and the oracle tree force
+    vh = [p[k].astype(float) + a.astype(float) * dt / 2 for k, a in zip(("vx", "vy", "vz"), a0)]
+    x1 = [q + v * dt for q, v in zip((x, y, z), vh)]
+    assert np.max(np.abs(gx - x1[0])) < 1e-9 and np.max(np.abs(gz - x1[2])) < 1e-9
+    t = oracle.Tree(*x1, m, 21, 16)
+    amag = np.sqrt(sum(a.astype(float) ** 2 for a in a0)).astype(np.float32).astype(float)
+    ox, oy, oz, _, _ = t.walk(oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, 64, amag, want_phi=False)
+    d = oracle.rel_err(ga[0].astype(float), ga[1].astype(float), ga[2].astype(float), ox, oy, oz)
+    assert np.median(d) < 5e-6
+    v1 = [v + a * dt / 2 for v, a in zip(vh, (ox, oy, oz))]
+    assert np.max(np.abs(gv[0] - v1[0])) < 1e-5 * np.max(np.abs(v1[0]))
+
+
+def test_diagnostics_vs_oracle(plummer8k):
+    p, (_, _, _, phi) = plummer8k
+    x, y, z, m = f64(p)
+    ref = oracle.diagnostics(x, y, z, p["vx"], p["vy"], p["vz"], m, phi.astype(np.float32))
+    ctx = nb.nbody_create(nb.nbody_config_default())
+    try:
+        got = nb.nbody_diagnostics(ctx, dev(x), dev(y), dev(z), dev(p["vx"]), dev(p["vy"]),
+                                   dev(p["vz"]), dev(p["m"]), dev(phi.astype(np.float32)))
+    finally:
+        nb.nbody_destroy(ctx)
+    scale = np.array([abs(ref[0]), abs(ref[1])] + [np.abs(ref[2:5]).max() + 1e-3] * 3 +
+                     [np.abs(ref[5:]).max() + 1e-3] * 3)
+    assert np.all(np.abs(got - ref) <= 1e-12 * scale + 1e-15)
+
+
+def test_bad_arguments_rejected_on_gpu():
+    ctx = nb.nbody_create(nb.nbody_config_default())
+    try:
+        out = [torch.empty(4, device="cuda") for _ in range(3)]
+        with pytest.raises(nb.NbodyError) as e:
+            nb.nbody_walk(ctx, None, *out)
+        assert e.value.status == nb.NBODY_ENOTBUILT
+        with pytest.raises(nb.NbodyError) as e:
+            nb.nbody_build_batched(ctx, [0, 5, 3], None, *[torch.zeros(3, device="cuda")] * 4)
+        assert e.value.status == nb.NBODY_EINVAL
+    finally:
+        nb.nbody_destroy(ctx)

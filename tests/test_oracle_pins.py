@@ -322,6 +322,21 @@ def test_tree_error_decreases_with_dacc():
         prev, prev_n = e50, nint.sum()
 
 
+def test_tree_walk_groups_subset_equals_full_walk():
+    p = ics.galaxy(6000, 15)
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    t = oracle.Tree(x, y, z, m, 21, 16)
+    aold = np.full(6000, 0.5)
+    fx, fy, fz, _, fn = t.walk(oracle.MAC_GROUP_ACC, 1.0, 0.01, 2 ** -7, 0.5, 32, aold)
+    f, c = t.groups(32)
+    sel = np.arange(0, f.size, 5)
+    gx, gy, gz, gn = t.walk_groups(sel, oracle.MAC_GROUP_ACC, 1.0, 0.01, 2 ** -7, 0.5, 32, aold)
+    members = np.concatenate([t.order()[f[g]:f[g] + c[g]] for g in sel])
+    assert np.array_equal(gx[members], fx[members]) and np.array_equal(gn[members], fn[members])
+    others = np.setdiff1d(np.arange(6000), members)
+    assert np.all(np.isnan(gx[others]))
+
+
 def test_tree_group_mac_not_looser_than_particle_mac():
     """The group distance |com - c_g| - r_g is a lower bound of every member's
     distance and amin <= |a_i|, so a group accepts a node only if every member
