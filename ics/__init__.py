@@ -98,7 +98,7 @@ def plummer(n: int, seed: int, rmax: float = 64.0, keep64: bool = False):
         todo = todo[~ok]
     v = q * np.sqrt(2.0) * (1.0 + r * r) ** -0.25
     vx, vy, vz = _isotropic(g, v)
-    m = np.full(n, 1.0 / n)
+    m = np.full(n, 1.0 / max(n, 1))
     return _pack(x, y, z, vx, vy, vz, m, keep64)
 
 
@@ -140,7 +140,7 @@ def hernquist(n: int, seed: int, a: float = 1.0, rtrunc_over_a: float = 100.0,
     s2 = _jeans_sigma2(rgrid, rho, mt)
     sig = np.sqrt(np.interp(r, rgrid, s2))
     vx, vy, vz = (g.normal(0.0, 1.0, n) * sig for _ in range(3))
-    m = np.full(n, 1.0 / n)
+    m = np.full(n, 1.0 / max(n, 1))
     return _pack(x, y, z, vx, vy, vz, m, keep64)
 
 

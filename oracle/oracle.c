@@ -420,27 +420,43 @@ void oracle_tree_order(const oracle_tree *t, int64_t *order)
 
 /* ------------------------------------------------------------------------ */
 /* Groups of particles sharing one interaction list (Sect. 1: 32 threads of a
- * warp share a list).  READING: a group is the largest node holding at most
- * group_size particles; a finest-level leaf holding more is cut into chunks. */
+ * warp share a list).  READING: under a node holding more than group_size
+ * particles, consecutive children (octant order) that each hold at most
+ * group_size are packed into runs of at most group_size particles, one group
+ * per run; children holding more are grouped recursively.  A root holding at
+ * most group_size is one group; a finest-level leaf holding more is cut into
+ * chunks. */
+static int64_t add_group(int64_t ng, int64_t f, int64_t c, int64_t *first, int64_t *count)
+{
+    if (first) { first[ng] = f; count[ng] = c; }
+    return ng + 1;
+}
+
 static int64_t groups_rec(const oracle_tree *t, int64_t id, int G, int64_t ng,
                           int64_t *first, int64_t *count)
 {
-    if (t->count[id] <= G) {
-        if (first) { first[ng] = t->first[id]; count[ng] = t->count[id]; }
-        return ng + 1;
-    }
+    if (t->count[id] <= G) return add_group(ng, t->first[id], t->count[id], first, count);
     if (t->nchild[id] == 0) {
-        for (int64_t s = 0; s < t->count[id]; s += G) {
-            if (first) {
-                first[ng] = t->first[id] + s;
-                count[ng] = (t->count[id] - s < G) ? t->count[id] - s : G;
-            }
-            ng++;
-        }
+        for (int64_t s = 0; s < t->count[id]; s += G)
+            ng = add_group(ng, t->first[id] + s, (t->count[id] - s < G) ? t->count[id] - s : G,
+                           first, count);
         return ng;
     }
-    for (int64_t c = t->child[id]; c < t->child[id] + t->nchild[id]; c++)
-        ng = groups_rec(t, c, G, ng, first, count);
+    int64_t run_first = -1, run_count = 0;
+    for (int64_t c = t->child[id]; c < t->child[id] + t->nchild[id]; c++) {
+        if (t->count[c] > G) {
+            if (run_count) ng = add_group(ng, run_first, run_count, first, count);
+            run_count = 0;
+            ng = groups_rec(t, c, G, ng, first, count);
+        } else if (run_count && run_count + t->count[c] <= G) {
+            run_count += t->count[c];
+        } else {
+            if (run_count) ng = add_group(ng, run_first, run_count, first, count);
+            run_first = t->first[c];
+            run_count = t->count[c];
+        }
+    }
+    if (run_count) ng = add_group(ng, run_first, run_count, first, count);
     return ng;
 }
 

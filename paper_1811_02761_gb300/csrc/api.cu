@@ -294,7 +294,7 @@ nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
                P<int32_t>(c->sys_root), c->nsm);
     build_groups(s, L, c->cfg.group_size, P<float4>(c->pos4), P<int64_t>(c->sys_off),
                  P<int32_t>(c->node_start), P<int32_t>(c->node_parent), P<int32_t>(c->node_count),
-                 P<int32_t>(c->node_nchild), P<int8_t>(c->node_level), c->ds,
+                 P<int32_t>(c->node_nchild), P<int32_t>(c->node_link), c->ds,
                  P<uint8_t>(c->gflag), c->grp_temp.p, P<int32_t>(c->grp_first),
                  P<int32_t>(c->grp_count), P<float4>(c->grp_sphere), P<int32_t>(c->grp_sys),
                  c->nsm);
@@ -734,6 +734,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     nbody_status st = upload_systems(ctx, nsys, offsets ? offsets : off1.data(), eps_sys);
     if (st != NBODY_OK) return st;
     const bool safe = any_zero_eps(ctx, nsys, eps_sys);
+    ctx->L = L;  // the walk's bounds checks read the particle count from here
     StepState S[2];
     for (int b = 0; b < 2; b++) {
         S[b].x = P<double>(ctx->st_buf[b][0]);

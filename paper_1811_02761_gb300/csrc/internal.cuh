@@ -139,7 +139,7 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                 int32_t *sys_root, int nsm);
 void build_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
                   const int64_t *d_off, const int32_t *node_start, const int32_t *node_parent,
-                  const int32_t *node_count, const int32_t *node_nchild, const int8_t *node_level,
+                  const int32_t *node_count, const int32_t *node_nchild, const int32_t *node_link,
                   DevState *ds, uint8_t *gflag, void *temp, int32_t *grp_first,
                   int32_t *grp_count, float4 *grp_sphere, int32_t *grp_sys, int nsm);
 void launch_group_alpha(cudaStream_t s, int64_t n, const DevState *ds, const int32_t *grp_first,

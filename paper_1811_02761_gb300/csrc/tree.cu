@@ -318,6 +318,10 @@ __global__ void __launch_bounds__(256) moments_kernel(
         for (;;) {
             int par = node_parent[nd];
             if (par < 0) break;
+            if (par >= nd) {  // parents precede children in level-major order
+                atomicOr(&ds_status(ds), kStatusBadTree);
+                break;
+            }
             __threadfence();
             int old = atomicAdd(&node_arrive[par], 1);
             if (old != node_nchild[par] - 1) break;
@@ -396,20 +400,40 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
 // ---------------------------------------------------------------- groups
 constexpr int FL_T = 1024, FL_IPT = 4, FL_CH = FL_T * FL_IPT;
 
-// A group is the largest node holding at most G particles; a finest-level
-// leaf holding more is cut into chunks of G.  Mark each group's first particle.
+// Groups (the particles that share one interaction list).  Under a node
+// holding more than G particles, consecutive children that each hold at most
+// G are packed greedily, in octant order, into runs of at most G particles;
+// each run is one group.  A root holding at most G is one group, and a
+// finest-level leaf holding more than G is cut into chunks of G.  Packing
+// siblings keeps a group inside its parent's cell while filling the warp.
+// Mark each group's first particle.
 __global__ void group_mark_kernel(const DevState *__restrict__ ds, int G,
                                   const int32_t *__restrict__ node_start,
                                   const int32_t *__restrict__ node_parent,
+                                  const int32_t *__restrict__ node_link,
                                   const int32_t *__restrict__ node_count,
                                   const int32_t *__restrict__ node_nchild, uint8_t *gflag) {
     const int nn = ds->nnodes;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
-        int cnt = node_count[id], par = node_parent[id];
+        const int cnt = node_count[id], nc = node_nchild[id];
         if (cnt <= G) {
-            if (par < 0 || node_count[par] > G) gflag[node_start[id]] = 1;
-        } else if (node_nchild[id] == 0) {
+            if (node_parent[id] < 0) gflag[node_start[id]] = 1;
+        } else if (nc == 0) {
             for (int k = 0; k < cnt; k += G) gflag[node_start[id] + k] = 1;
+        } else {
+            const int c0 = node_link[id];
+            int run = 0;
+            for (int c = c0; c < c0 + nc; c++) {
+                const int cc = node_count[c];
+                if (cc > G) {
+                    run = 0;  // grouped below that child
+                } else if (run == 0 || run + cc > G) {
+                    gflag[node_start[c]] = 1;
+                    run = cc;
+                } else {
+                    run += cc;
+                }
+            }
         }
     }
 }
@@ -508,14 +532,14 @@ __global__ void __launch_bounds__(256) group_info_kernel(Layout L, int G,
 
 void build_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
                   const int64_t *d_off, const int32_t *node_start, const int32_t *node_parent,
-                  const int32_t *node_count, const int32_t *node_nchild, const int8_t *node_level,
+                  const int32_t *node_count, const int32_t *node_nchild, const int32_t *node_link,
                   DevState *ds, uint8_t *gflag, void *temp, int32_t *grp_first,
                   int32_t *grp_count, float4 *grp_sphere, int32_t *grp_sys, int nsm) {
-    (void)node_level;
+
     cudaMemsetAsync(gflag, 0, (size_t)L.n, s);
     int mb = (int)((L.n + 255) / 256);
     if (mb > nsm * 16) mb = nsm * 16;
-    group_mark_kernel<<<mb, 256, 0, s>>>(ds, group_size, node_start, node_parent, node_count,
+    group_mark_kernel<<<mb, 256, 0, s>>>(ds, group_size, node_start, node_parent, node_link, node_count,
                                          node_nchild, gflag);
     int nb = (int)((L.n + FL_CH - 1) / FL_CH);
     uint32_t *bsum = (uint32_t *)temp;

@@ -172,7 +172,12 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
             const bool leaf = (meta & 1) != 0;
             const int mcount = meta >> 1;
             const bool open_leaf = has && !accept && leaf;
-            const bool open_node = has && !accept && !leaf;
+            // children sit on the next level, so their ids exceed the parent's:
+            // a descent that does not increase the id would be a corrupt tree
+            const bool bad_link = has && !accept && !leaf &&
+                                  (link <= node || mcount < 1 || mcount > 8 || link + mcount > nnodes);
+            if (bad_link) bad = true;
+            const bool open_node = has && !accept && !leaf && !bad_link;
 
             // ---- push the child ranges of opened internal nodes
             const unsigned om = __ballot_sync(NB_FULL, open_node);

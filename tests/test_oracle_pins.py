@@ -246,14 +246,27 @@ def test_tree_groups_partition(gal_tree):
         f, c = t.groups(G)
         assert np.all(c <= G) and np.all(c >= 1)
         assert f[0] == 0 and np.all(f[1:] == f[:-1] + c[:-1]) and f[-1] + c[-1] == t.n
-        # each group is a node whose parent holds more than G particles
-        key = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(nd["first"], nd["count"]))}
+        # each group is a run of consecutive siblings, each holding at most G,
+        # under a parent holding more than G; runs are packed greedily, so the
+        # next sibling after a run does not fit into it
+        by_first = {}
+        for i in range(nd["M"].size):
+            by_first.setdefault(int(nd["first"][i]), []).append(i)
         parent = np.full(nd["M"].size, -1)
         for i in np.flatnonzero(nd["nchild"] > 0):
             parent[nd["child"][i]:nd["child"][i] + nd["nchild"][i]] = i
         for a, b in zip(f, c):
-            i = key[(int(a), int(b))]
-            assert parent[i] < 0 or nd["count"][parent[i]] > G
+            # the deepest node starting at a whose parent holds more than G
+            cands = [i for i in by_first[int(a)] if parent[i] >= 0 and nd["count"][parent[i]] > G]
+            i = max(cands, key=lambda q: nd["level"][q])
+            par = parent[i]
+            sib = np.arange(nd["child"][par], nd["child"][par] + nd["nchild"][par])
+            k0 = int(np.flatnonzero(sib == i)[0])
+            tot, k = 0, k0
+            while k < sib.size and nd["count"][sib[k]] <= G and tot + nd["count"][sib[k]] <= G:
+                tot += nd["count"][sib[k]]
+                k += 1
+            assert tot == b, (a, b, tot)
 
 
 @pytest.mark.parametrize("mode", [oracle.MAC_PARTICLE_ACC, oracle.MAC_GROUP_ACC])
