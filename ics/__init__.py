@@ -271,6 +271,8 @@ def batched(nsys: int, seed: int, log2_min: float = 10.0, log2_max: float = 16.0
         parts.append(sub)
     out = {k: np.concatenate([p[k] for p in parts]) for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
     out["offsets"] = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    out["eps"] = (4.0 / sizes.astype(np.float64) ** (1.0 / 3.0)).astype(np.float32)
+    # eps_s = 4 / N_s^(1/3); an empty system gets eps = 1 (it has no particles)
+    out["eps"] = (4.0 / np.maximum(sizes, 1).astype(np.float64) ** (1.0 / 3.0)).astype(np.float32)
+    out["eps"][sizes == 0] = 1.0
     out["kind"] = kinds.astype(np.int32)
     return out

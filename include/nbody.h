@@ -74,7 +74,7 @@ typedef struct {
     int32_t ipl;         /* i-particles per lane of a walking warp: 1, 2 or 4 (2)   */
     int32_t list_depth;  /* interaction-list entries per warp, 64..1024, multiple
                             of 32 (default 256)                                    */
-    int32_t stack_depth; /* traversal stack entries per warp, 64..4096 (1024)       */
+    int32_t stack_depth; /* traversal stack entries per warp, 64..4096 (256)        */
     int32_t warps_per_block; /* walk warps per CTA, 1..16 (default 4)             */
     int32_t compensated; /* 1: per-flush partial sums added with Neumaier
                             compensation; 0: plain FP32 sums (default 0)          */

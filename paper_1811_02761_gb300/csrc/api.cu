@@ -298,7 +298,7 @@ nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
                  P<uint8_t>(c->gflag), c->grp_temp.p, P<int32_t>(c->grp_first),
                  P<int32_t>(c->grp_count), P<float4>(c->grp_sphere), P<int32_t>(c->grp_sys),
                  c->nsm);
-    c->kernels += 6 + 5;
+    c->kernels += 7 + 5;
     NB_CUDA(c, cudaGetLastError());
     return NBODY_OK;
 }
@@ -521,7 +521,7 @@ void nbody_config_default(nbody_config *c) {
     c->group_size = 64;
     c->ipl = 2;
     c->list_depth = 256;
-    c->stack_depth = 1024;
+    c->stack_depth = 256;
     c->warps_per_block = 4;
     c->compensated = 0;
     c->want_potential = 0;

@@ -14,19 +14,46 @@
 namespace nb {
 
 // ---------------------------------------------------------------- bounding cube
+// Per-system bounding box: each warp keeps running min/max while its chunks
+// stay in one system, the block merges its warps, and one set of atomics per
+// (block, system) publishes the result.
 template <typename T>
-__global__ void bbox_kernel(int64_t n, const T *__restrict__ x, const T *__restrict__ y,
-                            const T *__restrict__ z, const int64_t *__restrict__ off, int nsys,
-                            uint32_t *boxord) {
-    const unsigned lane = lane_id();
+__global__ void __launch_bounds__(256) bbox_kernel(int64_t n, const T *__restrict__ x,
+                                                   const T *__restrict__ y, const T *__restrict__ z,
+                                                   const int64_t *__restrict__ off, int nsys,
+                                                   uint32_t *boxord) {
+    __shared__ float sh_lo[8][3], sh_hi[8][3];
+    __shared__ int sh_s[8];
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const T *p[3] = {x, y, z};
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int cur = -1;
+    auto flush = [&](int s_) {
+        for (int a = 0; a < 3; a++)
+            for (int o = 16; o; o >>= 1) {
+                lo[a] = fminf(lo[a], __shfl_xor_sync(NB_FULL, lo[a], o));
+                hi[a] = fmaxf(hi[a], __shfl_xor_sync(NB_FULL, hi[a], o));
+            }
+        if (lane == 0 && s_ >= 0)
+            for (int a = 0; a < 3; a++) {
+                atomicMin(&boxord[s_ * 6 + a], f2ord(lo[a]));
+                atomicMax(&boxord[s_ * 6 + 3 + a], f2ord(hi[a]));
+            }
+        for (int a = 0; a < 3; a++) {
+            lo[a] = INFINITY;
+            hi[a] = -INFINITY;
+        }
+    };
     for (int64_t base = warp * 256; base < n; base += nwarps * 256) {
         int64_t last = (base + 256 < n ? base + 256 : n) - 1;
         int s0 = sys_of(off, nsys, base), s1 = sys_of(off, nsys, last);
         if (s0 == s1) {
-            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            if (s0 != cur) {
+                if (cur >= 0) flush(cur);
+                cur = s0;
+            }
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 int64_t i = base + k * 32 + lane;
@@ -37,21 +64,6 @@ __global__ void bbox_kernel(int64_t n, const T *__restrict__ x, const T *__restr
                         lo[a] = fminf(lo[a], v);
                         hi[a] = fmaxf(hi[a], v);
                     }
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    lo[a] = fminf(lo[a], __shfl_xor_sync(NB_FULL, lo[a], o));
-                    hi[a] = fmaxf(hi[a], __shfl_xor_sync(NB_FULL, hi[a], o));
-                }
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    atomicMin(&boxord[s0 * 6 + a], f2ord(lo[a]));
-                    atomicMax(&boxord[s0 * 6 + 3 + a], f2ord(hi[a]));
                 }
             }
         } else {
@@ -65,6 +77,44 @@ __global__ void bbox_kernel(int64_t n, const T *__restrict__ x, const T *__restr
                         atomicMax(&boxord[s * 6 + 3 + a], v);
                     }
                 }
+            }
+        }
+    }
+    // merge the warps of this block that ended in the same system
+    for (int a = 0; a < 3; a++)
+        for (int o = 16; o; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(NB_FULL, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(NB_FULL, hi[a], o));
+        }
+    if (lane == 0) {
+        sh_s[w] = cur;
+        for (int a = 0; a < 3; a++) {
+            sh_lo[w][a] = lo[a];
+            sh_hi[w][a] = hi[a];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int q = 0; q < nw; q++) {
+            int s = sh_s[q];
+            if (s < 0) continue;
+            float l3[3], h3[3];
+            for (int a = 0; a < 3; a++) {
+                l3[a] = sh_lo[q][a];
+                h3[a] = sh_hi[q][a];
+            }
+            for (int r = q + 1; r < nw; r++)
+                if (sh_s[r] == s) {
+                    for (int a = 0; a < 3; a++) {
+                        l3[a] = fminf(l3[a], sh_lo[r][a]);
+                        h3[a] = fmaxf(h3[a], sh_hi[r][a]);
+                    }
+                    sh_s[r] = -1;
+                }
+            for (int a = 0; a < 3; a++) {
+                atomicMin(&boxord[s * 6 + a], f2ord(l3[a]));
+                atomicMax(&boxord[s * 6 + 3 + a], f2ord(h3[a]));
             }
         }
     }

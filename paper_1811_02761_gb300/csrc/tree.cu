@@ -97,46 +97,40 @@ __global__ void __launch_bounds__(TB) leaflevel_kernel(Layout L, int cap,
     }
 }
 
-// One block: exclusive scan of each level's block counts; level offsets.
-__global__ void __launch_bounds__(1024) level_scan_kernel(int NL, uint32_t *blockcnt, int nblk,
-                                                          DevState *ds, int64_t cap_nodes) {
+// One block per level: exclusive scan of that level's block counts; the
+// level's node count goes to lvl_off[l + 1] (turned into offsets below).
+__global__ void __launch_bounds__(1024) level_scan_kernel(uint32_t *blockcnt, int nblk,
+                                                          DevState *ds) {
     __shared__ uint32_t sh[32];
-    __shared__ int32_t off;
-    if (threadIdx.x == 0) {
-        off = 0;
-        ds->lvl_off[0] = 0;
-    }
-    __syncthreads();
-    for (int l = 0; l < NL; l++) {
-        uint32_t carry = 0;
-        uint32_t *row = blockcnt + (int64_t)l * nblk;
-        for (int base = 0; base < nblk; base += 1024) {
-            int i = base + threadIdx.x;
-            uint32_t v = i < nblk ? row[i] : 0u;
-            uint32_t incl = (uint32_t)warp_incl_scan((int)v);
-            if (lane_id() == 31) sh[threadIdx.x >> 5] = incl;
-            __syncthreads();
-            if (threadIdx.x < 32) {
-                uint32_t t = sh[threadIdx.x];
-                t = (uint32_t)warp_incl_scan((int)t);
-                sh[threadIdx.x] = t;
-            }
-            __syncthreads();
-            uint32_t ex = incl - v + ((threadIdx.x >> 5) ? sh[(threadIdx.x >> 5) - 1] : 0u);
-            if (i < nblk) row[i] = carry + ex;
-            carry += sh[31];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            off += (int32_t)carry;
-            ds->lvl_off[l + 1] = off;
-        }
+    const int l = blockIdx.x;
+    uint32_t carry = 0;
+    uint32_t *row = blockcnt + (int64_t)l * nblk;
+    for (int base = 0; base < nblk; base += 1024) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < nblk ? row[i] : 0u;
+        uint32_t incl = (uint32_t)warp_incl_scan((int)v);
+        if (lane_id() == 31) sh[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x < 32) sh[threadIdx.x] = (uint32_t)warp_incl_scan((int)sh[threadIdx.x]);
+        __syncthreads();
+        uint32_t ex = incl - v + ((threadIdx.x >> 5) ? sh[(threadIdx.x >> 5) - 1] : 0u);
+        if (i < nblk) row[i] = carry + ex;
+        carry += sh[31];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        ds->nnodes = off;
-        if (off > cap_nodes) atomicOr(&ds->status, kStatusStackOverflow);
+    if (threadIdx.x == 0) ds->lvl_off[l + 1] = (int32_t)carry;
+}
+
+__global__ void level_offsets_kernel(int NL, DevState *ds, int64_t cap_nodes) {
+    if (threadIdx.x != 0) return;
+    int32_t off = 0;
+    ds->lvl_off[0] = 0;
+    for (int l = 0; l < NL; l++) {
+        off += ds->lvl_off[l + 1];
+        ds->lvl_off[l + 1] = off;
     }
+    ds->nnodes = off;
+    if (off > cap_nodes) atomicOr(&ds->status, kStatusStackOverflow);
 }
 
 // Writes every node: start, level, parent, first child / first particle and,
@@ -239,41 +233,49 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
     return (uint32_t)x;
 }
 
-// Cell of a node, widened by one finest cell on every side (covers the FP32
-// quantisation of member positions).
-struct Cell {
-    double lo[3], hi[3];
+// Centre and half-size of a node's cell, the half-size widened by one finest
+// cell (covers the FP32 quantisation of member positions).  FP32: the cell
+// side is the cube side scaled by an exact power of two.
+struct CellF {
+    float c[3];
+    float h;
 };
 
-__device__ __forceinline__ Cell node_cell(const Layout &L, uint64_t key, int level,
-                                          const SysBox *box) {
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+__device__ __forceinline__ CellF node_cell(const Layout &L, uint64_t key, int level,
+                                           const SysBox *box) {
     const int mbits = 3 * L.levels;
     int s = L.sysbits ? (int)(key >> mbits) : 0;
     SysBox b = box[s];
     uint64_t morton = mbits >= 64 ? key : (key & ((1ull << mbits) - 1ull));
     uint64_t prefix = morton >> (3 * (L.levels - level));
-    uint32_t c[3] = {compact3(prefix >> 2), compact3(prefix >> 1), compact3(prefix)};
-    double side = (double)b.L / (double)(1u << level);
-    double pad = (double)b.L / (double)(1u << L.levels);
-    double o[3] = {(double)b.x0, (double)b.y0, (double)b.z0};
-    Cell cell;
-    for (int a = 0; a < 3; a++) {
-        cell.lo[a] = o[a] + (double)c[a] * side - pad;
-        cell.hi[a] = o[a] + (double)(c[a] + 1) * side + pad;
-    }
+    uint32_t q[3] = {compact3(prefix >> 2), compact3(prefix >> 1), compact3(prefix)};
+    float side = b.L * pow2f(-level);
+    float o[3] = {b.x0, b.y0, b.z0};
+    CellF cell;
+    for (int a = 0; a < 3; a++) cell.c[a] = o[a] + ((float)q[a] + 0.5f) * side;
+    cell.h = 0.5f * side + b.L * pow2f(-L.levels);
     return cell;
 }
 
-__device__ __forceinline__ void write_node(int id, double cx, double cy, double cz, double M,
-                                           double b, float G, int link, int meta, float4 *nodeA,
+// Round-up factor for FP32 upper bounds (a few ulps of slack).
+constexpr float kUp = 1.0f + 0x1p-20f;
+
+__device__ __forceinline__ void write_node(int id, float cx, float cy, float cz, double M,
+                                           float b, float G, int link, int meta, float4 *nodeA,
                                            float4 *nodeB, Mom64 *mom64) {
-    float bf = __double2float_ru(b);
-    float q = __double2float_ru((double)G * M * (double)bf * (double)bf);
-    nodeA[id] = make_float4((float)cx, (float)cy, (float)cz, (float)M);
-    nodeB[id] = make_float4(bf, q, __int_as_float(link), __int_as_float(meta));
-    mom64[id] = make_Mom64(cx, cy, cz, M);
+    float q = __double2float_ru((double)G * M * (double)b * (double)b);
+    nodeA[id] = make_float4(cx, cy, cz, (float)M);
+    nodeB[id] = make_float4(b, q, __int_as_float(link), __int_as_float(meta));
+    mom64[id].w = M;
 }
 
+// Monopoles (centre of mass, mass) and node sizes b_J, bottom-up.  FP32 sums
+// relative to a reference point inside the node (first particle for leaves,
+// the cell centre for internal nodes) keep the error a few ulps of the node
+// size; masses are summed in FP64 (additions only).  b_J is rounded up so it
+// bounds the distance from the FP32 centre of mass to every member.
 __global__ void __launch_bounds__(256) moments_kernel(
     Layout L, const uint64_t *__restrict__ keys, const float4 *__restrict__ pos4,
     const SysBox *__restrict__ box, float G, DevState *ds,
@@ -284,35 +286,37 @@ __global__ void __launch_bounds__(256) moments_kernel(
     const int nn = ds->nnodes;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
         if (node_nchild[id] != 0) continue;
-        // leaf: FP64 sums over its particles
         const int first = node_link[id], cnt = node_count[id];
         if (first < 0 || cnt < 1 || (int64_t)first + cnt > L.n) {
             atomicOr(&ds_status(ds), kStatusBadTree);
             continue;
         }
-        double M = 0, sx = 0, sy = 0, sz = 0;
+        const float4 r0 = pos4[first];
+        double M = 0.0;
+        float mf = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f;
         for (int k = first; k < first + cnt; k++) {
-            float4 p = pos4[k];
+            const float4 p = pos4[k];
             M += (double)p.w;
-            sx += (double)p.w * (double)p.x;
-            sy += (double)p.w * (double)p.y;
-            sz += (double)p.w * (double)p.z;
+            mf += p.w;
+            sx = fmaf(p.w, p.x - r0.x, sx);
+            sy = fmaf(p.w, p.y - r0.y, sy);
+            sz = fmaf(p.w, p.z - r0.z, sz);
         }
-        double c[3];
-        if (M > 0) {
-            c[0] = sx / M; c[1] = sy / M; c[2] = sz / M;
+        float c[3];
+        if (mf > 0.0f) {
+            c[0] = r0.x + sx / mf; c[1] = r0.y + sy / mf; c[2] = r0.z + sz / mf;
         } else {
-            Cell cell = node_cell(L, keys[node_start[id]], node_level[id], box);
-            for (int a = 0; a < 3; a++) c[a] = 0.5 * (cell.lo[a] + cell.hi[a]);
+            CellF cell = node_cell(L, keys[node_start[id]], node_level[id], box);
+            for (int a = 0; a < 3; a++) c[a] = cell.c[a];
         }
-        double b2 = 0;
+        float b2 = 0.0f;
         for (int k = first; k < first + cnt; k++) {
-            float4 p = pos4[k];
-            double dx = (double)p.x - c[0], dy = (double)p.y - c[1], dz = (double)p.z - c[2];
-            b2 = fmax(b2, dx * dx + dy * dy + dz * dz);
+            const float4 p = pos4[k];
+            const float dx = p.x - c[0], dy = p.y - c[1], dz = p.z - c[2];
+            b2 = fmaxf(b2, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
         }
-        write_node(id, c[0], c[1], c[2], M, sqrt(b2), G, first, (cnt << 1) | 1, nodeA, nodeB,
-                   mom64);
+        write_node(id, c[0], c[1], c[2], M, __fsqrt_ru(b2) * kUp, G, first, (cnt << 1) | 1,
+                   nodeA, nodeB, mom64);
         // climb while this thread completes the last child of the parent
         int nd = id;
         for (;;) {
@@ -331,36 +335,38 @@ __global__ void __launch_bounds__(256) moments_kernel(
                 atomicOr(&ds_status(ds), kStatusBadTree);
                 break;
             }
-            double Mp = 0, px = 0, py = 0, pz = 0;
+            const CellF cell = node_cell(L, keys[node_start[par]], node_level[par], box);
+            double Mp = 0.0;
+            float mp = 0.0f, px = 0.0f, py = 0.0f, pz = 0.0f;
             int count = 0;
             for (int ch = c0; ch < c0 + nc; ch++) {
-                Mom64 mc = ldcg_mom(&mom64[ch]);
-                Mp += mc.w;
-                px += mc.w * mc.x;
-                py += mc.w * mc.y;
-                pz += mc.w * mc.z;
+                const float4 A = __ldcg(&nodeA[ch]);
+                Mp += __ldcg(&mom64[ch].w);
+                mp += A.w;
+                px = fmaf(A.w, A.x - cell.c[0], px);
+                py = fmaf(A.w, A.y - cell.c[1], py);
+                pz = fmaf(A.w, A.z - cell.c[2], pz);
                 count += __ldcg(&node_count[ch]);
             }
-            Cell cell = node_cell(L, keys[node_start[par]], node_level[par], box);
-            double cp[3];
-            if (Mp > 0) {
-                cp[0] = px / Mp; cp[1] = py / Mp; cp[2] = pz / Mp;
+            float cp[3];
+            if (mp > 0.0f) {
+                cp[0] = cell.c[0] + px / mp; cp[1] = cell.c[1] + py / mp; cp[2] = cell.c[2] + pz / mp;
             } else {
-                for (int a = 0; a < 3; a++) cp[a] = 0.5 * (cell.lo[a] + cell.hi[a]);
+                for (int a = 0; a < 3; a++) cp[a] = cell.c[a];
             }
-            double rec = 0;
+            float rec = 0.0f;
             for (int ch = c0; ch < c0 + nc; ch++) {
-                Mom64 mc = ldcg_mom(&mom64[ch]);
-                float bc = __ldcg(&nodeB[ch].x);
-                double dx = mc.x - cp[0], dy = mc.y - cp[1], dz = mc.z - cp[2];
-                rec = fmax(rec, sqrt(dx * dx + dy * dy + dz * dz) + (double)bc);
+                const float4 A = __ldcg(&nodeA[ch]);
+                const float bc = __ldcg(&nodeB[ch].x);
+                const float dx = A.x - cp[0], dy = A.y - cp[1], dz = A.z - cp[2];
+                rec = fmaxf(rec, __fadd_ru(__fsqrt_ru(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), bc));
             }
-            double c2 = 0;
+            float c2 = 0.0f;
             for (int a = 0; a < 3; a++) {
-                double e = fmax(cp[a] - cell.lo[a], cell.hi[a] - cp[a]);
-                c2 += e * e;
+                const float e = fabsf(cp[a] - cell.c[a]) + cell.h;
+                c2 = fmaf(e, e, c2);
             }
-            double bp = fmin(rec, sqrt(c2));
+            const float bp = fminf(rec, __fsqrt_ru(c2)) * kUp;
             node_count[par] = count;
             write_node(par, cp[0], cp[1], cp[2], Mp, bp, G, c0, nc << 1, nodeA, nodeB, mom64);
             nd = par;
@@ -383,7 +389,8 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
     const int nblk = (int)((L.n + TB - 1) / TB);
     uint32_t *blockcnt = (uint32_t *)temp;
     leaflevel_kernel<<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
-    level_scan_kernel<<<1, 1024, 0, s>>>(L.levels + 1, blockcnt, nblk, ds, cap_nodes);
+    level_scan_kernel<<<L.levels + 1, 1024, 0, s>>>(blockcnt, nblk, ds);
+    level_offsets_kernel<<<1, 32, 0, s>>>(L.levels + 1, ds, cap_nodes);
     cudaMemsetAsync(node_nchild, 0, (size_t)cap_nodes * sizeof(int32_t), s);
     nodes_kernel<<<nblk, TB, 0, s>>>(L, delta, leaflev, blockcnt, nblk, ds, cap_nodes, node_start,
                                      node_level, node_parent, node_link, node_count, node_nchild,

@@ -131,9 +131,12 @@ def test_tree_structure_and_moments(gen, n, cap):
     for c, k in ((0, "cx"), (1, "cy"), (2, "cz")):
         scale = np.maximum(np.abs(on[k][idx]), on["b"][idx] + 1e-3)
         assert np.all(np.abs(A[:, c] - on[k][idx]) <= 2e-6 * scale)
+    # b_J on the GPU bounds member distances from the FP32 centre of mass, so it
+    # may differ from the FP64 oracle's by a few FP32 ulps of the coordinates
     b_o = on["b"][idx]
-    assert np.all(B[:, 0] >= b_o * (1 - 1e-6))
-    assert np.all(B[:, 0] <= b_o * (1 + 1e-5) + 1e-6)
+    ulp = np.spacing(np.max(np.abs(A[:, :3]), axis=1).astype(np.float32)).astype(np.float64)
+    assert np.all(B[:, 0] >= b_o * (1 - 1e-6) - 2 * ulp)
+    assert np.all(B[:, 0] <= b_o * (1 + 1e-5) + 8 * ulp)
 
 
 def test_groups_bit_exact(plummer8k):
