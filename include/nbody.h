@@ -187,6 +187,25 @@ nbody_status nbody_diagnostics(nbody_ctx *ctx, int64_t n, const double *x, const
                                const float *vz, const float *m, const float *phi,
                                double *out);
 
+/* nbody_diagnostics without any device allocation (no counterpart in the
+ * paper: this serves callers that cannot call cudaMalloc -- for instance
+ * when a framework's caching allocator or a fixed arena already reserves the
+ * device memory, or when an allocation's implicit device-wide synchronisation
+ * is not acceptable inside a time-step loop).
+ * Same sums and result as nbody_diagnostics.  x, y, z (FP64), vx, vy, vz, m
+ * and phi (FP32, phi nullable) must be DEVICE pointers of n elements; out is
+ * 8 doubles, device or host.  Runs on cuda_stream (NULL = default stream)
+ * and synchronises it.  Its scratch is a fixed file-scope device array
+ * (1024 x 8 + 8 doubles, 65.6 KB per GPU, held until the process exits) that
+ * every call shares: calls that overlap on the GPU race on it.  The first
+ * call on a device looks up the array's device address; make that first call
+ * before any stream capture.  n must be in 1..2^31-1 (larger n: EINVAL).
+ * Errors: EINVAL (bad n, NULL or host input array), ECUDA. */
+nbody_status nbody_diagnostics_noalloc(int64_t n, const double *x, const double *y,
+                                       const double *z, const float *vx, const float *vy,
+                                       const float *vz, const float *m, const float *phi,
+                                       double *out, void *cuda_stream);
+
 /* Per-group cost log of the last walk: counts[g] = interaction-list entries
  * group g processed, groups in Morton order.  counts: int32 [cap] (host or
  * device); *n_groups receives the number of groups (may exceed cap: then

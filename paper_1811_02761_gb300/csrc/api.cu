@@ -19,6 +19,12 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+void nb::set_stateless_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;

@@ -207,6 +207,8 @@ void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *a
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
                         float *ay, float *az);
 size_t diag_temp_bytes();
+// Message returned by nbody_last_error(NULL, ...) on this thread.
+void set_stateless_error(const std::string &msg);
 void launch_diagnostics(cudaStream_t s, int64_t n, const double *x, const double *y,
                         const double *z, const float *vx, const float *vy, const float *vz,
                         const float *m, const float *phi, void *temp, double *d_out);

@@ -55,7 +55,8 @@ _lock = threading.Lock()
 EXPORTS = ("nbody_abi_version", "nbody_config_default", "nbody_create", "nbody_destroy",
            "nbody_set_config", "nbody_get_config", "nbody_build", "nbody_build_batched",
            "nbody_walk", "nbody_direct", "nbody_step", "nbody_step_batched", "nbody_diagnostics",
-           "nbody_get_group_costs", "nbody_export", "nbody_last_error")
+           "nbody_get_group_costs", "nbody_export", "nbody_last_error",
+           "nbody_diagnostics_noalloc")
 EXPORT_PERM, EXPORT_KEYS, EXPORT_NODE_LEVEL, EXPORT_NODE_START, EXPORT_NODE_COUNT, \
     EXPORT_NODE_PARENT, EXPORT_NODE_A, EXPORT_NODE_B, EXPORT_GROUP_FIRST, EXPORT_GROUP_COUNT, \
     EXPORT_GROUP_SPHERE, EXPORT_SYS_BOX = range(12)
@@ -97,6 +98,7 @@ def load(build_if_missing: bool = True):
             "nbody_step_batched": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                         f32, i32, C.POINTER(Stats)]),
             "nbody_diagnostics": (st, [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "nbody_diagnostics_noalloc": (st, [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "nbody_get_group_costs": (st, [vp, vp, i64, C.POINTER(i64)]),
             "nbody_export": (st, [vp, i32, vp, i64, C.POINTER(i64)]),
             "nbody_last_error": (st, [vp, C.c_char_p, C.c_size_t]),
@@ -273,6 +275,22 @@ def nbody_diagnostics(ctx, x, y, z, vx, vy, vz, m, phi=None) -> np.ndarray:
     _check(lib, ctx, lib.nbody_diagnostics(ctx, n, *d, *f, _ptr(phi, "float32", n, "phi", True),
                                            out.ctypes.data))
     return out
+
+
+def nbody_diagnostics_noalloc(x, y, z, vx, vy, vz, m, phi=None, out=None,
+                              stream=None) -> np.ndarray:
+    """FP64 diagnostics computed in the library's fixed scratch array, with no
+    device allocation; inputs must be device tensors.  `out` (8 doubles) may
+    be a device tensor or None (then a host array is returned)."""
+    lib = load()
+    n = _size(x)
+    res = np.zeros(8, np.float64) if out is None else out
+    d = [_ptr(a, "float64", n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"))]
+    f = [_ptr(a, "float32", n, nm) for a, nm in ((vx, "vx"), (vy, "vy"), (vz, "vz"), (m, "m"))]
+    _check(lib, None, lib.nbody_diagnostics_noalloc(n, *d, *f, _ptr(phi, "float32", n, "phi", True),
+                                                    _ptr(res, "float64", 8, "out"),
+                                                    _stream_ptr(stream)))
+    return res
 
 
 def nbody_get_group_costs(ctx, counts) -> int:
