@@ -59,9 +59,9 @@ __global__ void __launch_bounds__(DT) direct_kernel(int64_t n, const float *__re
             const float4 q = tile[k];
             const float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-            float rinv = rsqrtf(r2);
+            float rinv = rsqrt_fast(r2);
             if constexpr (COMP) rinv = rinv * (1.5f - 0.5f * r2 * rinv * rinv);
-            if constexpr (SAFE) rinv = r2 > 0.0f ? rinv : 0.0f;
+            if constexpr (SAFE) rinv = r2 >= 1.17549435e-38f ? rinv : 0.0f;
             const float mr = q.w * rinv;
             const float w3 = mr * rinv * rinv;
             T[0] = fmaf(w3, dx, T[0]);
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(DT) direct_kernel(int64_t n, const float *__re
         if (PHI) {
             float self = 0.0f;
             if (!SAFE) {
-                float rs = rsqrtf(eps2);
+                float rs = rsqrt_fast(eps2);
                 if (COMP) rs = rs * (1.5f - 0.5f * eps2 * rs * rs);
                 self = m[i] * rs;  // the j = i term, excluded by Eq. 1
             }

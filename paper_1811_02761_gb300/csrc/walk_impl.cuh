@@ -36,7 +36,10 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
     s = t;
 }
 
-template <int IPL, bool PHI, bool COMP, bool SAFE>
+// Eq. 1 for the first NQ i-slots of every lane against the nl list entries.
+// NQ = ceil(group size / 32) <= IPL, so a small group does not pay for the
+// lane slots it leaves empty.
+template <int NQ, int IPL, bool PHI, bool COMP, bool SAFE>
 __device__ __forceinline__ void flush_list(const float4 *list, int nl, float eps2,
                                            const float (&xi)[IPL], const float (&yi)[IPL],
                                            const float (&zi)[IPL], float (&acc)[IPL][4],
@@ -51,11 +54,11 @@ __device__ __forceinline__ void flush_list(const float4 *list, int nl, float eps
     for (int k = 0; k < nl; k++) {
         const float4 p = list[k];
 #pragma unroll
-        for (int q = 0; q < IPL; q++) {
+        for (int q = 0; q < NQ; q++) {
             const float dx = p.x - xi[q], dy = p.y - yi[q], dz = p.z - zi[q];
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-            float rinv = rsqrtf(r2);
-            if constexpr (SAFE) rinv = r2 > 0.0f ? rinv : 0.0f;
+            float rinv = rsqrt_fast(r2);
+            if constexpr (SAFE) rinv = r2 >= 1.17549435e-38f ? rinv : 0.0f;
             const float mr = p.w * rinv;
             const float w3 = mr * rinv * rinv;
             T[q][0] = fmaf(w3, dx, T[q][0]);
@@ -66,9 +69,27 @@ __device__ __forceinline__ void flush_list(const float4 *list, int nl, float eps
     }
     if constexpr (COMP) {
 #pragma unroll
-        for (int q = 0; q < IPL; q++)
+        for (int q = 0; q < NQ; q++)
 #pragma unroll
             for (int c = 0; c < 4; c++) neumaier_add(acc[q][c], cmp[q][c], part[q][c]);
+    }
+}
+
+template <int IPL, bool PHI, bool COMP, bool SAFE>
+__device__ __forceinline__ void flush_group(int cnt, const float4 *list, int nl, float eps2,
+                                            const float (&xi)[IPL], const float (&yi)[IPL],
+                                            const float (&zi)[IPL], float (&acc)[IPL][4],
+                                            float (&cmp)[IPL][4]) {
+    if constexpr (IPL == 1) {
+        flush_list<1, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+    } else if constexpr (IPL == 2) {
+        if (cnt <= 32) flush_list<1, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+        else flush_list<2, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+    } else {
+        if (cnt <= 32) flush_list<1, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+        else if (cnt <= 64) flush_list<2, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+        else if (cnt <= 96) flush_list<3, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+        else flush_list<4, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
     }
 }
 
@@ -160,7 +181,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
                 B = __ldg(&a.nodeB[node]);
             }
             const float dx = A.x - sph.x, dy = A.y - sph.y, dz = A.z - sph.z;
-            const float d = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) - sph.w;
+            const float d = sqrt_fast(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) - sph.w;
             bool accept;
             if (geometric) {
                 accept = has && d > B.x && B.x <= a.theta * d;
@@ -198,7 +219,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
             const int na = __popc(am);
             if (nl + na > D) {
                 __syncwarp();
-                flush_list<IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+                flush_group<IPL, PHI, COMP, SAFE>(cnt, list, nl, eps2, xi, yi, zi, acc, cmp);
                 entries += nl;
                 nl = 0;
                 __syncwarp();
@@ -221,7 +242,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
                     const int c = (pc - off) < 32 ? (pc - off) : 32;
                     if (nl + c > D) {
                         __syncwarp();
-                        flush_list<IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+                        flush_group<IPL, PHI, COMP, SAFE>(cnt, list, nl, eps2, xi, yi, zi, acc, cmp);
                         entries += nl;
                         nl = 0;
                         __syncwarp();
@@ -234,7 +255,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
         }
         if (nl > 0) {
             __syncwarp();
-            flush_list<IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+            flush_group<IPL, PHI, COMP, SAFE>(cnt, list, nl, eps2, xi, yi, zi, acc, cmp);
             entries += nl;
             nl = 0;
         }
@@ -242,7 +263,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
 
         // ---- results (G applied once; the potential's self term removed)
         const float G = a.G;
-        const float self = SAFE ? 0.0f : rsqrtf(eps2);
+        const float self = SAFE ? 0.0f : rsqrt_fast(eps2);
 #pragma unroll
         for (int q = 0; q < IPL; q++) {
             const int k = lane + 32 * q;
