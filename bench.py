@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("galaxy", "batched"), default="galaxy",
+                    help="galaxy: N=2^23 three-component galaxy (the headline); batched: 512 "
+                         "independent Plummer/Hernquist systems, one forest per step")
+    ap.add_argument("--nsys", type=int, default=512)
+    ap.add_argument("--per-system-steps", type=int, default=2,
+                    help="batched: steps timed for the one-call-per-system comparison")
     ap.add_argument("--n", type=int, default=1 << 23)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=4)
@@ -293,6 +299,106 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
+# ---------------------------------------------------------------------------- batched workload
+def run_batched(args, rank, world, local_rank):
+    """512 independent systems: one forest + one persistent walk per step
+    (CUDA graph of two steps) against one nbody_step call per system.  With N
+    ranks every rank takes whole systems (round robin by size), no collective."""
+    import torch
+    import torch.distributed as dist
+
+    import ics
+    import paper_1811_02761_gb300 as nb
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_1811_02761_gb300.sharding import local_csr, partition_systems
+    full = ics.batched(args.nsys, 4)
+    mine = partition_systems(np.diff(full["offsets"]), world)[rank]
+    off, idx = local_csr(full["offsets"], mine)
+    parts = {k: full[k][idx] for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
+    sizes = np.diff(off)
+    eps = full["eps"][mine]
+    n = int(off[-1])
+
+    def D(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    X = [D(parts[k].astype(np.float64)) for k in ("x", "y", "z")]
+    V = [D(parts[k]) for k in ("vx", "vy", "vz")]
+    M = D(parts["m"])
+    A = [torch.zeros(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    stream = torch.cuda.current_stream(dev)
+    cfg = nb.nbody_config_default(delta_acc=DACC, use_graph=1)
+    ctx = nb.nbody_create(cfg, stream)
+    try:
+        # initial accelerations: bootstrap walk of the forest
+        nb.nbody_build_batched(ctx, off, eps, *[D(parts[k]) for k in ("x", "y", "z")], M)
+        nb.nbody_walk(ctx, None, *A)
+        nb.nbody_step_batched(ctx, off, eps, *X, *V, M, *A, DT, max(args.warmup, 2))
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st = nb.nbody_step_batched(ctx, off, eps, *X, *V, M, *A, DT, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+    finally:
+        nb.nbody_destroy(ctx)
+    # the same systems, one nbody_step call per system and step
+    ctx = nb.nbody_create(nb.nbody_config_default(delta_acc=DACC), stream)
+    try:
+        def one_pass(k):
+            for j in range(len(sizes)):
+                a, b = int(off[j]), int(off[j + 1])
+                c2 = nb.nbody_config_default(delta_acc=DACC, eps=float(eps[j]))
+                nb.nbody_set_config(ctx, c2)
+                nb.nbody_step(ctx, *[t[a:b] for t in X], *[t[a:b] for t in V], M[a:b],
+                              *[t[a:b] for t in A], DT, k)
+        one_pass(1)
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        one_pass(args.per_system_steps)
+        torch.cuda.synchronize(dev)
+        per_sys = (time.perf_counter() - w0) / args.per_system_steps
+    finally:
+        nb.nbody_destroy(ctx)
+    t = torch.tensor([elapsed, float(st.interactions)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        t[0] = tm[0]
+    if rank != 0:
+        return None
+    elapsed_max, inter_all = float(t[0].item()), float(t[1].item())
+    s_per_step = elapsed_max / args.steps
+    return {
+        "metric": METRIC, "value": inter_all / elapsed_max / 1e9, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_per_step * 1e3,
+        "s_per_step": s_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Plummer/Hernquist systems)",
+        "config": {"workload": f"batched: {args.nsys} independent Plummer/Hernquist systems, "
+                               f"N_s = 2^(10+6U), eps_s = 4/N_s^(1/3), delta_acc=2^-9, "
+                               f"leapfrog dt=1/256; one forest and one persistent walk per step, "
+                               f"CUDA graph of two steps",
+                   "systems_this_rank": int(len(sizes)), "n_this_rank": n,
+                   "parallelism": f"whole systems per rank x{world}",
+                   "l2": "inputs larger than L2 (~8M particles)"},
+        "per_system_launches": {"s_per_step": per_sys,
+                                "note": "one nbody_step call (build + walk + kicks) per system "
+                                        "and step, eager launches"},
+        "speedup_vs_per_system": per_sys / s_per_step,
+        "interactions_per_step": float(st.interactions) / args.steps,
+        "gpu_launches": int(st.kernels),
+    }
+
+
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -349,7 +455,10 @@ def main():
             import torch.distributed as dist
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl")
-        out = run_ours(args, rank, world, local_rank)
+        if args.workload == "batched":
+            out = run_batched(args, rank, world, local_rank)
+        else:
+            out = run_ours(args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

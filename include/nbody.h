@@ -80,6 +80,9 @@ typedef struct {
                             compensation; 0: plain FP32 sums (default 0)          */
     int32_t want_potential; /* 1: also accumulate phi (default 0)                 */
     int32_t schedule;    /* nbody_schedule (default NBODY_SCHED_MORTON)             */
+    int32_t use_graph;   /* 1: nbody_step(_batched) replays a CUDA graph of two
+                            steps (captured on first use, on an internal stream
+                            ordered after cuda_stream); 0: eager launches (0)  */
 } nbody_config;
 
 typedef struct {

@@ -30,6 +30,17 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// What a captured step graph depends on: sizes, parameters and the buffers
+// its kernels were captured with.
+struct GraphKey {
+    int64_t n;
+    int32_t nsys;
+    float dt;
+    bool safe;
+    nbody_config cfg;
+    const void *bufs[8];
+};
+
 }  // namespace
 
 struct nbody_ctx {
@@ -67,6 +78,12 @@ struct nbody_ctx {
     int wev_used = 0;
     std::vector<cudaEvent_t> evpool;  // phase boundaries of asynchronous multi-step calls
     int evused = 0;
+    // CUDA graph of two leapfrog steps (nbody_config.use_graph)
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey{};
+    int64_t gkernels = 0;
+    bool capturing = false;  // enqueueing into a graph: no timing events
     int64_t kernels = 0;           // kernels launched by the current call
     bool built = false;
     bool eps_zero = false;  // some system of the last build has eps == 0
@@ -475,7 +492,7 @@ nbody_status run_walk(nbody_ctx *c, bool geometric, bool phi, bool safe, const i
                            P<float>(c->grp_alpha), c->nsm);
         c->kernels += 1;
     }
-    while ((int)c->wev.size() < c->wev_used + 2) {
+    while (!c->capturing && (int)c->wev.size() < c->wev_used + 2) {
         cudaEvent_t ev;
         NB_CUDA(c, cudaEventCreate(&ev));
         c->wev.push_back(ev);
@@ -487,11 +504,13 @@ nbody_status run_walk(nbody_ctx *c, bool geometric, bool phi, bool safe, const i
     a.az = az;
     a.phi = ph;
     a.acc_sorted = acc_sorted;
-    NB_CUDA(c, cudaEventRecord(c->wev[c->wev_used], c->stream));
+    if (!c->capturing) NB_CUDA(c, cudaEventRecord(c->wev[c->wev_used], c->stream));
     cudaError_t e = launch_walk(c->stream, a, walk_shape(c, geometric, phi, safe), c->nsm);
     if (e != cudaSuccess) return cuda_fail(c, e, "walk launch");
-    NB_CUDA(c, cudaEventRecord(c->wev[c->wev_used + 1], c->stream));
-    c->wev_used += 2;
+    if (!c->capturing) {
+        NB_CUDA(c, cudaEventRecord(c->wev[c->wev_used + 1], c->stream));
+        c->wev_used += 2;
+    }
     c->kernels += 1;
     return NBODY_OK;
 }
@@ -502,6 +521,7 @@ float collect_walk_ms(nbody_ctx *c, int *launches) {
     for (int k = 0; k + 1 < c->wev_used; k += 2) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, c->wev[k], c->wev[k + 1]) == cudaSuccess) t += ms;
+        else cudaGetLastError();  // a timing query must not leave an error behind
     }
     *launches = c->wev_used / 2;
     c->wev_used = 0;
@@ -532,6 +552,7 @@ void nbody_config_default(nbody_config *c) {
     c->compensated = 0;
     c->want_potential = 0;
     c->schedule = NBODY_SCHED_MORTON;
+    c->use_graph = 0;
 }
 
 nbody_status nbody_create(nbody_ctx **out, const nbody_config *cfg, void *cuda_stream) {
@@ -572,6 +593,8 @@ nbody_status nbody_destroy(nbody_ctx *ctx) {
     for (auto &ev : ctx->ev)
         if (ev) cudaEventDestroy(ev);
     for (auto ev : ctx->wev) cudaEventDestroy(ev);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     for (auto ev : ctx->evpool) cudaEventDestroy(ev);
     delete ctx;
     return NBODY_OK;
@@ -659,7 +682,7 @@ nbody_status nbody_walk(nbody_ctx *ctx, const float *a_old, float *ax, float *ay
     NB_CUDA(ctx, stage_out_finish(ctx, phi, dph, fb));
     st = read_status(ctx);
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    if (cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]) != cudaSuccess) cudaGetLastError();
     ctx->last.n_groups = ctx->h_ds->ngroups;
     ctx->last.interactions = (int64_t)ctx->h_ds->interactions;
     ctx->last.list_entries = (int64_t)ctx->h_ds->list_entries;
@@ -769,31 +792,107 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
                       (const float *)in[9], S[0], acc);
     ctx->kernels += 1;
     int cur = 0;
-    std::vector<int> marks;  // per step: event indices (build start, build end, walk end)
-    for (int it = 0; it < nsteps; it++) {
-        launch_kick_drift(s, n, S[cur], acc, 0.5f * dt, dt);
+    std::vector<int> marks;  // per eager step: event indices (build start, build end, walk end)
+
+    // One leapfrog step enqueued on ctx->stream.  With `timing`, phase
+    // boundaries are recorded with pool events (eager steps only).
+    auto one_step = [&](bool timing) -> nbody_status {
+        cudaStream_t q = ctx->stream;
+        launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt);
         ctx->kernels += 1;
-        cudaEvent_t e0, e1, e2;
-        NB_CUDA(ctx, pool_event(ctx, &e0));
-        NB_CUDA(ctx, cudaEventRecord(e0, s));
-        st = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
-        if (st != NBODY_OK) return st;
-        launch_permute_state(s, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur], P<float4>(ctx->pos4));
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+        if (timing) {
+            NB_CUDA(ctx, pool_event(ctx, &e0));
+            NB_CUDA(ctx, cudaEventRecord(e0, q));
+        }
+        nbody_status r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
+        if (r != NBODY_OK) return r;
+        launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur], P<float4>(ctx->pos4));
         ctx->kernels += 1;
         cur = 1 - cur;
-        st = build_tree_groups(ctx, L);
-        if (st != NBODY_OK) return st;
-        NB_CUDA(ctx, pool_event(ctx, &e1));
-        NB_CUDA(ctx, cudaEventRecord(e1, s));
-        NB_CUDA(ctx, cudaMemcpyAsync(ctx->aold_s.p, S[cur].aold, fb, cudaMemcpyDeviceToDevice, s));
-        st = run_walk(ctx, false, false, safe, nullptr, nullptr, nullptr, nullptr, nullptr, acc,
-                      false);
-        if (st != NBODY_OK) return st;
-        NB_CUDA(ctx, pool_event(ctx, &e2));
-        NB_CUDA(ctx, cudaEventRecord(e2, s));
-        launch_kick(s, n, S[cur], acc, 0.5f * dt);
+        r = build_tree_groups(ctx, L);
+        if (r != NBODY_OK) return r;
+        if (timing) {
+            NB_CUDA(ctx, pool_event(ctx, &e1));
+            NB_CUDA(ctx, cudaEventRecord(e1, q));
+        }
+        NB_CUDA(ctx, cudaMemcpyAsync(ctx->aold_s.p, S[cur].aold, fb, cudaMemcpyDeviceToDevice, q));
+        r = run_walk(ctx, false, false, safe, nullptr, nullptr, nullptr, nullptr, nullptr, acc, false);
+        if (r != NBODY_OK) return r;
+        if (timing) {
+            NB_CUDA(ctx, pool_event(ctx, &e2));
+            NB_CUDA(ctx, cudaEventRecord(e2, q));
+            marks.push_back(ctx->evused - 3);
+        }
+        launch_kick(q, n, S[cur], acc, 0.5f * dt);
         ctx->kernels += 1;
-        marks.push_back(ctx->evused - 3);
+        return NBODY_OK;
+    };
+
+    int eager = nsteps;
+    if (ctx->cfg.use_graph && nsteps >= 2) {
+        // Two steps per graph: the sort's ping-pong buffers and the state
+        // copies swap roles every step, so after two steps every pointer is
+        // back where the capture found it and the graph can be replayed.
+        GraphKey key;
+        std::memset(&key, 0, sizeof key);  // padding too: keys are compared bytewise
+        key.n = n;
+        key.nsys = nsys;
+        key.dt = dt;
+        key.safe = safe;
+        key.cfg = ctx->cfg;
+        key.bufs[0] = ctx->keys.p;
+        key.bufs[1] = ctx->vals.p;
+        key.bufs[2] = S[0].x;
+        key.bufs[3] = ctx->nodeA.p;
+        key.bufs[4] = ctx->grp_first.p;
+        key.bufs[5] = ctx->rs_temp.p;
+        key.bufs[6] = ctx->pos4.p;
+        key.bufs[7] = ctx->acc_s.p;
+        if (!ctx->gstream)
+            NB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+        if (!ctx->gexec || std::memcmp(&key, &ctx->gkey, sizeof key) != 0) {
+            if (ctx->gexec) {
+                cudaGraphExecDestroy(ctx->gexec);
+                ctx->gexec = nullptr;
+            }
+            cudaStream_t saved = ctx->stream;
+            ctx->stream = ctx->gstream;
+            ctx->capturing = true;
+            int64_t k0 = ctx->kernels;
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed);
+            nbody_status r1 = NBODY_OK, r2 = NBODY_OK;
+            if (ce == cudaSuccess) {
+                r1 = one_step(false);
+                if (r1 == NBODY_OK) r2 = one_step(false);
+                cudaError_t ee = cudaStreamEndCapture(ctx->gstream, &graph);
+                if (ce == cudaSuccess) ce = ee;
+            }
+            ctx->stream = saved;
+            ctx->capturing = false;
+            if (r1 != NBODY_OK) return r1;
+            if (r2 != NBODY_OK) return r2;
+            if (ce == cudaSuccess) ce = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return cuda_fail(ctx, ce, "step graph capture");
+            ctx->gkernels = ctx->kernels - k0;
+            ctx->kernels = k0;
+            ctx->gkey = key;
+        }
+        NB_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
+        NB_CUDA(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev[0], 0));
+        for (int it = 0; it + 1 < nsteps; it += 2) {
+            NB_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->gstream));
+            ctx->kernels += ctx->gkernels;
+        }
+        NB_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->gstream));
+        NB_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev[1], 0));
+        eager = nsteps % 2;
+    }
+    for (int it = 0; it < eager; it++) {
+        st = one_step(true);
+        if (st != NBODY_OK) return st;
     }
     // in[] are the device copies (the caller's arrays themselves when on the device)
     launch_store_state(s, n, S[cur], acc, (double *)in[0], (double *)in[1], (double *)in[2],
@@ -809,8 +908,11 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     float ms_build = 0.0f, ms_walk = 0.0f;
     for (int k : marks) {
         float a = 0, b = 0;
-        cudaEventElapsedTime(&a, ctx->evpool[k], ctx->evpool[k + 1]);
-        cudaEventElapsedTime(&b, ctx->evpool[k + 1], ctx->evpool[k + 2]);
+        if (cudaEventElapsedTime(&a, ctx->evpool[k], ctx->evpool[k + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&b, ctx->evpool[k + 1], ctx->evpool[k + 2]) != cudaSuccess) {
+            cudaGetLastError();
+            a = b = 0.0f;
+        }
         ms_build += a;
         ms_walk += b;
     }

@@ -34,7 +34,8 @@ class Config(C.Structure):
                 ("theta", C.c_float), ("leaf_cap", C.c_int32), ("group_size", C.c_int32),
                 ("ipl", C.c_int32), ("list_depth", C.c_int32), ("stack_depth", C.c_int32),
                 ("warps_per_block", C.c_int32), ("compensated", C.c_int32),
-                ("want_potential", C.c_int32), ("schedule", C.c_int32)]
+                ("want_potential", C.c_int32), ("schedule", C.c_int32),
+                ("use_graph", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -356,3 +356,30 @@ def test_bad_arguments_rejected_on_gpu():
         assert e.value.status == nb.NBODY_EINVAL
     finally:
         nb.nbody_destroy(ctx)
+
+
+# --------------------------------------------------------------------------- CUDA graph
+@pytest.mark.parametrize("nsteps", [4, 5])
+def test_step_graph_equals_eager(nsteps):
+    """The two-step CUDA graph replays exactly the eager launch sequence."""
+    sizes = [3000, 1, 700, 5000]
+    b = ics.batched(len(sizes), 9, sizes=sizes)
+    n = int(b["offsets"][-1])
+    res = []
+    for graph in (0, 1):
+        ctx = nb.nbody_create(nb.nbody_config_default(delta_acc=DACC, use_graph=graph))
+        try:
+            X = [dev(b[k].astype(np.float64)) for k in ("x", "y", "z")]
+            V = [dev(b[k]) for k in ("vx", "vy", "vz")]
+            A = [torch.zeros(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+            m = dev(b["m"])
+            nb.nbody_step_batched(ctx, b["offsets"], b["eps"], *X, *V, m, *A, 1.0 / 256, 1)
+            st = nb.nbody_step_batched(ctx, b["offsets"], b["eps"], *X, *V, m, *A, 1.0 / 256, nsteps)
+            # a second call replays the cached graph
+            st2 = nb.nbody_step_batched(ctx, b["offsets"], b["eps"], *X, *V, m, *A, 1.0 / 256, nsteps)
+            res.append([host(t) for t in X + V + A] + [st.interactions, st2.interactions])
+        finally:
+            nb.nbody_destroy(ctx)
+    for a, g in zip(res[0][:-2], res[1][:-2]):
+        assert np.array_equal(a, g)
+    assert res[0][-2:] == res[1][-2:]
