@@ -216,6 +216,38 @@ nbody_status nbody_diagnostics_noalloc(int64_t n, const double *x, const double 
 nbody_status nbody_get_group_costs(nbody_ctx *ctx, int32_t *counts, int64_t cap,
                                    int64_t *n_groups);
 
+/* Autotuner search space (the analogue of the paper's micro-benchmarked
+ * thread-block configuration, Sect. 2.2 Table 2).  Each list holds n_*
+ * candidates; combinations violating the config rules (leaf_cap <=
+ * group_size <= 32 ipl, group_size > 16 ipl) are skipped. */
+typedef struct {
+    int32_t n_leaf_cap, leaf_cap[4];
+    int32_t n_group_size, group_size[6];
+    int32_t n_ipl, ipl[3];
+    int32_t n_list_depth, list_depth[4];
+    int32_t n_warps_per_block, warps_per_block[4];
+    int32_t repeats;            /* timed walks per candidate (the minimum counts) */
+} nbody_tune_space;
+
+/* Default space: leaf_cap {8, 16}, group_size {32, 64, 128}, ipl {1, 2, 4},
+ * list_depth {128, 256}, warps_per_block {2, 4, 8}, repeats 2. */
+void nbody_tune_space_default(nbody_tune_space *space);
+
+/* Grid search over `space` for the fastest build + walk of the given systems
+ * (nsys = 1 and offsets = NULL for one system; arrays as in
+ * nbody_build_batched, a_old as in nbody_walk).  Every candidate is timed
+ * with CUDA events on the context's stream: build once per (leaf_cap,
+ * group_size), walk `repeats` times per (ipl, list_depth, warps_per_block).
+ * The context keeps the best configuration; *best receives it, *best_ms its
+ * build + walk time and *n_tried the number of timed candidates (all three
+ * nullable).  The context's other parameters (G, eps, delta_acc, ...) are
+ * kept.  Errors: EINVAL, ENOMEM, EOVERFLOW, ECUDA. */
+nbody_status nbody_autotune(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
+                            const float *eps_sys, const float *x, const float *y,
+                            const float *z, const float *m, const float *a_old,
+                            const nbody_tune_space *space, nbody_config *best, float *best_ms,
+                            int32_t *n_tried);
+
 /* Internal arrays of the last build, for inspection and testing. */
 typedef enum {
     NBODY_EXPORT_PERM = 0,         /* int32 [n]: caller index of sorted particle k  */

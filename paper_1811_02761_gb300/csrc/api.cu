@@ -998,6 +998,111 @@ nbody_status nbody_get_group_costs(nbody_ctx *ctx, int32_t *counts, int64_t cap,
     return NBODY_OK;
 }
 
+void nbody_tune_space_default(nbody_tune_space *sp) {
+    if (!sp) return;
+    std::memset(sp, 0, sizeof *sp);
+    sp->n_leaf_cap = 2;
+    sp->leaf_cap[0] = 8;
+    sp->leaf_cap[1] = 16;
+    sp->n_group_size = 3;
+    sp->group_size[0] = 32;
+    sp->group_size[1] = 64;
+    sp->group_size[2] = 128;
+    sp->n_ipl = 3;
+    sp->ipl[0] = 1;
+    sp->ipl[1] = 2;
+    sp->ipl[2] = 4;
+    sp->n_list_depth = 2;
+    sp->list_depth[0] = 128;
+    sp->list_depth[1] = 256;
+    sp->n_warps_per_block = 3;
+    sp->warps_per_block[0] = 2;
+    sp->warps_per_block[1] = 4;
+    sp->warps_per_block[2] = 8;
+    sp->repeats = 2;
+}
+
+nbody_status nbody_autotune(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
+                            const float *eps_sys, const float *x, const float *y,
+                            const float *z, const float *m, const float *a_old,
+                            const nbody_tune_space *space, nbody_config *best, float *best_ms,
+                            int32_t *n_tried) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    nbody_tune_space sp;
+    if (space) sp = *space; else nbody_tune_space_default(&sp);
+    if (sp.n_leaf_cap < 1 || sp.n_leaf_cap > 4 || sp.n_group_size < 1 || sp.n_group_size > 6 ||
+        sp.n_ipl < 1 || sp.n_ipl > 3 || sp.n_list_depth < 1 || sp.n_list_depth > 4 ||
+        sp.n_warps_per_block < 1 || sp.n_warps_per_block > 4 || sp.repeats < 1)
+        return fail(ctx, NBODY_EINVAL, "bad tune space");
+    if (nsys < 1) return fail(ctx, NBODY_EINVAL, "nsys must be >= 1");
+    int64_t n = 0;
+    if (nsys == 1 && !offsets) {
+        return fail(ctx, NBODY_EINVAL, "offsets is NULL (pass {0, n} for one system)");
+    }
+    nbody_status st = check_systems(ctx, nsys, offsets, eps_sys);
+    if (st != NBODY_OK) return st;
+    n = offsets[nsys];
+    const nbody_config base = ctx->cfg;
+    nbody_config bestc = base;
+    float bestt = INFINITY;
+    int tried = 0;
+    // outputs of the timed walks (device scratch owned by the context)
+    cudaError_t e = ensure(ctx->stage[9], (size_t)n * 4);
+    if (e == cudaSuccess) e = ensure(ctx->stage[10], (size_t)n * 4);
+    if (e == cudaSuccess) e = ensure(ctx->stage[11], (size_t)n * 4);
+    if (e != cudaSuccess) return fail(ctx, NBODY_ENOMEM, "allocation");
+    float *o0 = P<float>(ctx->stage[9]), *o1 = P<float>(ctx->stage[10]), *o2 = P<float>(ctx->stage[11]);
+    for (int il = 0; il < sp.n_leaf_cap; il++)
+        for (int ig = 0; ig < sp.n_group_size; ig++)
+            for (int ii = 0; ii < sp.n_ipl; ii++) {
+                nbody_config c = base;
+                c.leaf_cap = sp.leaf_cap[il];
+                c.group_size = sp.group_size[ig];
+                c.ipl = sp.ipl[ii];
+                if (c.group_size <= 16 * c.ipl) continue;  // wastes half the i-slots
+                std::string why;
+                c.list_depth = sp.list_depth[0];
+                c.warps_per_block = sp.warps_per_block[0];
+                if (!config_ok(&c, why)) continue;
+                ctx->cfg = c;
+                st = nbody_build_batched(ctx, nsys, offsets, eps_sys, x, y, z, m);
+                if (st != NBODY_OK) { ctx->cfg = base; return st; }
+                const float tb = ctx->last.ms_build;
+                for (int id = 0; id < sp.n_list_depth; id++)
+                    for (int iw = 0; iw < sp.n_warps_per_block; iw++) {
+                        nbody_config cw = c;
+                        cw.list_depth = sp.list_depth[id];
+                        cw.warps_per_block = sp.warps_per_block[iw];
+                        if (!config_ok(&cw, why)) continue;
+                        ctx->cfg = cw;  // walk-only parameters: the build stays valid
+                        float tw = INFINITY;
+                        for (int r = 0; r < sp.repeats; r++) {
+                            nbody_stats s2;
+                            st = nbody_walk(ctx, a_old, o0, o1, o2, nullptr, &s2);
+                            if (st == NBODY_EOVERFLOW) break;  // too shallow a stack: skip
+                            if (st != NBODY_OK) { ctx->cfg = base; return st; }
+                            tw = std::min(tw, s2.ms_walk_kernel);
+                        }
+                        if (st == NBODY_EOVERFLOW) continue;
+                        tried++;
+                        if (tb + tw < bestt) {
+                            bestt = tb + tw;
+                            bestc = cw;
+                        }
+                    }
+            }
+    if (!tried) {
+        ctx->cfg = base;
+        return fail(ctx, NBODY_EINVAL, "no valid candidate in the tune space");
+    }
+    ctx->cfg = bestc;
+    ctx->built = false;  // the last build used another candidate
+    if (best) *best = bestc;
+    if (best_ms) *best_ms = bestt;
+    if (n_tried) *n_tried = tried;
+    return NBODY_OK;
+}
+
 nbody_status nbody_export(nbody_ctx *ctx, int32_t what, void *dst, int64_t cap, int64_t *count) {
     if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
     if (!count || cap < 0 || (cap > 0 && !dst)) return fail(ctx, NBODY_EINVAL, "bad argument");

@@ -41,6 +41,15 @@ class Config(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneSpace(C.Structure):
+    _fields_ = [("n_leaf_cap", C.c_int32), ("leaf_cap", C.c_int32 * 4),
+                ("n_group_size", C.c_int32), ("group_size", C.c_int32 * 6),
+                ("n_ipl", C.c_int32), ("ipl", C.c_int32 * 3),
+                ("n_list_depth", C.c_int32), ("list_depth", C.c_int32 * 4),
+                ("n_warps_per_block", C.c_int32), ("warps_per_block", C.c_int32 * 4),
+                ("repeats", C.c_int32)]
+
+
 class Stats(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_groups", C.c_int64), ("interactions", C.c_int64),
                 ("list_entries", C.c_int64), ("max_stack", C.c_int32), ("levels", C.c_int32),
@@ -57,7 +66,7 @@ EXPORTS = ("nbody_abi_version", "nbody_config_default", "nbody_create", "nbody_d
            "nbody_set_config", "nbody_get_config", "nbody_build", "nbody_build_batched",
            "nbody_walk", "nbody_direct", "nbody_step", "nbody_step_batched", "nbody_diagnostics",
            "nbody_get_group_costs", "nbody_export", "nbody_last_error",
-           "nbody_diagnostics_noalloc")
+           "nbody_diagnostics_noalloc", "nbody_tune_space_default", "nbody_autotune")
 EXPORT_PERM, EXPORT_KEYS, EXPORT_NODE_LEVEL, EXPORT_NODE_START, EXPORT_NODE_COUNT, \
     EXPORT_NODE_PARENT, EXPORT_NODE_A, EXPORT_NODE_B, EXPORT_GROUP_FIRST, EXPORT_GROUP_COUNT, \
     EXPORT_GROUP_SPHERE, EXPORT_SYS_BOX = range(12)
@@ -102,6 +111,9 @@ def load(build_if_missing: bool = True):
             "nbody_diagnostics_noalloc": (st, [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "nbody_get_group_costs": (st, [vp, vp, i64, C.POINTER(i64)]),
             "nbody_export": (st, [vp, i32, vp, i64, C.POINTER(i64)]),
+            "nbody_tune_space_default": (None, [C.POINTER(TuneSpace)]),
+            "nbody_autotune": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(TuneSpace),
+                                    C.POINTER(Config), C.POINTER(f32), C.POINTER(i32)]),
             "nbody_last_error": (st, [vp, C.c_char_p, C.c_size_t]),
         }
         for name, (res, args) in sig.items():
@@ -300,6 +312,40 @@ def nbody_get_group_costs(ctx, counts) -> int:
     _check(lib, ctx, lib.nbody_get_group_costs(ctx, _ptr(counts, "int32", None, "counts"),
                                                _size(counts), C.byref(ng)))
     return int(ng.value)
+
+
+def nbody_tune_space_default(**overrides) -> TuneSpace:
+    """Default autotuner space; overrides are lists, e.g. ipl=[1, 2]."""
+    sp = TuneSpace()
+    load().nbody_tune_space_default(C.byref(sp))
+    for k, v in overrides.items():
+        if k == "repeats":
+            sp.repeats = int(v)
+            continue
+        arr = getattr(sp, k)
+        if len(v) > len(arr):
+            raise NbodyError(NBODY_EINVAL, f"at most {len(arr)} values for {k}")
+        for i, x in enumerate(v):
+            arr[i] = int(x)
+        setattr(sp, "n_" + k, len(v))
+    return sp
+
+
+def nbody_autotune(ctx, offsets, eps_sys, x, y, z, m, a_old=None, space=None):
+    """Grid search; returns (best Config, best build+walk ms, candidates timed)."""
+    lib = load()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nsys = off.size - 1
+    eps = None if eps_sys is None else np.ascontiguousarray(eps_sys, dtype=np.float32)
+    n = int(off[-1])
+    ps = [_ptr(a, "float32", n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (m, "m"))]
+    best, ms, tried = Config(), C.c_float(), C.c_int32()
+    _check(lib, ctx, lib.nbody_autotune(ctx, nsys, off.ctypes.data,
+                                        None if eps is None else eps.ctypes.data, *ps,
+                                        _ptr(a_old, "float32", n, "a_old", True),
+                                        C.byref(space) if space is not None else None,
+                                        C.byref(best), C.byref(ms), C.byref(tried)))
+    return best, float(ms.value), int(tried.value)
 
 
 def nbody_export(ctx, what: int) -> np.ndarray:
