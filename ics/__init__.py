@@ -26,7 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["plummer", "hernquist", "galaxy", "batched", "rng"]
+__all__ = ["plummer", "hernquist", "galaxy", "batched", "rng", "mlp_init"]
 
 
 def rng(seed: int, stream: int = 0) -> np.random.Generator:
@@ -276,3 +276,19 @@ def batched(nsys: int, seed: int, log2_min: float = 10.0, log2_max: float = 16.0
     out["eps"][sizes == 0] = 1.0
     out["kind"] = kinds.astype(np.int32)
     return out
+
+
+# ----------------------------------------------------------------------------
+# Initial weights of the cost model (seeded random numbers are inputs too)
+# ----------------------------------------------------------------------------
+def mlp_init(seed: int):
+    """He-uniform weights for the 8 -> 32 -> 32 -> 1 ReLU network, zero
+    biases, flattened as W1[8][32], b1[32], W2[32][32], b2[32], W3[32], b3."""
+    g = rng(seed, 31)
+
+    def he(fan_in, shape):
+        lim = np.sqrt(6.0 / fan_in)
+        return g.uniform(-lim, lim, shape)
+    parts = [he(8, (8, 32)).ravel(), np.zeros(32), he(32, (32, 32)).ravel(), np.zeros(32),
+             g.uniform(-1 / np.sqrt(32), 1 / np.sqrt(32), 32), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)

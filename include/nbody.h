@@ -248,6 +248,52 @@ nbody_status nbody_autotune(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets
                             const nbody_tune_space *space, nbody_config *best, float *best_ms,
                             int32_t *n_tried);
 
+/* ---------------------------------------------------------------------------
+ * Learned cost model ordering the persistent walk's queue (no counterpart in
+ * the paper; the scheduling layer around its walk).  An MLP 8 -> 32 -> 32 -> 1
+ * (ReLU) predicts log2 of each group's walk cost from 8 group features (log2
+ * count, log2 r_g, log2 min|a_old|, log2 distance to the system's centre of
+ * mass, cell level, log2 count per cell volume, log2 mean|a_old|, log2 N_sys),
+ * standardised with statistics frozen at the first training call.  Forward
+ * and backward passes use BF16 weights with FP32 accumulation; Adam keeps FP32
+ * master weights.  With schedule = NBODY_SCHED_MLP the walk pops groups in
+ * descending predicted cost (times the i-slots a group occupies); the
+ * accelerations are identical for every schedule.
+ * Parameter vector (NBODY_MLP_PARAMS floats): W1[8][32], b1[32], W2[32][32],
+ * b2[32], W3[32], b3 (W[i][j] connects input i to unit j). */
+#define NBODY_MLP_PARAMS 1377
+#define NBODY_MLP_FEATURES 8
+
+/* Set the parameters (host or device FP32 [NBODY_MLP_PARAMS], e.g. a seeded
+ * initialisation); resets the Adam moments and the feature statistics. */
+nbody_status nbody_mlp_set_params(nbody_ctx *ctx, const float *params);
+/* Current FP32 master parameters (host or device [NBODY_MLP_PARAMS]). */
+nbody_status nbody_mlp_get_params(nbody_ctx *ctx, float *params);
+
+/* Train on the groups and costs the last walk logged: `epochs` passes of Adam
+ * (learning rate lr) over minibatches of at most `batch` groups (strided
+ * through the Morton order), MSE on log2(cost).  *loss (nullable) receives
+ * the mean minibatch loss of the last epoch.  Errors: EINVAL (no params, no
+ * walk since the last build), ECUDA. */
+nbody_status nbody_mlp_train(nbody_ctx *ctx, int32_t epochs, float lr, int32_t batch,
+                             float *loss);
+
+/* Predicted log2 cost of every group of the last build (host or device FP32,
+ * cap entries); *n_groups receives the group count.  Also copies the groups'
+ * features (FP32 [groups][8], nullable).  Errors: EINVAL, ECUDA. */
+nbody_status nbody_mlp_predict(nbody_ctx *ctx, float *pred, float *features, int64_t cap,
+                               int64_t *n_groups);
+
+/* Stateless forward + MSE loss + gradient for n samples (n <= 2^20):
+ * features [n][8] and targets [n] (FP32, host or device), params
+ * [NBODY_MLP_PARAMS] (FP32, rounded to BF16 inside, as the training kernels
+ * use them), norm [16] (feature means then standard deviations; NULL = none).
+ * Outputs (host or device, nullable): pred [n], grad [NBODY_MLP_PARAMS] of the
+ * mean loss, loss (one float).  Errors: EINVAL, ENOMEM, ECUDA. */
+nbody_status nbody_mlp_eval(int64_t n, const float *features, const float *targets,
+                            const float *params, const float *norm, float *pred, float *grad,
+                            float *loss, void *cuda_stream);
+
 /* Internal arrays of the last build, for inspection and testing. */
 typedef enum {
     NBODY_EXPORT_PERM = 0,         /* int32 [n]: caller index of sorted particle k  */

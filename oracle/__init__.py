@@ -77,6 +77,8 @@ def _load():
         lib.oracle_drift.argtypes = [C.c_int64, d, d, d, d, d, d, C.c_double]
         lib.oracle_diagnostics.argtypes = [C.c_int64, d, d, d, d, d, d, d, d, d]
         lib.oracle_threads.restype = C.c_int
+        lib.oracle_mlp_params.restype = C.c_int
+        lib.oracle_mlp_eval.argtypes = [C.c_int64, d, d, d, d, d, d, d]
         _lib = lib
         return lib
 
@@ -272,6 +274,24 @@ def diagnostics(x, y, z, vx, vy, vz, m, phi=None):
     lib.oracle_diagnostics(arrs[0].size, *[_p(a, C.c_double) for a in arrs], _p(ph, C.c_double),
                            _p(out, C.c_double))
     return out
+
+
+def mlp_eval(feat, target, w, norm=None, want_grad=True):
+    """FP64 MLP forward, MSE and gradient.  Returns (pred, grad|None, loss)."""
+    lib = _load()
+    feat = _f64(feat).reshape(-1, 8)
+    target = _f64(target)
+    w = _f64(w)
+    n = target.size
+    assert w.size == lib.oracle_mlp_params() and feat.shape[0] == n
+    nm = _f64(norm) if norm is not None else None
+    pred = np.empty(n)
+    grad = np.empty(w.size) if want_grad else None
+    loss = np.empty(1)
+    lib.oracle_mlp_eval(n, _p(feat, C.c_double), _p(target, C.c_double), _p(w, C.c_double),
+                        _p(nm, C.c_double), _p(pred, C.c_double), _p(grad, C.c_double),
+                        _p(loss, C.c_double))
+    return pred, grad, float(loss[0])
 
 
 def rel_err(ax, ay, az, bx, by, bz):

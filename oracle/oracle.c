@@ -653,3 +653,66 @@ void oracle_diagnostics(int64_t n, const double *x, const double *y, const doubl
     }
     memcpy(out, s, sizeof s);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Cost-model MLP, 8 -> 32 -> 32 -> 1 with ReLU, mean-squared error.  Plain
+ * FP64 forward pass and backpropagation (chain rule written out), for the
+ * gradient checks of the GPU kernels.  Parameter vector: W1[8][32], b1[32],
+ * W2[32][32], b2[32], W3[32], b3. */
+#define MLP_IN 8
+#define MLP_H 32
+#define MLP_P (MLP_IN * MLP_H + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1)
+
+int oracle_mlp_params(void) { return MLP_P; }
+
+void oracle_mlp_eval(int64_t n, const double *feat, const double *target, const double *w,
+                     const double *norm, double *pred, double *grad, double *loss)
+{
+    const double *W1 = w, *b1 = W1 + MLP_IN * MLP_H, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
+    const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_H;
+    double *gW1 = grad, *gb1 = gW1 ? gW1 + MLP_IN * MLP_H : NULL, *gW2 = gb1 ? gb1 + MLP_H : NULL;
+    double *gb2 = gW2 ? gW2 + MLP_H * MLP_H : NULL, *gW3 = gb2 ? gb2 + MLP_H : NULL;
+    double *gb3 = gW3 ? gW3 + MLP_H : NULL;
+    if (grad) memset(grad, 0, MLP_P * sizeof(double));
+    double L = 0;
+    for (int64_t s = 0; s < n; s++) {
+        double x[MLP_IN], h1[MLP_H], h2[MLP_H];
+        for (int i = 0; i < MLP_IN; i++)
+            x[i] = norm ? (feat[s * MLP_IN + i] - norm[i]) / norm[MLP_IN + i] : feat[s * MLP_IN + i];
+        for (int j = 0; j < MLP_H; j++) {
+            double a = b1[j];
+            for (int i = 0; i < MLP_IN; i++) a += x[i] * W1[i * MLP_H + j];
+            h1[j] = a > 0 ? a : 0;
+        }
+        for (int k = 0; k < MLP_H; k++) {
+            double a = b2[k];
+            for (int j = 0; j < MLP_H; j++) a += h1[j] * W2[j * MLP_H + k];
+            h2[k] = a > 0 ? a : 0;
+        }
+        double y = b3[0];
+        for (int k = 0; k < MLP_H; k++) y += h2[k] * W3[k];
+        if (pred) pred[s] = y;
+        double e = y - target[s];
+        L += e * e / (double)n;
+        if (!grad) continue;
+        double dy = 2.0 * e / (double)n, d2[MLP_H], d1[MLP_H];
+        gb3[0] += dy;
+        for (int k = 0; k < MLP_H; k++) {
+            gW3[k] += dy * h2[k];
+            d2[k] = h2[k] > 0 ? dy * W3[k] : 0;
+            gb2[k] += d2[k];
+        }
+        for (int j = 0; j < MLP_H; j++) {
+            double a = 0;
+            for (int k = 0; k < MLP_H; k++) {
+                gW2[j * MLP_H + k] += h1[j] * d2[k];
+                a += d2[k] * W2[j * MLP_H + k];
+            }
+            d1[j] = h1[j] > 0 ? a : 0;
+            gb1[j] += d1[j];
+        }
+        for (int i = 0; i < MLP_IN; i++)
+            for (int j = 0; j < MLP_H; j++) gW1[i * MLP_H + j] += x[i] * d1[j];
+    }
+    if (loss) *loss = L;
+}

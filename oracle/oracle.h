@@ -121,6 +121,15 @@ void oracle_diagnostics(int64_t n, const double *x, const double *y, const doubl
                         const double *vx, const double *vy, const double *vz,
                         const double *m, const double *phi, double out[8]);
 
+/* Cost-model MLP (8 -> 32 -> 32 -> 1, ReLU), FP64: predictions, mean squared
+ * error and its gradient for n samples.  feat [n][8], target [n], w
+ * [oracle_mlp_params()] = W1[8][32], b1[32], W2[32][32], b2[32], W3[32], b3;
+ * norm [16] (means then standard deviations) or NULL.  pred, grad, loss
+ * nullable. */
+int oracle_mlp_params(void);
+void oracle_mlp_eval(int64_t n, const double *feat, const double *target, const double *w,
+                     const double *norm, double *pred, double *grad, double *loss);
+
 /* Number of threads OpenMP uses (1 without OpenMP). */
 int oracle_threads(void);
 

@@ -68,7 +68,13 @@ struct nbody_ctx {
     DevBuf sys_off, sys_box, sys_boxord, sys_eps2, sys_root;
     // walk / step
     DevBuf acc_s, aold_s;
-    DevBuf st_buf[2][9];
+    DevBuf st_buf[2][10];
+    // learned scheduling
+    DevBuf mlp_w, mlp_m1, mlp_m2, mlp_wb, mlp_norm, mlp_gpart, mlp_lpart, mlp_loss;
+    DevBuf feat, target, score, okey, okey_alt, oval, oval_alt, pcost_walk;
+    int mlp_t = 0;
+    bool mlp_ready = false, mlp_norm_set = false;
+    bool costs_valid = false;  // grp_cost holds the costs of the current groups
     // staging of host arrays
     DevBuf stage[12];
     double *h_diag = nullptr;  // pinned
@@ -97,7 +103,9 @@ struct nbody_ctx {
                          &node_parent, &node_link, &node_count, &node_nchild, &node_arrive,
                          &nodeA, &nodeB, &mom64, &gflag, &grp_first, &grp_count, &grp_sphere,
                          &grp_sys, &grp_alpha, &grp_cost, &grp_order, &sys_off, &sys_box,
-                         &sys_boxord, &sys_eps2, &sys_root, &acc_s, &aold_s};
+                         &sys_boxord, &sys_eps2, &sys_root, &acc_s, &aold_s, &mlp_w, &mlp_m1,
+                         &mlp_m2, &mlp_wb, &mlp_norm, &mlp_gpart, &mlp_lpart, &mlp_loss, &feat,
+                         &target, &score, &okey, &okey_alt, &oval, &oval_alt, &pcost_walk};
         for (DevBuf *b : all) owned.push_back(b);
         for (auto &a : st_buf)
             for (auto &b : a) owned.push_back(&b);
@@ -308,6 +316,7 @@ nbody_status build_core(nbody_ctx *c, const Layout &L, const void *x, const void
 
 nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
     cudaStream_t s = c->stream;
+    c->costs_valid = false;
     build_tree(s, L, P<uint64_t>(c->keys), P<float4>(c->pos4), P<SysBox>(c->sys_box),
                P<int64_t>(c->sys_off), c->cfg.leaf_cap, c->cfg.G, c->cap_nodes, P<int8_t>(c->delta),
                P<int8_t>(c->leaflev), c->tree_temp.p, c->ds, P<int32_t>(c->node_start),
@@ -480,10 +489,83 @@ cudaError_t pool_event(nbody_ctx *c, cudaEvent_t *out) {
     return cudaSuccess;
 }
 
+// Number of groups of the current build, read back to the host (a sync).
+nbody_status host_ngroups(nbody_ctx *c, int64_t *ng) {
+    NB_CUDA(c, cudaMemcpyAsync(&c->h_ds->ngroups, &c->ds->ngroups, sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    *ng = c->h_ds->ngroups;
+    return NBODY_OK;
+}
+
+cudaError_t ensure_mlp_buffers(nbody_ctx *c) {
+    const int64_t n = std::max<int64_t>(c->cap_n, 1);
+    cudaError_t e = ensure(c->feat, (size_t)n * 8 * sizeof(float));
+    if (e == cudaSuccess) e = ensure(c->target, (size_t)n * 4);
+    if (e == cudaSuccess) e = ensure(c->score, (size_t)n * 4);
+    if (e == cudaSuccess) e = ensure(c->okey, (size_t)n * 8);
+    if (e == cudaSuccess) e = ensure(c->okey_alt, (size_t)n * 8);
+    if (e == cudaSuccess) e = ensure(c->oval, (size_t)n * 4);
+    if (e == cudaSuccess) e = ensure(c->oval_alt, (size_t)n * 4);
+    return e;
+}
+
+void launch_features(nbody_ctx *c) {
+    launch_mlp_features(c->stream, c->L, c->ds, P<int32_t>(c->grp_first), P<int32_t>(c->grp_count),
+                        P<float4>(c->grp_sphere), P<int32_t>(c->grp_sys), P<float>(c->aold_s),
+                        P<uint64_t>(c->keys), P<float4>(c->nodeA), P<int32_t>(c->sys_root),
+                        P<SysBox>(c->sys_box), P<int64_t>(c->sys_off), P<float>(c->feat), c->nsm);
+    c->kernels += 1;
+}
+
+// Queue order of the walk for the configured schedule (NULL: Morton order).
+// pcost: per-particle cost of the previous walk (sorted order), for LASTCOST.
+nbody_status compute_order(nbody_ctx *c, const float *pcost, const int32_t **order) {
+    *order = nullptr;
+    const int sched = c->cfg.schedule;
+    if (sched == NBODY_SCHED_MORTON) return NBODY_OK;
+    if (sched == NBODY_SCHED_MLP && !c->mlp_ready)
+        return fail(c, NBODY_EINVAL, "schedule MLP needs parameters (nbody_mlp_set_params)");
+    if (sched == NBODY_SCHED_LASTCOST && !pcost)
+        return fail(c, NBODY_EINVAL, "schedule LASTCOST needs a previous walk");
+    int64_t ng = 0;
+    nbody_status st = host_ngroups(c, &ng);
+    if (st != NBODY_OK) return st;
+    if (ng < 1) return NBODY_OK;
+    cudaError_t e = ensure_mlp_buffers(c);
+    if (e != cudaSuccess) return fail(c, NBODY_ENOMEM, "allocation");
+    const int32_t *png = &c->ds->ngroups;
+    if (sched == NBODY_SCHED_MLP) {
+        launch_features(c);
+        launch_mlp_forward(c->stream, png, 0, P<float>(c->feat),
+                           reinterpret_cast<const __nv_bfloat16 *>(c->mlp_wb.p), P<float>(c->mlp_norm),
+                           P<float>(c->score), c->nsm);
+    } else {
+        launch_lastcost_score(c->stream, png, P<int32_t>(c->grp_first), pcost, P<float>(c->score),
+                              c->nsm);
+    }
+    launch_order_keys(c->stream, png, P<float>(c->score), P<int32_t>(c->grp_count),
+                      P<uint64_t>(c->okey), P<uint32_t>(c->oval), c->nsm);
+    c->kernels += 2 + 4 * 4;
+    if (radix_sort(c->stream, P<uint64_t>(c->okey), P<uint32_t>(c->oval), P<uint64_t>(c->okey_alt),
+                   P<uint32_t>(c->oval_alt), ng, 32, c->rs_temp.p)) {
+        std::swap(c->okey, c->okey_alt);
+        std::swap(c->oval, c->oval_alt);
+    }
+    NB_CUDA(c, cudaGetLastError());
+    *order = P<int32_t>(c->oval);
+    return NBODY_OK;
+}
+
 // Walk over the current groups; aold_s (sorted) must hold |a_old|.
 nbody_status run_walk(nbody_ctx *c, bool geometric, bool phi, bool safe, const int32_t *perm,
                       float *ax, float *ay, float *az, float *ph, float4 *acc_sorted,
-                      bool reset_accumulators = true) {
+                      bool reset_accumulators = true, const float *pcost = nullptr) {
+    const int32_t *order = nullptr;
+    if (!geometric) {
+        nbody_status so = compute_order(c, pcost, &order);
+        if (so != NBODY_OK) return so;
+    }
     nbody_status st = reset_walk_counters(c, reset_accumulators);
     if (st != NBODY_OK) return st;
     if (!geometric) {
@@ -498,6 +580,7 @@ nbody_status run_walk(nbody_ctx *c, bool geometric, bool phi, bool safe, const i
         c->wev.push_back(ev);
     }
     WalkArgs a = walk_args(c);
+    a.order = order;
     a.perm = perm;
     a.ax = ax;
     a.ay = ay;
@@ -512,6 +595,7 @@ nbody_status run_walk(nbody_ctx *c, bool geometric, bool phi, bool safe, const i
         c->wev_used += 2;
     }
     c->kernels += 1;
+    if (!geometric) c->costs_valid = true;
     return NBODY_OK;
 }
 
@@ -672,9 +756,16 @@ nbody_status nbody_walk(nbody_ctx *ctx, const float *a_old, float *ax, float *ay
         launch_acc_mag(s, n, P<float4>(ctx->acc_s), P<float>(ctx->aold_s));
         ctx->kernels += 1;
     }
+    const bool have_pcost = ctx->costs_valid && ctx->pcost_walk.p;
     st = run_walk(ctx, false, want_phi, safe, (const int32_t *)P<uint32_t>(ctx->vals),
-                  (float *)dax, (float *)day, (float *)daz, (float *)dph, nullptr);
+                  (float *)dax, (float *)day, (float *)daz, (float *)dph, nullptr, true,
+                  have_pcost ? P<float>(ctx->pcost_walk) : nullptr);
     if (st != NBODY_OK) return st;
+    if (ensure(ctx->pcost_walk, (size_t)n * 4) == cudaSuccess) {
+        launch_spread_cost(s, &ctx->ds->ngroups, P<int32_t>(ctx->grp_first), P<int32_t>(ctx->grp_count),
+                           P<int32_t>(ctx->grp_cost), P<float>(ctx->pcost_walk), ctx->nsm);
+        ctx->kernels += 1;
+    }
     NB_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
     NB_CUDA(ctx, stage_out_finish(ctx, ax, dax, fb));
     NB_CUDA(ctx, stage_out_finish(ctx, ay, day, fb));
@@ -756,7 +847,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     cudaError_t e = ensure_capacity(ctx, n, nsys, L.levels);
     for (int b = 0; b < 2 && e == cudaSuccess; b++) {
         for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure(ctx->st_buf[b][k], (size_t)n * 8);
-        for (int k = 3; k < 9 && e == cudaSuccess; k++) e = ensure(ctx->st_buf[b][k], (size_t)n * 4);
+        for (int k = 3; k < 10 && e == cudaSuccess; k++) e = ensure(ctx->st_buf[b][k], (size_t)n * 4);
     }
     if (e != cudaSuccess) return fail(ctx, NBODY_ENOMEM, std::string("allocation: ") + cudaGetErrorString(e));
     std::vector<int64_t> off1 = {0, n};
@@ -775,6 +866,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         S[b].m = P<float>(ctx->st_buf[b][6]);
         S[b].aold = P<float>(ctx->st_buf[b][7]);
         S[b].id = P<uint32_t>(ctx->st_buf[b][8]);
+        S[b].pcost = P<float>(ctx->st_buf[b][9]);
     }
     const size_t db = (size_t)n * 8, fb = (size_t)n * 4;
     const void *in[10];
@@ -817,8 +909,12 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             NB_CUDA(ctx, cudaEventRecord(e1, q));
         }
         NB_CUDA(ctx, cudaMemcpyAsync(ctx->aold_s.p, S[cur].aold, fb, cudaMemcpyDeviceToDevice, q));
-        r = run_walk(ctx, false, false, safe, nullptr, nullptr, nullptr, nullptr, nullptr, acc, false);
+        r = run_walk(ctx, false, false, safe, nullptr, nullptr, nullptr, nullptr, nullptr, acc, false,
+                     S[cur].pcost);
         if (r != NBODY_OK) return r;
+        launch_spread_cost(q, &ctx->ds->ngroups, P<int32_t>(ctx->grp_first), P<int32_t>(ctx->grp_count),
+                           P<int32_t>(ctx->grp_cost), S[cur].pcost, ctx->nsm);
+        ctx->kernels += 1;
         if (timing) {
             NB_CUDA(ctx, pool_event(ctx, &e2));
             NB_CUDA(ctx, cudaEventRecord(e2, q));
@@ -830,7 +926,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     };
 
     int eager = nsteps;
-    if (ctx->cfg.use_graph && nsteps >= 2) {
+    // a cost-ordered queue reads the group count on the host every step, so it
+    // runs eagerly
+    if (ctx->cfg.use_graph && nsteps >= 2 && ctx->cfg.schedule == NBODY_SCHED_MORTON) {
         // Two steps per graph: the sort's ping-pong buffers and the state
         // copies swap roles every step, so after two steps every pointer is
         // back where the capture found it and the graph can be replayed.
@@ -1146,6 +1244,175 @@ nbody_status nbody_export(nbody_ctx *ctx, int32_t what, void *dst, int64_t cap, 
         NB_CUDA(ctx, cudaMemcpyAsync(dst, src, (size_t)k * esz, kind, ctx->stream));
         NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     }
+    return NBODY_OK;
+}
+
+// ---------------------------------------------------------------- learned cost model
+static_assert(NBODY_MLP_PARAMS == nb::kMlpParams, "parameter count");
+
+static cudaError_t ensure_mlp_state(nbody_ctx *c) {
+    cudaError_t e = ensure(c->mlp_w, kMlpParams * 4);
+    if (e == cudaSuccess) e = ensure(c->mlp_m1, kMlpParams * 4);
+    if (e == cudaSuccess) e = ensure(c->mlp_m2, kMlpParams * 4);
+    if (e == cudaSuccess) e = ensure(c->mlp_wb, kMlpParams * 2);
+    if (e == cudaSuccess) e = ensure(c->mlp_norm, 16 * 4);
+    return e;
+}
+
+nbody_status nbody_mlp_set_params(nbody_ctx *ctx, const float *params) {
+    if (!ctx || !params) return fail(ctx, NBODY_EINVAL, "NULL argument");
+    cudaError_t e = ensure_mlp_state(ctx);
+    if (e != cudaSuccess) return fail(ctx, NBODY_ENOMEM, "allocation");
+    cudaMemcpyKind kind = is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    NB_CUDA(ctx, cudaMemcpyAsync(ctx->mlp_w.p, params, kMlpParams * 4, kind, ctx->stream));
+    NB_CUDA(ctx, cudaMemsetAsync(ctx->mlp_m1.p, 0, kMlpParams * 4, ctx->stream));
+    NB_CUDA(ctx, cudaMemsetAsync(ctx->mlp_m2.p, 0, kMlpParams * 4, ctx->stream));
+    launch_mlp_round(ctx->stream, P<float>(ctx->mlp_w), reinterpret_cast<__nv_bfloat16 *>(ctx->mlp_wb.p));
+    NB_CUDA(ctx, cudaGetLastError());
+    NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->mlp_t = 0;
+    ctx->mlp_ready = true;
+    ctx->mlp_norm_set = false;
+    return NBODY_OK;
+}
+
+nbody_status nbody_mlp_get_params(nbody_ctx *ctx, float *params) {
+    if (!ctx || !params) return fail(ctx, NBODY_EINVAL, "NULL argument");
+    if (!ctx->mlp_ready) return fail(ctx, NBODY_EINVAL, "no MLP parameters set");
+    cudaMemcpyKind kind = is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    NB_CUDA(ctx, cudaMemcpyAsync(params, ctx->mlp_w.p, kMlpParams * 4, kind, ctx->stream));
+    NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return NBODY_OK;
+}
+
+nbody_status nbody_mlp_train(nbody_ctx *ctx, int32_t epochs, float lr, int32_t batch, float *loss) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    if (!ctx->mlp_ready) return fail(ctx, NBODY_EINVAL, "no MLP parameters set");
+    if (!ctx->costs_valid) return fail(ctx, NBODY_EINVAL, "no walk since the last build");
+    if (epochs < 1 || batch < 32 || batch > (1 << 16) || !(lr > 0.0f))
+        return fail(ctx, NBODY_EINVAL, "epochs >= 1, 32 <= batch <= 65536, lr > 0");
+    int64_t ng = 0;
+    nbody_status st = host_ngroups(ctx, &ng);
+    if (st != NBODY_OK) return st;
+    if (ng < 1) return fail(ctx, NBODY_EINVAL, "no groups");
+    cudaStream_t s = ctx->stream;
+    const int64_t nbatches = (ng + batch - 1) / batch;
+    const int maxb = (int)((ng / nbatches + 1 + 127) / 128) + 1;
+    cudaError_t e = ensure_mlp_buffers(ctx);
+    if (e == cudaSuccess) e = ensure(ctx->mlp_gpart, (size_t)maxb * kMlpParams * 4);
+    if (e == cudaSuccess) e = ensure(ctx->mlp_lpart, (size_t)maxb * 4);
+    if (e == cudaSuccess) e = ensure(ctx->mlp_loss, (size_t)nbatches * 4);
+    if (e != cudaSuccess) return fail(ctx, NBODY_ENOMEM, "allocation");
+    const int32_t *png = &ctx->ds->ngroups;
+    ctx->kernels = 0;
+    launch_features(ctx);
+    launch_mlp_target(s, png, P<int32_t>(ctx->grp_cost), P<float>(ctx->target), ctx->nsm);
+    if (!ctx->mlp_norm_set) {
+        launch_mlp_norm(s, png, P<float>(ctx->feat), P<float>(ctx->mlp_norm));
+        ctx->mlp_norm_set = true;
+    }
+    __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(ctx->mlp_wb.p);
+    for (int ep = 0; ep < epochs; ep++)
+        for (int64_t k = 0; k < nbatches; k++) {
+            const int count = (int)((ng - 1 - k) / nbatches + 1);
+            ctx->mlp_t += 1;
+            e = launch_mlp_train_step(s, P<float>(ctx->feat), P<float>(ctx->target), k, nbatches,
+                                      count, wb, P<float>(ctx->mlp_norm), P<float>(ctx->mlp_gpart),
+                                      P<float>(ctx->mlp_lpart), nullptr,
+                                      P<float>(ctx->mlp_loss) + k, P<float>(ctx->mlp_w),
+                                      P<float>(ctx->mlp_m1), P<float>(ctx->mlp_m2), wb, lr,
+                                      ctx->mlp_t, true);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp train step");
+        }
+    std::vector<float> h((size_t)nbatches);
+    NB_CUDA(ctx, cudaMemcpyAsync(h.data(), ctx->mlp_loss.p, (size_t)nbatches * 4,
+                                 cudaMemcpyDeviceToHost, s));
+    NB_CUDA(ctx, cudaStreamSynchronize(s));
+    double m = 0;
+    for (float v : h) m += v;
+    if (loss) *loss = (float)(m / (double)nbatches);
+    return NBODY_OK;
+}
+
+nbody_status nbody_mlp_predict(nbody_ctx *ctx, float *pred, float *features, int64_t cap,
+                               int64_t *n_groups) {
+    if (!ctx || !n_groups || cap < 0) return fail(ctx, NBODY_EINVAL, "bad argument");
+    if (!ctx->mlp_ready) return fail(ctx, NBODY_EINVAL, "no MLP parameters set");
+    int64_t ng = 0;
+    nbody_status st = host_ngroups(ctx, &ng);
+    if (st != NBODY_OK) return st;
+    *n_groups = ng;
+    if (ensure_mlp_buffers(ctx) != cudaSuccess) return fail(ctx, NBODY_ENOMEM, "allocation");
+    launch_features(ctx);
+    launch_mlp_forward(ctx->stream, &ctx->ds->ngroups, 0, P<float>(ctx->feat),
+                       reinterpret_cast<const __nv_bfloat16 *>(ctx->mlp_wb.p),
+                       ctx->mlp_norm_set ? P<float>(ctx->mlp_norm) : nullptr, P<float>(ctx->score),
+                       ctx->nsm);
+    NB_CUDA(ctx, cudaGetLastError());
+    const int64_t k = std::min(cap, ng);
+    if (k > 0 && pred) {
+        cudaMemcpyKind kind = is_device_ptr(pred) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        NB_CUDA(ctx, cudaMemcpyAsync(pred, ctx->score.p, (size_t)k * 4, kind, ctx->stream));
+    }
+    if (k > 0 && features) {
+        cudaMemcpyKind kind = is_device_ptr(features) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        NB_CUDA(ctx, cudaMemcpyAsync(features, ctx->feat.p, (size_t)k * 8 * 4, kind, ctx->stream));
+    }
+    NB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return NBODY_OK;
+}
+
+nbody_status nbody_mlp_eval(int64_t n, const float *features, const float *targets,
+                            const float *params, const float *norm, float *pred, float *grad,
+                            float *loss, void *cuda_stream) {
+    if (n < 1 || n > (1 << 20) || !features || !targets || !params)
+        return fail(nullptr, NBODY_EINVAL, "bad argument (1 <= n <= 2^20, non-NULL inputs)");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int nb = (int)((n + 127) / 128);
+    // one device block: features, targets, params, norm, pred, grad, partials, loss, bf16 params
+    const size_t fsz = (size_t)n * 8 * 4, tsz = (size_t)n * 4, psz = kMlpParams * 4;
+    const size_t total = fsz + tsz + psz + 64 + tsz + psz + (size_t)nb * psz + (size_t)nb * 4 + 16 +
+                         kMlpParams * 2 + 1024;
+    char *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, total);
+    if (e != cudaSuccess) return fail(nullptr, NBODY_ENOMEM, "allocation");
+    auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    size_t o = 0;
+    float *dfeat = (float *)(buf + o); o = align(o + fsz);
+    float *dtarget = (float *)(buf + o); o = align(o + tsz);
+    float *dparams = (float *)(buf + o); o = align(o + psz);
+    float *dnorm = (float *)(buf + o); o = align(o + 64);
+    float *dpred = (float *)(buf + o); o = align(o + tsz);
+    float *dgrad = (float *)(buf + o); o = align(o + psz);
+    float *dgpart = (float *)(buf + o); o = align(o + (size_t)nb * psz);
+    float *dlpart = (float *)(buf + o); o = align(o + (size_t)nb * 4);
+    float *dloss = (float *)(buf + o); o = align(o + 16);
+    __nv_bfloat16 *dwb = (__nv_bfloat16 *)(buf + o);
+    auto h2d = [&](void *dst, const void *src, size_t b) {
+        return cudaMemcpyAsync(dst, src, b, is_device_ptr(src) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyHostToDevice, s);
+    };
+    e = h2d(dfeat, features, fsz);
+    if (e == cudaSuccess) e = h2d(dtarget, targets, tsz);
+    if (e == cudaSuccess) e = h2d(dparams, params, psz);
+    if (e == cudaSuccess && norm) e = h2d(dnorm, norm, 64);
+    if (e == cudaSuccess) {
+        launch_mlp_round(s, dparams, dwb);
+        launch_mlp_forward(s, nullptr, n, dfeat, dwb, norm ? dnorm : nullptr, dpred, 152);
+        e = launch_mlp_train_step(s, dfeat, dtarget, 0, 1, (int)n, dwb, norm ? dnorm : nullptr,
+                                  dgpart, dlpart, dgrad, dloss, nullptr, nullptr, nullptr, nullptr,
+                                  0.0f, 1, false);
+    }
+    auto d2h = [&](void *dst, const void *src, size_t b) {
+        return cudaMemcpyAsync(dst, src, b, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyDeviceToHost, s);
+    };
+    if (e == cudaSuccess && pred) e = d2h(pred, dpred, tsz);
+    if (e == cudaSuccess && grad) e = d2h(grad, dgrad, psz);
+    if (e == cudaSuccess && loss) e = d2h(loss, dloss, 4);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "nbody_mlp_eval");
     return NBODY_OK;
 }
 

@@ -72,6 +72,7 @@ __global__ void permute_state_kernel(int64_t n, const uint32_t *__restrict__ per
         dst.m[i] = mj;
         dst.aold[i] = src.aold[j];
         dst.id[i] = src.id[j];
+        if (src.pcost) dst.pcost[i] = src.pcost[j];
     }
 }
 
@@ -96,6 +97,7 @@ __global__ void load_state_kernel(int64_t n, const double *x, const double *y, c
         acc[i] = make_float4(a0, a1, a2, 0.0f);
         st.aold[i] = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
         st.id[i] = (uint32_t)i;
+        if (st.pcost) st.pcost[i] = 1.0f;
     }
 }
 

@@ -17,6 +17,7 @@
 //              delta_acc * min |a_old|, system id, cost log
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +31,7 @@ namespace nb {
 
 constexpr int kMaxLevels = 21;              // 21 bits per axis -> 63-bit keys
 constexpr int kMaxNL = kMaxLevels + 1;      // levels 0..21
+constexpr int kMlpParams = 8 * 32 + 32 + 32 * 32 + 32 + 32 + 1;  // 8 -> 32 -> 32 -> 1
 constexpr int kStatusStackOverflow = 1;
 constexpr int kStatusBadTree = 2;  // an index failed a bounds check (skipped)
 
@@ -202,12 +204,38 @@ void launch_acc_mag(cudaStream_t s, int64_t n, const float4 *acc_sorted, float *
 void launch_gather_f32(cudaStream_t s, int64_t n, const uint32_t *perm, const float *src,
                        float *dst);
 
+// mlp.cu
+void launch_mlp_features(cudaStream_t s, const Layout &L, const DevState *ds,
+                         const int32_t *grp_first, const int32_t *grp_count,
+                         const float4 *grp_sphere, const int32_t *grp_sys, const float *aold,
+                         const uint64_t *keys, const float4 *nodeA, const int32_t *sys_root,
+                         const SysBox *box, const int64_t *off, float *feat, int nsm);
+void launch_mlp_forward(cudaStream_t s, const int32_t *pn, int64_t n, const float *feat,
+                        const __nv_bfloat16 *wb, const float *norm, float *pred, int nsm);
+size_t mlp_grad_smem();
+cudaError_t launch_mlp_train_step(cudaStream_t s, const float *feat, const float *target,
+                                  int64_t base, int64_t stride, int count,
+                                  const __nv_bfloat16 *wb, const float *norm, float *gpart,
+                                  float *lpart, float *grad, float *loss, float *w, float *m1,
+                                  float *m2, __nv_bfloat16 *wb_out, float lr, int t, bool update);
+void launch_mlp_round(cudaStream_t s, const float *w, __nv_bfloat16 *wb);
+void launch_mlp_norm(cudaStream_t s, const int32_t *pn, const float *feat, float *norm);
+void launch_mlp_target(cudaStream_t s, const int32_t *pn, const int32_t *cost, float *target,
+                       int nsm);
+void launch_order_keys(cudaStream_t s, const int32_t *pn, const float *score,
+                       const int32_t *grp_count, uint64_t *key, uint32_t *val, int nsm);
+void launch_lastcost_score(cudaStream_t s, const int32_t *pn, const int32_t *grp_first,
+                           const float *pcost, float *score, int nsm);
+void launch_spread_cost(cudaStream_t s, const int32_t *pn, const int32_t *grp_first,
+                        const int32_t *grp_count, const int32_t *cost, float *pcost, int nsm);
+
 // integrate.cu
 struct StepState {
     double *x, *y, *z;
     float *vx, *vy, *vz, *m;
     float *aold;
     uint32_t *id;    // caller index of each sorted particle
+    float *pcost;    // cost of each particle's group in the last walk (may be NULL)
 };
 void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
                        float dt);

@@ -66,7 +66,10 @@ EXPORTS = ("nbody_abi_version", "nbody_config_default", "nbody_create", "nbody_d
            "nbody_set_config", "nbody_get_config", "nbody_build", "nbody_build_batched",
            "nbody_walk", "nbody_direct", "nbody_step", "nbody_step_batched", "nbody_diagnostics",
            "nbody_get_group_costs", "nbody_export", "nbody_last_error",
-           "nbody_diagnostics_noalloc", "nbody_tune_space_default", "nbody_autotune")
+           "nbody_diagnostics_noalloc", "nbody_tune_space_default", "nbody_autotune",
+           "nbody_mlp_set_params", "nbody_mlp_get_params", "nbody_mlp_train",
+           "nbody_mlp_predict", "nbody_mlp_eval")
+MLP_PARAMS, MLP_FEATURES = 1377, 8
 EXPORT_PERM, EXPORT_KEYS, EXPORT_NODE_LEVEL, EXPORT_NODE_START, EXPORT_NODE_COUNT, \
     EXPORT_NODE_PARENT, EXPORT_NODE_A, EXPORT_NODE_B, EXPORT_GROUP_FIRST, EXPORT_GROUP_COUNT, \
     EXPORT_GROUP_SPHERE, EXPORT_SYS_BOX = range(12)
@@ -112,6 +115,11 @@ def load(build_if_missing: bool = True):
             "nbody_get_group_costs": (st, [vp, vp, i64, C.POINTER(i64)]),
             "nbody_export": (st, [vp, i32, vp, i64, C.POINTER(i64)]),
             "nbody_tune_space_default": (None, [C.POINTER(TuneSpace)]),
+            "nbody_mlp_set_params": (st, [vp, vp]),
+            "nbody_mlp_get_params": (st, [vp, vp]),
+            "nbody_mlp_train": (st, [vp, i32, f32, i32, C.POINTER(f32)]),
+            "nbody_mlp_predict": (st, [vp, vp, vp, i64, C.POINTER(i64)]),
+            "nbody_mlp_eval": (st, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
             "nbody_autotune": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(TuneSpace),
                                     C.POINTER(Config), C.POINTER(f32), C.POINTER(i32)]),
             "nbody_last_error": (st, [vp, C.c_char_p, C.c_size_t]),
@@ -346,6 +354,54 @@ def nbody_autotune(ctx, offsets, eps_sys, x, y, z, m, a_old=None, space=None):
                                         C.byref(space) if space is not None else None,
                                         C.byref(best), C.byref(ms), C.byref(tried)))
     return best, float(ms.value), int(tried.value)
+
+
+def nbody_mlp_set_params(ctx, params):
+    lib = load()
+    _check(lib, ctx, lib.nbody_mlp_set_params(ctx, _ptr(params, "float32", MLP_PARAMS, "params")))
+
+
+def nbody_mlp_get_params(ctx) -> np.ndarray:
+    lib = load()
+    out = np.empty(MLP_PARAMS, np.float32)
+    _check(lib, ctx, lib.nbody_mlp_get_params(ctx, out.ctypes.data))
+    return out
+
+
+def nbody_mlp_train(ctx, epochs=1, lr=1e-3, batch=4096) -> float:
+    lib = load()
+    loss = C.c_float()
+    _check(lib, ctx, lib.nbody_mlp_train(ctx, int(epochs), float(lr), int(batch), C.byref(loss)))
+    return float(loss.value)
+
+
+def nbody_mlp_predict(ctx, want_features=False):
+    """(predicted log2 cost per group, features or None) of the last build."""
+    lib = load()
+    ng = C.c_int64()
+    _check(lib, ctx, lib.nbody_mlp_predict(ctx, None, None, 0, C.byref(ng)))
+    pred = np.empty(ng.value, np.float32)
+    feat = np.empty((ng.value, MLP_FEATURES), np.float32) if want_features else None
+    _check(lib, ctx, lib.nbody_mlp_predict(ctx, pred.ctypes.data if pred.size else None,
+                                           feat.ctypes.data if feat is not None and pred.size else None,
+                                           ng.value, C.byref(ng)))
+    return pred, feat
+
+
+def nbody_mlp_eval(features, targets, params, norm=None, stream=None):
+    """Stateless forward/loss/gradient: returns (pred, grad, loss)."""
+    lib = load()
+    n = _size(targets)
+    pred = np.empty(n, np.float32)
+    grad = np.empty(MLP_PARAMS, np.float32)
+    loss = np.empty(1, np.float32)
+    _check(lib, None, lib.nbody_mlp_eval(n, _ptr(features, "float32", n * MLP_FEATURES, "features"),
+                                         _ptr(targets, "float32", n, "targets"),
+                                         _ptr(params, "float32", MLP_PARAMS, "params"),
+                                         _ptr(norm, "float32", 16, "norm", True),
+                                         pred.ctypes.data, grad.ctypes.data, loss.ctypes.data,
+                                         _stream_ptr(stream)))
+    return pred, grad, float(loss[0])
 
 
 def nbody_export(ctx, what: int) -> np.ndarray:

@@ -441,3 +441,46 @@ def test_diagnostics_two_body_closed_form():
     assert np.allclose(d[2:5], [1.0 - 1.0, 0.0 + 4.0, 0.5], rtol=1e-15)
     # L = sum m r x v ; particle 1: r = (3,4,0), v = (-0.5, 2, 0) -> (0, 0, 3*2 - 4*-0.5) = 8, times 2
     assert np.allclose(d[5:], [0.0, 0.0, 16.0], rtol=1e-15)
+
+
+# --------------------------------------------------------------------------- cost-model MLP
+def _mlp_case(seed, n=40):
+    g = ics.rng(seed, 3)
+    w = ics.mlp_init(seed).astype(np.float64)
+    w[8 * 32:8 * 32 + 32] = g.normal(scale=0.1, size=32)          # b1
+    w[-1] = 0.3                                                    # b3
+    feat = g.normal(size=(n, 8))
+    target = g.normal(size=n)
+    norm = np.concatenate([g.normal(scale=0.1, size=8), g.uniform(0.5, 2.0, 8)])
+    return feat, target, w, norm
+
+
+def test_mlp_gradient_matches_finite_differences():
+    feat, target, w, norm = _mlp_case(1)
+    _, grad, loss = oracle.mlp_eval(feat, target, w, norm)
+    h = 1e-6
+    g = ics.rng(2, 4)
+    for p in g.choice(w.size, 60, replace=False):
+        wp, wm = w.copy(), w.copy()
+        wp[p] += h
+        wm[p] -= h
+        fd = (oracle.mlp_eval(feat, target, wp, norm, False)[2] -
+              oracle.mlp_eval(feat, target, wm, norm, False)[2]) / (2 * h)
+        assert abs(fd - grad[p]) <= 1e-6 * max(1.0, abs(grad[p])) + 1e-9, (p, fd, grad[p])
+
+
+def test_mlp_closed_forms():
+    feat, target, w, norm = _mlp_case(3)
+    # all weights zero: y = b3, loss = mean (b3 - t)^2, only b3 has a gradient
+    z = np.zeros_like(w)
+    z[-1] = 0.7
+    pred, grad, loss = oracle.mlp_eval(feat, target, z, norm)
+    assert np.all(pred == 0.7)
+    assert np.isclose(loss, np.mean((0.7 - target) ** 2), rtol=1e-14)
+    assert np.isclose(grad[-1], 2 * np.mean(0.7 - target), rtol=1e-14)
+    assert np.all(grad[:-1] == 0)
+    # a hidden unit with a very negative bias is dead: its weights get no gradient
+    w2 = w.copy()
+    w2[8 * 32 + 5] = -1e6                                          # b1[5]
+    _, g2, _ = oracle.mlp_eval(feat, target, w2, norm)
+    assert np.all(g2[5:8 * 32:32] == 0) and g2[8 * 32 + 5] == 0
