@@ -49,10 +49,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("galaxy", "batched"), default="galaxy",
+    ap.add_argument("--workload", choices=("galaxy", "batched", "learned"), default="galaxy",
                     help="galaxy: N=2^23 three-component galaxy (the headline); batched: 512 "
                          "independent Plummer/Hernquist systems, one forest per step")
     ap.add_argument("--nsys", type=int, default=512)
+    ap.add_argument("--train-steps", type=int, default=20)
+    ap.add_argument("--train-epochs", type=int, default=2)
     ap.add_argument("--per-system-steps", type=int, default=2,
                     help="batched: steps timed for the one-call-per-system comparison")
     ap.add_argument("--n", type=int, default=1 << 23)
@@ -399,6 +401,93 @@ def run_batched(args, rank, world, local_rank):
     }
 
 
+# ---------------------------------------------------------------------------- learned schedule
+def run_learned(args, rank, world, local_rank):
+    """Galaxy at N = 25 * 2^20: the cost model is trained online on the first
+    `train_steps` steps (Morton order), then the remaining steps run three
+    times from the same state -- MLP-ordered queue, Morton order, last-step
+    cost order -- and the walk-kernel times are compared.  The final states
+    must agree bit for bit (the order never changes a group's result)."""
+    import torch
+
+    import ics
+    import paper_1811_02761_gb300 as nb
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n if args.n != (1 << 23) else 25 * (1 << 20)
+    p = ics.galaxy(n, args.seed)
+
+    def D(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    X = [D(p[k]) for k in ("x64", "y64", "z64")]
+    V = [D(p[k]) for k in ("vx", "vy", "vz")]
+    M = D(p["m"])
+    A = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    stream = torch.cuda.current_stream(dev)
+    ctx = nb.nbody_create(nb.nbody_config_default(eps=EPS, delta_acc=DACC), stream)
+    out = {}
+    try:
+        nb.nbody_build(ctx, *[D(p[k]) for k in ("x", "y", "z")], M)
+        nb.nbody_walk(ctx, None, *A)
+        nb.nbody_mlp_set_params(ctx, ics.mlp_init(args.seed))
+        losses = []
+        t0 = time.perf_counter()
+        for _ in range(args.train_steps):
+            nb.nbody_step(ctx, *X, *V, M, *A, DT, 1)
+            losses.append(nb.nbody_mlp_train(ctx, epochs=args.train_epochs, lr=2e-3, batch=4096))
+        train_s = time.perf_counter() - t0
+        pred, _ = nb.nbody_mlp_predict(ctx)
+        cost = np.empty(pred.size, np.int32)
+        nb.nbody_get_group_costs(ctx, cost)
+        corr = float(np.corrcoef(pred, np.log2(np.maximum(cost, 1)))[0, 1])
+        snap = [t.clone() for t in X + V + A]
+        runs = args.steps - args.train_steps
+        finals = {}
+        for name, sched in (("mlp", nb.SCHED_MLP), ("morton", nb.SCHED_MORTON),
+                            ("lastcost", nb.SCHED_LASTCOST)):
+            for t, s0 in zip(X + V + A, snap):
+                t.copy_(s0)
+            cfg = nb.nbody_get_config(ctx)
+            cfg.schedule = sched
+            nb.nbody_set_config(ctx, cfg)
+            torch.cuda.synchronize(dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            st = nb.nbody_step(ctx, *X, *V, M, *A, DT, runs)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            out[name] = {"walk_ms_per_step": st.ms_walk_kernel / max(st.walk_launches, 1),
+                         "s_per_step": ev0.elapsed_time(ev1) / 1e3 / runs,
+                         "interactions_per_step": st.interactions / runs}
+            finals[name] = [t.cpu().numpy() for t in X + V + A]
+        same = all(np.array_equal(a, b) for k in ("morton", "lastcost")
+                   for a, b in zip(finals["mlp"], finals[k]))
+    finally:
+        nb.nbody_destroy(ctx)
+    if rank != 0:
+        return None
+    base = out["morton"]["walk_ms_per_step"]
+    return {
+        "metric": METRIC, "value": out["mlp"]["interactions_per_step"] / out["mlp"]["s_per_step"] / 1e9,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.train_steps,
+        "ms_per_step": out["mlp"]["s_per_step"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded three-component galaxy)",
+        "config": {"workload": f"learned scheduling: galaxy N={n}, {args.train_steps} training "
+                               f"steps (Morton order, {args.train_epochs} epochs each), then "
+                               f"{args.steps - args.train_steps} steps per schedule from the same state",
+                   "n": n},
+        "schedules": out,
+        "mlp_vs_morton_walk_speedup": base / out["mlp"]["walk_ms_per_step"],
+        "lastcost_vs_morton_walk_speedup": base / out["lastcost"]["walk_ms_per_step"],
+        "bitwise_identical_final_states": same,
+        "train": {"losses_first_last": [losses[0], losses[-1]], "seconds": train_s,
+                  "pred_vs_cost_correlation": corr},
+    }
+
+
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -457,6 +546,8 @@ def main():
             dist.init_process_group("nccl")
         if args.workload == "batched":
             out = run_batched(args, rank, world, local_rank)
+        elif args.workload == "learned":
+            out = run_learned(args, rank, world, local_rank)
         else:
             out = run_ours(args, rank, world, local_rank)
         if world > 1:

@@ -537,9 +537,10 @@ nbody_status compute_order(nbody_ctx *c, const float *pcost, const int32_t **ord
     const int32_t *png = &c->ds->ngroups;
     if (sched == NBODY_SCHED_MLP) {
         launch_features(c);
+        const float *nrm = c->mlp_norm_set ? P<float>(c->mlp_norm) : nullptr;
         launch_mlp_forward(c->stream, png, 0, P<float>(c->feat),
-                           reinterpret_cast<const __nv_bfloat16 *>(c->mlp_wb.p), P<float>(c->mlp_norm),
-                           P<float>(c->score), c->nsm);
+                           reinterpret_cast<const __nv_bfloat16 *>(c->mlp_wb.p), nrm,
+                           nrm ? nrm + 16 : nullptr, P<float>(c->score), c->nsm);
     } else {
         launch_lastcost_score(c->stream, png, P<int32_t>(c->grp_first), pcost, P<float>(c->score),
                               c->nsm);
@@ -1255,7 +1256,7 @@ static cudaError_t ensure_mlp_state(nbody_ctx *c) {
     if (e == cudaSuccess) e = ensure(c->mlp_m1, kMlpParams * 4);
     if (e == cudaSuccess) e = ensure(c->mlp_m2, kMlpParams * 4);
     if (e == cudaSuccess) e = ensure(c->mlp_wb, kMlpParams * 2);
-    if (e == cudaSuccess) e = ensure(c->mlp_norm, 16 * 4);
+    if (e == cudaSuccess) e = ensure(c->mlp_norm, 32 * 4);
     return e;
 }
 
@@ -1306,11 +1307,13 @@ nbody_status nbody_mlp_train(nbody_ctx *ctx, int32_t epochs, float lr, int32_t b
     const int32_t *png = &ctx->ds->ngroups;
     ctx->kernels = 0;
     launch_features(ctx);
-    launch_mlp_target(s, png, P<int32_t>(ctx->grp_cost), P<float>(ctx->target), ctx->nsm);
-    if (!ctx->mlp_norm_set) {
-        launch_mlp_norm(s, png, P<float>(ctx->feat), P<float>(ctx->mlp_norm));
+    if (!ctx->mlp_norm_set) {  // freeze feature and target statistics
+        launch_mlp_target(s, png, P<int32_t>(ctx->grp_cost), nullptr, P<float>(ctx->target), ctx->nsm);
+        launch_mlp_norm(s, png, P<float>(ctx->feat), P<float>(ctx->target), P<float>(ctx->mlp_norm));
         ctx->mlp_norm_set = true;
     }
+    launch_mlp_target(s, png, P<int32_t>(ctx->grp_cost), P<float>(ctx->mlp_norm) + 16,
+                      P<float>(ctx->target), ctx->nsm);
     __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(ctx->mlp_wb.p);
     for (int ep = 0; ep < epochs; ep++)
         for (int64_t k = 0; k < nbatches; k++) {
@@ -1344,10 +1347,10 @@ nbody_status nbody_mlp_predict(nbody_ctx *ctx, float *pred, float *features, int
     *n_groups = ng;
     if (ensure_mlp_buffers(ctx) != cudaSuccess) return fail(ctx, NBODY_ENOMEM, "allocation");
     launch_features(ctx);
+    const float *nrm = ctx->mlp_norm_set ? P<float>(ctx->mlp_norm) : nullptr;
     launch_mlp_forward(ctx->stream, &ctx->ds->ngroups, 0, P<float>(ctx->feat),
-                       reinterpret_cast<const __nv_bfloat16 *>(ctx->mlp_wb.p),
-                       ctx->mlp_norm_set ? P<float>(ctx->mlp_norm) : nullptr, P<float>(ctx->score),
-                       ctx->nsm);
+                       reinterpret_cast<const __nv_bfloat16 *>(ctx->mlp_wb.p), nrm,
+                       nrm ? nrm + 16 : nullptr, P<float>(ctx->score), ctx->nsm);
     NB_CUDA(ctx, cudaGetLastError());
     const int64_t k = std::min(cap, ng);
     if (k > 0 && pred) {
@@ -1398,7 +1401,7 @@ nbody_status nbody_mlp_eval(int64_t n, const float *features, const float *targe
     if (e == cudaSuccess && norm) e = h2d(dnorm, norm, 64);
     if (e == cudaSuccess) {
         launch_mlp_round(s, dparams, dwb);
-        launch_mlp_forward(s, nullptr, n, dfeat, dwb, norm ? dnorm : nullptr, dpred, 152);
+        launch_mlp_forward(s, nullptr, n, dfeat, dwb, norm ? dnorm : nullptr, nullptr, dpred, 152);
         e = launch_mlp_train_step(s, dfeat, dtarget, 0, 1, (int)n, dwb, norm ? dnorm : nullptr,
                                   dgpart, dlpart, dgrad, dloss, nullptr, nullptr, nullptr, nullptr,
                                   0.0f, 1, false);

@@ -211,7 +211,8 @@ void launch_mlp_features(cudaStream_t s, const Layout &L, const DevState *ds,
                          const uint64_t *keys, const float4 *nodeA, const int32_t *sys_root,
                          const SysBox *box, const int64_t *off, float *feat, int nsm);
 void launch_mlp_forward(cudaStream_t s, const int32_t *pn, int64_t n, const float *feat,
-                        const __nv_bfloat16 *wb, const float *norm, float *pred, int nsm);
+                        const __nv_bfloat16 *wb, const float *norm, const float *tnorm,
+                        float *pred, int nsm);
 size_t mlp_grad_smem();
 cudaError_t launch_mlp_train_step(cudaStream_t s, const float *feat, const float *target,
                                   int64_t base, int64_t stride, int count,
@@ -219,8 +220,10 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, const float *feat, const float
                                   float *lpart, float *grad, float *loss, float *w, float *m1,
                                   float *m2, __nv_bfloat16 *wb_out, float lr, int t, bool update);
 void launch_mlp_round(cudaStream_t s, const float *w, __nv_bfloat16 *wb);
-void launch_mlp_norm(cudaStream_t s, const int32_t *pn, const float *feat, float *norm);
-void launch_mlp_target(cudaStream_t s, const int32_t *pn, const int32_t *cost, float *target,
+void launch_mlp_norm(cudaStream_t s, const int32_t *pn, const float *feat, const float *target,
+                     float *norm);
+void launch_mlp_target(cudaStream_t s, const int32_t *pn, const int32_t *cost, const float *tnorm,
+                       float *target,
                        int nsm);
 void launch_order_keys(cudaStream_t s, const int32_t *pn, const float *score,
                        const int32_t *grp_count, uint64_t *key, uint32_t *val, int nsm);

@@ -127,18 +127,22 @@ __device__ __forceinline__ float mlp_fwd(const MlpSmem &S, const float *x, float
     return y;
 }
 
+// tnorm (nullable): target mean and standard deviation; the network output
+// is de-standardised with them.
 __global__ void __launch_bounds__(128) mlp_forward_kernel(const int32_t *__restrict__ pn, int64_t n_host,
                                                           const float *__restrict__ feat,
                                                           const __nv_bfloat16 *__restrict__ wb,
                                                           const float *__restrict__ norm,
+                                                          const float *__restrict__ tnorm,
                                                           float *__restrict__ pred) {
     __shared__ MlpSmem S;
     load_weights(S, wb, norm);
+    const float tm = tnorm ? tnorm[0] : 0.0f, ts = tnorm ? tnorm[1] : 1.0f;
     const int64_t n = pn ? (int64_t)*pn : n_host;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (int64_t)gridDim.x * blockDim.x) {
         float xn[kIn], h1[kH], h2[kH];
-        pred[g] = mlp_fwd(S, feat + g * kIn, xn, h1, h2);
+        pred[g] = fmaf(mlp_fwd(S, feat + g * kIn, xn, h1, h2), ts, tm);
     }
 }
 
@@ -272,24 +276,26 @@ __global__ void mlp_round_kernel(const float *__restrict__ w, __nv_bfloat16 *__r
     if (p < kMlpParams) wb[p] = __float2bfloat16_rn(w[p]);
 }
 
-// Per-feature mean and standard deviation over n samples (one block).
+// Mean and standard deviation of each feature and of the raw target over n
+// samples (one block): norm = {mean[8], std[8], target mean, target std}.
 __global__ void mlp_norm_kernel(const int32_t *__restrict__ pn, const float *__restrict__ feat,
-                                float *__restrict__ norm) {
-    __shared__ double s1[256][kIn], s2[256][kIn];
+                                const float *__restrict__ target, float *__restrict__ norm) {
+    constexpr int C = kIn + 1;
+    __shared__ double s1[256][C], s2[256][C];
     const int64_t n = *pn;
-    double a[kIn] = {0}, b[kIn] = {0};
+    double a[C] = {0}, b[C] = {0};
     for (int64_t g = threadIdx.x; g < n; g += blockDim.x)
-        for (int i = 0; i < kIn; i++) {
-            const double v = feat[g * kIn + i];
+        for (int i = 0; i < C; i++) {
+            const double v = i < kIn ? feat[g * kIn + i] : target[g];
             a[i] += v;
             b[i] += v * v;
         }
-    for (int i = 0; i < kIn; i++) {
+    for (int i = 0; i < C; i++) {
         s1[threadIdx.x][i] = a[i];
         s2[threadIdx.x][i] = b[i];
     }
     __syncthreads();
-    if (threadIdx.x < kIn) {
+    if (threadIdx.x < C) {
         double t1 = 0, t2 = 0;
         for (int q = 0; q < 256; q++) {
             t1 += s1[q][threadIdx.x];
@@ -297,17 +303,25 @@ __global__ void mlp_norm_kernel(const int32_t *__restrict__ pn, const float *__r
         }
         const double mean = n ? t1 / (double)n : 0.0;
         const double var = n ? t2 / (double)n - mean * mean : 1.0;
-        norm[threadIdx.x] = (float)mean;
-        norm[kIn + threadIdx.x] = (float)sqrt(var > 1e-12 ? var : 1.0);
+        const float sd = (float)sqrt(var > 1e-12 ? var : 1.0);
+        if (threadIdx.x < kIn) {
+            norm[threadIdx.x] = (float)mean;
+            norm[kIn + threadIdx.x] = sd;
+        } else {
+            norm[2 * kIn] = (float)mean;
+            norm[2 * kIn + 1] = sd;
+        }
     }
 }
 
-// log2 of the logged cost of each group (list entries, at least 1).
+// log2 of the logged cost of each group (list entries, at least 1), then
+// standardised with the frozen target statistics once they exist.
 __global__ void mlp_target_kernel(const int32_t *__restrict__ pn, const int32_t *__restrict__ cost,
-                                  float *__restrict__ target) {
+                                  const float *__restrict__ tnorm, float *__restrict__ target) {
     const int n = *pn;
+    const float tm = tnorm ? tnorm[0] : 0.0f, its = tnorm ? 1.0f / tnorm[1] : 1.0f;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x)
-        target[g] = __log2f((float)max(cost[g], 1));
+        target[g] = (__log2f((float)max(cost[g], 1)) - tm) * its;
 }
 
 // Queue keys: descending score -> ascending key; value = group id.  The score
@@ -357,8 +371,9 @@ void launch_mlp_features(cudaStream_t s, const Layout &L, const DevState *ds,
 }
 
 void launch_mlp_forward(cudaStream_t s, const int32_t *pn, int64_t n, const float *feat,
-                        const __nv_bfloat16 *wb, const float *norm, float *pred, int nsm) {
-    mlp_forward_kernel<<<nsm * 4, 128, 0, s>>>(pn, n, feat, wb, norm, pred);
+                        const __nv_bfloat16 *wb, const float *norm, const float *tnorm,
+                        float *pred, int nsm) {
+    mlp_forward_kernel<<<nsm * 4, 128, 0, s>>>(pn, n, feat, wb, norm, tnorm, pred);
 }
 
 size_t mlp_grad_smem() { return sizeof(GradSmem); }
@@ -390,13 +405,14 @@ void launch_mlp_round(cudaStream_t s, const float *w, __nv_bfloat16 *wb) {
     mlp_round_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(w, wb);
 }
 
-void launch_mlp_norm(cudaStream_t s, const int32_t *pn, const float *feat, float *norm) {
-    mlp_norm_kernel<<<1, 256, 0, s>>>(pn, feat, norm);
+void launch_mlp_norm(cudaStream_t s, const int32_t *pn, const float *feat, const float *target,
+                     float *norm) {
+    mlp_norm_kernel<<<1, 256, 0, s>>>(pn, feat, target, norm);
 }
 
-void launch_mlp_target(cudaStream_t s, const int32_t *pn, const int32_t *cost, float *target,
-                       int nsm) {
-    mlp_target_kernel<<<nsm * 4, 256, 0, s>>>(pn, cost, target);
+void launch_mlp_target(cudaStream_t s, const int32_t *pn, const int32_t *cost, const float *tnorm,
+                       float *target, int nsm) {
+    mlp_target_kernel<<<nsm * 4, 256, 0, s>>>(pn, cost, tnorm, target);
 }
 
 void launch_order_keys(cudaStream_t s, const int32_t *pn, const float *score,
