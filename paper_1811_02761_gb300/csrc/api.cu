@@ -90,6 +90,7 @@ struct nbody_ctx {
     GraphKey gkey{};
     int64_t gkernels = 0;
     bool capturing = false;  // enqueueing into a graph: no timing events
+    int walk_warps = 0;      // resident warps of the last walk launch
     int64_t kernels = 0;           // kernels launched by the current call
     bool built = false;
     bool eps_zero = false;  // some system of the last build has eps == 0
@@ -437,6 +438,7 @@ WalkShape walk_shape(nbody_ctx *c, bool geometric, bool phi, bool safe) {
     sh.compensated = c->cfg.compensated != 0;
     sh.safe = safe;
     sh.warps_per_block = c->cfg.warps_per_block;
+    sh.warps_launched = &c->walk_warps;
     return sh;
 }
 
@@ -532,6 +534,10 @@ nbody_status compute_order(nbody_ctx *c, const float *pcost, const int32_t **ord
     nbody_status st = host_ngroups(c, &ng);
     if (st != NBODY_OK) return st;
     if (ng < 1) return NBODY_OK;
+    // With no more groups than resident walk warps every group starts at once:
+    // no order can shorten the walk, and Morton order keeps neighbouring
+    // groups (which read the same nodes) together.
+    if (ng <= c->walk_warps) return NBODY_OK;
     cudaError_t e = ensure_mlp_buffers(c);
     if (e != cudaSuccess) return fail(c, NBODY_ENOMEM, "allocation");
     const int32_t *png = &c->ds->ngroups;

@@ -195,6 +195,7 @@ struct WalkShape {
     bool compensated;
     bool safe;                  // some eps == 0: guard the self term
     int warps_per_block;
+    int *warps_launched;        // host, nullable: receives the resident walk warps
 };
 cudaError_t launch_walk(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm);
 cudaError_t launch_direct(cudaStream_t s, int64_t n, const float *x, const float *y,

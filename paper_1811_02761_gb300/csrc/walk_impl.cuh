@@ -320,6 +320,7 @@ cudaError_t launch_walk_ipl(cudaStream_t s, const WalkArgs &a, const WalkShape &
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (sh.warps_launched) *sh.warps_launched = nsm * per_sm * sh.warps_per_block;
     k<<<nsm * per_sm, threads, smem, s>>>(a, sh.geometric ? 1 : 0);
     return cudaGetLastError();
 }
