@@ -36,60 +36,100 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
     s = t;
 }
 
+// The interaction list of a warp holds entries in pairs, structure-of-arrays
+// within the pair: LA[k] = (x_2k, x_2k+1, y_2k, y_2k+1) and LB[k] = (z_2k,
+// z_2k+1, m_2k, m_2k+1).  Two LDS.128 broadcasts then give every lane two
+// entries laid out for Blackwell's packed FP32 instructions (FFMA2/FADD2/
+// FMUL2), which evaluate Eq. 1 for both entries against one i-particle in one
+// instruction each -- half the issue slots of scalar code, which is what
+// bounds this loop.
+__device__ __forceinline__ void list_put(float4 *LA, float4 *LB, int e, float4 v) {
+    float *pa = reinterpret_cast<float *>(LA + (e >> 1));
+    float *pb = reinterpret_cast<float *>(LB + (e >> 1));
+    const int h = e & 1;
+    pa[h] = v.x;
+    pa[2 + h] = v.y;
+    pb[h] = v.z;
+    pb[2 + h] = v.w;
+}
+
+// Per-lane i-slot state: negated position, broadcast to both halves of a
+// packed pair, and the running sums (ax, ay, az, phi) with compensation.
+template <int IPL>
+struct ISlots {
+    float2 nx[IPL], ny[IPL], nz[IPL];
+    float mi[IPL];
+    float acc[IPL][4], cmp[IPL][4];
+};
+
 // Eq. 1 for the first NQ i-slots of every lane against the nl list entries.
 // NQ = ceil(group size / 32) <= IPL, so a small group does not pay for the
-// lane slots it leaves empty.
+// lane slots it leaves empty.  Each flush forms packed partial sums that are
+// folded into the running sums at its end (Neumaier-compensated with COMP).
 template <int NQ, int IPL, bool PHI, bool COMP, bool SAFE>
-__device__ __forceinline__ void flush_list(const float4 *list, int nl, float eps2,
-                                           const float (&xi)[IPL], const float (&yi)[IPL],
-                                           const float (&zi)[IPL], float (&acc)[IPL][4],
-                                           float (&cmp)[IPL][4]) {
-    float part[IPL][4];
-    if constexpr (COMP) {
-#pragma unroll
-        for (int q = 0; q < IPL; q++) part[q][0] = part[q][1] = part[q][2] = part[q][3] = 0.0f;
+__device__ __forceinline__ void flush_list(float4 *LA, float4 *LB, int nl, float eps2,
+                                           ISlots<IPL> &I) {
+    if (nl & 1) {  // pad to a whole pair with a massless, distant entry
+        if (lane_id() == 0) list_put(LA, LB, nl, make_float4(1e18f, 1e18f, 1e18f, 0.0f));
+        __syncwarp();
     }
-    float(&T)[IPL][4] = COMP ? part : acc;
-#pragma unroll 4
-    for (int k = 0; k < nl; k++) {
-        const float4 p = list[k];
+    const int np = (nl + 1) >> 1;
+    const float2 e2 = make_float2(eps2, eps2);
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
+    float2 sx[NQ], sy[NQ], sz[NQ], sp[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) sx[q] = sy[q] = sz[q] = sp[q] = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+    for (int k = 0; k < np; k++) {
+        const float4 A = LA[k], B = LB[k];
+        const float2 px = make_float2(A.x, A.y), py = make_float2(A.z, A.w);
+        const float2 pz = make_float2(B.x, B.y), pm = make_float2(B.z, B.w);
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            const float dx = p.x - xi[q], dy = p.y - yi[q], dz = p.z - zi[q];
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-            float rinv = rsqrt_fast(r2);
-            if constexpr (SAFE) rinv = r2 >= 1.17549435e-38f ? rinv : 0.0f;
-            const float mr = p.w * rinv;
-            const float w3 = mr * rinv * rinv;
-            T[q][0] = fmaf(w3, dx, T[q][0]);
-            T[q][1] = fmaf(w3, dy, T[q][1]);
-            T[q][2] = fmaf(w3, dz, T[q][2]);
-            if constexpr (PHI) T[q][3] -= mr;
+            const float2 dx = __fadd2_rn(px, I.nx[q]);
+            const float2 dy = __fadd2_rn(py, I.ny[q]);
+            const float2 dz = __fadd2_rn(pz, I.nz[q]);
+            float2 r2 = __ffma2_rn(dx, dx, e2);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            float2 ri = make_float2(rsqrt_fast(r2.x), rsqrt_fast(r2.y));
+            if constexpr (SAFE) {
+                ri.x = r2.x >= 1.17549435e-38f ? ri.x : 0.0f;
+                ri.y = r2.y >= 1.17549435e-38f ? ri.y : 0.0f;
+            }
+            const float2 mr = __fmul2_rn(pm, ri);
+            const float2 w3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
+            sx[q] = __ffma2_rn(w3, dx, sx[q]);
+            sy[q] = __ffma2_rn(w3, dy, sy[q]);
+            sz[q] = __ffma2_rn(w3, dz, sz[q]);
+            if constexpr (PHI) sp[q] = __ffma2_rn(mr, neg1, sp[q]);
         }
     }
-    if constexpr (COMP) {
 #pragma unroll
-        for (int q = 0; q < NQ; q++)
+    for (int q = 0; q < NQ; q++) {
+        const float part[4] = {sx[q].x + sx[q].y, sy[q].x + sy[q].y, sz[q].x + sz[q].y,
+                               sp[q].x + sp[q].y};
 #pragma unroll
-            for (int c = 0; c < 4; c++) neumaier_add(acc[q][c], cmp[q][c], part[q][c]);
+        for (int c = 0; c < 4; c++) {
+            if constexpr (COMP) neumaier_add(I.acc[q][c], I.cmp[q][c], part[c]);
+            else I.acc[q][c] += part[c];
+        }
     }
 }
 
 template <int IPL, bool PHI, bool COMP, bool SAFE>
-__device__ __forceinline__ void flush_group(int cnt, const float4 *list, int nl, float eps2,
-                                            const float (&xi)[IPL], const float (&yi)[IPL],
-                                            const float (&zi)[IPL], float (&acc)[IPL][4],
-                                            float (&cmp)[IPL][4]) {
+__device__ __forceinline__ void flush_group(int cnt, float4 *LA, float4 *LB, int nl, float eps2,
+                                            ISlots<IPL> &I) {
     if constexpr (IPL == 1) {
-        flush_list<1, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+        flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
     } else if constexpr (IPL == 2) {
-        if (cnt <= 32) flush_list<1, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
-        else flush_list<2, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+        if (cnt <= 32) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
+        else flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
     } else {
-        if (cnt <= 32) flush_list<1, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
-        else if (cnt <= 64) flush_list<2, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
-        else if (cnt <= 96) flush_list<3, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
-        else flush_list<4, IPL, PHI, COMP, SAFE>(list, nl, eps2, xi, yi, zi, acc, cmp);
+        if (cnt <= 32) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
+        else if (cnt <= 64) flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
+        else if (cnt <= 96) flush_list<3, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
+        else flush_list<4, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
     }
 }
 
@@ -98,8 +138,10 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
     extern __shared__ __align__(16) unsigned char walk_smem[];
     const int D = a.list_depth, S = a.stack_depth;
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    // per warp: the paired list (D entries = D/2 pairs in LA and LB) + stack
     const size_t per_warp = (size_t)D * sizeof(float4) + (size_t)S * sizeof(uint32_t);
-    float4 *list = reinterpret_cast<float4 *>(walk_smem + w * per_warp);
+    float4 *LA = reinterpret_cast<float4 *>(walk_smem + w * per_warp);
+    float4 *LB = LA + D / 2;
     uint32_t *stk = reinterpret_cast<uint32_t *>(walk_smem + w * per_warp + (size_t)D * sizeof(float4));
     DevState *ds = a.ds;
     const int ng = ds->ngroups;
@@ -123,15 +165,17 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
         const float eps2 = a.sys_eps2[sys];
         const int root = a.sys_root[sys];
 
-        float xi[IPL], yi[IPL], zi[IPL], mi[IPL];
-        float acc[IPL][4], cmp[IPL][4];
+        ISlots<IPL> I;
 #pragma unroll
         for (int q = 0; q < IPL; q++) {
             const int k = lane + 32 * q;
             float4 p = k < cnt ? a.pos4[first + k] : make_float4(sph.x, sph.y, sph.z, 0.0f);
-            xi[q] = p.x; yi[q] = p.y; zi[q] = p.z; mi[q] = p.w;
+            I.nx[q] = make_float2(-p.x, -p.x);
+            I.ny[q] = make_float2(-p.y, -p.y);
+            I.nz[q] = make_float2(-p.z, -p.z);
+            I.mi[q] = p.w;
 #pragma unroll
-            for (int c = 0; c < 4; c++) acc[q][c] = cmp[q][c] = 0.0f;
+            for (int c = 0; c < 4; c++) I.acc[q][c] = I.cmp[q][c] = 0.0f;
         }
 
         if (lane == 0) stk[0] = (uint32_t)root << 3;  // one node: the system's root
@@ -219,12 +263,12 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
             const int na = __popc(am);
             if (nl + na > D) {
                 __syncwarp();
-                flush_group<IPL, PHI, COMP, SAFE>(cnt, list, nl, eps2, xi, yi, zi, acc, cmp);
+                flush_group<IPL, PHI, COMP, SAFE>(cnt, LA, LB, nl, eps2, I);
                 entries += nl;
                 nl = 0;
                 __syncwarp();
             }
-            if (accept) list[nl + __popc(am & lt)] = A;
+            if (accept) list_put(LA, LB, nl + __popc(am & lt), A);
             nl += na;
 
             // ---- particles of opened leaves join the list
@@ -242,12 +286,12 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
                     const int c = (pc - off) < 32 ? (pc - off) : 32;
                     if (nl + c > D) {
                         __syncwarp();
-                        flush_group<IPL, PHI, COMP, SAFE>(cnt, list, nl, eps2, xi, yi, zi, acc, cmp);
+                        flush_group<IPL, PHI, COMP, SAFE>(cnt, LA, LB, nl, eps2, I);
                         entries += nl;
                         nl = 0;
                         __syncwarp();
                     }
-                    if ((int)lane < c) list[nl + lane] = __ldg(&a.pos4[pf + off + lane]);
+                    if ((int)lane < c) list_put(LA, LB, nl + lane, __ldg(&a.pos4[pf + off + lane]));
                     nl += c;
                 }
             }
@@ -255,7 +299,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
         }
         if (nl > 0) {
             __syncwarp();
-            flush_group<IPL, PHI, COMP, SAFE>(cnt, list, nl, eps2, xi, yi, zi, acc, cmp);
+            flush_group<IPL, PHI, COMP, SAFE>(cnt, LA, LB, nl, eps2, I);
             entries += nl;
             nl = 0;
         }
@@ -270,8 +314,8 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
             if (k < cnt) {
                 float r[4];
 #pragma unroll
-                for (int c = 0; c < 4; c++) r[c] = COMP ? acc[q][c] + cmp[q][c] : acc[q][c];
-                const float ph = PHI ? G * (r[3] + mi[q] * self) : 0.0f;
+                for (int c = 0; c < 4; c++) r[c] = COMP ? I.acc[q][c] + I.cmp[q][c] : I.acc[q][c];
+                const float ph = PHI ? G * (r[3] + I.mi[q] * self) : 0.0f;
                 const int i = first + k;
                 if (a.perm) {
                     const int o = a.perm[i];
@@ -297,8 +341,6 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
         if (overflow) atomicOr(&ds->status, kStatusStackOverflow);
     }
     if (bad) atomicOr(&ds->status, kStatusBadTree);
-    if (lane == 0) {
-    }
 }
 
 template <int IPL>
