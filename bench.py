@@ -49,9 +49,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("galaxy", "batched", "learned"), default="galaxy",
+    ap.add_argument("--workload", choices=("galaxy", "batched", "learned", "precision"),
+                    default="galaxy",
                     help="galaxy: N=2^23 three-component galaxy (the headline); batched: 512 "
-                         "independent Plummer/Hernquist systems, one forest per step")
+                         "independent Plummer/Hernquist systems, one forest per step; learned: "
+                         "MLP-ordered walk queue at N=25*2^20; precision: delta_acc sweep, plain "
+                         "vs compensated, error vs FP64 direct, FP64 energy/momentum drift")
     ap.add_argument("--nsys", type=int, default=512)
     ap.add_argument("--train-steps", type=int, default=20)
     ap.add_argument("--train-epochs", type=int, default=2)
@@ -62,6 +65,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--error-sample", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-sample", type=int, default=1 << 16)
+    ap.add_argument("--sweep-max", type=int, default=20)
+    ap.add_argument("--drift-steps", type=int, default=256)
+    ap.add_argument("--drift-every", type=int, default=32)
     ap.add_argument("--cpu-group-stride", type=int, default=32,
                     help="CPU baseline walks every k-th group of the full tree")
     return ap.parse_args()
@@ -154,6 +161,19 @@ def cpu_oracle_sample(p, group_stride, a_old=None):
 
 
 # ---------------------------------------------------------------------------- our arm
+def oracle_force_error(final, sample, seed):
+    """Relative error of the GPU accelerations against FP64 direct summation
+    (the oracle) on `sample` seeded particles at the final positions."""
+    import oracle
+    xs, ms, ga = final
+    tg = np.random.default_rng(seed).choice(ms.size, sample, replace=False)
+    bx, by, bz, _ = oracle.direct_targets(*xs, ms, tg, 1.0, EPS)
+    e = oracle.rel_err(*[a[tg].astype(np.float64) for a in ga], bx, by, bz)
+    return {"p50": oracle.percentile_nearest_rank(e, 50),
+            "p99": oracle.percentile_nearest_rank(e, 99), "max": float(e.max()),
+            "sample": int(sample), "vs": "FP64 direct summation at the final positions"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -225,20 +245,11 @@ def run_ours(args, rank, world, local_rank):
         e2e_wall = time.perf_counter() - w0
         e2e_s = max(e0.elapsed_time(e1) / 1e3, e2e_wall)
 
-        # force error of the final accelerations on a seeded sample (FP64 direct)
-        err = None
-        if rank == 0 and args.error_sample > 0:
-            import oracle
-            xs = [a.cpu().numpy().astype(np.float32).astype(np.float64) for a in X64]
-            ms = M.cpu().numpy().astype(np.float64)
-            tg = np.random.default_rng(args.seed).choice(n, args.error_sample, replace=False)
-            bx, by, bz, _ = oracle.direct_targets(*xs, ms, tg, 1.0, EPS)
-            ga = [a.cpu().numpy()[tg].astype(np.float64) for a in A]
-            e = oracle.rel_err(*ga, bx, by, bz)
-            err = {"p50": oracle.percentile_nearest_rank(e, 50),
-                   "p99": oracle.percentile_nearest_rank(e, 99), "max": float(e.max()),
-                   "sample": int(args.error_sample),
-                   "vs": "FP64 direct summation at the final positions"}
+        # final state on the host, for the oracle leg's force-error check
+        final = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            final = ([a.cpu().numpy().astype(np.float32).astype(np.float64) for a in X64],
+                     M.cpu().numpy().astype(np.float64), [a.cpu().numpy() for a in A])
     finally:
         nb.nbody_destroy(ctx)
 
@@ -257,8 +268,11 @@ def run_ours(args, rank, world, local_rank):
     peak_med = 2 * FP32_LANES_PER_SM * nsm * med * 1e6 / 1e12 if med else None
     whole_tflops = FLOPS_PER_INTERACTION * inter_per_step / s_per_step / 1e12
 
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    # oracle leg (rank 0, N = 1): the FP64 oracle tree walk on a bounded
+    # sample, timed on the host cores, and the FP64 direct sum at the final
+    # positions that states the force error of the GPU accelerations
+    cpu, err = None, None
+    if final is not None:
         ni, walk_s, build_s, thr, nsel, ng = cpu_oracle_sample(p, args.cpu_group_stride)
         cpu = {"value": ni / walk_s / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"FP64 oracle tree walk (group-mode acceleration MAC) of every "
@@ -266,6 +280,8 @@ def run_ours(args, rank, world, local_rank):
                          f"interactions) of the same N={n} galaxy; full oracle tree build "
                          f"{build_s:.2f} s timed separately",
                "build_s": build_s, "walk_s": walk_s}
+        if args.error_sample > 0:
+            err = oracle_force_error(final, args.error_sample, args.seed)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -488,6 +504,152 @@ def run_learned(args, rank, world, local_rank):
     }
 
 
+# ---------------------------------------------------------------------------- precision sweep
+def run_precision(args, rank, world, local_rank):
+    """Precision sweep on the galaxy: one tree, walks at delta_acc = 2^-1 ..
+    2^-sweep_max with plain and with compensated accumulation, each walk's
+    per-particle relative acceleration error against FP64 direct summation
+    (the oracle leg: the FP64 oracle on the host cores, run in a thread beside
+    the GPU work) on sweep_sample seeded particles; then the FP64 energy and
+    momentum drift of drift_steps leapfrog steps, plain and compensated, at
+    delta_acc = 2^-9.  Only rank 0 runs it."""
+    import threading
+
+    import torch
+
+    import ics
+    import paper_1811_02761_gb300 as nb
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    p = ics.galaxy(n, args.seed)
+    tg = np.sort(np.random.default_rng(args.seed + 1).choice(n, args.sweep_sample, replace=False))
+
+    ref = {}
+
+    def oracle_leg():
+        import oracle
+        xs = [np.asarray(p[k], np.float64) for k in ("x", "y", "z", "m")]
+        t0 = time.perf_counter()
+        ref["b"] = oracle.direct_targets(*xs, tg, 1.0, EPS)[:3]
+        ref["s"] = time.perf_counter() - t0
+        ref["threads"] = oracle.threads()
+
+    th = threading.Thread(target=oracle_leg, daemon=True)
+    th.start()
+
+    def D(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    M = D(p["m"])
+    stream = torch.cuda.current_stream(dev)
+    ctx = nb.nbody_create(nb.nbody_config_default(eps=EPS, delta_acc=DACC), stream)
+    rows, drift = [], {}
+    try:
+        A = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+        nb.nbody_build(ctx, *[D(p[k]) for k in ("x", "y", "z")], M)
+        nb.nbody_walk(ctx, None, *A)
+        amag = torch.sqrt(A[0] ** 2 + A[1] ** 2 + A[2] ** 2).contiguous()
+        nb.nbody_walk(ctx, amag, *A)
+        amag = torch.sqrt(A[0] ** 2 + A[1] ** 2 + A[2] ** 2).contiguous()
+        tgd = torch.from_numpy(tg).to(dev)
+        for k in range(1, args.sweep_max + 1):
+            for comp in (0, 1):
+                cfg = nb.nbody_get_config(ctx)
+                cfg.delta_acc, cfg.compensated = 2.0 ** -k, comp
+                while True:
+                    nb.nbody_set_config(ctx, cfg)
+                    try:
+                        st = nb.nbody_walk(ctx, amag, *A)
+                        break
+                    except nb.NbodyError as e:
+                        if e.status != nb.NBODY_EOVERFLOW or cfg.stack_depth >= 4096:
+                            raise
+                        cfg.stack_depth *= 2
+                ms = st.ms_walk_kernel / max(st.walk_launches, 1)
+                rows.append({"log2_delta_acc": -k, "compensated": comp, "walk_ms": ms,
+                             "interactions": int(st.interactions),
+                             "ginter_s": st.interactions / ms / 1e6,
+                             "stack_depth": int(cfg.stack_depth), "max_stack": int(st.max_stack),
+                             "a": [a[tgd].cpu().numpy().astype(np.float64) for a in A]})
+
+        for comp in (0, 1):
+            cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, compensated=comp)
+            nb.nbody_set_config(ctx, cfg)
+            X64 = [D(p[k]) for k in ("x64", "y64", "z64")]
+            V = [D(p[k]) for k in ("vx", "vy", "vz")]
+            nb.nbody_build(ctx, *[x.float() for x in X64], M)
+            nb.nbody_walk(ctx, None, *A)
+            phi = torch.empty(n, dtype=torch.float32, device=dev)
+            At = [torch.empty_like(a) for a in A]
+
+            def diagnose():
+                c2 = nb.nbody_get_config(ctx)
+                c2.want_potential = 1
+                nb.nbody_set_config(ctx, c2)
+                nb.nbody_build(ctx, *[x.float() for x in X64], M)
+                am = torch.sqrt(A[0] ** 2 + A[1] ** 2 + A[2] ** 2).contiguous()
+                nb.nbody_walk(ctx, am, *At, phi)
+                c2.want_potential = 0
+                nb.nbody_set_config(ctx, c2)
+                return nb.nbody_diagnostics(ctx, *X64, *V, M, phi)
+
+            d0 = diagnose()
+            hist, t_s, steps_done = [], 0.0, 0
+            while steps_done < args.drift_steps:
+                k = min(args.drift_every, args.drift_steps - steps_done)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                nb.nbody_step(ctx, *X64, *V, M, *A, DT, k)
+                ev1.record(stream)
+                torch.cuda.synchronize(dev)
+                t_s += ev0.elapsed_time(ev1) / 1e3
+                steps_done += k
+                hist.append((steps_done, diagnose()))
+            e0 = d0[0] + d0[1]
+            pscale = np.sqrt(2.0 * d0[0] * float(M.double().sum()))
+            drift[f"compensated={comp}"] = {
+                "E0": e0, "steps": steps_done, "s_per_step": t_s / steps_done,
+                "max_rel_dE": max(abs(d[0] + d[1] - e0) / abs(e0) for _, d in hist),
+                "final_rel_dE": (hist[-1][1][0] + hist[-1][1][1] - e0) / abs(e0),
+                "max_dP_over_rms_momentum": max(float(np.linalg.norm(d[2:5] - d0[2:5])) / pscale
+                                                for _, d in hist),
+                "max_rel_dL": max(float(np.linalg.norm(d[5:8] - d0[5:8]) /
+                                        max(np.linalg.norm(d0[5:8]), 1e-300)) for _, d in hist),
+                "every": args.drift_every}
+    finally:
+        nb.nbody_destroy(ctx)
+    th.join()
+
+    import oracle
+    bx, by, bz = ref["b"]
+    table = []
+    for r in rows:
+        e = oracle.rel_err(*r.pop("a"), bx, by, bz)
+        r.update(p50=oracle.percentile_nearest_rank(e, 50), p99=oracle.percentile_nearest_rank(e, 99),
+                 max=float(e.max()))
+        table.append(r)
+    head = next(r for r in table if r["log2_delta_acc"] == -9 and r["compensated"] == 0)
+    ni = tg.size * n
+    return {
+        "metric": METRIC, "value": head["ginter_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": 1, "warmup": 2, "ms_per_step": head["walk_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded three-component galaxy)",
+        "config": {"workload": f"precision sweep: galaxy N={n}, delta_acc 2^-1..2^-{args.sweep_max}, "
+                               f"plain vs compensated FP32 accumulation, error vs FP64 direct on "
+                               f"{tg.size} seeded particles; {args.drift_steps} leapfrog steps "
+                               f"dt=1/256 for the FP64 energy/momentum drift", "n": n},
+        "sweep": table, "drift": drift,
+        "cpu_baseline": {"value": ni / ref["s"] / 1e9, "unit": UNIT, "cores": ref["threads"],
+                         "kind": "oracle",
+                         "sample": f"FP64 direct summation (oracle) for {tg.size} targets over all "
+                                   f"{n} particles ({ni} interactions), run beside the GPU sweep"},
+    }
+
+
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -548,6 +710,8 @@ def main():
             out = run_batched(args, rank, world, local_rank)
         elif args.workload == "learned":
             out = run_learned(args, rank, world, local_rank)
+        elif args.workload == "precision":
+            out = run_precision(args, rank, world, local_rank)
         else:
             out = run_ours(args, rank, world, local_rank)
         if world > 1:
