@@ -189,9 +189,9 @@ bool config_ok(const nbody_config *c, std::string &why) {
     if (c->stack_depth < 64 || c->stack_depth > 4096) return bad("stack_depth must be in 64..4096");
     if (c->warps_per_block < 1 || c->warps_per_block > 16) return bad("warps_per_block must be in 1..16");
     if (c->schedule < 0 || c->schedule > 2) return bad("schedule must be 0, 1 or 2");
-    size_t smem = (size_t)c->warps_per_block *
-                  ((size_t)c->list_depth * 16 + (size_t)c->stack_depth * 4);
-    if (smem > 227 * 1024) return bad("warps_per_block * (16 list_depth + 4 stack_depth) exceeds 227 KB");
+    size_t smem = (size_t)c->warps_per_block * nb::walk_smem_per_warp(c->list_depth, c->stack_depth);
+    if (smem > 227 * 1024)
+        return bad("warps_per_block * (16 list_depth + 4 stack_depth + 128) exceeds 227 KB");
     return true;
 }
 

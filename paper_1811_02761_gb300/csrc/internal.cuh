@@ -164,6 +164,14 @@ void launch_group_alpha(cudaStream_t s, int64_t n, const DevState *ds, const int
                         float *grp_alpha, int nsm);
 
 // walk.cu
+// Shared memory of one walk warp: the list (16 B per entry), the traversal
+// stack (4 B per entry) and kWalkScratch words for compacting opened leaves,
+// rounded up to 16 B so that every warp's list stays float4-aligned.
+constexpr int kWalkScratch = 32;
+__host__ __device__ inline size_t walk_smem_per_warp(int list_depth, int stack_depth) {
+    const size_t b = (size_t)list_depth * 16 + (size_t)stack_depth * 4 + (size_t)kWalkScratch * 4;
+    return (b + 15) & ~(size_t)15;
+}
 struct WalkArgs {
     const float4 *pos4;
     const float4 *nodeA;

@@ -53,6 +53,12 @@ __device__ __forceinline__ void list_put(float4 *LA, float4 *LB, int e, float4 v
     pb[2 + h] = v.w;
 }
 
+// Unroll depth of the flush loop over entry pairs (build-time tunable).
+#ifndef NB_FLUSH_UNROLL
+#define NB_FLUSH_UNROLL 1
+#endif
+constexpr int kFlushUnroll = NB_FLUSH_UNROLL;
+
 // Per-lane i-slot state: negated position, broadcast to both halves of a
 // packed pair, and the running sums (ax, ay, az, phi) with compensation.
 template <int IPL>
@@ -79,7 +85,7 @@ __device__ __forceinline__ void flush_list(float4 *LA, float4 *LB, int nl, float
     float2 sx[NQ], sy[NQ], sz[NQ], sp[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; q++) sx[q] = sy[q] = sz[q] = sp[q] = make_float2(0.0f, 0.0f);
-#pragma unroll 2
+#pragma unroll kFlushUnroll
     for (int k = 0; k < np; k++) {
         const float4 A = LA[k], B = LB[k];
         const float2 px = make_float2(A.x, A.y), py = make_float2(A.z, A.w);
@@ -133,16 +139,24 @@ __device__ __forceinline__ void flush_group(int cnt, float4 *LA, float4 *LB, int
     }
 }
 
+// Build-time tuning of the walk kernel (register budget via a minimum number
+// of resident CTAs of 128 threads, and the unroll depth of the flush loop).
+#ifndef NB_WALK_MIN_CTAS
+#define NB_WALK_MIN_CTAS 2
+#endif
+
 template <int IPL, bool PHI, bool COMP, bool SAFE>
-__global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
+__global__ void __launch_bounds__(512, NB_WALK_MIN_CTAS) walk_kernel(WalkArgs a, int geometric) {
     extern __shared__ __align__(16) unsigned char walk_smem[];
     const int D = a.list_depth, S = a.stack_depth;
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
-    // per warp: the paired list (D entries = D/2 pairs in LA and LB) + stack
-    const size_t per_warp = (size_t)D * sizeof(float4) + (size_t)S * sizeof(uint32_t);
+    // per warp: the paired list (D entries = D/2 pairs in LA and LB), the
+    // stack and kWalkScratch words for the leaf compaction
+    const size_t per_warp = walk_smem_per_warp(D, S);
     float4 *LA = reinterpret_cast<float4 *>(walk_smem + w * per_warp);
     float4 *LB = LA + D / 2;
     uint32_t *stk = reinterpret_cast<uint32_t *>(walk_smem + w * per_warp + (size_t)D * sizeof(float4));
+    int *scr = reinterpret_cast<int *>(stk + S);
     DevState *ds = a.ds;
     const int ng = ds->ngroups;
     const int nnodes = ds->nnodes;
@@ -271,19 +285,27 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
             if (accept) list_put(LA, LB, nl + __popc(am & lt), A);
             nl += na;
 
-            // ---- particles of opened leaves join the list
-            unsigned lm = __ballot_sync(NB_FULL, open_leaf);
-            while (lm) {
-                const int src = __ffs(lm) - 1;
-                lm &= lm - 1;
-                const int pf = __shfl_sync(NB_FULL, link, src);
-                int pc = __shfl_sync(NB_FULL, mcount, src);
-                if (pf < 0 || pc < 0 || pf + pc > npart) {
-                    bad = true;
-                    pc = 0;
-                }
-                for (int off = 0; off < pc; off += 32) {
-                    const int c = (pc - off) < 32 ? (pc - off) : 32;
+            // ---- particles of opened leaves join the list, 32 per chunk: the
+            // opened leaves are compacted to lanes 0..nlf-1 (through the warp's
+            // scratch words), their counts scanned, and each chunk's slots are
+            // mapped to their leaf with a bit map of the leaf starts, as in the
+            // pop above -- one load latency per 32 particles, not per leaf
+            const bool leaf_ok = open_leaf && link >= 0 && mcount >= 1 && link + mcount <= npart;
+            if (open_leaf && !leaf_ok) bad = true;
+            const unsigned lm = __ballot_sync(NB_FULL, leaf_ok);
+            if (lm) {
+                const int nlf = __popc(lm);
+                if (leaf_ok) scr[__popc(lm & lt)] = (int)lane;
+                __syncwarp();
+                const int src = (int)lane < nlf ? scr[lane] : 0;
+                const int lf = __shfl_sync(NB_FULL, link, src);
+                const int lcs = __shfl_sync(NB_FULL, mcount, src);
+                const int lc = (int)lane < nlf ? lcs : 0;
+                const int lincl = warp_incl_scan(lc);
+                const int lexcl = lincl - lc;
+                const int total = __shfl_sync(NB_FULL, lincl, 31);
+                for (int base = 0; base < total; base += 32) {
+                    const int c = (total - base) < 32 ? (total - base) : 32;
                     if (nl + c > D) {
                         __syncwarp();
                         flush_group<IPL, PHI, COMP, SAFE>(cnt, LA, LB, nl, eps2, I);
@@ -291,7 +313,17 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
                         nl = 0;
                         __syncwarp();
                     }
-                    if ((int)lane < c) list_put(LA, LB, nl + lane, __ldg(&a.pos4[pf + off + lane]));
+                    // leaves are in increasing start order with counts >= 1, so
+                    // the owner of slot base+lane is the last leaf starting at
+                    // or before it: those before the chunk plus the starts
+                    // inside it up to this lane
+                    const bool starts = lc > 0 && lexcl >= base && lexcl < base + 32;
+                    const unsigned smap = __reduce_or_sync(NB_FULL, starts ? 1u << (lexcl - base) : 0u);
+                    const int before = __popc(__ballot_sync(NB_FULL, lc > 0 && lexcl < base));
+                    const int k = before + __popc(smap & (0xffffffffu >> (31 - lane))) - 1;
+                    const int of = __shfl_sync(NB_FULL, lf, k & 31);
+                    const int oex = __shfl_sync(NB_FULL, lexcl, k & 31);
+                    if ((int)lane < c) list_put(LA, LB, nl + lane, __ldg(&a.pos4[of + base + (int)lane - oex]));
                     nl += c;
                 }
             }
@@ -346,8 +378,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs a, int geometric) {
 template <int IPL>
 cudaError_t launch_walk_ipl(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm) {
     const int threads = 32 * sh.warps_per_block;
-    const size_t smem = (size_t)sh.warps_per_block *
-                        ((size_t)a.list_depth * sizeof(float4) + (size_t)a.stack_depth * sizeof(uint32_t));
+    const size_t smem = (size_t)sh.warps_per_block * walk_smem_per_warp(a.list_depth, a.stack_depth);
     void (*k)(WalkArgs, int);
     if (sh.potential) {
         if (sh.compensated) k = sh.safe ? walk_kernel<IPL, true, true, true> : walk_kernel<IPL, true, true, false>;

@@ -215,6 +215,23 @@ def test_walk_deterministic(plummer8k):
     assert np.array_equal(a1, a2)
 
 
+@pytest.mark.parametrize("wpb,stack,depth", [(3, 97, 96), (1, 65, 64), (16, 130, 128)])
+def test_walk_launch_shape_does_not_change_forces(plummer8k, wpb, stack, depth):
+    """Warps per CTA, stack depth (also ones that are not a multiple of 4) and
+    list depth change only how the groups are laid out on the GPU, and the
+    flush points, never a group's traversal: the MAC decisions and the
+    interaction count are identical and the forces agree to rounding."""
+    p, (ax, ay, az, _) = plummer8k
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2).astype(np.float32)
+    base = nb.nbody_config_default(eps=EPS, delta_acc=DACC)
+    (a1, _, _, _), st1, _ = gpu_walk(p, base, a_old=amag)
+    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, warps_per_block=wpb,
+                                  stack_depth=stack, list_depth=depth)
+    (a2, _, _, _), st2, _ = gpu_walk(p, cfg, a_old=amag)
+    assert st1.interactions == st2.interactions
+    assert np.max(np.abs(a1 - a2)) <= 1e-5 * np.max(np.abs(a1))
+
+
 # --------------------------------------------------------------------------- edge cases
 @pytest.mark.parametrize("n", [1, 2, 15, 16, 17, 100, 8192 + 13])
 def test_walk_small_and_ragged_n(n):
