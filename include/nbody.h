@@ -71,7 +71,9 @@ typedef struct {
                             no |a_old| is given, 0 < theta < 1 (default 0.5)        */
     int32_t leaf_cap;    /* max particles in a leaf, 1..32 (default 16)             */
     int32_t group_size;  /* max particles sharing one list, leaf_cap..32*ipl (64)   */
-    int32_t ipl;         /* i-particles per lane of a walking warp: 1, 2 or 4 (2)   */
+    int32_t ipl;         /* most i-particles a lane of a walking warp holds, 1..4;
+                            a group is tiled over the lanes as q <= ipl particles
+                            per lane times 32 / ceil(size / q) list splits (3)    */
     int32_t list_depth;  /* interaction-list entries per warp, 64..1024, multiple
                             of 32 (default 256)                                    */
     int32_t stack_depth; /* traversal stack entries per warp, 64..4096 (256)        */
@@ -219,7 +221,8 @@ nbody_status nbody_get_group_costs(nbody_ctx *ctx, int32_t *counts, int64_t cap,
 /* Autotuner search space (the analogue of the paper's micro-benchmarked
  * thread-block configuration, Sect. 2.2 Table 2).  Each list holds n_*
  * candidates; combinations violating the config rules (leaf_cap <=
- * group_size <= 32 ipl, group_size > 16 ipl) are skipped. */
+ * group_size <= 32 ipl) are skipped, and so are those with group_size <=
+ * 8 ipl, whose extra i-slots no lane tiling would use. */
 typedef struct {
     int32_t n_leaf_cap, leaf_cap[4];
     int32_t n_group_size, group_size[6];
@@ -229,7 +232,7 @@ typedef struct {
     int32_t repeats;            /* timed walks per candidate (the minimum counts) */
 } nbody_tune_space;
 
-/* Default space: leaf_cap {8, 16}, group_size {32, 64, 128}, ipl {1, 2, 4},
+/* Default space: leaf_cap {8, 16}, group_size {32, 64, 128}, ipl {2, 3, 4},
  * list_depth {128, 256}, warps_per_block {2, 4, 8}, repeats 2. */
 void nbody_tune_space_default(nbody_tune_space *space);
 

@@ -176,7 +176,7 @@ bool config_ok(const nbody_config *c, std::string &why) {
     if (!(c->delta_acc >= 0.0f) || !std::isfinite(c->delta_acc)) return bad("delta_acc must be finite and >= 0");
     if (!(c->theta > 0.0f && c->theta < 1.0f)) return bad("theta must be in (0, 1)");
     if (!std::isfinite(c->G)) return bad("G must be finite");
-    if (c->ipl != 1 && c->ipl != 2 && c->ipl != 4) return bad("ipl must be 1, 2 or 4");
+    if (c->ipl < 1 || c->ipl > 4) return bad("ipl must be in 1..4");
     if (c->leaf_cap < 1 || c->leaf_cap > 32) return bad("leaf_cap must be in 1..32");
     if (c->group_size < c->leaf_cap || c->group_size > 32 * c->ipl) {
         snprintf(buf, sizeof buf, "group_size must be in leaf_cap..32*ipl (%d..%d)", c->leaf_cap,
@@ -636,7 +636,7 @@ void nbody_config_default(nbody_config *c) {
     c->theta = 0.5f;
     c->leaf_cap = 16;
     c->group_size = 64;
-    c->ipl = 2;
+    c->ipl = 3;
     c->list_depth = 256;
     c->stack_depth = 256;
     c->warps_per_block = 4;
@@ -1114,8 +1114,8 @@ void nbody_tune_space_default(nbody_tune_space *sp) {
     sp->group_size[1] = 64;
     sp->group_size[2] = 128;
     sp->n_ipl = 3;
-    sp->ipl[0] = 1;
-    sp->ipl[1] = 2;
+    sp->ipl[0] = 2;
+    sp->ipl[1] = 3;
     sp->ipl[2] = 4;
     sp->n_list_depth = 2;
     sp->list_depth[0] = 128;
@@ -1164,7 +1164,7 @@ nbody_status nbody_autotune(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets
                 c.leaf_cap = sp.leaf_cap[il];
                 c.group_size = sp.group_size[ig];
                 c.ipl = sp.ipl[ii];
-                if (c.group_size <= 16 * c.ipl) continue;  // wastes half the i-slots
+                if (c.group_size <= 8 * c.ipl) continue;  // slots beyond any useful tile
                 std::string why;
                 c.list_depth = sp.list_depth[0];
                 c.warps_per_block = sp.warps_per_block[0];

@@ -9,12 +9,14 @@ template <int IPL>
 cudaError_t launch_walk_ipl(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm);
 extern template cudaError_t launch_walk_ipl<1>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
 extern template cudaError_t launch_walk_ipl<2>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
+extern template cudaError_t launch_walk_ipl<3>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
 extern template cudaError_t launch_walk_ipl<4>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
 
 cudaError_t launch_walk(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm) {
     switch (sh.ipl) {
         case 1: return launch_walk_ipl<1>(s, a, sh, nsm);
         case 2: return launch_walk_ipl<2>(s, a, sh, nsm);
+        case 3: return launch_walk_ipl<3>(s, a, sh, nsm);
         case 4: return launch_walk_ipl<4>(s, a, sh, nsm);
         default: return cudaErrorInvalidValue;
     }

@@ -5,7 +5,9 @@
 //   * persistent grid, one warp per i-group, groups popped from a device queue
 //     (one atomicAdd per group); the queue order is Morton order or a cost
 //     order chosen by the scheduler;
-//   * each lane holds IPL i-particles (group <= 32*IPL particles);
+//   * each lane holds up to IPL i-particles (group <= 32*IPL particles); a
+//     group is tiled over the lanes as q particles per lane times s splits
+//     of the list, so that few lanes idle in the flush (lane_tile below);
 //   * traversal: a per-warp stack in shared memory whose entries are child
 //     ranges (first node, count <= 8).  Each round the warp pops up to 32
 //     nodes (one per lane), evaluates the MAC of Eq. 2 against the group's
@@ -14,9 +16,10 @@
 //       opened internal node -> its child range is pushed,
 //       opened leaf          -> its particles join the list;
 //   * the list (float4 x, y, z, m in shared memory) is flushed whenever the
-//     next append would overflow it: every lane evaluates Eq. 1 for its IPL
-//     particles against every entry, reading each entry as one broadcast
-//     LDS.128 -- 12 FP32-pipe instructions + 1 MUFU.RSQ per interaction;
+//     next append would overflow it: every lane evaluates Eq. 1 for its q
+//     particles against its split of the entries, read as pairs (two LDS.128)
+//     laid out for the packed FP32 instructions -- 12 FP32-pipe operations +
+//     1 MUFU.RSQ per interaction;
 //   * optional Neumaier compensation of the per-flush partial sums.
 // No warp ever waits on another warp or CTA.
 #pragma once
@@ -60,21 +63,26 @@ __device__ __forceinline__ void list_put(float4 *LA, float4 *LB, int e, float4 v
 constexpr int kFlushUnroll = NB_FLUSH_UNROLL;
 
 // Per-lane i-slot state: negated position, broadcast to both halves of a
-// packed pair, and the running sums (ax, ay, az, phi) with compensation.
+// packed pair, and the running sums of (ax, ay, az, phi): packed pairs that
+// every flush accumulates into (plain), or scalars with Neumaier compensation
+// that take each flush's packed partial sums (compensated).  Only the members
+// a variant uses occupy registers.
 template <int IPL>
 struct ISlots {
     float2 nx[IPL], ny[IPL], nz[IPL];
     float mi[IPL];
+    float2 run[IPL][4];
     float acc[IPL][4], cmp[IPL][4];
 };
 
-// Eq. 1 for the first NQ i-slots of every lane against the nl list entries.
-// NQ = ceil(group size / 32) <= IPL, so a small group does not pay for the
-// lane slots it leaves empty.  Each flush forms packed partial sums that are
-// folded into the running sums at its end (Neumaier-compensated with COMP).
+// Eq. 1 for the first NQ i-slots of a lane against its share of the nl list
+// entries: the entry pairs k0, k0 + ks, k0 + 2 ks, ... (see the lane tiling
+// below).  Plain sums accumulate straight into the packed running sums; with
+// COMP each flush forms packed partial sums that are folded into the running
+// sums at its end with Neumaier compensation.
 template <int NQ, int IPL, bool PHI, bool COMP, bool SAFE>
-__device__ __forceinline__ void flush_list(float4 *LA, float4 *LB, int nl, float eps2,
-                                           ISlots<IPL> &I) {
+__device__ __forceinline__ void flush_list(float4 *LA, float4 *LB, int nl, float eps2, int k0,
+                                           int ks, ISlots<IPL> &I) {
     if (nl & 1) {  // pad to a whole pair with a massless, distant entry
         if (lane_id() == 0) list_put(LA, LB, nl, make_float4(1e18f, 1e18f, 1e18f, 0.0f));
         __syncwarp();
@@ -84,9 +92,18 @@ __device__ __forceinline__ void flush_list(float4 *LA, float4 *LB, int nl, float
     const float2 neg1 = make_float2(-1.0f, -1.0f);
     float2 sx[NQ], sy[NQ], sz[NQ], sp[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; q++) sx[q] = sy[q] = sz[q] = sp[q] = make_float2(0.0f, 0.0f);
+    for (int q = 0; q < NQ; q++) {
+        if constexpr (COMP) {
+            sx[q] = sy[q] = sz[q] = sp[q] = make_float2(0.0f, 0.0f);
+        } else {
+            sx[q] = I.run[q][0];
+            sy[q] = I.run[q][1];
+            sz[q] = I.run[q][2];
+            sp[q] = I.run[q][3];
+        }
+    }
 #pragma unroll kFlushUnroll
-    for (int k = 0; k < np; k++) {
+    for (int k = k0; k < np; k += ks) {
         const float4 A = LA[k], B = LB[k];
         const float2 px = make_float2(A.x, A.y), py = make_float2(A.z, A.w);
         const float2 pz = make_float2(B.x, B.y), pm = make_float2(B.z, B.w);
@@ -113,40 +130,87 @@ __device__ __forceinline__ void flush_list(float4 *LA, float4 *LB, int nl, float
     }
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
-        const float part[4] = {sx[q].x + sx[q].y, sy[q].x + sy[q].y, sz[q].x + sz[q].y,
-                               sp[q].x + sp[q].y};
+        if constexpr (COMP) {
+            const float part[4] = {sx[q].x + sx[q].y, sy[q].x + sy[q].y, sz[q].x + sz[q].y,
+                                   sp[q].x + sp[q].y};
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            if constexpr (COMP) neumaier_add(I.acc[q][c], I.cmp[q][c], part[c]);
-            else I.acc[q][c] += part[c];
+            for (int c = 0; c < 4; c++) neumaier_add(I.acc[q][c], I.cmp[q][c], part[c]);
+        } else {
+            I.run[q][0] = sx[q];
+            I.run[q][1] = sy[q];
+            I.run[q][2] = sz[q];
+            I.run[q][3] = sp[q];
         }
     }
 }
 
 template <int IPL, bool PHI, bool COMP, bool SAFE>
-__device__ __forceinline__ void flush_group(int cnt, float4 *LA, float4 *LB, int nl, float eps2,
-                                            ISlots<IPL> &I) {
+__device__ __forceinline__ void flush_group(int q, int k0, int ks, float4 *LA, float4 *LB, int nl,
+                                            float eps2, ISlots<IPL> &I) {
     if constexpr (IPL == 1) {
-        flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
+        flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
     } else if constexpr (IPL == 2) {
-        if (cnt <= 32) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
-        else flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
+        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        else flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+    } else if constexpr (IPL == 3) {
+        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        else if (q == 2) flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        else flush_list<3, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
     } else {
-        if (cnt <= 32) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
-        else if (cnt <= 64) flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
-        else if (cnt <= 96) flush_list<3, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
-        else flush_list<4, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, I);
+        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        else if (q == 2) flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        else if (q == 3) flush_list<3, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        else flush_list<4, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
     }
 }
 
-// Build-time tuning of the walk kernel (register budget via a minimum number
-// of resident CTAs of 128 threads, and the unroll depth of the flush loop).
-#ifndef NB_WALK_MIN_CTAS
-#define NB_WALK_MIN_CTAS 2
+// Lane tiling of a group of cnt particles: each lane holds q <= IPL of them
+// (the t-th at index row + P t), P = ceil(cnt / q) rows, and the list is cut
+// into s = floor(32 / P) splits; lane L is row L % P of split L / P (lanes
+// with L / P >= s stay idle) and takes the entry pairs split, split + s, ...
+// The q with the least work per lane, q / s, is chosen (the smallest such q).
+// Against one slot layout of ceil(cnt / 32) particles per lane this recovers
+// most of the lanes a group smaller than a multiple of 32 leaves empty; the
+// splits are summed once per group.
+struct LaneTile {
+    int q, P, s;
+};
+template <int IPL>
+__device__ __forceinline__ LaneTile lane_tile(int cnt) {
+    LaneTile t{IPL, 32, 1};
+    bool found = false;
+#pragma unroll
+    for (int q = 1; q <= IPL; q++) {
+        const int P = (cnt + q - 1) / q;
+        if (P > 32) continue;
+        const int s = 32 / P;
+        if (!found || q * t.s < t.q * s) {
+            t = LaneTile{q, P, s};
+            found = true;
+        }
+    }
+    return t;
+}
+
+// Register budget of the walk kernel per thread: 64 (32 resident warps per
+// SM) while a lane holds at most two i-particles; more slots need more
+// registers for the positions and sums they keep (build-time tunable).
+#ifndef NB_WALK_REGS_2
+#define NB_WALK_REGS_2 64
 #endif
+#ifndef NB_WALK_REGS_3
+#define NB_WALK_REGS_3 80
+#endif
+#ifndef NB_WALK_REGS_4
+#define NB_WALK_REGS_4 96
+#endif
+template <int IPL>
+constexpr int walk_regs() {
+    return IPL <= 2 ? NB_WALK_REGS_2 : (IPL == 3 ? NB_WALK_REGS_3 : NB_WALK_REGS_4);
+}
 
 template <int IPL, bool PHI, bool COMP, bool SAFE>
-__global__ void __launch_bounds__(512, NB_WALK_MIN_CTAS) walk_kernel(WalkArgs a, int geometric) {
+__global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geometric) {
     extern __shared__ __align__(16) unsigned char walk_smem[];
     const int D = a.list_depth, S = a.stack_depth;
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
@@ -179,17 +243,26 @@ __global__ void __launch_bounds__(512, NB_WALK_MIN_CTAS) walk_kernel(WalkArgs a,
         const float eps2 = a.sys_eps2[sys];
         const int root = a.sys_root[sys];
 
+        if (cnt > 32 * IPL) bad = true;  // larger than the group size allows
+        const LaneTile tile = lane_tile<IPL>(cnt);
+        const int row = (int)lane % tile.P, split = (int)lane / tile.P;
+        const int k0 = split < tile.s ? split : (1 << 30);  // idle lanes take no pairs
+
         ISlots<IPL> I;
 #pragma unroll
         for (int q = 0; q < IPL; q++) {
-            const int k = lane + 32 * q;
-            float4 p = k < cnt ? a.pos4[first + k] : make_float4(sph.x, sph.y, sph.z, 0.0f);
+            const int k = row + tile.P * q;
+            float4 p = (q < tile.q && k < cnt) ? a.pos4[first + k]
+                                              : make_float4(sph.x, sph.y, sph.z, 0.0f);
             I.nx[q] = make_float2(-p.x, -p.x);
             I.ny[q] = make_float2(-p.y, -p.y);
             I.nz[q] = make_float2(-p.z, -p.z);
             I.mi[q] = p.w;
 #pragma unroll
-            for (int c = 0; c < 4; c++) I.acc[q][c] = I.cmp[q][c] = 0.0f;
+            for (int c = 0; c < 4; c++) {
+                I.acc[q][c] = I.cmp[q][c] = 0.0f;
+                I.run[q][c] = make_float2(0.0f, 0.0f);
+            }
         }
 
         if (lane == 0) stk[0] = (uint32_t)root << 3;  // one node: the system's root
@@ -277,7 +350,7 @@ __global__ void __launch_bounds__(512, NB_WALK_MIN_CTAS) walk_kernel(WalkArgs a,
             const int na = __popc(am);
             if (nl + na > D) {
                 __syncwarp();
-                flush_group<IPL, PHI, COMP, SAFE>(cnt, LA, LB, nl, eps2, I);
+                flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, LB, nl, eps2, I);
                 entries += nl;
                 nl = 0;
                 __syncwarp();
@@ -308,7 +381,7 @@ __global__ void __launch_bounds__(512, NB_WALK_MIN_CTAS) walk_kernel(WalkArgs a,
                     const int c = (total - base) < 32 ? (total - base) : 32;
                     if (nl + c > D) {
                         __syncwarp();
-                        flush_group<IPL, PHI, COMP, SAFE>(cnt, LA, LB, nl, eps2, I);
+                        flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, LB, nl, eps2, I);
                         entries += nl;
                         nl = 0;
                         __syncwarp();
@@ -331,22 +404,43 @@ __global__ void __launch_bounds__(512, NB_WALK_MIN_CTAS) walk_kernel(WalkArgs a,
         }
         if (nl > 0) {
             __syncwarp();
-            flush_group<IPL, PHI, COMP, SAFE>(cnt, LA, LB, nl, eps2, I);
+            flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, LB, nl, eps2, I);
             entries += nl;
             nl = 0;
         }
         __syncwarp();
+
+        // ---- sum the list splits of every particle onto split 0
+        for (int t = 1; t < tile.s; t++) {
+            const int src = row + tile.P * t;
+#pragma unroll
+            for (int q = 0; q < IPL; q++) {
+                if (q < tile.q) {  // warp-uniform
+#pragma unroll
+                    for (int c = 0; c < (PHI ? 4 : 3); c++) {
+                        const float mine = COMP ? I.acc[q][c] + I.cmp[q][c]
+                                                : I.run[q][c].x + I.run[q][c].y;
+                        const float v = __shfl_sync(NB_FULL, mine, src);
+                        if (split == 0) {
+                            if constexpr (COMP) neumaier_add(I.acc[q][c], I.cmp[q][c], v);
+                            else I.run[q][c].x += v;
+                        }
+                    }
+                }
+            }
+        }
 
         // ---- results (G applied once; the potential's self term removed)
         const float G = a.G;
         const float self = SAFE ? 0.0f : rsqrt_fast(eps2);
 #pragma unroll
         for (int q = 0; q < IPL; q++) {
-            const int k = lane + 32 * q;
-            if (k < cnt) {
+            const int k = row + tile.P * q;
+            if (split == 0 && q < tile.q && k < cnt) {
                 float r[4];
 #pragma unroll
-                for (int c = 0; c < 4; c++) r[c] = COMP ? I.acc[q][c] + I.cmp[q][c] : I.acc[q][c];
+                for (int c = 0; c < 4; c++)
+                    r[c] = COMP ? I.acc[q][c] + I.cmp[q][c] : I.run[q][c].x + I.run[q][c].y;
                 const float ph = PHI ? G * (r[3] + I.mi[q] * self) : 0.0f;
                 const int i = first + k;
                 if (a.perm) {

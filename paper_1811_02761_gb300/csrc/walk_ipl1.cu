@@ -1,4 +1,4 @@
-// walk_ipl1.cu -- instances of the tree walk with 1 i-particle(s) per lane
+// walk_ipl1.cu -- instances of the tree walk with up to 1 i-particle per lane
 // (separate translation unit so the instances compile in parallel).
 #include "walk_impl.cuh"
 

@@ -1,4 +1,4 @@
-// walk_ipl4.cu -- instances of the tree walk with 4 i-particle(s) per lane
+// walk_ipl4.cu -- instances of the tree walk with up to 4 i-particles per lane
 // (separate translation unit so the instances compile in parallel).
 #include "walk_impl.cuh"
 

@@ -38,7 +38,7 @@ def test_abi_version_and_defaults():
     assert c.group_size <= 32 * c.ipl
 
 
-@pytest.mark.parametrize("bad", [dict(ipl=3), dict(leaf_cap=0), dict(group_size=8, leaf_cap=16),
+@pytest.mark.parametrize("bad", [dict(ipl=5), dict(ipl=0), dict(leaf_cap=0), dict(group_size=8, leaf_cap=16),
                                  dict(group_size=128, ipl=2), dict(list_depth=100),
                                  dict(eps=-1.0), dict(theta=1.5), dict(delta_acc=-1e-3),
                                  dict(warps_per_block=16, list_depth=1024, stack_depth=4096)])
