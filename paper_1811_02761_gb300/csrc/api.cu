@@ -60,8 +60,8 @@ struct nbody_ctx {
     DevBuf keys, keys_alt, vals, vals_alt, pos4, delta, leaflev;
     DevBuf rs_temp, tree_temp, grp_temp, diag_temp, diag_out;
     // nodes
-    DevBuf node_start, node_level, node_parent, node_link, node_count, node_nchild, node_arrive;
-    DevBuf nodeA, nodeB, mom64;
+    DevBuf node_start, node_level, node_parent, node_link, node_count, node_nchild;
+    DevBuf nodeA, nodeB, mass2;
     // groups
     DevBuf gflag, grp_first, grp_count, grp_sphere, grp_sys, grp_alpha, grp_cost, grp_order;
     // systems
@@ -101,8 +101,8 @@ struct nbody_ctx {
     nbody_ctx() {
         DevBuf *all[] = {&keys, &keys_alt, &vals, &vals_alt, &pos4, &delta, &leaflev, &rs_temp,
                          &tree_temp, &grp_temp, &diag_temp, &diag_out, &node_start, &node_level,
-                         &node_parent, &node_link, &node_count, &node_nchild, &node_arrive,
-                         &nodeA, &nodeB, &mom64, &gflag, &grp_first, &grp_count, &grp_sphere,
+                         &node_parent, &node_link, &node_count, &node_nchild,
+                         &nodeA, &nodeB, &mass2, &gflag, &grp_first, &grp_count, &grp_sphere,
                          &grp_sys, &grp_alpha, &grp_cost, &grp_order, &sys_off, &sys_box,
                          &sys_boxord, &sys_eps2, &sys_root, &acc_s, &aold_s, &mlp_w, &mlp_m1,
                          &mlp_m2, &mlp_wb, &mlp_norm, &mlp_gpart, &mlp_lpart, &mlp_loss, &feat,
@@ -263,9 +263,8 @@ cudaError_t ensure_capacity(nbody_ctx *c, int64_t n, int nsys, int levels) {
         NB_E(ensure(c->node_start, cn * 4)); NB_E(ensure(c->node_level, cn));
         NB_E(ensure(c->node_parent, cn * 4)); NB_E(ensure(c->node_link, cn * 4));
         NB_E(ensure(c->node_count, cn * 4)); NB_E(ensure(c->node_nchild, cn * 4));
-        NB_E(ensure(c->node_arrive, cn * 4));
         NB_E(ensure(c->nodeA, cn * 16)); NB_E(ensure(c->nodeB, cn * 16));
-        NB_E(ensure(c->mom64, cn * 32));
+        NB_E(ensure(c->mass2, cn * 8));
         c->cap_nodes = cn;
     }
     if (nsys > c->cap_sys) {
@@ -322,8 +321,8 @@ nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
                P<int64_t>(c->sys_off), c->cfg.leaf_cap, c->cfg.G, c->cap_nodes, P<int8_t>(c->delta),
                P<int8_t>(c->leaflev), c->tree_temp.p, c->ds, P<int32_t>(c->node_start),
                P<int8_t>(c->node_level), P<int32_t>(c->node_parent), P<int32_t>(c->node_link),
-               P<int32_t>(c->node_count), P<int32_t>(c->node_nchild), P<int32_t>(c->node_arrive),
-               P<float4>(c->nodeA), P<float4>(c->nodeB), P<Mom64>(c->mom64),
+               P<int32_t>(c->node_count), P<int32_t>(c->node_nchild),
+               P<float4>(c->nodeA), P<float4>(c->nodeB), P<float2>(c->mass2),
                P<int32_t>(c->sys_root), c->nsm);
     build_groups(s, L, c->cfg.group_size, P<float4>(c->pos4), P<int64_t>(c->sys_off),
                  P<int32_t>(c->node_start), P<int32_t>(c->node_parent), P<int32_t>(c->node_count),
@@ -331,7 +330,9 @@ nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
                  P<uint8_t>(c->gflag), c->grp_temp.p, P<int32_t>(c->grp_first),
                  P<int32_t>(c->grp_count), P<float4>(c->grp_sphere), P<int32_t>(c->grp_sys),
                  c->nsm);
-    c->kernels += 7 + 5;
+    // tree: leaflevel, level scan, level offsets, nodes, two system-root
+    // kernels, leaf moments, one internal-moments launch per level; groups: 5
+    c->kernels += 6 + 1 + L.levels + 5;
     NB_CUDA(c, cudaGetLastError());
     return NBODY_OK;
 }
@@ -873,7 +874,10 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         S[b].m = P<float>(ctx->st_buf[b][6]);
         S[b].aold = P<float>(ctx->st_buf[b][7]);
         S[b].id = P<uint32_t>(ctx->st_buf[b][8]);
-        S[b].pcost = P<float>(ctx->st_buf[b][9]);
+        // the per-particle cost of the last walk is carried only for the
+        // schedule that reads it
+        S[b].pcost = ctx->cfg.schedule == NBODY_SCHED_LASTCOST ? P<float>(ctx->st_buf[b][9])
+                                                               : nullptr;
     }
     const size_t db = (size_t)n * 8, fb = (size_t)n * 4;
     const void *in[10];
@@ -919,9 +923,12 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         r = run_walk(ctx, false, false, safe, nullptr, nullptr, nullptr, nullptr, nullptr, acc, false,
                      S[cur].pcost);
         if (r != NBODY_OK) return r;
-        launch_spread_cost(q, &ctx->ds->ngroups, P<int32_t>(ctx->grp_first), P<int32_t>(ctx->grp_count),
-                           P<int32_t>(ctx->grp_cost), S[cur].pcost, ctx->nsm);
-        ctx->kernels += 1;
+        if (S[cur].pcost) {
+            launch_spread_cost(q, &ctx->ds->ngroups, P<int32_t>(ctx->grp_first),
+                               P<int32_t>(ctx->grp_count), P<int32_t>(ctx->grp_cost), S[cur].pcost,
+                               ctx->nsm);
+            ctx->kernels += 1;
+        }
         if (timing) {
             NB_CUDA(ctx, pool_event(ctx, &e2));
             NB_CUDA(ctx, cudaEventRecord(e2, q));

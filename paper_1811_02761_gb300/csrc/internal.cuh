@@ -12,7 +12,8 @@
 //              nodeB[k] float4 (b_J, G M b_J^2, link, meta)      -- walk data
 //                link = first child (internal) or first particle (leaf)
 //                meta = (nchild << 1) | 0 (internal), (count << 1) | 1 (leaf)
-//              mom64[k] Mom64 (com.x, com.y, com.z, M)        -- FP64 moments
+//              mass2[k] float2 (hi, lo): M as an unevaluated sum of two
+//                floats (about 48 bits), for the bottom-up mass sums
 //   groups     Morton order: first, count, sphere (centre, radius), alpha =
 //              delta_acc * min |a_old|, system id, cost log
 #pragma once
@@ -48,20 +49,23 @@ struct DevState {
     int32_t lvl_off[kMaxNL + 1];
 };
 
-// FP64 monopole of a node: centre of mass and mass.
-struct __align__(32) Mom64 {
-    double x, y, z, w;
-};
-__host__ __device__ __forceinline__ Mom64 make_Mom64(double x, double y, double z, double w) {
-    Mom64 r;
-    r.x = x; r.y = y; r.z = z; r.w = w;
-    return r;
+// Error-free transformations in FP32 (Knuth's TwoSum, Dekker's Fast2Sum)
+// and the "double-float" sum built from them: a value hi + lo with |lo| <=
+// ulp(hi) / 2 carries about 48 significant bits with FP32 arithmetic only.
+// (GB300 runs FP64 at a small fraction of its FP32 rate.)
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
 }
-// L2-coherent load (bypasses L1), for data another thread just published.
-__device__ __forceinline__ Mom64 ldcg_mom(const Mom64 *p) {
-    const double2 *q = reinterpret_cast<const double2 *>(p);
-    double2 a = __ldcg(q), b = __ldcg(q + 1);
-    return make_Mom64(a.x, a.y, b.x, b.y);
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float2 s = two_sum(a.x, b.x);
+    return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
 }
 
 // Geometry of one system: cube corner, side and the FP32 quantisation scale.
@@ -152,8 +156,7 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                 int64_t cap_nodes, int8_t *delta, int8_t *leaflev, void *temp, DevState *ds,
                 int32_t *node_start, int8_t *node_level, int32_t *node_parent,
                 int32_t *node_link, int32_t *node_count, int32_t *node_nchild,
-                int32_t *node_arrive, float4 *nodeA, float4 *nodeB, Mom64 *mom64,
-                int32_t *sys_root, int nsm);
+                float4 *nodeA, float4 *nodeB, float2 *mass2, int32_t *sys_root, int nsm);
 void build_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
                   const int64_t *d_off, const int32_t *node_start, const int32_t *node_parent,
                   const int32_t *node_count, const int32_t *node_nchild, const int32_t *node_link,

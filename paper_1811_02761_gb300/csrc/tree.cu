@@ -12,14 +12,14 @@
 //     L_i = min(levels, 1 + min over boundary pairs (left <= i < right,
 //               right - left <= leaf_cap) of max(delta_left, delta_right)),
 // because a run bounded by two boundaries whose shared levels are both below
-// l+1 is cut at level l+1.  So the whole tree comes from per-particle work in
-// a window of 2*leaf_cap boundaries plus one scan per level -- no level-by-
-// level launches and no global synchronisation (the paper's calcNode needs
-// 21 grid-wide barriers per step, App. A).
+// l+1 is cut at level l+1.  So the whole tree structure comes from
+// per-particle work in a window of 2*leaf_cap boundaries plus one scan per
+// level -- no level-by-level launches.
 //
-// Monopoles are accumulated bottom-up in FP64 with "last child arrives"
-// atomic counters: the thread that finishes the last child of a node computes
-// the node.  Nothing spins.
+// Monopoles are accumulated bottom-up: all leaves in one launch, then one
+// launch per level for the internal nodes, deepest level first; the stream
+// order between launches stands in for the grid-wide barriers of the
+// paper's calcNode (App. A).
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -45,6 +45,8 @@ __device__ __forceinline__ uint32_t level_mask(int d, int L) {
 
 // delta, leaf level and per-level node counts of each block of TB particles.
 constexpr int kMaxCap = 32;
+// CAPT: a power of two >= cap, the unrolled length of the window loops.
+template <int CAPT>
 __global__ void __launch_bounds__(TB) leaflevel_kernel(Layout L, int cap,
                                                        const uint64_t *__restrict__ keys,
                                                        int8_t *__restrict__ delta,
@@ -72,9 +74,12 @@ __global__ void __launch_bounds__(TB) leaflevel_kernel(Layout L, int cap,
         int R = 127, best = 127;
         // R = min delta over boundaries i+1..i+k; a run [i-cap+k, right) with
         // right <= i-cap+k+cap is cut at level max(delta_left, R) + 1.
-        for (int k = 1; k <= cap; k++) {
-            if (i + k <= n) R = min(R, sd[ti + k]);
-            if (i - cap + k >= 0) best = min(best, max(sd[ti - cap + k], R));
+#pragma unroll
+        for (int k = 1; k <= CAPT; k++) {
+            if (k <= cap) {
+                if (i + k <= n) R = min(R, sd[ti + k]);
+                if (i - cap + k >= 0) best = min(best, max(sd[ti - cap + k], R));
+            }
         }
         int Li = min(L.levels, best + 1);
         int di = sd[ti];
@@ -85,8 +90,13 @@ __global__ void __launch_bounds__(TB) leaflevel_kernel(Layout L, int cap,
     }
     const int NL = L.levels + 1;
     const unsigned w = threadIdx.x >> 5;
-    for (int l = 0; l < NL; l++) {
-        unsigned b = __ballot_sync(NB_FULL, (mask >> l) & 1u);
+    // per-warp node counts, visiting only the levels some lane starts a node at
+    if (lane_id() < (unsigned)NL) wc[lane_id()][w] = 0u;
+    __syncwarp();
+    const unsigned any = __reduce_or_sync(NB_FULL, mask);
+    for (unsigned m = any; m; m &= m - 1) {
+        const int l = __ffs(m) - 1;
+        const unsigned b = __ballot_sync(NB_FULL, (mask >> l) & 1u);
         if (lane_id() == 0) wc[l][w] = (uint32_t)__popc(b);
     }
     __syncthreads();
@@ -135,6 +145,13 @@ __global__ void level_offsets_kernel(int NL, DevState *ds, int64_t cap_nodes) {
 
 // Writes every node: start, level, parent, first child / first particle and,
 // for leaves, the particle count.  Children bump their parent's child count.
+// The node at level l starting at particle i gets the id
+//   lvl_off[l] + (nodes of level l in earlier blocks) + (in earlier warps of
+//   this block) + (in earlier lanes of this warp),
+// and only the levels at which some lane of the warp starts a node are
+// visited.  A particle's nodes sit on the consecutive levels delta_i + 1 ..
+// L_i, so each one's parent is the particle's previous node, and the first
+// one's parent is the last node of level delta_i starting before particle i.
 __global__ void __launch_bounds__(TB) nodes_kernel(Layout L, const int8_t *__restrict__ delta,
                                                    const int8_t *__restrict__ leaflev,
                                                    const uint32_t *__restrict__ blockcnt, int nblk,
@@ -142,8 +159,9 @@ __global__ void __launch_bounds__(TB) nodes_kernel(Layout L, const int8_t *__res
                                                    int64_t cap_nodes, int32_t *node_start,
                                                    int8_t *node_level, int32_t *node_parent,
                                                    int32_t *node_link, int32_t *node_count,
-                                                   int32_t *node_nchild, int32_t *node_arrive) {
+                                                   int32_t *node_nchild) {
     __shared__ uint32_t wc[kMaxNL][TB / 32];
+    __shared__ int32_t sbase[kMaxNL];
     const int64_t n = L.n;
     const int NL = L.levels + 1;
     const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
@@ -155,8 +173,15 @@ __global__ void __launch_bounds__(TB) nodes_kernel(Layout L, const int8_t *__res
         Li = leaflev[i];
         mask = level_mask(di, Li);
     }
-    for (int l = 0; l < NL; l++) {
-        unsigned b = __ballot_sync(NB_FULL, (mask >> l) & 1u);
+    for (int t = threadIdx.x; t < kMaxNL * (TB / 32); t += TB) (&wc[0][0])[t] = 0u;
+    if (threadIdx.x < NL)
+        sbase[threadIdx.x] = ds->lvl_off[threadIdx.x] +
+                             (int32_t)blockcnt[(int64_t)threadIdx.x * nblk + blockIdx.x];
+    __syncthreads();
+    const unsigned any = __reduce_or_sync(NB_FULL, mask);
+    for (unsigned m = any; m; m &= m - 1) {
+        const int l = __ffs(m) - 1;
+        const unsigned b = __ballot_sync(NB_FULL, (mask >> l) & 1u);
         if (lane_id() == 0) wc[l][w] = (uint32_t)__popc(b);
     }
     __syncthreads();
@@ -170,41 +195,35 @@ __global__ void __launch_bounds__(TB) nodes_kernel(Layout L, const int8_t *__res
     }
     __syncthreads();
     const unsigned lt = lanemask_lt();
-    int prev_excl = 0, prev_bit = 0, prev_id = -1;
-    bool prev_internal = false;
-    for (int l = 0; l < NL; l++) {
-        int bit = (mask >> l) & 1u;
-        unsigned b = __ballot_sync(NB_FULL, bit);
-        int excl = ds->lvl_off[l] + (int)blockcnt[(int64_t)l * nblk + blockIdx.x] + (int)wc[l][w] +
-                   __popc(b & lt);
-        if (prev_internal) node_link[prev_id] = excl;  // first child starts at i too
-        if (bit && excl < cap_nodes) {
-            int id = excl;
+    // id of the last node of level di starting before i (no lane of this warp
+    // starts one there unless the loop below finds that level in `any`)
+    int pex = di >= 0 ? sbase[di] + (int)wc[di][w] : 0;
+    int prev_id = -1;
+    // warp-uniform level set: the levels with nodes plus every lane's di
+    const unsigned visit = any | __reduce_or_sync(NB_FULL, di >= 0 ? (1u << di) : 0u);
+    for (unsigned m = visit; m; m &= m - 1) {
+        const int l = __ffs(m) - 1;
+        const int bit = (mask >> l) & 1u;
+        const unsigned b = __ballot_sync(NB_FULL, bit);
+        const int ex = sbase[l] + (int)wc[l][w] + __popc(b & lt);
+        if (l == di) pex = ex;
+        if (!bit) continue;
+        const int id = ex;
+        if (prev_id >= 0 && prev_id < cap_nodes) node_link[prev_id] = id;  // first child
+        if (id < cap_nodes) {
             node_start[id] = (int32_t)i;
             node_level[id] = (int8_t)l;
-            node_arrive[id] = 0;
-            if (l > 0) {
-                int par = prev_excl + prev_bit - 1;
-                node_parent[id] = par;
-                atomicAdd(&node_nchild[par], 1);
-            } else {
-                node_parent[id] = -1;
-            }
+            const int par = prev_id >= 0 ? prev_id : (di >= 0 ? pex - 1 : -1);
+            node_parent[id] = par;
+            if (par >= 0) atomicAdd(&node_nchild[par], 1);
             if (l == Li) {  // leaf: particles until the next boundary above level l
                 int64_t j = i + 1;
                 while (j < n && delta[j] >= l) j++;
                 node_link[id] = (int32_t)i;
                 node_count[id] = (int32_t)(j - i);
-                prev_internal = false;
-            } else {
-                prev_internal = true;
-                prev_id = id;
             }
-        } else {
-            prev_internal = false;
         }
-        prev_excl = excl;
-        prev_bit = bit;
+        prev_id = id;
     }
 }
 
@@ -222,6 +241,8 @@ __global__ void sys_root_init_kernel(int nsys, int32_t *sys_root) {
 
 // ---------------------------------------------------------------- moments
 __device__ __forceinline__ int &ds_status(DevState *ds) { return ds->status; }
+
+
 
 __device__ __forceinline__ uint32_t compact3(uint64_t x) {
     x &= 0x1249249249249249ull;
@@ -254,6 +275,7 @@ __device__ __forceinline__ CellF node_cell(const Layout &L, uint64_t key, int le
     float side = b.L * pow2f(-level);
     float o[3] = {b.x0, b.y0, b.z0};
     CellF cell;
+#pragma unroll
     for (int a = 0; a < 3; a++) cell.c[a] = o[a] + ((float)q[a] + 0.5f) * side;
     cell.h = 0.5f * side + b.L * pow2f(-L.levels);
     return cell;
@@ -262,116 +284,205 @@ __device__ __forceinline__ CellF node_cell(const Layout &L, uint64_t key, int le
 // Round-up factor for FP32 upper bounds (a few ulps of slack).
 constexpr float kUp = 1.0f + 0x1p-20f;
 
-__device__ __forceinline__ void write_node(int id, float cx, float cy, float cz, double M,
+// Node record: centre of mass, mass (hi + lo), size b and the MAC numerator
+// G M b^2, rounded up from the FP32 values.
+__device__ __forceinline__ void write_node(int id, float cx, float cy, float cz, float2 M,
                                            float b, float G, int link, int meta, float4 *nodeA,
-                                           float4 *nodeB, Mom64 *mom64) {
-    float q = __double2float_ru((double)G * M * (double)b * (double)b);
-    nodeA[id] = make_float4(cx, cy, cz, (float)M);
+                                           float4 *nodeB, float2 *mass2) {
+    const float Mup = M.y > 0.0f ? __int_as_float(__float_as_int(M.x) + 1) : M.x;  // M.x >= 0
+    const float q = __fmul_ru(__fmul_ru(__fmul_ru(G, Mup), b), b);
+    nodeA[id] = make_float4(cx, cy, cz, M.x);
     nodeB[id] = make_float4(b, q, __int_as_float(link), __int_as_float(meta));
-    mom64[id].w = M;
+    mass2[id] = M;
 }
 
 // Monopoles (centre of mass, mass) and node sizes b_J, bottom-up.  FP32 sums
 // relative to a reference point inside the node (first particle for leaves,
 // the cell centre for internal nodes) keep the error a few ulps of the node
-// size; masses are summed in FP64 (additions only).  b_J is rounded up so it
-// bounds the distance from the FP32 centre of mass to every member.
-__global__ void __launch_bounds__(256) moments_kernel(
+// size; masses are summed as double-float pairs (about 48 bits, FP32
+// arithmetic only).  b_J is rounded up so it bounds the distance from the
+// FP32 centre of mass to every member.
+//
+// Leaves first, all levels at once: a team of T lanes takes one leaf, lane j
+// loading members j, j + T, ... (coalesced); the sums and the largest member
+// distance are team reductions.
+template <int T>
+__global__ void __launch_bounds__(256) leaf_moments_kernel(
     Layout L, const uint64_t *__restrict__ keys, const float4 *__restrict__ pos4,
     const SysBox *__restrict__ box, float G, DevState *ds,
     const int32_t *__restrict__ node_start, const int8_t *__restrict__ node_level,
-    const int32_t *__restrict__ node_parent, const int32_t *__restrict__ node_link,
-    int32_t *node_count, const int32_t *__restrict__ node_nchild, int32_t *node_arrive,
-    float4 *nodeA, float4 *nodeB, Mom64 *mom64) {
+    const int32_t *__restrict__ node_link, const int32_t *__restrict__ node_count,
+    const int32_t *__restrict__ node_nchild, float4 *nodeA, float4 *nodeB, float2 *mass2) {
+    constexpr int TEAMS = 32 / T;
     const int nn = ds->nnodes;
-    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += gridDim.x * blockDim.x) {
-        if (node_nchild[id] != 0) continue;
-        const int first = node_link[id], cnt = node_count[id];
-        if (first < 0 || cnt < 1 || (int64_t)first + cnt > L.n) {
-            atomicOr(&ds_status(ds), kStatusBadTree);
-            continue;
-        }
-        const float4 r0 = pos4[first];
-        double M = 0.0;
-        float mf = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f;
-        for (int k = first; k < first + cnt; k++) {
-            const float4 p = pos4[k];
-            M += (double)p.w;
-            mf += p.w;
-            sx = fmaf(p.w, p.x - r0.x, sx);
-            sy = fmaf(p.w, p.y - r0.y, sy);
-            sz = fmaf(p.w, p.z - r0.z, sz);
-        }
-        float c[3];
-        if (mf > 0.0f) {
-            c[0] = r0.x + sx / mf; c[1] = r0.y + sy / mf; c[2] = r0.z + sz / mf;
-        } else {
-            CellF cell = node_cell(L, keys[node_start[id]], node_level[id], box);
-            for (int a = 0; a < 3; a++) c[a] = cell.c[a];
-        }
-        float b2 = 0.0f;
-        for (int k = first; k < first + cnt; k++) {
-            const float4 p = pos4[k];
-            const float dx = p.x - c[0], dy = p.y - c[1], dz = p.z - c[2];
-            b2 = fmaxf(b2, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-        }
-        write_node(id, c[0], c[1], c[2], M, __fsqrt_ru(b2) * kUp, G, first, (cnt << 1) | 1,
-                   nodeA, nodeB, mom64);
-        // climb while this thread completes the last child of the parent
-        int nd = id;
-        for (;;) {
-            int par = node_parent[nd];
-            if (par < 0) break;
-            if (par >= nd) {  // parents precede children in level-major order
-                atomicOr(&ds_status(ds), kStatusBadTree);
-                break;
+    const int lane = (int)lane_id(), team = lane / T, tl = lane % T;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool bad = false;
+    for (int64_t base = wid * 32; base < nn; base += nw * 32) {
+        const int id0 = (int)base + lane;
+        unsigned lm = __ballot_sync(NB_FULL, id0 < nn && node_nchild[id0] == 0);
+        while (lm) {
+            // team t takes the t-th remaining leaf of this chunk
+            int mine = -1;
+#pragma unroll
+            for (int t = 0; t < TEAMS; t++) {
+                const int b = lm ? __ffs(lm) - 1 : -1;
+                if (b >= 0) lm &= lm - 1;
+                if (t == team) mine = b;
             }
-            __threadfence();
-            int old = atomicAdd(&node_arrive[par], 1);
-            if (old != node_nchild[par] - 1) break;
-            __threadfence();
-            const int c0 = node_link[par], nc = node_nchild[par];
-            if (c0 <= par || c0 + nc > nn) {
-                atomicOr(&ds_status(ds), kStatusBadTree);
-                break;
+            const int id = mine >= 0 ? (int)base + mine : -1;
+            int first = 0, cnt = 0;
+            if (id >= 0) {
+                first = node_link[id];
+                cnt = node_count[id];
+                if (first < 0 || cnt < 1 || (int64_t)first + cnt > L.n) {
+                    bad = true;
+                    cnt = 0;
+                }
             }
-            const CellF cell = node_cell(L, keys[node_start[par]], node_level[par], box);
-            double Mp = 0.0;
-            float mp = 0.0f, px = 0.0f, py = 0.0f, pz = 0.0f;
-            int count = 0;
-            for (int ch = c0; ch < c0 + nc; ch++) {
-                const float4 A = __ldcg(&nodeA[ch]);
-                Mp += __ldcg(&mom64[ch].w);
-                mp += A.w;
-                px = fmaf(A.w, A.x - cell.c[0], px);
-                py = fmaf(A.w, A.y - cell.c[1], py);
-                pz = fmaf(A.w, A.z - cell.c[2], pz);
-                count += __ldcg(&node_count[ch]);
+            // a leaf may hold more than T members (leaf_cap > T, or a
+            // finest-level leaf): chunks of T, as many as the warp's largest
+            const int nch = __reduce_max_sync(NB_FULL, (cnt + T - 1) / T);
+            const float4 r0 = cnt > 0 ? pos4[first] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 M = make_float2(0.0f, 0.0f);
+            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+            for (int ch = 0; ch < nch; ch++) {
+                const int k = ch * T + tl;
+                if (k < cnt) {
+                    const float4 p = pos4[first + k];
+                    M = df_add(M, make_float2(p.w, 0.0f));
+                    sx = fmaf(p.w, p.x - r0.x, sx);
+                    sy = fmaf(p.w, p.y - r0.y, sy);
+                    sz = fmaf(p.w, p.z - r0.z, sz);
+                }
             }
-            float cp[3];
-            if (mp > 0.0f) {
-                cp[0] = cell.c[0] + px / mp; cp[1] = cell.c[1] + py / mp; cp[2] = cell.c[2] + pz / mp;
-            } else {
-                for (int a = 0; a < 3; a++) cp[a] = cell.c[a];
+#pragma unroll
+            for (int o = T / 2; o > 0; o >>= 1) {
+                const float2 Mo = make_float2(__shfl_xor_sync(NB_FULL, M.x, o),
+                                              __shfl_xor_sync(NB_FULL, M.y, o));
+                M = df_add(M, Mo);
+                sx += __shfl_xor_sync(NB_FULL, sx, o);
+                sy += __shfl_xor_sync(NB_FULL, sy, o);
+                sz += __shfl_xor_sync(NB_FULL, sz, o);
             }
-            float rec = 0.0f;
-            for (int ch = c0; ch < c0 + nc; ch++) {
-                const float4 A = __ldcg(&nodeA[ch]);
-                const float bc = __ldcg(&nodeB[ch].x);
-                const float dx = A.x - cp[0], dy = A.y - cp[1], dz = A.z - cp[2];
-                rec = fmaxf(rec, __fadd_ru(__fsqrt_ru(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), bc));
+            float c[3] = {r0.x, r0.y, r0.z};
+            if (M.x > 0.0f) {
+                const float inv = 1.0f / M.x;
+                c[0] = fmaf(sx, inv, c[0]); c[1] = fmaf(sy, inv, c[1]); c[2] = fmaf(sz, inv, c[2]);
+            } else if (cnt > 0) {
+                const CellF cell = node_cell(L, keys[node_start[id]], node_level[id], box);
+#pragma unroll
+                for (int a = 0; a < 3; a++) c[a] = cell.c[a];
             }
-            float c2 = 0.0f;
-            for (int a = 0; a < 3; a++) {
-                const float e = fabsf(cp[a] - cell.c[a]) + cell.h;
-                c2 = fmaf(e, e, c2);
+            float b2 = 0.0f;
+            for (int ch = 0; ch < nch; ch++) {
+                const int k = ch * T + tl;
+                if (k < cnt) {
+                    const float4 p = pos4[first + k];
+                    const float dx = p.x - c[0], dy = p.y - c[1], dz = p.z - c[2];
+                    b2 = fmaxf(b2, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                }
             }
-            const float bp = fminf(rec, __fsqrt_ru(c2)) * kUp;
-            node_count[par] = count;
-            write_node(par, cp[0], cp[1], cp[2], Mp, bp, G, c0, nc << 1, nodeA, nodeB, mom64);
-            nd = par;
+#pragma unroll
+            for (int o = T / 2; o > 0; o >>= 1) b2 = fmaxf(b2, __shfl_xor_sync(NB_FULL, b2, o));
+            if (tl == 0 && cnt > 0)
+                write_node(id, c[0], c[1], c[2], M, __fsqrt_ru(b2) * kUp, G, first,
+                           (cnt << 1) | 1, nodeA, nodeB, mass2);
         }
     }
+    if (bad) atomicOr(&ds_status(ds), kStatusBadTree);
+}
+
+// Internal nodes of one level, after every deeper level: a team of 8 lanes
+// per node, lane j loading child j (children are contiguous, at most 8).
+// Sums relative to the cell centre; the size is
+//   b = min(max_c (|com_c - com| + b_c), distance from com to the farthest
+//           corner of the cell widened by one finest cell),
+// rounded up.
+__global__ void __launch_bounds__(256) internal_moments_kernel(
+    Layout L, int level, const uint64_t *__restrict__ keys, const SysBox *__restrict__ box,
+    float G, DevState *ds, const int32_t *__restrict__ node_start,
+    const int32_t *__restrict__ node_link, int32_t *node_count,
+    const int32_t *__restrict__ node_nchild, float4 *nodeA, float4 *nodeB, float2 *mass2) {
+    const int lo = ds->lvl_off[level], hi = ds->lvl_off[level + 1];
+    const int nn = ds->nnodes;
+    const int lane = (int)lane_id(), team = lane >> 3, tl = lane & 7;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool bad = false;
+    for (int64_t base = lo + wid * 32; base < hi; base += nw * 32) {
+        const int id0 = (int)base + lane;
+        unsigned im = __ballot_sync(NB_FULL, id0 < hi && node_nchild[id0] != 0);
+        while (im) {
+            int mine = -1;
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int b = im ? __ffs(im) - 1 : -1;
+                if (b >= 0) im &= im - 1;
+                if (t == team) mine = b;
+            }
+            const int par = mine >= 0 ? (int)base + mine : -1;
+            int c0 = 0, nc = 0;
+            if (par >= 0) {
+                c0 = node_link[par];
+                nc = node_nchild[par];
+                if (c0 <= par || nc < 1 || nc > 8 || c0 + nc > nn) {
+                    bad = true;
+                    nc = 0;
+                }
+            }
+            CellF cell{{0.f, 0.f, 0.f}, 0.f};
+            if (nc > 0) cell = node_cell(L, keys[node_start[par]], level, box);
+            float2 Mp = make_float2(0.0f, 0.0f);
+            float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
+            float bc = 0.0f;
+            int count = 0;
+            if (tl < nc) {
+                A = nodeA[c0 + tl];
+                bc = nodeB[c0 + tl].x;
+                Mp = mass2[c0 + tl];
+                count = node_count[c0 + tl];
+            }
+            float px = A.w * (A.x - cell.c[0]);
+            float py = A.w * (A.y - cell.c[1]);
+            float pz = A.w * (A.z - cell.c[2]);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                const float2 Mo = make_float2(__shfl_xor_sync(NB_FULL, Mp.x, o),
+                                              __shfl_xor_sync(NB_FULL, Mp.y, o));
+                Mp = df_add(Mp, Mo);
+                px += __shfl_xor_sync(NB_FULL, px, o);
+                py += __shfl_xor_sync(NB_FULL, py, o);
+                pz += __shfl_xor_sync(NB_FULL, pz, o);
+                count += __shfl_xor_sync(NB_FULL, count, o);
+            }
+            float cp[3] = {cell.c[0], cell.c[1], cell.c[2]};
+            if (Mp.x > 0.0f) {
+                const float inv = 1.0f / Mp.x;
+                cp[0] = fmaf(px, inv, cp[0]); cp[1] = fmaf(py, inv, cp[1]); cp[2] = fmaf(pz, inv, cp[2]);
+            }
+            float rec = 0.0f;
+            if (tl < nc) {
+                const float dx = A.x - cp[0], dy = A.y - cp[1], dz = A.z - cp[2];
+                rec = __fadd_ru(__fsqrt_ru(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), bc);
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) rec = fmaxf(rec, __shfl_xor_sync(NB_FULL, rec, o));
+            if (nc > 0 && tl == 0) {
+                float c2 = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const float e = fabsf(cp[a] - cell.c[a]) + cell.h;
+                    c2 = fmaf(e, e, c2);
+                }
+                const float bp = fminf(rec, __fsqrt_ru(c2)) * kUp;
+                node_count[par] = count;
+                write_node(par, cp[0], cp[1], cp[2], Mp, bp, G, c0, nc << 1, nodeA, nodeB, mass2);
+            }
+        }
+    }
+    if (bad) atomicOr(&ds_status(ds), kStatusBadTree);
 }
 
 size_t tree_temp_bytes(int64_t n, int levels) {
@@ -384,24 +495,39 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                 int64_t cap_nodes, int8_t *delta, int8_t *leaflev, void *temp, DevState *ds,
                 int32_t *node_start, int8_t *node_level, int32_t *node_parent,
                 int32_t *node_link, int32_t *node_count, int32_t *node_nchild,
-                int32_t *node_arrive, float4 *nodeA, float4 *nodeB, Mom64 *mom64,
-                int32_t *sys_root, int nsm) {
+                float4 *nodeA, float4 *nodeB, float2 *mass2, int32_t *sys_root, int nsm) {
     const int nblk = (int)((L.n + TB - 1) / TB);
     uint32_t *blockcnt = (uint32_t *)temp;
-    leaflevel_kernel<<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
+    if (leaf_cap <= 8)
+        leaflevel_kernel<8><<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
+    else if (leaf_cap <= 16)
+        leaflevel_kernel<16><<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
+    else
+        leaflevel_kernel<32><<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
     level_scan_kernel<<<L.levels + 1, 1024, 0, s>>>(blockcnt, nblk, ds);
     level_offsets_kernel<<<1, 32, 0, s>>>(L.levels + 1, ds, cap_nodes);
     cudaMemsetAsync(node_nchild, 0, (size_t)cap_nodes * sizeof(int32_t), s);
     nodes_kernel<<<nblk, TB, 0, s>>>(L, delta, leaflev, blockcnt, nblk, ds, cap_nodes, node_start,
-                                     node_level, node_parent, node_link, node_count, node_nchild,
-                                     node_arrive);
+                                     node_level, node_parent, node_link, node_count, node_nchild);
     sys_root_init_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(L.nsys, sys_root);
     sys_root_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(ds, node_start, d_off, L.nsys, sys_root);
-    int mb = (int)((L.n + 255) / 256);
-    if (mb > nsm * 16) mb = nsm * 16;
-    moments_kernel<<<mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start, node_level,
-                                      node_parent, node_link, node_count, node_nchild, node_arrive,
-                                      nodeA, nodeB, mom64);
+    // leaves: one warp per 32 nodes; internal nodes: one launch per level,
+    // deepest first (level `levels` holds leaves only)
+    int64_t mb = (L.n / 4 + 255) / 256;
+    if (mb > (int64_t)nsm * 8) mb = (int64_t)nsm * 8;
+    if (mb < 1) mb = 1;
+    if (leaf_cap <= 4)
+        leaf_moments_kernel<4><<<(int)mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start,
+                                                       node_level, node_link, node_count,
+                                                       node_nchild, nodeA, nodeB, mass2);
+    else
+        leaf_moments_kernel<8><<<(int)mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start,
+                                                       node_level, node_link, node_count,
+                                                       node_nchild, nodeA, nodeB, mass2);
+    const int ib = nsm * 4;
+    for (int l = L.levels - 1; l >= 0; l--)
+        internal_moments_kernel<<<ib, 256, 0, s>>>(L, l, keys, d_box, G, ds, node_start, node_link,
+                                                   node_count, node_nchild, nodeA, nodeB, mass2);
 }
 
 // ---------------------------------------------------------------- groups
