@@ -42,6 +42,26 @@ FLOPS_PER_INTERACTION = 22  # 3 sub, 3 FMA (r^2+eps^2), rsqrt = 4, 3 mul, 3 FMA
 EPS, DACC, DT = 1.0 / 64, 2.0 ** -9, 1.0 / 256
 FP32_LANES_PER_SM = 128
 
+# DRAM traffic of walk_kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the N=2^22 galaxy, per particle; the launch at the
+# bench's N is scaled by particles.  It is reported only while the walk source
+# is the one the counters were taken on (sha256 of walk_impl.cuh).
+WALK_TRAFFIC = {"bytes_per_particle": (108.068352e6 + 44.594432e6) / 4194304,
+                "walk_impl_sha256": "1c9fef915d19ae87b6974fe5dfb67df19972272ccf631ea31aceb1e61f650979",
+                "capture": "profiles/walk_kernel_galaxy_2e22.md (N=2^22, scaled by particles)"}
+
+
+def walk_traffic(n):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1811_02761_gb300", "csrc", "walk_impl.cuh")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None, "walk source not found"
+    if sha != WALK_TRAFFIC["walk_impl_sha256"]:
+        return None, "walk kernel changed since the ncu capture"
+    return WALK_TRAFFIC["bytes_per_particle"] * n, WALK_TRAFFIC["capture"]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -69,7 +89,7 @@ def parse():
     ap.add_argument("--sweep-max", type=int, default=20)
     ap.add_argument("--drift-steps", type=int, default=256)
     ap.add_argument("--drift-every", type=int, default=32)
-    ap.add_argument("--cpu-group-stride", type=int, default=32,
+    ap.add_argument("--cpu-group-stride", type=int, default=1,
                     help="CPU baseline walks every k-th group of the full tree")
     return ap.parse_args()
 
@@ -267,6 +287,7 @@ def run_ours(args, rank, world, local_rank):
     med = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else None
     peak_med = 2 * FP32_LANES_PER_SM * nsm * med * 1e6 / 1e12 if med else None
     whole_tflops = FLOPS_PER_INTERACTION * inter_per_step / s_per_step / 1e12
+    traffic, traffic_note = walk_traffic(n)
 
     # oracle leg (rank 0, N = 1): the FP64 oracle tree walk on a bounded
     # sample, timed on the host cores, and the FP64 direct sum at the final
@@ -275,10 +296,11 @@ def run_ours(args, rank, world, local_rank):
     if final is not None:
         ni, walk_s, build_s, thr, nsel, ng = cpu_oracle_sample(p, args.cpu_group_stride)
         cpu = {"value": ni / walk_s / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": f"FP64 oracle tree walk (group-mode acceleration MAC) of every "
-                         f"{args.cpu_group_stride}th group ({nsel} of {ng} groups, {ni} "
-                         f"interactions) of the same N={n} galaxy; full oracle tree build "
-                         f"{build_s:.2f} s timed separately",
+               "sample": f"FP64 oracle tree walk (group-mode acceleration MAC) of "
+                         f"{'every group' if args.cpu_group_stride == 1 else f'every {args.cpu_group_stride}-th group'} "
+                         f"({nsel} of {ng} groups, {ni} interactions) of the same N={n} galaxy "
+                         f"at its initial positions; oracle tree build {build_s:.2f} s timed "
+                         f"separately",
                "build_s": build_s, "walk_s": walk_s}
         if args.error_sample > 0:
             err = oracle_force_error(final, args.error_sample, args.seed)
@@ -298,8 +320,8 @@ def run_ours(args, rank, world, local_rank):
         "walk_phase_ms_per_step": st.ms_walk / steps,
         "nodes": st.n_nodes, "groups": st.n_groups, "max_stack": st.max_stack,
         "roofline": {"bound": "alu", "achieved": walk_tflops, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": walk_tflops / peak_tflops, "traffic": None,
-                     "kernel": "walk_kernel",
+                     "unit": "TFLOP/s", "frac": walk_tflops / peak_tflops, "traffic": traffic,
+                     "traffic_note": traffic_note, "kernel": "walk_kernel",
                      "peak_note": f"FP32 2 x {FP32_LANES_PER_SM} lanes x {nsm} SMs x {sm_max:.0f} MHz "
                                   f"(max clock, MEASURED_PEAKS sm_max_mhz)",
                      "frac_at_median_clock": (walk_tflops / peak_med) if peak_med else None},

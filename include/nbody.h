@@ -50,7 +50,7 @@ typedef enum {
     NBODY_EINVAL = 1,    /* bad argument (n < 0, NULL, eps < 0, bad config)  */
     NBODY_ENOMEM = 2,    /* device or host allocation failed                 */
     NBODY_EOVERFLOW = 3, /* a traversal stack overflowed; results invalid    */
-    NBODY_ETIMEOUT = 4,  /* reserved: a bounded device wait ran out          */
+    NBODY_ETIMEOUT = 4,  /* a bounded device wait ran out; results invalid  */
     NBODY_ECUDA = 5,     /* a CUDA runtime call failed (see nbody_last_error)*/
     NBODY_ENOTBUILT = 6  /* nbody_walk before nbody_build                    */
 } nbody_status;

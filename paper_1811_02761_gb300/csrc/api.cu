@@ -298,11 +298,13 @@ nbody_status build_core(nbody_ctx *c, const Layout &L, const void *x, const void
     launch_bbox(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<uint32_t>(c->sys_boxord),
                 P<SysBox>(c->sys_box), c->nsm);
     c->kernels += 3;
+    radix_prepare(s, L.n, c->rs_temp.p);
     launch_keys(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<SysBox>(c->sys_box),
-                P<uint64_t>(c->keys), P<uint32_t>(c->vals));
-    c->kernels += 1 + 4 * ((L.keybits + 8) / 9);
+                P<uint64_t>(c->keys), P<uint32_t>(c->vals), c->rs_temp.p, c->nsm);
+    c->kernels += 1 + radix_passes(L.keybits);
     if (radix_sort(s, P<uint64_t>(c->keys), P<uint32_t>(c->vals), P<uint64_t>(c->keys_alt),
-                   P<uint32_t>(c->vals_alt), L.n, L.keybits, c->rs_temp.p)) {
+                   P<uint32_t>(c->vals_alt), L.n, L.keybits, c->rs_temp.p, true, &c->ds->status,
+                   c->nsm)) {
         std::swap(c->keys, c->keys_alt);
         std::swap(c->vals, c->vals_alt);
     }
@@ -385,6 +387,8 @@ nbody_status check_systems(nbody_ctx *c, int32_t nsys, const int64_t *offsets,
 nbody_status read_status(nbody_ctx *c) {
     NB_CUDA(c, cudaMemcpyAsync(c->h_ds, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->h_ds->status & kStatusTimeout)
+        return fail(c, NBODY_ETIMEOUT, "a bounded device wait (radix-sort look-back) ran out");
     if (c->h_ds->status & kStatusBadTree)
         return fail(c, NBODY_ECUDA, "internal error: a tree index failed its bounds check");
     if (c->h_ds->status & kStatusStackOverflow)
@@ -554,9 +558,11 @@ nbody_status compute_order(nbody_ctx *c, const float *pcost, const int32_t **ord
     }
     launch_order_keys(c->stream, png, P<float>(c->score), P<int32_t>(c->grp_count),
                       P<uint64_t>(c->okey), P<uint32_t>(c->oval), c->nsm);
-    c->kernels += 2 + 4 * 4;
+    // score (MLP: features + forward) and order keys; histogram + passes
+    c->kernels += (sched == NBODY_SCHED_MLP ? 3 : 2) + 1 + radix_passes(32);
     if (radix_sort(c->stream, P<uint64_t>(c->okey), P<uint32_t>(c->oval), P<uint64_t>(c->okey_alt),
-                   P<uint32_t>(c->oval_alt), ng, 32, c->rs_temp.p)) {
+                   P<uint32_t>(c->oval_alt), ng, 32, c->rs_temp.p, false, &c->ds->status,
+                   c->nsm)) {
         std::swap(c->okey, c->okey_alt);
         std::swap(c->oval, c->oval_alt);
     }

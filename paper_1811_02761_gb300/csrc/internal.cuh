@@ -35,6 +35,7 @@ constexpr int kMaxNL = kMaxLevels + 1;      // levels 0..21
 constexpr int kMlpParams = 8 * 32 + 32 + 32 * 32 + 32 + 32 + 1;  // 8 -> 32 -> 32 -> 1
 constexpr int kStatusStackOverflow = 1;
 constexpr int kStatusBadTree = 2;  // an index failed a bounds check (skipped)
+constexpr int kStatusTimeout = 4;  // a bounded device wait ran out (results invalid)
 
 // Device-resident counters and small per-build values.
 struct DevState {
@@ -136,14 +137,25 @@ __device__ __forceinline__ int sys_of(const int64_t *off, int nsys, int64_t i) {
 // sort.cu
 void launch_bbox(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
                  bool dbl, const int64_t *d_off, uint32_t *d_boxord, SysBox *d_box, int nsm);
+// Morton keys (vals = 0..n-1).  With sort_temp (cleared by radix_prepare),
+// the kernel also accumulates the radix sort's digit histograms, and the
+// sort is then called with hist_done = true.
 void launch_keys(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
                  bool dbl, const int64_t *d_off, const SysBox *d_box, uint64_t *keys,
-                 uint32_t *vals);
+                 uint32_t *vals, void *sort_temp, int nsm);
 size_t radix_temp_bytes(int64_t n);
+// Clears the sort's counters, histograms and look-back words (one memset).
+void radix_prepare(cudaStream_t s, int64_t n, void *temp);
 // Sorts (keys, vals) by the low `bits` bits of keys, stably (ties keep their
-// input order).  Returns 1 if the result ended in the alt buffers, else 0.
+// input order); vals must hold 0..n-1 on entry.  hist_done: the histograms in
+// temp are already complete (launch_keys with sort_temp); else the sort
+// clears temp and computes them.  Device-side failures (a look-back wait
+// that ran out, a destination out of range) are or-ed into *status.
+// Returns 1 if the result ended in the alt buffers, else 0.
 int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
-               uint32_t *vals_alt, int64_t n, int bits, void *temp);
+               uint32_t *vals_alt, int64_t n, int bits, void *temp, bool hist_done,
+               int32_t *status, int nsm);
+int radix_passes(int bits);
 // Single-block exclusive scan of sums[0..nb) in place (total to *total_out).
 void launch_scan_sums(cudaStream_t s, uint32_t *sums, int nb, int32_t *total_out);
 void launch_gather_pos4(cudaStream_t s, int64_t n, const uint32_t *perm, const void *x,

@@ -2,11 +2,12 @@
 // build ("makeTree", Sect. 2.2; its time is dominated by the radix sort of
 // the space-filling-curve keys, Sect. 4.1).
 //
-// All passes are HBM-bound.  The radix sort is reduce-then-scan: per pass a
-// tile histogram, a device-wide exclusive scan of the digit-major counts, and
-// a stable scatter that ranks keys inside a tile with warp match/popc and
-// stages the tile in shared memory so global writes are runs of one digit.
-// There is no inter-CTA waiting anywhere.
+// All passes are HBM-bound.  The radix sort is a one-sweep LSD sort: the
+// digit histograms of every pass come from the key kernel's single read of
+// the positions, and each pass is one kernel that ranks a tile's keys with
+// warp match/popc, finds the tile's global offsets by a bounded decoupled
+// look-back, and stages the tile in shared memory so global writes are runs
+// of one digit.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -194,50 +195,52 @@ __device__ __forceinline__ uint32_t quantise(float v, float v0, float scale, uin
     return c > top ? top : c;
 }
 
-template <typename T>
-__global__ void keys_kernel(Layout L, const T *__restrict__ x, const T *__restrict__ y,
-                            const T *__restrict__ z, const int64_t *__restrict__ off,
-                            const SysBox *__restrict__ box, uint64_t *__restrict__ keys,
-                            uint32_t *__restrict__ vals) {
-    const uint32_t top = (1u << L.levels) - 1u;
-    const int mbits = 3 * L.levels;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int s = sys_of(off, L.nsys, i);
-        SysBox b = box[s];
-        uint32_t qx = quantise((float)x[i], b.x0, b.scale, top);
-        uint32_t qy = quantise((float)y[i], b.y0, b.scale, top);
-        uint32_t qz = quantise((float)z[i], b.z0, b.scale, top);
-        uint64_t k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-        if (L.sysbits) k |= (uint64_t)s << mbits;
-        keys[i] = k;
-        vals[i] = (uint32_t)i;
-    }
-}
-
-void launch_keys(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
-                 bool dbl, const int64_t *d_off, const SysBox *d_box, uint64_t *keys,
-                 uint32_t *vals) {
-    int blocks = (int)((L.n + 255) / 256);
-    if (blocks > 65535 * 8) blocks = 65535 * 8;
-    if (dbl)
-        keys_kernel<double><<<blocks, 256, 0, s>>>(L, (const double *)x, (const double *)y,
-                                                   (const double *)z, d_off, d_box, keys, vals);
-    else
-        keys_kernel<float><<<blocks, 256, 0, s>>>(L, (const float *)x, (const float *)y,
-                                                  (const float *)z, d_off, d_box, keys, vals);
-}
-
 // ---------------------------------------------------------------- radix sort
+// One-sweep LSD radix sort: 9-bit digits; the digit histograms of all passes
+// come from one read of the keys (fused into the key kernel, or a separate
+// histogram kernel), then one kernel per pass.  In a pass, each CTA takes the
+// next tile (4096 keys) from an atomic counter, ranks its keys by digit with
+// warp match/popc, and finds how many keys of each digit precede the tile by
+// a decoupled look-back over the per-(tile, digit) words of the tiles before
+// it: a tile first publishes its own digit counts (an "aggregate"), then,
+// walking back, adds aggregates until it meets a tile that has published its
+// inclusive prefix, and publishes its own.  Tiles take their numbers in the
+// order the CTAs start, so a tile only ever waits for tiles that are already
+// running, and those publish their aggregates without waiting for anyone.
+// Every wait is bounded (RS_SPIN_LIMIT polls); on expiry the kernel records
+// kStatusTimeout and carries on, and a destination outside [0, n) is skipped
+// and recorded, so a failure is reported, never a hang or a wild write.
 constexpr int RS_BITS = 9;
 constexpr int RS_BINS = 1 << RS_BITS;
+constexpr int RS_MAXPASS = 8;
 constexpr int RS_THREADS = 512;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_IPT = 8;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
+constexpr int RS_SPIN_LIMIT = 1 << 20;
 constexpr int SCAN_T = 1024;
 constexpr int SCAN_IPT = 4;
 constexpr int SCAN_CH = SCAN_T * SCAN_IPT;
+static_assert(RS_BINS == RS_THREADS, "one digit per thread");
+
+// Look-back word of one (tile, digit): bits 63..60 = pass + 1 (a word left by
+// another pass or sort reads as "not yet published"), bit 59 = inclusive
+// prefix (else aggregate), bits 58..0 = the count.
+constexpr unsigned long long RS_INCL = 1ull << 59;
+constexpr unsigned long long RS_CNT = RS_INCL - 1;
+
+// Temporary layout: tile counters, digit histograms, look-back words.
+constexpr size_t RS_OFF_HIST = 256;
+constexpr size_t RS_OFF_STATUS = RS_OFF_HIST + (size_t)RS_MAXPASS * RS_BINS * sizeof(uint32_t);
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // Exclusive scan of one value per thread over a block of NT threads.
 template <int NT>
@@ -259,29 +262,103 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh /* 
     return r;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const uint64_t *__restrict__ keys,
-                                                             int64_t n, int shift,
-                                                             uint32_t *__restrict__ counts,
-                                                             int ntiles) {
-    __shared__ uint32_t h[RS_BINS];
-    for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) h[d] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    const unsigned lane = lane_id();
-#pragma unroll
-    for (int k = 0; k < RS_IPT; k++) {
-        int64_t i = base + k * RS_THREADS + threadIdx.x;
-        bool ok = i < n;
-        unsigned act = __ballot_sync(NB_FULL, ok);
-        if (ok) {
-            uint32_t d = (uint32_t)(keys[i] >> shift) & (RS_BINS - 1);
-            unsigned peers = __match_any_sync(act, d);
-            if (lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+// Adds one key (if `valid`) to the shared digit histograms of `passes`
+// passes.  A digit shared by every valid lane of the warp (the common case
+// for the high digits of keys in near-sorted order) costs one atomic.
+__device__ __forceinline__ void hist_add(uint32_t (*h)[RS_BINS], uint64_t key, bool valid,
+                                         int passes) {
+    const unsigned vm = __ballot_sync(NB_FULL, valid);
+    if (!vm) return;
+    const int leader = __ffs(vm) - 1;
+    for (int p = 0; p < passes; p++) {
+        const uint32_t d = (uint32_t)(key >> (p * RS_BITS)) & (RS_BINS - 1);
+        const uint32_t d0 = __shfl_sync(NB_FULL, d, leader);
+        if (__all_sync(NB_FULL, !valid || d == d0)) {
+            if ((int)lane_id() == leader) atomicAdd(&h[p][d0], (uint32_t)__popc(vm));
+        } else if (valid) {
+            atomicAdd(&h[p][d], 1u);
         }
     }
+}
+
+// Publishes a block's shared histograms (non-zero bins only).
+__device__ __forceinline__ void hist_flush(uint32_t (*h)[RS_BINS], int passes, uint32_t *g) {
     __syncthreads();
-    for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS)
-        counts[(int64_t)d * ntiles + blockIdx.x] = h[d];
+    for (int i = threadIdx.x; i < passes * RS_BINS; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&g[i], c);
+    }
+}
+
+__device__ __forceinline__ void hist_zero(uint32_t (*h)[RS_BINS], int passes) {
+    for (int i = threadIdx.x; i < passes * RS_BINS; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) rs_hist_kernel(const uint64_t *__restrict__ keys, int64_t n,
+                                                      int passes, uint32_t *hist) {
+    __shared__ uint32_t h[RS_MAXPASS][RS_BINS];
+    hist_zero(h, passes);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool ok = i < n;
+        hist_add(h, ok ? keys[i] : 0ull, ok, passes);
+    }
+    hist_flush(h, passes, hist);
+}
+
+// Morton key of every particle; with `hist`, also the digit histograms of
+// all radix-sort passes (the sort then needs no histogram pass of its own).
+template <typename T>
+__global__ void __launch_bounds__(256) keys_kernel(Layout L, const T *__restrict__ x,
+                                                   const T *__restrict__ y,
+                                                   const T *__restrict__ z,
+                                                   const int64_t *__restrict__ off,
+                                                   const SysBox *__restrict__ box,
+                                                   uint64_t *__restrict__ keys,
+                                                   uint32_t *__restrict__ vals, uint32_t *hist,
+                                                   int passes) {
+    __shared__ uint32_t h[RS_MAXPASS][RS_BINS];
+    if (hist) hist_zero(h, passes);
+    const uint32_t top = (1u << L.levels) - 1u;
+    const int mbits = 3 * L.levels;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < L.n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        uint64_t k = 0;
+        if (i < L.n) {
+            int s = sys_of(off, L.nsys, i);
+            SysBox b = box[s];
+            uint32_t qx = quantise((float)x[i], b.x0, b.scale, top);
+            uint32_t qy = quantise((float)y[i], b.y0, b.scale, top);
+            uint32_t qz = quantise((float)z[i], b.z0, b.scale, top);
+            k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+            if (L.sysbits) k |= (uint64_t)s << mbits;
+            keys[i] = k;
+            vals[i] = (uint32_t)i;
+        }
+        if (hist) hist_add(h, k, i < L.n, passes);
+    }
+    if (hist) hist_flush(h, passes, hist);
+}
+
+void launch_keys(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
+                 bool dbl, const int64_t *d_off, const SysBox *d_box, uint64_t *keys,
+                 uint32_t *vals, void *sort_temp, int nsm) {
+    int64_t b = (L.n + 255) / 256;
+    int blocks = (int)(b < (int64_t)nsm * 8 ? b : (int64_t)nsm * 8);
+    if (blocks < 1) blocks = 1;
+    const int passes = (L.keybits + RS_BITS - 1) / RS_BITS;
+    uint32_t *hist = sort_temp ? (uint32_t *)((char *)sort_temp + RS_OFF_HIST) : nullptr;
+    if (dbl)
+        keys_kernel<double><<<blocks, 256, 0, s>>>(L, (const double *)x, (const double *)y,
+                                                   (const double *)z, d_off, d_box, keys, vals,
+                                                   hist, passes);
+    else
+        keys_kernel<float><<<blocks, 256, 0, s>>>(L, (const float *)x, (const float *)y,
+                                                  (const float *)z, d_off, d_box, keys, vals,
+                                                  hist, passes);
 }
 
 // In-place exclusive scan of a[0..len) in chunks of SCAN_CH; chunk totals go
@@ -328,33 +405,50 @@ void launch_scan_sums(cudaStream_t s, uint32_t *sums, int nb, int32_t *total_out
 }
 
 struct RsShared {
-    uint32_t whist[RS_WARPS][RS_BINS];
-    uint32_t tdoff[RS_BINS];
-    uint32_t goff[RS_BINS];
-    uint32_t wsum[RS_THREADS / 32];
-    uint64_t sk[RS_TILE];
-    uint32_t sv[RS_TILE];
+    union {
+        uint32_t whist[RS_WARPS][RS_BINS];  // per-warp digit counts, then offsets
+        struct {
+            uint64_t k[RS_TILE];
+            uint32_t v[RS_TILE];
+        } st;                                // the tile in digit order
+    } u;
+    uint32_t loff[RS_BINS];  // first tile slot of each digit
+    uint32_t goff[RS_BINS];  // destination of tile slot p with digit d: goff[d] + p
+    uint32_t wsum[RS_WARPS];
+    int tile;
+    int flags;
 };
 
+// One pass over the digit at `shift`.  vin is ignored on the first pass
+// (values = input positions).
 template <bool FIRST>
-__global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(
+__global__ void __launch_bounds__(RS_THREADS, 2) rs_onesweep_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ counts,
-    const uint32_t *__restrict__ sums, int ntiles) {
+    uint32_t *__restrict__ vout, int64_t n, int shift, int pass, int ntiles, void *temp,
+    int32_t *status) {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     RsShared &S = *reinterpret_cast<RsShared *>(rs_smem);
+    uint32_t *counter = (uint32_t *)temp;
+    const uint32_t *hist = (const uint32_t *)((char *)temp + RS_OFF_HIST) + pass * RS_BINS;
+    unsigned long long *look = (unsigned long long *)((char *)temp + RS_OFF_STATUS);
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
-    const int tile = blockIdx.x;
+    const int d = threadIdx.x;  // the digit this thread scans and looks back for
+
+    if (threadIdx.x == 0) {
+        S.tile = (int)atomicAdd(&counter[pass], 1u);
+        S.flags = 0;
+    }
+    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&S.u.whist[0][0])[i] = 0;
+    __syncthreads();
+    const int tile = S.tile;
+    if (tile >= ntiles) return;  // block-uniform; the grid has exactly ntiles CTAs
     const int64_t base = (int64_t)tile * RS_TILE;
     const int valid = (int)((n - base) < RS_TILE ? (n - base) : RS_TILE);
 
-    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS)
-        (&S.whist[0][0])[i] = 0;
-    __syncthreads();
-
     uint64_t key[RS_IPT];
     uint32_t val[RS_IPT], dg[RS_IPT], rk[RS_IPT];
-    // warp-striped: warp w owns the contiguous run [w*32*IPT, (w+1)*32*IPT)
+    // warp-striped: warp w owns the contiguous run [w*32*IPT, (w+1)*32*IPT);
+    // keys past n get digit RS_BINS-1 and rank last in the tile
 #pragma unroll
     for (int k = 0; k < RS_IPT; k++) {
         int64_t i = base + (int64_t)w * 32 * RS_IPT + k * 32 + lane;
@@ -371,91 +465,127 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(
 #pragma unroll
     for (int k = 0; k < RS_IPT; k++) {
         unsigned peers = __match_any_sync(NB_FULL, dg[k]);
-        uint32_t b = S.whist[w][dg[k]];
+        uint32_t b = S.u.whist[w][dg[k]];
         __syncwarp();
-        if ((peers & lt) == 0) S.whist[w][dg[k]] = b + (uint32_t)__popc(peers);
+        if ((peers & lt) == 0) S.u.whist[w][dg[k]] = b + (uint32_t)__popc(peers);
         __syncwarp();
         rk[k] = b + (uint32_t)__popc(peers & lt);
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps, then over digits
-    for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) {
-        uint32_t run = 0;
+    // digit d: exclusive prefix over the warps, and the tile's count
+    uint32_t tot = 0;
 #pragma unroll
-        for (int q = 0; q < RS_WARPS; q++) {
-            uint32_t c = S.whist[q][d];
-            S.whist[q][d] = run;
-            run += c;
+    for (int q = 0; q < RS_WARPS; q++) {
+        uint32_t c = S.u.whist[q][d];
+        S.u.whist[q][d] = tot;
+        tot += c;
+    }
+    const uint32_t lex = block_excl_scan<RS_THREADS>(tot, S.wsum, nullptr);
+    const uint32_t gstart = block_excl_scan<RS_THREADS>(hist[d], S.wsum, nullptr);
+    S.loff[d] = lex;
+
+    // decoupled look-back for digit d
+    const unsigned long long tag = (unsigned long long)(pass + 1) << 60;
+    const unsigned long long mine =
+        tot - (d == RS_BINS - 1 ? (uint32_t)(RS_TILE - valid) : 0u);  // keys past n excluded
+    unsigned long long *slot = look + (size_t)tile * RS_BINS + d;
+    unsigned long long excl = 0;
+    if (tile == 0) {
+        st_relaxed_u64(slot, tag | RS_INCL | mine);
+    } else {
+        st_relaxed_u64(slot, tag | mine);
+        int j = tile - 1, spins = 0;
+        while (j >= 0) {
+            const unsigned long long v = ld_relaxed_u64(look + (size_t)j * RS_BINS + d);
+            if ((v >> 60) != (unsigned long long)(pass + 1)) {
+                if (++spins > RS_SPIN_LIMIT) {
+                    atomicOr(&S.flags, kStatusTimeout);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            excl += v & RS_CNT;
+            if (v & RS_INCL) break;
+            j--;
         }
-        S.tdoff[d] = run;
+        st_relaxed_u64(slot, tag | RS_INCL | (excl + mine));
     }
+    S.goff[d] = (uint32_t)((unsigned long long)gstart + excl) - lex;
     __syncthreads();
-    static_assert(RS_BINS == RS_THREADS, "one digit per thread");
-    {
-        uint32_t tot = S.tdoff[threadIdx.x];
-        uint32_t ex = block_excl_scan<RS_THREADS>(tot, S.wsum, nullptr);
-        S.tdoff[threadIdx.x] = ex;
-        int64_t ci = (int64_t)threadIdx.x * ntiles + tile;
-        S.goff[threadIdx.x] = counts[ci] + sums[ci / SCAN_CH] - ex;
-    }
-    __syncthreads();
+    uint32_t pos[RS_IPT];
+#pragma unroll
+    for (int k = 0; k < RS_IPT; k++) pos[k] = S.loff[dg[k]] + S.u.whist[w][dg[k]] + rk[k];
+    __syncthreads();  // the staging area overlays the per-warp counts
 #pragma unroll
     for (int k = 0; k < RS_IPT; k++) {
-        uint32_t pos = S.tdoff[dg[k]] + S.whist[w][dg[k]] + rk[k];
-        S.sk[pos] = key[k];
-        S.sv[pos] = val[k];
+        S.u.st.k[pos[k]] = key[k];
+        S.u.st.v[pos[k]] = val[k];
     }
     __syncthreads();
+    bool bad = false;
     for (int p = threadIdx.x; p < valid; p += RS_THREADS) {
-        uint64_t kk = S.sk[p];
-        uint32_t d = (uint32_t)(kk >> shift) & (RS_BINS - 1);
-        uint32_t dst = S.goff[d] + (uint32_t)p;
-        kout[dst] = kk;
-        vout[dst] = S.sv[p];
+        const uint64_t kk = S.u.st.k[p];
+        const uint32_t dd = (uint32_t)(kk >> shift) & (RS_BINS - 1);
+        const uint32_t dst = S.goff[dd] + (uint32_t)p;
+        if (dst < (uint64_t)n) {
+            kout[dst] = kk;
+            vout[dst] = S.u.st.v[p];
+        } else {
+            bad = true;
+        }
     }
+    if (bad) atomicOr(&S.flags, kStatusBadTree);
+    __syncthreads();
+    if (threadIdx.x == 0 && S.flags) atomicOr(status, S.flags);
 }
 
 size_t radix_temp_bytes(int64_t n) {
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-    int64_t len = ntiles * RS_BINS;
-    int64_t nch = (len + SCAN_CH - 1) / SCAN_CH;
-    return (size_t)(len + nch + 64) * sizeof(uint32_t);
+    return RS_OFF_STATUS + (size_t)ntiles * RS_BINS * sizeof(unsigned long long);
+}
+
+void radix_prepare(cudaStream_t s, int64_t n, void *temp) {
+    cudaMemsetAsync(temp, 0, radix_temp_bytes(n), s);
 }
 
 int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
-               uint32_t *vals_alt, int64_t n, int bits, void *temp) {
+               uint32_t *vals_alt, int64_t n, int bits, void *temp, bool hist_done,
+               int32_t *status, int nsm) {
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(rs_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(rs_onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(RsShared));
-        cudaFuncSetAttribute(rs_scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(rs_onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(RsShared));
         attr_done = true;
     }
-    int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
-    int64_t len = (int64_t)ntiles * RS_BINS;
-    int nch = (int)((len + SCAN_CH - 1) / SCAN_CH);
-    uint32_t *counts = (uint32_t *)temp;
-    uint32_t *sums = counts + len;
-    int passes = (bits + RS_BITS - 1) / RS_BITS;
+    const int passes = (bits + RS_BITS - 1) / RS_BITS;
+    if (!hist_done) {
+        radix_prepare(s, n, temp);
+        int64_t b = (n + 255) / 256;
+        int blocks = (int)(b < (int64_t)nsm * 8 ? b : (int64_t)nsm * 8);
+        if (blocks < 1) blocks = 1;
+        rs_hist_kernel<<<blocks, 256, 0, s>>>(keys, n, passes, (uint32_t *)((char *)temp + RS_OFF_HIST));
+    }
+    const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
     uint64_t *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     for (int p = 0; p < passes; p++) {
-        int shift = p * RS_BITS;
-        rs_hist_kernel<<<ntiles, RS_THREADS, 0, s>>>(kin, n, shift, counts, ntiles);
-        scan_chunks_kernel<<<nch, SCAN_T, 0, s>>>(counts, len, sums);
-        scan_sums_kernel<<<1, SCAN_T, 0, s>>>(sums, nch, nullptr);
+        const int shift = p * RS_BITS;
         if (p == 0)
-            rs_scatter_kernel<true><<<ntiles, RS_THREADS, sizeof(RsShared), s>>>(
-                kin, vin, kout, vout, n, shift, counts, sums, ntiles);
+            rs_onesweep_kernel<true><<<ntiles, RS_THREADS, sizeof(RsShared), s>>>(
+                kin, vin, kout, vout, n, shift, p, ntiles, temp, status);
         else
-            rs_scatter_kernel<false><<<ntiles, RS_THREADS, sizeof(RsShared), s>>>(
-                kin, vin, kout, vout, n, shift, counts, sums, ntiles);
+            rs_onesweep_kernel<false><<<ntiles, RS_THREADS, sizeof(RsShared), s>>>(
+                kin, vin, kout, vout, n, shift, p, ntiles, temp, status);
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
     }
     return kin != keys;  // 1: the sorted result is in the alt buffers
 }
+
+int radix_passes(int bits) { return (bits + RS_BITS - 1) / RS_BITS; }
 
 // ---------------------------------------------------------------- gather
 template <typename T>
