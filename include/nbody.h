@@ -320,6 +320,19 @@ typedef enum {
  * EINVAL, ECUDA. */
 nbody_status nbody_export(nbody_ctx *ctx, int32_t what, void *dst, int64_t cap, int64_t *count);
 
+/* Self-tests of the library's failure paths (no counterpart in the paper).
+ * NBODY_SELFTEST_SORT_WAIT: runs one radix-sort pass kernel on a two-tile
+ * input whose first tile is never processed, so the second tile's look-back
+ * (the decoupled look-back of the one-sweep sort, the library's only device
+ * wait) finds nothing to wait for; the wait is bounded (2^20 polls) and the
+ * kernel records a timeout and finishes.  Returns the status the device
+ * reported: NBODY_ETIMEOUT when the bound works.  Allocates and frees its own
+ * buffers (about 200 KB) and synchronises cuda_stream (NULL = default
+ * stream).  The device stays usable afterwards.  Errors: EINVAL (unknown
+ * test), ECUDA. */
+#define NBODY_SELFTEST_SORT_WAIT 1
+nbody_status nbody_selftest(int32_t which, void *cuda_stream);
+
 /* Message of the last error of this context (or of the last stateless call
  * on this thread if ctx is NULL), NUL-terminated, truncated to len. */
 nbody_status nbody_last_error(const nbody_ctx *ctx, char *buf, size_t len);

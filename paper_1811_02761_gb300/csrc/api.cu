@@ -1438,6 +1438,26 @@ nbody_status nbody_mlp_eval(int64_t n, const float *features, const float *targe
     return NBODY_OK;
 }
 
+nbody_status nbody_selftest(int32_t which, void *cuda_stream) {
+    if (which != NBODY_SELFTEST_SORT_WAIT) return fail(nullptr, NBODY_EINVAL, "unknown self-test");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int32_t *dstat = nullptr;
+    cudaError_t e = cudaMalloc(&dstat, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "nbody_selftest");
+    int32_t h = 0;
+    e = cudaMemsetAsync(dstat, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = radix_selftest_wait(s, dstat);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dstat, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dstat);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "nbody_selftest");
+    if (h & kStatusTimeout) {
+        set_stateless_error("self-test: the radix-sort look-back wait ran out as intended");
+        return NBODY_ETIMEOUT;
+    }
+    return NBODY_OK;
+}
+
 nbody_status nbody_last_error(const nbody_ctx *ctx, char *buf, size_t len) {
     if (!buf || len == 0) return NBODY_EINVAL;
     const std::string &m = ctx ? ctx->err : g_last_error;

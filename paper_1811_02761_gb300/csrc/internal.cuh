@@ -156,6 +156,9 @@ int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_al
                uint32_t *vals_alt, int64_t n, int bits, void *temp, bool hist_done,
                int32_t *status, int nsm);
 int radix_passes(int bits);
+// Runs the radix pass kernel on an input whose look-back can never complete
+// and waits for it; the bounded wait records kStatusTimeout in *status.
+cudaError_t radix_selftest_wait(cudaStream_t s, int32_t *status);
 // Single-block exclusive scan of sums[0..nb) in place (total to *total_out).
 void launch_scan_sums(cudaStream_t s, uint32_t *sums, int nb, int32_t *total_out);
 void launch_gather_pos4(cudaStream_t s, int64_t n, const uint32_t *perm, const void *x,

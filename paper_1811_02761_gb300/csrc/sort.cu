@@ -218,6 +218,7 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_IPT = 8;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
 constexpr int RS_SPIN_LIMIT = 1 << 20;
+constexpr int RS_LB = 4;  // look-back words loaded per round trip
 constexpr int SCAN_T = 1024;
 constexpr int SCAN_IPT = 4;
 constexpr int SCAN_CH = SCAN_T * SCAN_IPT;
@@ -442,6 +443,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) rs_onesweep_kernel(
     __syncthreads();
     const int tile = S.tile;
     if (tile >= ntiles) return;  // block-uniform; the grid has exactly ntiles CTAs
+    const uint32_t hd = hist[d];
     const int64_t base = (int64_t)tile * RS_TILE;
     const int valid = (int)((n - base) < RS_TILE ? (n - base) : RS_TILE);
 
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) rs_onesweep_kernel(
         tot += c;
     }
     const uint32_t lex = block_excl_scan<RS_THREADS>(tot, S.wsum, nullptr);
-    const uint32_t gstart = block_excl_scan<RS_THREADS>(hist[d], S.wsum, nullptr);
+    const uint32_t gstart = block_excl_scan<RS_THREADS>(hd, S.wsum, nullptr);
     S.loff[d] = lex;
 
     // decoupled look-back for digit d
@@ -494,20 +496,38 @@ __global__ void __launch_bounds__(RS_THREADS, 2) rs_onesweep_kernel(
         st_relaxed_u64(slot, tag | RS_INCL | mine);
     } else {
         st_relaxed_u64(slot, tag | mine);
+        // walk back RS_LB words per round trip: the words of tiles j, j-1,
+        // ... are loaded together and consumed in order until an inclusive
+        // prefix; a word not yet published is polled again (bounded)
         int j = tile - 1, spins = 0;
-        while (j >= 0) {
-            const unsigned long long v = ld_relaxed_u64(look + (size_t)j * RS_BINS + d);
-            if ((v >> 60) != (unsigned long long)(pass + 1)) {
+        bool done = false;
+        while (!done) {
+            unsigned long long v[RS_LB];
+#pragma unroll
+            for (int u = 0; u < RS_LB; u++)
+                v[u] = (j - u >= 0) ? ld_relaxed_u64(look + (size_t)(j - u) * RS_BINS + d)
+                                    : (tag | RS_INCL);  // before tile 0: prefix 0
+            int used = 0;
+            bool stalled = false;
+#pragma unroll
+            for (int u = 0; u < RS_LB; u++) {
+                if (done || stalled) continue;
+                if ((v[u] >> 60) != (unsigned long long)(pass + 1)) {
+                    stalled = true;
+                    continue;
+                }
+                excl += v[u] & RS_CNT;
+                used++;
+                if (v[u] & RS_INCL) done = true;
+            }
+            j -= used;
+            if (stalled && !done) {
                 if (++spins > RS_SPIN_LIMIT) {
                     atomicOr(&S.flags, kStatusTimeout);
                     break;
                 }
                 __nanosleep(32);
-                continue;
             }
-            excl += v & RS_CNT;
-            if (v & RS_INCL) break;
-            j--;
         }
         st_relaxed_u64(slot, tag | RS_INCL | (excl + mine));
     }
@@ -586,6 +606,37 @@ int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_al
 }
 
 int radix_passes(int bits) { return (bits + RS_BITS - 1) / RS_BITS; }
+
+// Self-test of the bounded look-back wait: one pass over two tiles in which
+// tile 0 is never taken (the tile counter starts at 1), so the only CTA takes
+// tile 1 and its look-back finds no word for tile 0.  The wait must run out,
+// record kStatusTimeout in *status and let the kernel finish.
+cudaError_t radix_selftest_wait(cudaStream_t s, int32_t *status) {
+    const int64_t n = 2 * RS_TILE;
+    void *buf = nullptr;
+    const size_t kb = (size_t)n * sizeof(uint64_t), vb = (size_t)n * sizeof(uint32_t);
+    const size_t tb = radix_temp_bytes(n);
+    cudaError_t e = cudaMalloc(&buf, 2 * kb + 2 * vb + tb);
+    if (e != cudaSuccess) return e;
+    char *p = (char *)buf;
+    uint64_t *kin = (uint64_t *)p, *kout = (uint64_t *)(p + kb);
+    uint32_t *vin = (uint32_t *)(p + 2 * kb), *vout = (uint32_t *)(p + 2 * kb + vb);
+    void *temp = p + 2 * kb + 2 * vb;
+    const uint32_t one = 1;
+    e = cudaFuncSetAttribute(rs_onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(RsShared));
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, 2 * kb + 2 * vb + tb, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(temp, &one, sizeof one, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        rs_onesweep_kernel<true><<<1, RS_THREADS, sizeof(RsShared), s>>>(kin, vin, kout, vout, n, 0, 0,
+                                                                         2, temp, status);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
+    cudaFree(buf);
+    return e;
+}
 
 // ---------------------------------------------------------------- gather
 template <typename T>

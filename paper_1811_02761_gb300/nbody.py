@@ -68,7 +68,7 @@ EXPORTS = ("nbody_abi_version", "nbody_config_default", "nbody_create", "nbody_d
            "nbody_get_group_costs", "nbody_export", "nbody_last_error",
            "nbody_diagnostics_noalloc", "nbody_tune_space_default", "nbody_autotune",
            "nbody_mlp_set_params", "nbody_mlp_get_params", "nbody_mlp_train",
-           "nbody_mlp_predict", "nbody_mlp_eval")
+           "nbody_mlp_predict", "nbody_mlp_eval", "nbody_selftest")
 MLP_PARAMS, MLP_FEATURES = 1377, 8
 EXPORT_PERM, EXPORT_KEYS, EXPORT_NODE_LEVEL, EXPORT_NODE_START, EXPORT_NODE_COUNT, \
     EXPORT_NODE_PARENT, EXPORT_NODE_A, EXPORT_NODE_B, EXPORT_GROUP_FIRST, EXPORT_GROUP_COUNT, \
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
             "nbody_mlp_eval": (st, [i64, vp, vp, vp, vp, vp, vp, vp, vp]),
             "nbody_autotune": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(TuneSpace),
                                     C.POINTER(Config), C.POINTER(f32), C.POINTER(i32)]),
+            "nbody_selftest": (st, [i32, vp]),
             "nbody_last_error": (st, [vp, C.c_char_p, C.c_size_t]),
         }
         for name, (res, args) in sig.items():
@@ -414,6 +415,15 @@ def nbody_export(ctx, what: int) -> np.ndarray:
     _check(lib, ctx, lib.nbody_export(ctx, int(what), out.ctypes.data if out.size else None,
                                       cnt.value, C.byref(cnt)))
     return out.reshape(-1, width) if width > 1 else out
+
+
+SELFTEST_SORT_WAIT = 1
+
+
+def nbody_selftest(which, stream=None) -> int:
+    """Runs a self-test of a failure path; returns the status it produced
+    (NBODY_ETIMEOUT for SELFTEST_SORT_WAIT when the wait bound works)."""
+    return int(load().nbody_selftest(int(which), _stream_ptr(stream)))
 
 
 def nbody_last_error(ctx=None) -> str:

@@ -375,6 +375,29 @@ def test_bad_arguments_rejected_on_gpu():
         nb.nbody_destroy(ctx)
 
 
+def test_sort_lookback_wait_is_bounded(plummer8k):
+    """The one-sweep sort's look-back is the library's only device wait.  The
+    self-test gives it a predecessor tile that never publishes: the wait must
+    run out, be reported as ETIMEOUT, and leave the device usable."""
+    import time
+    t0 = time.perf_counter()
+    assert nb.nbody_selftest(nb.nbody.SELFTEST_SORT_WAIT) == nb.NBODY_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    assert "ran out" in nb.nbody_last_error()
+    assert nb.nbody_selftest(99) == nb.NBODY_EINVAL
+    # the device still answers: a normal build and walk afterwards succeed
+    p, _ = plummer8k
+    X = [dev(p[k]) for k in ("x", "y", "z", "m")]
+    ctx = nb.nbody_create(nb.nbody_config_default(eps=1 / 128))
+    try:
+        nb.nbody_build(ctx, *X)
+        out = [torch.empty(X[0].numel(), device="cuda") for _ in range(3)]
+        nb.nbody_walk(ctx, None, *out)
+        assert all(torch.isfinite(o).all() for o in out)
+    finally:
+        nb.nbody_destroy(ctx)
+
+
 # --------------------------------------------------------------------------- CUDA graph
 @pytest.mark.parametrize("nsteps", [4, 5])
 def test_step_graph_equals_eager(nsteps):
