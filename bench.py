@@ -69,15 +69,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("galaxy", "batched", "learned", "precision"),
+    ap.add_argument("--workload", choices=("galaxy", "batched", "learned", "precision", "scaling"),
                     default="galaxy",
                     help="galaxy: N=2^23 three-component galaxy (the headline); batched: 512 "
                          "independent Plummer/Hernquist systems, one forest per step; learned: "
                          "MLP-ordered walk queue at N=25*2^20; precision: delta_acc sweep, plain "
-                         "vs compensated, error vs FP64 direct, FP64 energy/momentum drift")
+                         "vs compensated, error vs FP64 direct, FP64 energy/momentum drift; "
+                         "scaling: the galaxy step from N=2^10 to N=25*2^20 with its breakdown")
     ap.add_argument("--nsys", type=int, default=512)
     ap.add_argument("--train-steps", type=int, default=20)
     ap.add_argument("--train-epochs", type=int, default=2)
+    ap.add_argument("--schedules", action="store_true",
+                    help="batched: also train the cost model and time each queue schedule")
     ap.add_argument("--per-system-steps", type=int, default=2,
                     help="batched: steps timed for the one-call-per-system comparison")
     ap.add_argument("--n", type=int, default=1 << 23)
@@ -407,6 +410,7 @@ def run_batched(args, rank, world, local_rank):
         per_sys = (time.perf_counter() - w0) / args.per_system_steps
     finally:
         nb.nbody_destroy(ctx)
+    sched = batched_schedules(args, off, eps, parts, stream, dev) if args.schedules else None
     t = torch.tensor([elapsed, float(st.interactions)], dtype=torch.float64, device=dev)
     if world > 1:
         tm = t[:1].clone()
@@ -434,9 +438,68 @@ def run_batched(args, rank, world, local_rank):
                                 "note": "one nbody_step call (build + walk + kicks) per system "
                                         "and step, eager launches"},
         "speedup_vs_per_system": per_sys / s_per_step,
+        "schedules": sched,
         "interactions_per_step": float(st.interactions) / args.steps,
         "gpu_launches": int(st.kernels),
     }
+
+
+def batched_schedules(args, off, eps, parts, stream, dev):
+    """The batched forest under each queue schedule, eager launches (a
+    cost-ordered queue reads the group count on the host every step): the
+    cost model is trained online on `train_steps` Morton-order steps, then
+    `steps` steps run from the same state per schedule.  Final states must
+    agree bit for bit."""
+    import torch
+
+    import ics
+    import paper_1811_02761_gb300 as nb
+
+    def D(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    n = int(off[-1])
+    X = [D(parts[k].astype(np.float64)) for k in ("x", "y", "z")]
+    V = [D(parts[k]) for k in ("vx", "vy", "vz")]
+    M = D(parts["m"])
+    A = [torch.zeros(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    ctx = nb.nbody_create(nb.nbody_config_default(delta_acc=DACC), stream)
+    out, finals = {}, {}
+    try:
+        nb.nbody_build_batched(ctx, off, eps, *[D(parts[k]) for k in ("x", "y", "z")], M)
+        nb.nbody_walk(ctx, None, *A)
+        nb.nbody_mlp_set_params(ctx, ics.mlp_init(args.seed))
+        losses = []
+        for _ in range(args.train_steps):
+            nb.nbody_step_batched(ctx, off, eps, *X, *V, M, *A, DT, 1)
+            losses.append(nb.nbody_mlp_train(ctx, epochs=args.train_epochs, lr=2e-3, batch=4096))
+        snap = [t.clone() for t in X + V + A]
+        for name, sc in (("morton", nb.SCHED_MORTON), ("mlp", nb.SCHED_MLP),
+                         ("lastcost", nb.SCHED_LASTCOST)):
+            for t, s0 in zip(X + V + A, snap):
+                t.copy_(s0)
+            cfg = nb.nbody_get_config(ctx)
+            cfg.schedule = sc
+            nb.nbody_set_config(ctx, cfg)
+            torch.cuda.synchronize(dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            st = nb.nbody_step_batched(ctx, off, eps, *X, *V, M, *A, DT, args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            out[name] = {"walk_ms_per_step": st.ms_walk_kernel / max(st.walk_launches, 1),
+                         "s_per_step": ev0.elapsed_time(ev1) / 1e3 / args.steps}
+            finals[name] = [t.cpu().numpy() for t in X + V + A]
+    finally:
+        nb.nbody_destroy(ctx)
+    base = out["morton"]["walk_ms_per_step"]
+    return {"eager": out,
+            "mlp_vs_morton_walk_speedup": base / out["mlp"]["walk_ms_per_step"],
+            "lastcost_vs_morton_walk_speedup": base / out["lastcost"]["walk_ms_per_step"],
+            "bitwise_identical_final_states": all(
+                np.array_equal(a, b) for k in ("mlp", "lastcost")
+                for a, b in zip(finals["morton"], finals[k])),
+            "train_losses_first_last": [losses[0], losses[-1]] if losses else None}
 
 
 # ---------------------------------------------------------------------------- learned schedule
@@ -523,6 +586,72 @@ def run_learned(args, rank, world, local_rank):
         "bitwise_identical_final_states": same,
         "train": {"losses_first_last": [losses[0], losses[-1]], "seconds": train_s,
                   "pred_vs_cost_correlation": corr},
+    }
+
+
+# ---------------------------------------------------------------------------- N scaling
+def run_scaling(args, rank, world, local_rank):
+    """The galaxy step at N = 2^10, 2^12, ..., 2^24 and 25 * 2^20: s/step,
+    walk and build time per step, interactions per particle and rate (the
+    N dependence the paper measures in Sect. 4.1).  Rank 0 only."""
+    import torch
+
+    import ics
+    import paper_1811_02761_gb300 as nb
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    peak = 2 * FP32_LANES_PER_SM * props.multi_processor_count * float(
+        peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    sizes = [1 << k for k in range(10, 25, 2)] + [25 * (1 << 20)]
+    rows = []
+    stream = torch.cuda.current_stream(dev)
+
+    def D(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    for n in sizes:
+        p = ics.galaxy(n, args.seed)
+        X64 = [D(p[k]) for k in ("x64", "y64", "z64")]
+        V = [D(p[k]) for k in ("vx", "vy", "vz")]
+        M = D(p["m"])
+        A = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+        ctx = nb.nbody_create(nb.nbody_config_default(eps=EPS, delta_acc=DACC), stream)
+        try:
+            nb.nbody_build(ctx, *[D(p[k]) for k in ("x", "y", "z")], M)
+            nb.nbody_walk(ctx, None, *A)
+            nb.nbody_step(ctx, *X64, *V, M, *A, DT, args.warmup)
+            steps = max(args.steps, 4)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            ev0.record(stream)
+            st = nb.nbody_step(ctx, *X64, *V, M, *A, DT, steps)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+        finally:
+            nb.nbody_destroy(ctx)
+        s = ev0.elapsed_time(ev1) / 1e3 / steps
+        walk_ms = st.ms_walk_kernel / max(st.walk_launches, 1)
+        ipp = st.interactions / steps / n
+        rows.append({"n": n, "s_per_step": s, "walk_ms": walk_ms, "build_ms": st.ms_build / steps,
+                     "interactions_per_particle": ipp,
+                     "ginter_s": st.interactions / steps / s / 1e9,
+                     "walk_fp32_peak_frac": FLOPS_PER_INTERACTION * ipp * n / (walk_ms / 1e3) / 1e12 / peak,
+                     "groups": int(st.n_groups), "nodes": int(st.n_nodes)})
+        del X64, V, M, A
+        torch.cuda.empty_cache()
+    head = next(r for r in rows if r["n"] == 1 << 24)
+    return {
+        "metric": METRIC, "value": head["ginter_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": max(args.steps, 4), "warmup": args.warmup, "ms_per_step": head["s_per_step"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded three-component galaxy)",
+        "config": {"workload": "N scaling: galaxy N = 2^10 .. 2^24 and 25*2^20, eps=1/64, "
+                               "delta_acc=2^-9, shared-step leapfrog dt=1/256; value is the N=2^24 row"},
+        "rows": rows,
     }
 
 
@@ -734,6 +863,8 @@ def main():
             out = run_learned(args, rank, world, local_rank)
         elif args.workload == "precision":
             out = run_precision(args, rank, world, local_rank)
+        elif args.workload == "scaling":
+            out = run_scaling(args, rank, world, local_rank)
         else:
             out = run_ours(args, rank, world, local_rank)
         if world > 1:

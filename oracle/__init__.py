@@ -61,6 +61,7 @@ def _load():
         lib.oracle_tree_build.argtypes = [C.c_int64, d, d, d, d, C.c_int, C.c_int]
         lib.oracle_tree_build.restype = C.c_void_p
         lib.oracle_tree_free.argtypes = [C.c_void_p]
+        lib.oracle_tree_refit.argtypes = [C.c_void_p, d, d, d]
         lib.oracle_tree_nnodes.argtypes = [C.c_void_p]
         lib.oracle_tree_nnodes.restype = C.c_int64
         lib.oracle_tree_cube.argtypes = [C.c_void_p, f32]
@@ -223,6 +224,13 @@ class Tree:
         c = np.empty(self.n, np.int64)
         ng = self._lib.oracle_tree_groups(self._h, group_size, _p(f, C.c_int64), _p(c, C.c_int64))
         return f[:ng].copy(), c[:ng].copy()
+
+    def refit(self, x, y, z):
+        """Replace the positions (same particles, caller order) and recompute
+        the node moments on the same tree (no rebuild)."""
+        self._x, self._y, self._z = _f64(x), _f64(y), _f64(z)
+        self._lib.oracle_tree_refit(self._h, _p(self._x, C.c_double), _p(self._y, C.c_double),
+                                    _p(self._z, C.c_double))
 
     def walk(self, mode=MAC_GROUP_ACC, G=1.0, eps=0.0, delta_acc=2.0 ** -9, theta=0.5,
              group_size=32, a_old=None, want_phi=True):

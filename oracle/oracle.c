@@ -282,7 +282,7 @@ static void node_cell(const oracle_tree *t, int64_t id, uint32_t c[3])
  * the distance from com to the farthest corner of the node's cell, the cell
  * being widened by one finest-level cell width on every side to cover the
  * FP32 quantisation. */
-static void node_moments(oracle_tree *t)
+static void node_moments(oracle_tree *t, int refit)
 {
     for (int64_t id = t->nn - 1; id >= 0; id--) {
         double M = 0, sx = 0, sy = 0, sz = 0;
@@ -332,7 +332,9 @@ static void node_moments(oracle_tree *t)
                 c2 += e * e;
             }
             double corner = sqrt(c2);
-            bb = rec < corner ? rec : corner;
+            /* after a refit members may have left the cell: the recurrence
+             * alone still bounds every member's distance */
+            bb = (refit || rec < corner) ? rec : corner;
         }
         t->b[id] = bb;
     }
@@ -369,7 +371,7 @@ oracle_tree *oracle_tree_build(int64_t n, const double *x, const double *y, cons
             t->key[i] = oracle_interleave(t->q[0][i], t->q[1][i], t->q[2][i], levels);
         int64_t root = new_node(t);
         ok = root == 0 && build_rec(t, root, 0, 0, 0, n, tmp);
-        if (ok) node_moments(t);
+        if (ok) node_moments(t, 0);
     }
     free(fx); free(fy); free(fz); free(tmp);
     if (!ok) {
@@ -377,6 +379,22 @@ oracle_tree *oracle_tree_build(int64_t n, const double *x, const double *y, cons
         return NULL;
     }
     return t;
+}
+
+/* Refit: the tree kept between rebuilds (the paper's code rebuilds its tree
+ * only every few steps while the node moments, "calcNode", are recomputed
+ * every step; Sect. 1 and Sect. 4.1).  Node membership, tree order and
+ * groups stay as built; the positions are replaced and the moments
+ * recomputed.  READING for b_J after a refit: members may have left their
+ * node's cell, so the cell-corner bound is dropped -- leaves take the exact
+ * largest member distance, internal nodes max_c(|com_c - com| + b_c). */
+void oracle_tree_refit(oracle_tree *t, const double *x, const double *y, const double *z)
+{
+    size_t nd = (size_t)t->n * sizeof(double);
+    memcpy(t->x, x, nd);
+    memcpy(t->y, y, nd);
+    memcpy(t->z, z, nd);
+    node_moments(t, 1);
 }
 
 void oracle_tree_free(oracle_tree *t)

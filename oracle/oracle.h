@@ -66,6 +66,10 @@ typedef struct oracle_tree oracle_tree;
  * contiguously in octant order.  Returns NULL on allocation failure. */
 oracle_tree *oracle_tree_build(int64_t n, const double *x, const double *y, const double *z,
                                const double *m, int levels, int leaf_cap);
+/* Replace the positions of a built tree (same particles, caller order) and
+ * recompute its moments without rebuilding: membership, order and groups
+ * stay; b_J of internal nodes uses only the child recurrence. */
+void oracle_tree_refit(oracle_tree *t, const double *x, const double *y, const double *z);
 void oracle_tree_free(oracle_tree *t);
 int64_t oracle_tree_nnodes(const oracle_tree *t);
 void oracle_tree_cube(const oracle_tree *t, float cube[4]);

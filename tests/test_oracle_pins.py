@@ -284,6 +284,105 @@ def test_tree_dacc_zero_is_direct(mode):
     assert np.all(nint == 3000)
 
 
+# --------------------------------------------------------------------------- refit
+def _moved(p, seed, scale):
+    """Positions displaced by seeded Gaussian steps of `scale`, plus a few
+    particles thrown across the system (far outside their cells)."""
+    g = np.random.default_rng(seed)
+    x, y, z = (p[k].astype(float) + g.normal(scale=scale, size=p[k].size) for k in ("x", "y", "z"))
+    far = g.choice(x.size, 16, replace=False)
+    x[far], y[far], z[far] = -x[far], z[far], y[far]
+    return x, y, z
+
+
+def test_refit_moments_follow_the_definition():
+    """After a refit the tree keeps its membership; the moments must be those
+    of the members at their new positions (mass, centre of mass by
+    definition, b_J >= the exact largest member distance, exact for leaves)."""
+    p = ics.galaxy(6000, 9)
+    x0, y0, z0, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    t = oracle.Tree(x0, y0, z0, m, 21, 8)
+    before = t.nodes()
+    x, y, z = _moved(p, 1, 0.05)
+    t.refit(x, y, z)
+    nd = t.nodes()
+    order = t.order()
+    for k in ("level", "first", "count", "nchild", "child"):
+        assert np.array_equal(nd[k], before[k])
+    leaf = nd["nchild"] == 0
+    moved_away = 0
+    for i in range(nd["M"].size):
+        mem = order[nd["first"][i]:nd["first"][i] + nd["count"][i]]
+        M = m[mem].sum()
+        com = np.array([(m[mem] * q[mem]).sum() / M for q in (x, y, z)])
+        assert np.isclose(nd["M"][i], M, rtol=1e-14)
+        assert np.allclose([nd["cx"][i], nd["cy"][i], nd["cz"][i]], com, rtol=1e-13, atol=1e-13)
+        rmax = np.sqrt((x[mem] - com[0]) ** 2 + (y[mem] - com[1]) ** 2 + (z[mem] - com[2]) ** 2).max()
+        if leaf[i]:
+            assert np.isclose(nd["b"][i], rmax, rtol=1e-14, atol=1e-15)
+        else:
+            assert nd["b"][i] >= rmax * (1 - 1e-14)
+            moved_away += nd["b"][i] > before["b"][i]
+    assert moved_away > 0  # the thrown particles enlarge their ancestors
+
+
+def test_refit_at_the_same_positions_keeps_mass_and_centre():
+    """Refitting to unchanged positions reproduces M and the centre of mass
+    exactly; b_J can only grow (the cell-corner bound is dropped)."""
+    p = ics.plummer(4000, 10)
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    t = oracle.Tree(x, y, z, m, 21, 16)
+    a = t.nodes()
+    t.refit(x, y, z)
+    b = t.nodes()
+    for k in ("M", "cx", "cy", "cz"):
+        assert np.array_equal(a[k], b[k])
+    leaf = a["nchild"] == 0
+    assert np.array_equal(a["b"][leaf], b["b"][leaf])
+    assert np.all(b["b"][~leaf] >= a["b"][~leaf])
+
+
+@pytest.mark.parametrize("mode", [oracle.MAC_PARTICLE_ACC, oracle.MAC_GROUP_ACC])
+def test_refit_dacc_zero_is_direct_at_the_new_positions(mode):
+    """With delta_acc = 0 the walk of a refitted tree is the direct sum of
+    Eq. 1 over the new positions: a refit that kept any stale position or
+    moment would fail."""
+    p = ics.plummer(2500, 11)
+    x0, y0, z0, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    t = oracle.Tree(x0, y0, z0, m, 21, 8)
+    x, y, z = _moved(p, 2, 0.1)
+    t.refit(x, y, z)
+    ax, ay, az, phi = oracle.direct(x, y, z, m, 1.0, 1 / 64)
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    bx, by, bz, bphi, _ = t.walk(mode, 1.0, 1 / 64, 0.0, 0.5, 32, amag)
+    assert np.max(oracle.rel_err(bx, by, bz, ax, ay, az)) < 1e-13
+    assert np.allclose(bphi, phi, rtol=1e-13)
+
+
+def test_refit_error_stays_bounded_by_the_mac():
+    """After one leapfrog-sized displacement the refitted tree's errors at
+    delta_acc = 2^-9 stay close to a fresh tree's: the MAC still bounds them
+    because b_J still bounds every member's distance."""
+    p = ics.plummer(8192, 12)
+    x0, y0, z0, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    t = oracle.Tree(x0, y0, z0, m, 21, 16)
+    dt = 1.0 / 256
+    x, y, z = (p[k].astype(float) + dt * p["v" + k].astype(float) for k in ("x", "y", "z"))
+    t.refit(x, y, z)
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 1 / 128, want_phi=False)
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    rx, ry, rz, _, nr = t.walk(oracle.MAC_GROUP_ACC, 1.0, 1 / 128, 2.0 ** -9, 0.5, 64, amag,
+                               want_phi=False)
+    f = oracle.Tree(x, y, z, m, 21, 16)
+    fx, fy, fz, _, nf = f.walk(oracle.MAC_GROUP_ACC, 1.0, 1 / 128, 2.0 ** -9, 0.5, 64, amag,
+                               want_phi=False)
+    er = oracle.rel_err(rx, ry, rz, ax, ay, az)
+    ef = oracle.rel_err(fx, fy, fz, ax, ay, az)
+    for q in (50, 99):
+        assert oracle.percentile_nearest_rank(er, q) <= 1.5 * oracle.percentile_nearest_rank(ef, q)
+    assert nr.sum() >= 0.9 * nf.sum()
+
+
 def test_tree_tiny_theta_is_direct():
     p = ics.plummer(2000, 9)
     x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
