@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define NBODY_ABI_VERSION 1
+#define NBODY_ABI_VERSION 2
 
 typedef enum {
     NBODY_OK = 0,
@@ -84,7 +84,19 @@ typedef struct {
     int32_t schedule;    /* nbody_schedule (default NBODY_SCHED_MORTON)             */
     int32_t use_graph;   /* 1: nbody_step(_batched) replays a CUDA graph of two
                             steps (captured on first use, on an internal stream
-                            ordered after cuda_stream); 0: eager launches (0)  */
+                            ordered after cuda_stream; only with
+                            rebuild_interval = 1); 0: eager launches (0)     */
+    int32_t rebuild_interval; /* tree rebuilds in nbody_step(_batched): 1 = every
+                            step (default); k >= 2 = every k-th step of a call,
+                            the steps between refit the tree (nbody_refit:
+                            moments and group spheres at the new positions,
+                            structure kept); 0 = automatic: rebuild when the
+                            last step cost more than the mean step of the cycle
+                            since the last rebuild (nbody_rebuild_due; the
+                            paper's code tunes its rebuild interval by timing,
+                            Sect. 1 and 4.1), at most every 32 steps; this
+                            synchronises the stream after every step.  The
+                            first step of every call rebuilds.  0..1024.     */
 } nbody_config;
 
 typedef struct {
@@ -100,6 +112,8 @@ typedef struct {
     float ms_walk;         /* device time of the walk phase(s) (CUDA events)   */
     float ms_walk_kernel;  /* device time of the walk kernel launches alone    */
     int32_t walk_launches; /* walk kernel launches behind ms_walk_kernel       */
+    int32_t rebuilds;      /* steps of the last nbody_step call that rebuilt the
+                              tree (the others refitted it)                    */
 } nbody_stats;
 
 typedef struct nbody_ctx nbody_ctx;
@@ -141,6 +155,23 @@ nbody_status nbody_build(nbody_ctx *ctx, int64_t n, const float *x, const float 
 nbody_status nbody_build_batched(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
                                  const float *eps_sys, const float *x, const float *y,
                                  const float *z, const float *m);
+
+/* Refit the tree of the last build to new positions of the same particles
+ * (caller order, FP32 [n], host or device): the node structure, tree order
+ * and groups are kept; node monopoles, sizes b_J (from the child recurrence
+ * only, as members may have left their cells) and group spheres are
+ * recomputed -- the paper's calcNode without makeTree (its code rebuilds the
+ * tree only every few steps, Sect. 1 and 4.1).  m must be the masses of the
+ * build.  Errors: ENOTBUILT, EINVAL, ECUDA. */
+nbody_status nbody_refit(nbody_ctx *ctx, const float *x, const float *y, const float *z,
+                         const float *m);
+
+/* Policy of rebuild_interval = 0: cost_ms[0] is the step that rebuilt the
+ * tree, cost_ms[1..m-1] the refitted steps since (tree phase + walk, device
+ * time).  Returns 1 when the last step cost more than the mean of the m steps
+ * (continuing to refit would raise the mean cost per step), else 0; m < 2
+ * returns 0.  Host-only, needs no device. */
+int32_t nbody_rebuild_due(const float *cost_ms, int32_t m);
 
 /* Tree accelerations for every particle of the last build (Eq. 1 evaluated
  * over the interaction lists of Sect. 1, nodes accepted by Eq. 2).

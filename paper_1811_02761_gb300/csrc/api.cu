@@ -189,6 +189,8 @@ bool config_ok(const nbody_config *c, std::string &why) {
     if (c->stack_depth < 64 || c->stack_depth > 4096) return bad("stack_depth must be in 64..4096");
     if (c->warps_per_block < 1 || c->warps_per_block > 16) return bad("warps_per_block must be in 1..16");
     if (c->schedule < 0 || c->schedule > 2) return bad("schedule must be 0, 1 or 2");
+    if (c->rebuild_interval < 0 || c->rebuild_interval > 1024)
+        return bad("rebuild_interval must be in 0..1024");
     size_t smem = (size_t)c->warps_per_block * nb::walk_smem_per_warp(c->list_depth, c->stack_depth);
     if (smem > 227 * 1024)
         return bad("warps_per_block * (16 list_depth + 4 stack_depth + 128) exceeds 227 KB");
@@ -335,6 +337,24 @@ nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
     // tree: leaflevel, level scan, level offsets, nodes, two system-root
     // kernels, leaf moments, one internal-moments launch per level; groups: 5
     c->kernels += 6 + 1 + L.levels + 5;
+    NB_CUDA(c, cudaGetLastError());
+    return NBODY_OK;
+}
+
+// Refit of the current tree to the positions now in pos4 (sorted order):
+// moments with the child-recurrence b_J, then the group spheres.
+nbody_status refit_tree_groups(nbody_ctx *c, const Layout &L) {
+    cudaStream_t s = c->stream;
+    c->costs_valid = false;
+    tree_moments(s, L, P<uint64_t>(c->keys), P<float4>(c->pos4), P<SysBox>(c->sys_box),
+                 c->cfg.leaf_cap, c->cfg.G, c->ds, P<int32_t>(c->node_start),
+                 P<int8_t>(c->node_level), P<int32_t>(c->node_link), P<int32_t>(c->node_count),
+                 P<int32_t>(c->node_nchild), P<float4>(c->nodeA), P<float4>(c->nodeB),
+                 P<float2>(c->mass2), c->nsm, true);
+    refit_groups(s, L, c->cfg.group_size, P<float4>(c->pos4), P<int64_t>(c->sys_off), c->ds,
+                 P<int32_t>(c->grp_first), P<int32_t>(c->grp_count), P<float4>(c->grp_sphere),
+                 P<int32_t>(c->grp_sys), c->nsm);
+    c->kernels += 1 + L.levels + 1;
     NB_CUDA(c, cudaGetLastError());
     return NBODY_OK;
 }
@@ -651,6 +671,7 @@ void nbody_config_default(nbody_config *c) {
     c->want_potential = 0;
     c->schedule = NBODY_SCHED_MORTON;
     c->use_graph = 0;
+    c->rebuild_interval = 1;
 }
 
 nbody_status nbody_create(nbody_ctx **out, const nbody_config *cfg, void *cuda_stream) {
@@ -722,6 +743,43 @@ nbody_status nbody_build(nbody_ctx *ctx, int64_t n, const float *x, const float 
     if (!x || !y || !z || !m) return fail(ctx, NBODY_EINVAL, "NULL array");
     ctx->built = false;
     return do_build(ctx, n, 1, nullptr, nullptr, x, y, z, m);
+}
+
+nbody_status nbody_refit(nbody_ctx *ctx, const float *x, const float *y, const float *z,
+                         const float *m) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    if (!x || !y || !z || !m) return fail(ctx, NBODY_EINVAL, "NULL array");
+    if (!ctx->built) return fail(ctx, NBODY_ENOTBUILT, "nbody_refit before nbody_build");
+    const int64_t n = ctx->L.n;
+    const size_t fb = (size_t)n * 4;
+    const void *dx, *dy, *dz, *dm;
+    NB_CUDA(ctx, stage_in(ctx, 0, x, fb, &dx));
+    NB_CUDA(ctx, stage_in(ctx, 1, y, fb, &dy));
+    NB_CUDA(ctx, stage_in(ctx, 2, z, fb, &dz));
+    NB_CUDA(ctx, stage_in(ctx, 3, m, fb, &dm));
+    ctx->kernels = 0;
+    NB_CUDA(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+    // the new positions into the build's sorted order (vals maps sorted
+    // index -> caller index)
+    launch_gather_pos4(ctx->stream, n, P<uint32_t>(ctx->vals), dx, dy, dz, false,
+                       (const float *)dm, P<float4>(ctx->pos4));
+    ctx->kernels += 1;
+    nbody_status st = refit_tree_groups(ctx, ctx->L);
+    if (st != NBODY_OK) return st;
+    NB_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+    st = read_status(ctx);
+    if (st != NBODY_OK) return st;
+    NB_CUDA(ctx, cudaEventElapsedTime(&ctx->last_ms_build, ctx->ev[0], ctx->ev[1]));
+    ctx->last.ms_build = ctx->last_ms_build;
+    ctx->last.kernels = ctx->kernels;
+    return NBODY_OK;
+}
+
+int32_t nbody_rebuild_due(const float *cost_ms, int32_t m) {
+    if (!cost_ms || m < 2) return 0;
+    double sum = 0.0;
+    for (int32_t i = 0; i < m; i++) sum += (double)cost_ms[i];
+    return (double)cost_ms[m - 1] * (double)m > sum ? 1 : 0;
 }
 
 nbody_status nbody_build_batched(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
@@ -904,22 +962,33 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     std::vector<int> marks;  // per eager step: event indices (build start, build end, walk end)
 
     // One leapfrog step enqueued on ctx->stream.  With `timing`, phase
-    // boundaries are recorded with pool events (eager steps only).
-    auto one_step = [&](bool timing) -> nbody_status {
+    // boundaries are recorded with pool events (eager steps only).  A step
+    // either rebuilds the tree (keys, sort, state permutation, tree, groups)
+    // or refits the current one (moments and group spheres at the drifted
+    // positions, which the kick-drift writes to pos4 in place).
+    int rebuilds = 0;
+    auto one_step = [&](bool timing, bool rebuild) -> nbody_status {
         cudaStream_t q = ctx->stream;
-        launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt);
+        launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt, rebuild ? nullptr : P<float4>(ctx->pos4));
         ctx->kernels += 1;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         if (timing) {
             NB_CUDA(ctx, pool_event(ctx, &e0));
             NB_CUDA(ctx, cudaEventRecord(e0, q));
         }
-        nbody_status r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
-        if (r != NBODY_OK) return r;
-        launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur], P<float4>(ctx->pos4));
-        ctx->kernels += 1;
-        cur = 1 - cur;
-        r = build_tree_groups(ctx, L);
+        nbody_status r;
+        if (rebuild) {
+            r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
+            if (r != NBODY_OK) return r;
+            launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
+                                 P<float4>(ctx->pos4));
+            ctx->kernels += 1;
+            cur = 1 - cur;
+            r = build_tree_groups(ctx, L);
+            rebuilds++;
+        } else {
+            r = refit_tree_groups(ctx, L);
+        }
         if (r != NBODY_OK) return r;
         if (timing) {
             NB_CUDA(ctx, pool_event(ctx, &e1));
@@ -947,8 +1016,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
 
     int eager = nsteps;
     // a cost-ordered queue reads the group count on the host every step, so it
-    // runs eagerly
-    if (ctx->cfg.use_graph && nsteps >= 2 && ctx->cfg.schedule == NBODY_SCHED_MORTON) {
+    // runs eagerly; so do steps that may refit instead of rebuilding
+    if (ctx->cfg.use_graph && nsteps >= 2 && ctx->cfg.schedule == NBODY_SCHED_MORTON &&
+        ctx->cfg.rebuild_interval == 1) {
         // Two steps per graph: the sort's ping-pong buffers and the state
         // copies swap roles every step, so after two steps every pointer is
         // back where the capture found it and the graph can be replayed.
@@ -982,8 +1052,8 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             cudaError_t ce = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed);
             nbody_status r1 = NBODY_OK, r2 = NBODY_OK;
             if (ce == cudaSuccess) {
-                r1 = one_step(false);
-                if (r1 == NBODY_OK) r2 = one_step(false);
+                r1 = one_step(false, true);
+                if (r1 == NBODY_OK) r2 = one_step(false, true);
                 cudaError_t ee = cudaStreamEndCapture(ctx->gstream, &graph);
                 if (ce == cudaSuccess) ce = ee;
             }
@@ -1003,14 +1073,40 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         for (int it = 0; it + 1 < nsteps; it += 2) {
             NB_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->gstream));
             ctx->kernels += ctx->gkernels;
+            rebuilds += 2;
         }
         NB_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->gstream));
         NB_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev[1], 0));
         eager = nsteps % 2;
     }
+    // Rebuild schedule of the eager steps: every rebuild_interval-th step, or
+    // (interval 0) when nbody_rebuild_due says the last step raised the mean
+    // cost of the current cycle -- measured per step, so the stream is
+    // synchronised after each step -- and at most every kAutoMaxInterval.
+    constexpr int kAutoMaxInterval = 32;
+    const int interval = ctx->cfg.rebuild_interval;
+    std::vector<float> cycle;
+    int since = 0;
     for (int it = 0; it < eager; it++) {
-        st = one_step(true);
+        bool rebuild = (it == 0 && eager == nsteps) || interval == 1;
+        if (!rebuild && interval > 1) rebuild = since >= interval;
+        if (!rebuild && interval == 0)
+            rebuild = since >= kAutoMaxInterval ||
+                      nbody_rebuild_due(cycle.data(), (int32_t)cycle.size()) != 0;
+        if (rebuild) {
+            since = 0;
+            cycle.clear();
+        }
+        st = one_step(true, rebuild);
         if (st != NBODY_OK) return st;
+        since++;
+        if (interval == 0) {
+            const int k = marks.back();
+            float c = 0.0f;
+            NB_CUDA(ctx, cudaEventSynchronize(ctx->evpool[k + 2]));
+            NB_CUDA(ctx, cudaEventElapsedTime(&c, ctx->evpool[k], ctx->evpool[k + 2]));
+            cycle.push_back(c);
+        }
     }
     // in[] are the device copies (the caller's arrays themselves when on the device)
     launch_store_state(s, n, S[cur], acc, (double *)in[0], (double *)in[1], (double *)in[2],
@@ -1045,6 +1141,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     ctx->last.ms_walk = ms_walk;
     ctx->last.ms_walk_kernel = collect_walk_ms(ctx, &ctx->last.walk_launches);
     ctx->last.kernels = ctx->kernels;
+    ctx->last.rebuilds = rebuilds;
     if (stats) *stats = ctx->last;
     // the sorted state no longer matches a caller-order build
     ctx->built = false;

@@ -21,7 +21,7 @@ static inline int grid_for(int64_t n, int threads = 256) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
 __global__ void kick_drift_kernel(int64_t n, StepState st, const float4 *__restrict__ acc,
-                                  float hdt, double dt) {
+                                  float hdt, double dt, float4 *pos4) {
     NB_GRID_LOOP(i, n) {
         float4 a = acc[i];
         float vx = fmaf(a.x, hdt, st.vx[i]);
@@ -30,9 +30,13 @@ __global__ void kick_drift_kernel(int64_t n, StepState st, const float4 *__restr
         st.vx[i] = vx;
         st.vy[i] = vy;
         st.vz[i] = vz;
-        st.x[i] += (double)vx * dt;
-        st.y[i] += (double)vy * dt;
-        st.z[i] += (double)vz * dt;
+        const double x = st.x[i] + (double)vx * dt;
+        const double y = st.y[i] + (double)vy * dt;
+        const double z = st.z[i] + (double)vz * dt;
+        st.x[i] = x;
+        st.y[i] = y;
+        st.z[i] = z;
+        if (pos4) pos4[i] = make_float4((float)x, (float)y, (float)z, st.m[i]);
     }
 }
 
@@ -47,8 +51,8 @@ __global__ void kick_kernel(int64_t n, StepState st, const float4 *__restrict__ 
 }
 
 void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
-                       float dt) {
-    kick_drift_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, hdt, (double)dt);
+                       float dt, float4 *pos4) {
+    kick_drift_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, hdt, (double)dt, pos4);
 }
 
 void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt) {

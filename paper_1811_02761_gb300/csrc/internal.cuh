@@ -172,6 +172,16 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                 int32_t *node_start, int8_t *node_level, int32_t *node_parent,
                 int32_t *node_link, int32_t *node_count, int32_t *node_nchild,
                 float4 *nodeA, float4 *nodeB, float2 *mass2, int32_t *sys_root, int nsm);
+// Node moments of the current tree from pos4 (refit: positions moved since
+// the build; b_J of internal nodes from the child recurrence only).
+void tree_moments(cudaStream_t s, const Layout &L, const uint64_t *keys, const float4 *pos4,
+                  const SysBox *d_box, int leaf_cap, float G, DevState *ds,
+                  const int32_t *node_start, const int8_t *node_level, const int32_t *node_link,
+                  int32_t *node_count, const int32_t *node_nchild, float4 *nodeA, float4 *nodeB,
+                  float2 *mass2, int nsm, bool refit);
+void refit_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
+                  const int64_t *d_off, DevState *ds, const int32_t *grp_first,
+                  int32_t *grp_count, float4 *grp_sphere, int32_t *grp_sys, int nsm);
 void build_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
                   const int64_t *d_off, const int32_t *node_start, const int32_t *node_parent,
                   const int32_t *node_count, const int32_t *node_nchild, const int32_t *node_link,
@@ -267,8 +277,9 @@ struct StepState {
     uint32_t *id;    // caller index of each sorted particle
     float *pcost;    // cost of each particle's group in the last walk (may be NULL)
 };
+// pos4 (nullable): also refresh the FP32 walk copy (x, y, z, m) in place.
 void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
-                       float dt);
+                       float dt, float4 *pos4);
 void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt);
 void launch_permute_state(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
                           StepState dst, float4 *pos4);

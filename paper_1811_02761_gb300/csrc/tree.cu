@@ -399,9 +399,10 @@ __global__ void __launch_bounds__(256) leaf_moments_kernel(
 // Sums relative to the cell centre; the size is
 //   b = min(max_c (|com_c - com| + b_c), distance from com to the farthest
 //           corner of the cell widened by one finest cell),
-// rounded up.
+// rounded up.  After a refit (refit != 0: positions moved since the build,
+// members may have left the cell) only the child recurrence bounds b.
 __global__ void __launch_bounds__(256) internal_moments_kernel(
-    Layout L, int level, const uint64_t *__restrict__ keys, const SysBox *__restrict__ box,
+    Layout L, int level, int refit, const uint64_t *__restrict__ keys, const SysBox *__restrict__ box,
     float G, DevState *ds, const int32_t *__restrict__ node_start,
     const int32_t *__restrict__ node_link, int32_t *node_count,
     const int32_t *__restrict__ node_nchild, float4 *nodeA, float4 *nodeB, float2 *mass2) {
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(256) internal_moments_kernel(
                     const float e = fabsf(cp[a] - cell.c[a]) + cell.h;
                     c2 = fmaf(e, e, c2);
                 }
-                const float bp = fminf(rec, __fsqrt_ru(c2)) * kUp;
+                const float bp = (refit ? rec : fminf(rec, __fsqrt_ru(c2))) * kUp;
                 node_count[par] = count;
                 write_node(par, cp[0], cp[1], cp[2], Mp, bp, G, c0, nc << 1, nodeA, nodeB, mass2);
             }
@@ -511,8 +512,18 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                                      node_level, node_parent, node_link, node_count, node_nchild);
     sys_root_init_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(L.nsys, sys_root);
     sys_root_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(ds, node_start, d_off, L.nsys, sys_root);
-    // leaves: one warp per 32 nodes; internal nodes: one launch per level,
-    // deepest first (level `levels` holds leaves only)
+    tree_moments(s, L, keys, pos4, d_box, leaf_cap, G, ds, node_start, node_level, node_link,
+                 node_count, node_nchild, nodeA, nodeB, mass2, nsm, false);
+}
+
+// Moments of every node of the current tree from pos4: leaves in one launch
+// (one warp per 32 nodes), internal nodes one launch per level, deepest
+// first (level `levels` holds leaves only).
+void tree_moments(cudaStream_t s, const Layout &L, const uint64_t *keys, const float4 *pos4,
+                  const SysBox *d_box, int leaf_cap, float G, DevState *ds,
+                  const int32_t *node_start, const int8_t *node_level, const int32_t *node_link,
+                  int32_t *node_count, const int32_t *node_nchild, float4 *nodeA, float4 *nodeB,
+                  float2 *mass2, int nsm, bool refit) {
     int64_t mb = (L.n / 4 + 255) / 256;
     if (mb > (int64_t)nsm * 8) mb = (int64_t)nsm * 8;
     if (mb < 1) mb = 1;
@@ -526,8 +537,9 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                                                        node_nchild, nodeA, nodeB, mass2);
     const int ib = nsm * 4;
     for (int l = L.levels - 1; l >= 0; l--)
-        internal_moments_kernel<<<ib, 256, 0, s>>>(L, l, keys, d_box, G, ds, node_start, node_link,
-                                                   node_count, node_nchild, nodeA, nodeB, mass2);
+        internal_moments_kernel<<<ib, 256, 0, s>>>(L, l, refit ? 1 : 0, keys, d_box, G, ds,
+                                                   node_start, node_link, node_count, node_nchild,
+                                                   nodeA, nodeB, mass2);
 }
 
 // ---------------------------------------------------------------- groups
@@ -682,6 +694,15 @@ void build_groups(cudaStream_t s, const Layout &L, int group_size, const float4 
     int gb = nsm * 8;
     group_info_kernel<<<gb, 256, 0, s>>>(L, group_size, pos4, d_off, ds, grp_first, grp_count,
                                          grp_sphere, grp_sys);
+}
+
+// Spheres (and counts, systems) of the existing groups from pos4: after a
+// refit the membership stays and only the geometry is recomputed.
+void refit_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
+                  const int64_t *d_off, DevState *ds, const int32_t *grp_first,
+                  int32_t *grp_count, float4 *grp_sphere, int32_t *grp_sys, int nsm) {
+    group_info_kernel<<<nsm * 8, 256, 0, s>>>(L, group_size, pos4, d_off, ds, grp_first, grp_count,
+                                              grp_sphere, grp_sys);
 }
 
 // alpha_g = delta_acc * min over members of |a_old| (Eq. 2 per group).

@@ -35,7 +35,7 @@ class Config(C.Structure):
                 ("ipl", C.c_int32), ("list_depth", C.c_int32), ("stack_depth", C.c_int32),
                 ("warps_per_block", C.c_int32), ("compensated", C.c_int32),
                 ("want_potential", C.c_int32), ("schedule", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("rebuild_interval", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -54,7 +54,8 @@ class Stats(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_groups", C.c_int64), ("interactions", C.c_int64),
                 ("list_entries", C.c_int64), ("max_stack", C.c_int32), ("levels", C.c_int32),
                 ("kernels", C.c_int64), ("ms_build", C.c_float), ("ms_walk", C.c_float),
-                ("ms_walk_kernel", C.c_float), ("walk_launches", C.c_int32)]
+                ("ms_walk_kernel", C.c_float), ("walk_launches", C.c_int32),
+                ("rebuilds", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -68,7 +69,8 @@ EXPORTS = ("nbody_abi_version", "nbody_config_default", "nbody_create", "nbody_d
            "nbody_get_group_costs", "nbody_export", "nbody_last_error",
            "nbody_diagnostics_noalloc", "nbody_tune_space_default", "nbody_autotune",
            "nbody_mlp_set_params", "nbody_mlp_get_params", "nbody_mlp_train",
-           "nbody_mlp_predict", "nbody_mlp_eval", "nbody_selftest")
+           "nbody_mlp_predict", "nbody_mlp_eval", "nbody_selftest",
+           "nbody_refit", "nbody_rebuild_due")
 MLP_PARAMS, MLP_FEATURES = 1377, 8
 EXPORT_PERM, EXPORT_KEYS, EXPORT_NODE_LEVEL, EXPORT_NODE_START, EXPORT_NODE_COUNT, \
     EXPORT_NODE_PARENT, EXPORT_NODE_A, EXPORT_NODE_B, EXPORT_GROUP_FIRST, EXPORT_GROUP_COUNT, \
@@ -123,6 +125,8 @@ def load(build_if_missing: bool = True):
             "nbody_autotune": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(TuneSpace),
                                     C.POINTER(Config), C.POINTER(f32), C.POINTER(i32)]),
             "nbody_selftest": (st, [i32, vp]),
+            "nbody_refit": (st, [vp, vp, vp, vp, vp]),
+            "nbody_rebuild_due": (i32, [C.POINTER(f32), i32]),
             "nbody_last_error": (st, [vp, C.c_char_p, C.c_size_t]),
         }
         for name, (res, args) in sig.items():
@@ -415,6 +419,20 @@ def nbody_export(ctx, what: int) -> np.ndarray:
     _check(lib, ctx, lib.nbody_export(ctx, int(what), out.ctypes.data if out.size else None,
                                       cnt.value, C.byref(cnt)))
     return out.reshape(-1, width) if width > 1 else out
+
+
+def nbody_refit(ctx, x, y, z, m):
+    """Refit the last build's tree to new positions of the same particles."""
+    lib = load()
+    n = _size(x)
+    ps = [_ptr(a, "float32", n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (m, "m"))]
+    _check(lib, ctx, lib.nbody_refit(ctx, *ps))
+
+
+def nbody_rebuild_due(cost_ms) -> bool:
+    """Host-only rebuild policy of rebuild_interval = 0 (see nbody.h)."""
+    a = np.ascontiguousarray(cost_ms, dtype=np.float32)
+    return bool(load().nbody_rebuild_due(a.ctypes.data_as(C.POINTER(C.c_float)), a.size))
 
 
 SELFTEST_SORT_WAIT = 1

@@ -1,0 +1,142 @@
+"""Tree refit on the GPU (nbody_refit, rebuild_interval) against the FP64
+oracle's refit: the structure is kept, moments and group spheres follow the
+new positions, and the walk over the refitted tree meets the same error rule
+as over a fresh tree (p50/p99 within 1.1x the oracle's + 1e-6)."""
+import numpy as np
+import pytest
+
+import ics
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1811_02761_gb300 as nb  # noqa: E402
+
+EPS, DACC = 1.0 / 64, 2.0 ** -9
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def moved(p, seed, scale):
+    g = np.random.default_rng(seed)
+    out = [(p[k] + g.normal(scale=scale, size=p[k].size)).astype(np.float32) for k in ("x", "y", "z")]
+    far = g.choice(out[0].size, 8, replace=False)
+    out[0][far] = -out[0][far]
+    return out
+
+
+@pytest.mark.parametrize("gen,n,cap", [(ics.galaxy, 20000, 16), (ics.plummer, 8192, 8)])
+def test_refit_moments_groups_and_walk_vs_oracle(gen, n, cap):
+    p = gen(n, 21)
+    m = p["m"]
+    x1, y1, z1 = moved(p, 3, 0.02)
+    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, leaf_cap=cap)
+    ctx = nb.nbody_create(cfg)
+    try:
+        nb.nbody_build(ctx, *[dev(p[k]) for k in ("x", "y", "z")], dev(m))
+        f0 = nb.nbody_export(ctx, nb.nbody.EXPORT_GROUP_FIRST)
+        nb.nbody_refit(ctx, dev(x1), dev(y1), dev(z1), dev(m))
+        f1 = nb.nbody_export(ctx, nb.nbody.EXPORT_GROUP_FIRST)
+        assert np.array_equal(f0, f1)
+        lev = nb.nbody_export(ctx, nb.nbody.EXPORT_NODE_LEVEL).astype(np.int64)
+        start = nb.nbody_export(ctx, nb.nbody.EXPORT_NODE_START).astype(np.int64)
+        A = nb.nbody_export(ctx, nb.nbody.EXPORT_NODE_A)
+        B = nb.nbody_export(ctx, nb.nbody.EXPORT_NODE_B)
+        sph = nb.nbody_export(ctx, nb.nbody.EXPORT_GROUP_SPHERE)
+        # accelerations over the refitted tree
+        X1 = [a.astype(np.float64) for a in (x1, y1, z1)]
+        ax, ay, az, _ = oracle.direct(*X1, m.astype(np.float64), 1.0, EPS, want_phi=False)
+        amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2).astype(np.float32)
+        out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+        st = nb.nbody_walk(ctx, dev(amag), *out)
+        g = [o.cpu().numpy().astype(np.float64) for o in out]
+    finally:
+        nb.nbody_destroy(ctx)
+    t = oracle.Tree(p["x"], p["y"], p["z"], m, 21, cap)
+    t.refit(*X1)
+    on = t.nodes()
+    key = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(on["level"], on["first"]))}
+    idx = np.array([key[(int(a), int(b))] for a, b in zip(lev, start)])
+    assert np.allclose(A[:, 3], on["M"][idx], rtol=2e-6)
+    for c, k in ((0, "cx"), (1, "cy"), (2, "cz")):
+        scale = np.maximum(np.abs(on[k][idx]), on["b"][idx] + 1e-3)
+        assert np.all(np.abs(A[:, c] - on[k][idx]) <= 2e-6 * scale)
+    b_o = on["b"][idx]
+    ulp = np.spacing(np.max(np.abs(A[:, :3]), axis=1).astype(np.float32)).astype(np.float64)
+    assert np.all(B[:, 0] >= b_o * (1 - 1e-6) - 2 * ulp)
+    assert np.all(B[:, 0] <= b_o * (1 + 1e-5) + 8 * ulp)
+    # group spheres enclose the members at the new positions
+    order = t.order()
+    cnt = np.diff(np.append(f1, n))
+    for gi in range(0, f1.size, 11):
+        mem = order[f1[gi]:f1[gi] + cnt[gi]]
+        d = np.sqrt((X1[0][mem] - sph[gi, 0]) ** 2 + (X1[1][mem] - sph[gi, 1]) ** 2 +
+                    (X1[2][mem] - sph[gi, 2]) ** 2)
+        assert d.max() <= sph[gi, 3] * (1 + 1e-6) + 1e-6
+    ox, oy, oz, _, nint = t.walk(oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, cfg.group_size,
+                                 amag.astype(np.float64), want_phi=False)
+    eg = oracle.rel_err(*g, ax, ay, az)
+    eo = oracle.rel_err(ox, oy, oz, ax, ay, az)
+    for q in (50, 99):
+        pg, po = oracle.percentile_nearest_rank(eg, q), oracle.percentile_nearest_rank(eo, q)
+        assert pg <= 1.1 * po + 1e-6, (q, pg, po)
+    assert abs(st.interactions - nint.sum()) <= 0.01 * nint.sum()
+
+
+def test_refit_needs_a_build():
+    ctx = nb.nbody_create(nb.nbody_config_default())
+    try:
+        z = torch.zeros(4, device="cuda")
+        with pytest.raises(nb.NbodyError) as e:
+            nb.nbody_refit(ctx, z, z, z, z)
+        assert e.value.status == nb.NBODY_ENOTBUILT
+    finally:
+        nb.nbody_destroy(ctx)
+
+
+def _run_steps(p, interval, steps, n):
+    X = [dev(p[k].astype(np.float64)) for k in ("x", "y", "z")]
+    V = [dev(p[k]) for k in ("vx", "vy", "vz")]
+    M = dev(p["m"])
+    A = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    ctx = nb.nbody_create(nb.nbody_config_default(eps=EPS, delta_acc=DACC,
+                                                  rebuild_interval=interval))
+    try:
+        nb.nbody_build(ctx, *[dev(p[k]) for k in ("x", "y", "z")], M)
+        nb.nbody_walk(ctx, None, *A)
+        st = nb.nbody_step(ctx, *X, *V, M, *A, 1.0 / 256, steps)
+    finally:
+        nb.nbody_destroy(ctx)
+    return [t.cpu().numpy() for t in X], [t.cpu().numpy() for t in A], st
+
+
+@pytest.mark.parametrize("interval,want", [(4, 3), (0, None), (1, 10)])
+def test_step_with_rebuild_interval(interval, want):
+    """Leapfrog steps that refit between rebuilds: the rebuild count follows
+    the interval, and the accelerations at the final positions meet the
+    error rule against FP64 direct summation as well as the every-step run."""
+    n = 1 << 14
+    p = ics.galaxy(n, 22)
+    steps = 10
+    Xi, Ai, st = _run_steps(p, interval, steps, n)
+    if want is not None:
+        assert st.rebuilds == want, st.rebuilds
+    else:
+        assert 1 <= st.rebuilds <= steps
+    X1, A1, _ = _run_steps(p, 1, steps, n)
+    m = p["m"].astype(np.float64)
+    for X, A in ((Xi, Ai), (X1, A1)):
+        Xf = [a.astype(np.float32).astype(np.float64) for a in X]
+        ax, ay, az, _ = oracle.direct(*Xf, m, 1.0, EPS, want_phi=False)
+        e = oracle.rel_err(*[a.astype(np.float64) for a in A], ax, ay, az)
+        if X is Xi:
+            ei = e
+        else:
+            e1 = e
+    for q in (50, 99):
+        assert oracle.percentile_nearest_rank(ei, q) <= 1.5 * oracle.percentile_nearest_rank(e1, q) + 1e-6
+    # the trajectories stay close (forces differ only by tree error)
+    assert np.max(np.abs(Xi[0] - X1[0])) < 1e-4

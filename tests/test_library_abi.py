@@ -32,16 +32,18 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_abi_version_and_defaults():
-    assert nb.nbody_abi_version() == 1
+    assert nb.nbody_abi_version() == 2
     c = nb.nbody_config_default()
     assert c.G == 1.0 and c.delta_acc == 2.0 ** -9 and c.leaf_cap == 16
     assert c.group_size <= 32 * c.ipl
+    assert c.rebuild_interval == 1
 
 
 @pytest.mark.parametrize("bad", [dict(ipl=5), dict(ipl=0), dict(leaf_cap=0), dict(group_size=8, leaf_cap=16),
                                  dict(group_size=128, ipl=2), dict(list_depth=100),
                                  dict(eps=-1.0), dict(theta=1.5), dict(delta_acc=-1e-3),
-                                 dict(warps_per_block=16, list_depth=1024, stack_depth=4096)])
+                                 dict(warps_per_block=16, list_depth=1024, stack_depth=4096),
+                                 dict(rebuild_interval=-1), dict(rebuild_interval=2000)])
 def test_create_rejects_bad_config_before_any_device_work(bad):
     with pytest.raises(nb.NbodyError) as e:
         nb.nbody_create(nb.nbody_config_default(**bad))
@@ -64,3 +66,24 @@ def test_binding_rejects_wrong_dtypes():
     assert isinstance(lib, ctypes.CDLL)
     with pytest.raises(nb.NbodyError):
         nb.nbody.nbody_build(None, np.zeros(4, np.float64), *[np.zeros(4, np.float32)] * 3)
+
+
+def test_rebuild_policy_minimises_the_mean_step_cost():
+    """rebuild_interval = 0 (host-only policy): with a walk that slows down
+    linearly after each rebuild (cost B + w after a rebuild, R + w + g k after
+    k refits) the policy must pick the interval that minimises the mean cost
+    per step, about sqrt(2 (B - R) / g); with no slow-down it never rebuilds."""
+    B, R, w, g = 3.0, 0.6, 7.0, 0.05
+
+    def cycle(k):
+        return [B + w] + [R + w + g * j for j in range(1, k)]
+
+    def mean(k):
+        return sum(cycle(k)) / k
+
+    best = min(range(1, 200), key=mean)
+    # the policy's first "rebuild now" after steps 0..m-1 of the cycle
+    m = next(m for m in range(2, 200) if nb.nbody_rebuild_due(cycle(m)))
+    assert abs((m - 1) - best) <= 1, (m, best)
+    assert not any(nb.nbody_rebuild_due([B + w] + [R + w] * k) for k in range(1, 100))
+    assert not nb.nbody_rebuild_due([5.0]) and not nb.nbody_rebuild_due([])
