@@ -25,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 MAC_PARTICLE_ACC, MAC_GROUP_ACC, MAC_PARTICLE_GEO, MAC_GROUP_GEO = 0, 1, 2, 3
+QUADRUPOLE = 16  # or-ed into a MAC mode: accepted nodes add their quadrupole
 
 
 def build(force: bool = False) -> str:
@@ -62,6 +63,7 @@ def _load():
         lib.oracle_tree_build.restype = C.c_void_p
         lib.oracle_tree_free.argtypes = [C.c_void_p]
         lib.oracle_tree_refit.argtypes = [C.c_void_p, d, d, d]
+        lib.oracle_tree_quadrupoles.argtypes = [C.c_void_p, d]
         lib.oracle_tree_nnodes.argtypes = [C.c_void_p]
         lib.oracle_tree_nnodes.restype = C.c_int64
         lib.oracle_tree_cube.argtypes = [C.c_void_p, f32]
@@ -213,6 +215,12 @@ class Tree:
                                     _p(o["cz"], C.c_double), _p(o["M"], C.c_double),
                                     _p(o["b"], C.c_double))
         return o
+
+    def quadrupoles(self):
+        """Traceless quadrupole of every node, shape (nodes, 6): xx, yy, zz, xy, xz, yz."""
+        out = np.empty((self.nnodes, 6))
+        self._lib.oracle_tree_quadrupoles(self._h, _p(out, C.c_double))
+        return out
 
     def order(self):
         out = np.empty(self.n, np.int64)

@@ -41,6 +41,30 @@ static inline void kernel_term(double dx, double dy, double dz, double mj, doubl
     s[3] -= mj * rinv;
 }
 
+/* A node's pseudo particle with its quadrupole (an extension beyond the
+ * paper's monopoles): the potential of mass M and traceless quadrupole Q at
+ * offset s = r_i - com is -M/|s| - s.Q.s / (2 |s|^5); its negative gradient,
+ * written with d = com - r_i = -s, is
+ *     M d / r^3 - Q d / r^5 + (5/2) (d.Q.d) d / r^7,
+ * and, as for the monopole, |d|^2 is softened to |d|^2 + eps^2 in every
+ * power of r.  Q = {xx, yy, zz, xy, xz, yz}. */
+static inline void quad_term(double dx, double dy, double dz, double M, const double *Q,
+                             double e2, double *s)
+{
+    double r2 = dx * dx + dy * dy + dz * dz + e2;
+    double rinv = 1.0 / sqrt(r2), rinv2 = rinv * rinv;
+    double rinv3 = rinv * rinv2, rinv5 = rinv3 * rinv2, rinv7 = rinv5 * rinv2;
+    double qx = Q[0] * dx + Q[3] * dy + Q[4] * dz;
+    double qy = Q[3] * dx + Q[1] * dy + Q[5] * dz;
+    double qz = Q[4] * dx + Q[5] * dy + Q[2] * dz;
+    double dqd = dx * qx + dy * qy + dz * qz;
+    double c = M * rinv3 + 2.5 * dqd * rinv7;
+    s[0] += c * dx - qx * rinv5;
+    s[1] += c * dy - qy * rinv5;
+    s[2] += c * dz - qz * rinv5;
+    s[3] -= M * rinv + 0.5 * dqd * rinv5;
+}
+
 static void direct_one(int64_t n, const double *x, const double *y, const double *z,
                        const double *m, int64_t i, double G, double e2, double *out)
 {
@@ -175,6 +199,7 @@ struct oracle_tree {
     int64_t *first, *count, *child;
     uint64_t *prefix;
     double *cx, *cy, *cz, *M, *b;
+    double *Q; /* traceless quadrupole about com: 6 per node (xx, yy, zz, xy, xz, yz) */
 };
 
 static int grow_nodes(oracle_tree *t)
@@ -185,6 +210,11 @@ static int grow_nodes(oracle_tree *t)
     GROW(first, int64_t); GROW(count, int64_t); GROW(child, int64_t);
     GROW(prefix, uint64_t);
     GROW(cx, double); GROW(cy, double); GROW(cz, double); GROW(M, double); GROW(b, double);
+    {
+        void *p_ = realloc(t->Q, (size_t)nc * 6 * sizeof(double));
+        if (!p_) return 0;
+        t->Q = (double *)p_;
+    }
 #undef GROW
     t->capn = nc;
     return 1;
@@ -310,6 +340,22 @@ static void node_moments(oracle_tree *t, int refit)
         }
         t->M[id] = M;
         t->cx[id] = com[0]; t->cy[id] = com[1]; t->cz[id] = com[2];
+        /* quadrupole (an extension beyond the paper's monopoles): the
+         * traceless tensor Q_ab = sum_k m_k (3 s_a s_b - |s|^2 delta_ab) of the
+         * members' offsets s from the centre of mass */
+        double q6[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t k = t->first[id]; k < t->first[id] + t->count[id]; k++) {
+            int64_t p = t->order[k];
+            double sx_ = t->x[p] - com[0], sy_ = t->y[p] - com[1], sz_ = t->z[p] - com[2];
+            double r2_ = sx_ * sx_ + sy_ * sy_ + sz_ * sz_, mk = t->m[p];
+            q6[0] += mk * (3 * sx_ * sx_ - r2_);
+            q6[1] += mk * (3 * sy_ * sy_ - r2_);
+            q6[2] += mk * (3 * sz_ * sz_ - r2_);
+            q6[3] += mk * 3 * sx_ * sy_;
+            q6[4] += mk * 3 * sx_ * sz_;
+            q6[5] += mk * 3 * sy_ * sz_;
+        }
+        memcpy(t->Q + 6 * id, q6, sizeof q6);
         double bb;
         if (t->nchild[id] == 0) {
             bb = 0;
@@ -405,6 +451,7 @@ void oracle_tree_free(oracle_tree *t)
     free(t->key); free(t->order);
     free(t->lev); free(t->nchild); free(t->first); free(t->count); free(t->child);
     free(t->prefix); free(t->cx); free(t->cy); free(t->cz); free(t->M); free(t->b);
+    free(t->Q);
     free(t);
 }
 
@@ -429,6 +476,11 @@ void oracle_tree_nodes(const oracle_tree *t, int32_t *level, uint64_t *prefix,
         if (M) M[i] = t->M[i];
         if (b) b[i] = t->b[i];
     }
+}
+
+void oracle_tree_quadrupoles(const oracle_tree *t, double *q6)
+{
+    memcpy(q6, t->Q, (size_t)t->nn * 6 * sizeof(double));
 }
 
 void oracle_tree_order(const oracle_tree *t, int64_t *order)
@@ -499,7 +551,7 @@ static inline int mac_accept(int geometric, double d, double bJ, double MJ, doub
 
 typedef struct {
     const oracle_tree *t;
-    int geometric;
+    int geometric, quad;
     double G, e2, dacc, theta;
 } walk_ctx;
 
@@ -520,8 +572,12 @@ static void walk_list(const walk_ctx *w, int64_t k0, int64_t cnt, const double c
             /* the node's pseudo particle enters every member's list */
             for (int64_t k = 0; k < cnt; k++) {
                 int64_t i = t->order[k0 + k];
-                kernel_term(t->cx[J] - t->x[i], t->cy[J] - t->y[i], t->cz[J] - t->z[i], t->M[J],
-                            w->e2, acc + 4 * k);
+                if (w->quad)
+                    quad_term(t->cx[J] - t->x[i], t->cy[J] - t->y[i], t->cz[J] - t->z[i], t->M[J],
+                              t->Q + 6 * J, w->e2, acc + 4 * k);
+                else
+                    kernel_term(t->cx[J] - t->x[i], t->cy[J] - t->y[i], t->cz[J] - t->z[i],
+                                t->M[J], w->e2, acc + 4 * k);
                 nint[k]++;
             }
         } else if (t->nchild[J] == 0) {
@@ -548,7 +604,9 @@ static void tree_walk_impl(const oracle_tree *t, int mode, double G, double eps,
                            int64_t nsel, const int64_t *sel,
                            double *ax, double *ay, double *az, double *phi, int64_t *ninter)
 {
-    walk_ctx w = {t, mode == ORACLE_MAC_PARTICLE_GEO || mode == ORACLE_MAC_GROUP_GEO, G,
+    const int quad = (mode & ORACLE_QUADRUPOLE) != 0;
+    mode &= ~ORACLE_QUADRUPOLE;
+    walk_ctx w = {t, mode == ORACLE_MAC_PARTICLE_GEO || mode == ORACLE_MAC_GROUP_GEO, quad, G,
                   eps * eps, delta_acc, theta};
     int group_mode = (mode == ORACLE_MAC_GROUP_ACC || mode == ORACLE_MAC_GROUP_GEO);
     int64_t ng;

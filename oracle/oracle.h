@@ -70,6 +70,9 @@ oracle_tree *oracle_tree_build(int64_t n, const double *x, const double *y, cons
  * recompute its moments without rebuilding: membership, order and groups
  * stay; b_J of internal nodes uses only the child recurrence. */
 void oracle_tree_refit(oracle_tree *t, const double *x, const double *y, const double *z);
+/* Traceless quadrupole of every node about its centre of mass, 6 doubles per
+ * node (xx, yy, zz, xy, xz, yz), Q_ab = sum m (3 s_a s_b - |s|^2 delta_ab). */
+void oracle_tree_quadrupoles(const oracle_tree *t, double *q6);
 void oracle_tree_free(oracle_tree *t);
 int64_t oracle_tree_nnodes(const oracle_tree *t);
 void oracle_tree_cube(const oracle_tree *t, float cube[4]);
@@ -95,6 +98,9 @@ int64_t oracle_tree_groups(const oracle_tree *t, int group_size, int64_t *first,
 #define ORACLE_MAC_GROUP_ACC    1 /* Eq. 2 per group:    d = |com_J - c_g| - r_g      */
 #define ORACLE_MAC_PARTICLE_GEO 2 /* opening angle b_J <= theta d, per particle       */
 #define ORACLE_MAC_GROUP_GEO    3 /* opening angle b_J <= theta d, per group          */
+/* Or-ed into a mode: accepted nodes contribute their monopole plus their
+ * traceless quadrupole (an extension beyond the paper's monopoles). */
+#define ORACLE_QUADRUPOLE      16
 
 /* Tree force for every particle.  a_old (caller order, may be NULL for the
  * geometric modes) holds |a_i^old|.  Outputs in caller order; ninter

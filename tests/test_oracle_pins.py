@@ -416,6 +416,111 @@ def test_tree_distant_cluster_is_its_monopole():
     assert np.allclose([ax[k], ay[k], az[k]], want, rtol=1e-12)
 
 
+# --------------------------------------------------------------------------- quadrupoles
+def _far_cluster_walk(cl, mc, eps, quad, target=(0.0, 0.0, 0.0), leaf_cap=1):
+    """Walk for one light target far from a cluster; returns its acceleration
+    and interaction count (2 when the cluster is accepted as one node: that
+    node plus the target's own leaf, whose zero self term is counted)."""
+    x = np.concatenate([cl[:, 0], [target[0]]])
+    y = np.concatenate([cl[:, 1], [target[1]]])
+    z = np.concatenate([cl[:, 2], [target[2]]])
+    m = np.concatenate([mc, [1e-9]])
+    t = oracle.Tree(x, y, z, m, 21, leaf_cap)
+    mode = oracle.MAC_PARTICLE_GEO | (oracle.QUADRUPOLE if quad else 0)
+    ax, ay, az, phi, nint = t.walk(mode, 1.0, eps, 0.0, 0.5, 1, None)
+    k = mc.size
+    return np.array([ax[k], ay[k], az[k]]), phi[k], nint[k], t
+
+
+def test_quadrupole_dumbbell_closed_form():
+    """Two masses m at com +- b x, target at distance D on the axis, eps = 0:
+    Q = diag(4 m b^2, -2 m b^2, -2 m b^2) and the quadrupole-corrected pull is
+    2m/D^2 + 6 m b^2/D^4 (the first two terms of m/(D-b)^2 + m/(D+b)^2, hand
+    expansion), the potential -2m/D - 2 m b^2/D^3."""
+    m, b, D = 1.5, 0.01, 60.0
+    cl = np.array([[D - b, 0.0, 0.0], [D + b, 0.0, 0.0]])
+    a, phi, nint, t = _far_cluster_walk(cl, np.array([m, m]), 0.0, True)
+    assert nint == 2
+    assert np.isclose(a[0], 2 * m / D ** 2 + 6 * m * b ** 2 / D ** 4, rtol=1e-13)
+    assert abs(a[1]) < 1e-18 and abs(a[2]) < 1e-18
+    assert np.isclose(phi, -2 * m / D - 2 * m * b ** 2 / D ** 3, rtol=1e-13)
+    nd = t.nodes()
+    Q = t.quadrupoles()
+    node = int(np.flatnonzero((nd["count"] == 2) & np.isclose(nd["M"], 2 * m))[0])
+    assert np.allclose(Q[node], [4 * m * b * b, -2 * m * b * b, -2 * m * b * b, 0, 0, 0],
+                       rtol=1e-9, atol=1e-18)
+    # its error against the exact pull is fourth order, the monopole's second
+    exact = m / (D - b) ** 2 + m / (D + b) ** 2
+    mono, _, _, _ = _far_cluster_walk(cl, np.array([m, m]), 0.0, False)
+    assert abs(a[0] - exact) / exact < 6 * (b / D) ** 4
+    assert abs(mono[0] - exact) / exact > 2.9 * (b / D) ** 2
+
+
+def test_quadrupole_far_field_convergence_order():
+    """For a generic compact cluster the monopole's relative error falls as
+    (b/D)^2 and the quadrupole's as (b/D)^3 (the dipole vanishes about the
+    centre of mass; the octupole is next): doubling D divides them by about 4
+    and 8."""
+    g = ics.rng(31)
+    k = 24
+    u = np.array([0.6, -0.48, 0.64])
+    off = g.normal(scale=0.05, size=(k, 3))
+    mc = g.uniform(0.5, 2.0, k)
+    errs = {}
+    for quad in (False, True):
+        e = []
+        for D in (40.0, 80.0, 160.0):
+            cl = off + D * u
+            a, _, nint, _ = _far_cluster_walk(cl, mc, 0.0, quad)
+            assert nint == 2
+            d = cl  # target at the origin
+            want = (mc[:, None] * d / (d * d).sum(1, keepdims=True) ** 1.5).sum(0)
+            e.append(np.linalg.norm(a - want) / np.linalg.norm(want))
+        errs[quad] = e
+    for e0, e1 in zip(errs[False], errs[False][1:]):
+        assert 3.5 < e0 / e1 < 4.5
+    for e0, e1 in zip(errs[True], errs[True][1:]):
+        assert 7.0 < e0 / e1 < 9.0
+    assert errs[True][0] < 0.1 * errs[False][0]
+
+
+def test_quadrupole_vanishes_for_cubic_symmetry():
+    """Equal masses on the vertices of a cube have zero quadrupole: the
+    quadrupole walk equals the monopole walk."""
+    v = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)], float) * 0.02
+    cl = v + np.array([50.0, 20.0, -30.0])
+    mc = np.full(8, 0.7)
+    aq, pq, nq, t = _far_cluster_walk(cl, mc, 0.1, True, leaf_cap=4)
+    am, pm, nm, _ = _far_cluster_walk(cl, mc, 0.1, False, leaf_cap=4)
+    assert nq == nm == 2
+    nd = t.nodes()
+    node = int(np.flatnonzero(nd["count"] == 8)[-1])
+    # zero up to the rounding of the offsets (|s| = 0.035 at coordinates ~60)
+    assert np.max(np.abs(t.quadrupoles()[node])) < 1e-11 * (mc * (v * v).sum(1)).sum()
+    assert np.allclose(aq, am, rtol=1e-12) and np.isclose(pq, pm, rtol=1e-12)
+
+
+def test_quadrupoles_are_traceless_and_lower_the_error(gal_tree):
+    """Every node's quadrupole is traceless; with the same MAC the quadrupole
+    walk's error percentiles are below the monopole walk's."""
+    p, t = gal_tree
+    Q = t.quadrupoles()
+    nd = t.nodes()
+    scale = nd["M"] * nd["b"] ** 2 + 1e-300
+    assert np.all(np.abs(Q[:, 0] + Q[:, 1] + Q[:, 2]) <= 1e-12 * scale)
+    x, y, z, m = (p[k].astype(float) for k in ("x", "y", "z", "m"))
+    ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 1 / 64, want_phi=False)
+    amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
+    e = {}
+    for quad in (0, oracle.QUADRUPOLE):
+        bx, by, bz, _, _ = t.walk(oracle.MAC_GROUP_ACC | quad, 1.0, 1 / 64, 2.0 ** -9, 0.5, 64,
+                                  amag, want_phi=False)
+        e[quad] = oracle.rel_err(bx, by, bz, ax, ay, az)
+    for q in (50, 99):
+        assert (oracle.percentile_nearest_rank(e[oracle.QUADRUPOLE], q) <
+                0.7 * oracle.percentile_nearest_rank(e[0], q))
+
+
 def test_tree_error_decreases_with_dacc():
     n = 1 << 13
     p = ics.plummer(n, 1)
