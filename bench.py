@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--per-system-steps", type=int, default=2,
                     help="batched: steps timed for the one-call-per-system comparison")
     ap.add_argument("--n", type=int, default=1 << 23)
+    ap.add_argument("--quadrupole", type=int, default=0, choices=(0, 1),
+                    help="galaxy: nodes carry quadrupoles (an extension beyond the paper's "
+                         "monopoles); precision: add a quadrupole sweep")
     ap.add_argument("--rebuild-interval", type=int, default=1,
                     help="galaxy: tree rebuilt every k-th step, refitted between (0: automatic, "
                          "by timing); the headline configuration rebuilds every step")
@@ -226,7 +229,8 @@ def run_ours(args, rank, world, local_rank):
     M = D(p["m"])
     A = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
     stream = torch.cuda.current_stream(dev)
-    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, rebuild_interval=args.rebuild_interval)
+    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, rebuild_interval=args.rebuild_interval,
+                                  quadrupole=args.quadrupole)
     ctx = nb.nbody_create(cfg, stream)
     try:
         # accelerations at t = 0 (bootstrap MAC), then warm-up steps
@@ -329,6 +333,8 @@ def run_ours(args, rank, world, local_rank):
         "walk_phase_ms_per_step": st.ms_walk / steps,
         "nodes": st.n_nodes, "groups": st.n_groups, "max_stack": st.max_stack,
         "rebuilds": int(st.rebuilds),
+        "quadrupole": args.quadrupole,
+        "quad_interactions_per_step": st.quad_interactions / steps,
         "roofline": {"bound": "alu", "achieved": walk_tflops, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": walk_tflops / peak_tflops, "traffic": traffic,
                      "traffic_note": traffic_note, "kernel": "walk_kernel",
@@ -713,10 +719,14 @@ def run_precision(args, rank, world, local_rank):
         nb.nbody_walk(ctx, amag, *A)
         amag = torch.sqrt(A[0] ** 2 + A[1] ** 2 + A[2] ** 2).contiguous()
         tgd = torch.from_numpy(tg).to(dev)
+        variants = [(0, 0), (1, 0)] + ([(0, 1)] if args.quadrupole else [])
         for k in range(1, args.sweep_max + 1):
-            for comp in (0, 1):
+            for comp, quad in variants:
                 cfg = nb.nbody_get_config(ctx)
-                cfg.delta_acc, cfg.compensated = 2.0 ** -k, comp
+                cfg.delta_acc, cfg.compensated, cfg.quadrupole = 2.0 ** -k, comp, quad
+                if quad != nb.nbody_get_config(ctx).quadrupole:
+                    nb.nbody_set_config(ctx, cfg)
+                    nb.nbody_build(ctx, *[D(p[k2]) for k2 in ("x", "y", "z")], M)
                 while True:
                     nb.nbody_set_config(ctx, cfg)
                     try:
@@ -727,8 +737,9 @@ def run_precision(args, rank, world, local_rank):
                             raise
                         cfg.stack_depth *= 2
                 ms = st.ms_walk_kernel / max(st.walk_launches, 1)
-                rows.append({"log2_delta_acc": -k, "compensated": comp, "walk_ms": ms,
-                             "interactions": int(st.interactions),
+                rows.append({"log2_delta_acc": -k, "compensated": comp, "quadrupole": quad,
+                             "walk_ms": ms, "interactions": int(st.interactions),
+                             "quad_interactions": int(st.quad_interactions),
                              "ginter_s": st.interactions / ms / 1e6,
                              "stack_depth": int(cfg.stack_depth), "max_stack": int(st.max_stack),
                              "a": [a[tgd].cpu().numpy().astype(np.float64) for a in A]})
@@ -789,7 +800,8 @@ def run_precision(args, rank, world, local_rank):
         r.update(p50=oracle.percentile_nearest_rank(e, 50), p99=oracle.percentile_nearest_rank(e, 99),
                  max=float(e.max()))
         table.append(r)
-    head = next(r for r in table if r["log2_delta_acc"] == -9 and r["compensated"] == 0)
+    head = next(r for r in table if r["log2_delta_acc"] == -9 and r["compensated"] == 0
+                and r["quadrupole"] == 0)
     ni = tg.size * n
     return {
         "metric": METRIC, "value": head["ginter_s"], "unit": UNIT, "n_gpus": 1,

@@ -97,6 +97,12 @@ typedef struct {
                             Sect. 1 and 4.1), at most every 32 steps; this
                             synchronises the stream after every step.  The
                             first step of every call rebuilds.  0..1024.     */
+    int32_t quadrupole;  /* 1: nodes also carry their traceless quadrupole
+                            Q_ab = sum m (3 s_a s_b - |s|^2 delta_ab) about the
+                            centre of mass, and an accepted node contributes
+                            M d/r^3 - Q d/r^5 + 5/2 (d.Q.d) d/r^7 (r^2 = |d|^2 +
+                            eps^2; an extension beyond the paper's monopoles,
+                            same MAC); 0: monopoles (default)                */
 } nbody_config;
 
 typedef struct {
@@ -114,6 +120,8 @@ typedef struct {
     int32_t walk_launches; /* walk kernel launches behind ms_walk_kernel       */
     int32_t rebuilds;      /* steps of the last nbody_step call that rebuilt the
                               tree (the others refitted it)                    */
+    int64_t quad_interactions; /* of `interactions`, those with quadrupole
+                              nodes (quadrupole = 1)                          */
 } nbody_stats;
 
 typedef struct nbody_ctx nbody_ctx;
@@ -342,7 +350,9 @@ typedef enum {
     NBODY_EXPORT_GROUP_FIRST = 8,  /* int32 [groups]: first sorted particle         */
     NBODY_EXPORT_GROUP_COUNT = 9,  /* int32 [groups]                                */
     NBODY_EXPORT_GROUP_SPHERE = 10,/* float4 [groups]: centre, radius               */
-    NBODY_EXPORT_SYS_BOX = 11      /* float4 [nsys]: x0, y0, z0, L of each cube     */
+    NBODY_EXPORT_SYS_BOX = 11,     /* float4 [nsys]: x0, y0, z0, L of each cube     */
+    NBODY_EXPORT_NODE_Q = 12       /* float [nodes][8]: quadrupole xx, yy, zz, xy,
+                                      xz, yz, 0, 0 (quadrupole = 1 only)         */
 } nbody_export_what;
 
 /* Copy internal array `what` of the last build into dst (host or device),

@@ -61,7 +61,7 @@ struct nbody_ctx {
     DevBuf rs_temp, tree_temp, grp_temp, diag_temp, diag_out;
     // nodes
     DevBuf node_start, node_level, node_parent, node_link, node_count, node_nchild;
-    DevBuf nodeA, nodeB, mass2;
+    DevBuf nodeA, nodeB, mass2, nodeQ;
     // groups
     DevBuf gflag, grp_first, grp_count, grp_sphere, grp_sys, grp_alpha, grp_cost, grp_order;
     // systems
@@ -102,7 +102,7 @@ struct nbody_ctx {
         DevBuf *all[] = {&keys, &keys_alt, &vals, &vals_alt, &pos4, &delta, &leaflev, &rs_temp,
                          &tree_temp, &grp_temp, &diag_temp, &diag_out, &node_start, &node_level,
                          &node_parent, &node_link, &node_count, &node_nchild,
-                         &nodeA, &nodeB, &mass2, &gflag, &grp_first, &grp_count, &grp_sphere,
+                         &nodeA, &nodeB, &mass2, &nodeQ, &gflag, &grp_first, &grp_count, &grp_sphere,
                          &grp_sys, &grp_alpha, &grp_cost, &grp_order, &sys_off, &sys_box,
                          &sys_boxord, &sys_eps2, &sys_root, &acc_s, &aold_s, &mlp_w, &mlp_m1,
                          &mlp_m2, &mlp_wb, &mlp_norm, &mlp_gpart, &mlp_lpart, &mlp_loss, &feat,
@@ -191,9 +191,12 @@ bool config_ok(const nbody_config *c, std::string &why) {
     if (c->schedule < 0 || c->schedule > 2) return bad("schedule must be 0, 1 or 2");
     if (c->rebuild_interval < 0 || c->rebuild_interval > 1024)
         return bad("rebuild_interval must be in 0..1024");
-    size_t smem = (size_t)c->warps_per_block * nb::walk_smem_per_warp(c->list_depth, c->stack_depth);
+    if (c->quadrupole != 0 && c->quadrupole != 1) return bad("quadrupole must be 0 or 1");
+    size_t smem = (size_t)c->warps_per_block *
+                  nb::walk_smem_per_warp(c->list_depth, c->stack_depth, c->quadrupole != 0);
     if (smem > 227 * 1024)
-        return bad("warps_per_block * (16 list_depth + 4 stack_depth + 128) exceeds 227 KB");
+        return bad("warps_per_block * (16 list_depth + 4 stack_depth + 128, + 12 list_depth with "
+                   "quadrupoles) exceeds 227 KB");
     return true;
 }
 
@@ -266,7 +269,7 @@ cudaError_t ensure_capacity(nbody_ctx *c, int64_t n, int nsys, int levels) {
         NB_E(ensure(c->node_parent, cn * 4)); NB_E(ensure(c->node_link, cn * 4));
         NB_E(ensure(c->node_count, cn * 4)); NB_E(ensure(c->node_nchild, cn * 4));
         NB_E(ensure(c->nodeA, cn * 16)); NB_E(ensure(c->nodeB, cn * 16));
-        NB_E(ensure(c->mass2, cn * 8));
+        NB_E(ensure(c->mass2, cn * 8)); NB_E(ensure(c->nodeQ, cn * 32));
         c->cap_nodes = cn;
     }
     if (nsys > c->cap_sys) {
@@ -327,7 +330,7 @@ nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
                P<int8_t>(c->node_level), P<int32_t>(c->node_parent), P<int32_t>(c->node_link),
                P<int32_t>(c->node_count), P<int32_t>(c->node_nchild),
                P<float4>(c->nodeA), P<float4>(c->nodeB), P<float2>(c->mass2),
-               P<int32_t>(c->sys_root), c->nsm);
+               c->cfg.quadrupole ? P<float4>(c->nodeQ) : nullptr, P<int32_t>(c->sys_root), c->nsm);
     build_groups(s, L, c->cfg.group_size, P<float4>(c->pos4), P<int64_t>(c->sys_off),
                  P<int32_t>(c->node_start), P<int32_t>(c->node_parent), P<int32_t>(c->node_count),
                  P<int32_t>(c->node_nchild), P<int32_t>(c->node_link), c->ds,
@@ -350,7 +353,8 @@ nbody_status refit_tree_groups(nbody_ctx *c, const Layout &L) {
                  c->cfg.leaf_cap, c->cfg.G, c->ds, P<int32_t>(c->node_start),
                  P<int8_t>(c->node_level), P<int32_t>(c->node_link), P<int32_t>(c->node_count),
                  P<int32_t>(c->node_nchild), P<float4>(c->nodeA), P<float4>(c->nodeB),
-                 P<float2>(c->mass2), c->nsm, true);
+                 P<float2>(c->mass2), c->cfg.quadrupole ? P<float4>(c->nodeQ) : nullptr, c->nsm,
+                 true);
     refit_groups(s, L, c->cfg.group_size, P<float4>(c->pos4), P<int64_t>(c->sys_off), c->ds,
                  P<int32_t>(c->grp_first), P<int32_t>(c->grp_count), P<float4>(c->grp_sphere),
                  P<int32_t>(c->grp_sys), c->nsm);
@@ -462,6 +466,7 @@ WalkShape walk_shape(nbody_ctx *c, bool geometric, bool phi, bool safe) {
     sh.potential = phi;
     sh.compensated = c->cfg.compensated != 0;
     sh.safe = safe;
+    sh.quad = c->cfg.quadrupole != 0;
     sh.warps_per_block = c->cfg.warps_per_block;
     sh.warps_launched = &c->walk_warps;
     return sh;
@@ -472,6 +477,7 @@ WalkArgs walk_args(nbody_ctx *c) {
     a.pos4 = P<float4>(c->pos4);
     a.nodeA = P<float4>(c->nodeA);
     a.nodeB = P<float4>(c->nodeB);
+    a.nodeQ = P<float4>(c->nodeQ);
     a.grp_first = P<int32_t>(c->grp_first);
     a.grp_count = P<int32_t>(c->grp_count);
     a.grp_sphere = P<float4>(c->grp_sphere);
@@ -497,7 +503,7 @@ nbody_status reset_walk_counters(nbody_ctx *c, bool accumulators) {
     if (accumulators) {
         NB_CUDA(c, cudaMemsetAsync(base + offsetof(DevState, max_stack), 0, sizeof(int32_t), c->stream));
         NB_CUDA(c, cudaMemsetAsync(base + offsetof(DevState, list_entries), 0,
-                                   2 * sizeof(unsigned long long), c->stream));
+                                   3 * sizeof(unsigned long long), c->stream));
     }
     return NBODY_OK;
 }
@@ -672,6 +678,7 @@ void nbody_config_default(nbody_config *c) {
     c->schedule = NBODY_SCHED_MORTON;
     c->use_graph = 0;
     c->rebuild_interval = 1;
+    c->quadrupole = 0;
 }
 
 nbody_status nbody_create(nbody_ctx **out, const nbody_config *cfg, void *cuda_stream) {
@@ -849,6 +856,7 @@ nbody_status nbody_walk(nbody_ctx *ctx, const float *a_old, float *ax, float *ay
     ctx->last.n_groups = ctx->h_ds->ngroups;
     ctx->last.interactions = (int64_t)ctx->h_ds->interactions;
     ctx->last.list_entries = (int64_t)ctx->h_ds->list_entries;
+    ctx->last.quad_interactions = (int64_t)ctx->h_ds->quad_entries;
     ctx->last.max_stack = ctx->h_ds->max_stack;
     ctx->last.ms_walk = ms;
     ctx->last.ms_walk_kernel = collect_walk_ms(ctx, &ctx->last.walk_launches);
@@ -1136,6 +1144,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     ctx->last.levels = L.levels;
     ctx->last.interactions = (int64_t)ctx->h_ds->interactions;
     ctx->last.list_entries = (int64_t)ctx->h_ds->list_entries;
+    ctx->last.quad_interactions = (int64_t)ctx->h_ds->quad_entries;
     ctx->last.max_stack = ctx->h_ds->max_stack;
     ctx->last.ms_build = ms_build;
     ctx->last.ms_walk = ms_walk;
@@ -1340,6 +1349,9 @@ nbody_status nbody_export(nbody_ctx *ctx, int32_t what, void *dst, int64_t cap, 
         case NBODY_EXPORT_GROUP_FIRST: src = ctx->grp_first.p; len = ng; break;
         case NBODY_EXPORT_GROUP_COUNT: src = ctx->grp_count.p; len = ng; break;
         case NBODY_EXPORT_GROUP_SPHERE: src = ctx->grp_sphere.p; len = ng; esz = 16; break;
+        case NBODY_EXPORT_NODE_Q:
+            if (!ctx->cfg.quadrupole) return fail(ctx, NBODY_EINVAL, "quadrupoles are off");
+            src = ctx->nodeQ.p; len = nn; esz = 32; break;
         case NBODY_EXPORT_SYS_BOX: {
             // SysBox is 32 bytes; export the first 16 (x0, y0, z0, L) of each
             *count = ctx->L.nsys;

@@ -47,6 +47,7 @@ struct DevState {
     int32_t pad0;
     unsigned long long list_entries;
     unsigned long long interactions;
+    unsigned long long quad_entries;  // list entries that were quadrupole nodes
     int32_t lvl_off[kMaxNL + 1];
 };
 
@@ -171,14 +172,16 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                 int64_t cap_nodes, int8_t *delta, int8_t *leaflev, void *temp, DevState *ds,
                 int32_t *node_start, int8_t *node_level, int32_t *node_parent,
                 int32_t *node_link, int32_t *node_count, int32_t *node_nchild,
-                float4 *nodeA, float4 *nodeB, float2 *mass2, int32_t *sys_root, int nsm);
+                float4 *nodeA, float4 *nodeB, float2 *mass2, float4 *nodeQ, int32_t *sys_root,
+                int nsm);
 // Node moments of the current tree from pos4 (refit: positions moved since
 // the build; b_J of internal nodes from the child recurrence only).
+// nodeQ (nullable): also the traceless quadrupoles, 2 float4 per node.
 void tree_moments(cudaStream_t s, const Layout &L, const uint64_t *keys, const float4 *pos4,
                   const SysBox *d_box, int leaf_cap, float G, DevState *ds,
                   const int32_t *node_start, const int8_t *node_level, const int32_t *node_link,
                   int32_t *node_count, const int32_t *node_nchild, float4 *nodeA, float4 *nodeB,
-                  float2 *mass2, int nsm, bool refit);
+                  float2 *mass2, float4 *nodeQ, int nsm, bool refit);
 void refit_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
                   const int64_t *d_off, DevState *ds, const int32_t *grp_first,
                   int32_t *grp_count, float4 *grp_sphere, int32_t *grp_sys, int nsm);
@@ -196,14 +199,22 @@ void launch_group_alpha(cudaStream_t s, int64_t n, const DevState *ds, const int
 // stack (4 B per entry) and kWalkScratch words for compacting opened leaves,
 // rounded up to 16 B so that every warp's list stays float4-aligned.
 constexpr int kWalkScratch = 32;
-__host__ __device__ inline size_t walk_smem_per_warp(int list_depth, int stack_depth) {
-    const size_t b = (size_t)list_depth * 16 + (size_t)stack_depth * 4 + (size_t)kWalkScratch * 4;
+// With quadrupoles, accepted nodes go to a second list of walk_quad_depth
+// entries of 40 B (centre of mass and mass, then the six quadrupole terms).
+__host__ __device__ inline int walk_quad_depth(int list_depth) {
+    return list_depth / 4 > 32 ? list_depth / 4 : 32;
+}
+__host__ __device__ inline size_t walk_smem_per_warp(int list_depth, int stack_depth,
+                                                     bool quad = false) {
+    const size_t b = (size_t)list_depth * 16 + (quad ? (size_t)walk_quad_depth(list_depth) * 40 : 0) +
+                     (size_t)stack_depth * 4 + (size_t)kWalkScratch * 4;
     return (b + 15) & ~(size_t)15;
 }
 struct WalkArgs {
     const float4 *pos4;
     const float4 *nodeA;
     const float4 *nodeB;
+    const float4 *nodeQ;       // 2 per node: (xx, yy, zz, xy), (xz, yz, 0, 0); quadrupole walk only
     const int32_t *grp_first;
     const int32_t *grp_count;
     const float4 *grp_sphere;
@@ -230,6 +241,7 @@ struct WalkShape {
     bool potential;
     bool compensated;
     bool safe;                  // some eps == 0: guard the self term
+    bool quad;                  // accepted nodes add their quadrupole
     int warps_per_block;
     int *warps_launched;        // host, nullable: receives the resident walk warps
 };

@@ -296,6 +296,26 @@ __device__ __forceinline__ void write_node(int id, float cx, float cy, float cz,
     mass2[id] = M;
 }
 
+// Quadrupole (an extension beyond the paper's monopoles): the traceless
+// Q_ab = sum m (3 s_a s_b - |s|^2 delta_ab) over offsets s from the centre of
+// mass; q = {xx, yy, zz, xy, xz, yz}.  A child of mass m at offset s with its
+// own quadrupole Qc contributes Qc plus the point-mass term (parallel axes).
+__device__ __forceinline__ void quad_add(float q[6], float m, float dx, float dy, float dz,
+                                         float r2) {
+    const float m3 = 3.0f * m;
+    q[0] = fmaf(m3 * dx, dx, fmaf(-m, r2, q[0]));
+    q[1] = fmaf(m3 * dy, dy, fmaf(-m, r2, q[1]));
+    q[2] = fmaf(m3 * dz, dz, fmaf(-m, r2, q[2]));
+    q[3] = fmaf(m3 * dx, dy, q[3]);
+    q[4] = fmaf(m3 * dx, dz, q[4]);
+    q[5] = fmaf(m3 * dy, dz, q[5]);
+}
+
+__device__ __forceinline__ void write_quad(int id, const float q[6], float4 *nodeQ) {
+    nodeQ[2 * id] = make_float4(q[0], q[1], q[2], q[3]);
+    nodeQ[2 * id + 1] = make_float4(q[4], q[5], 0.0f, 0.0f);
+}
+
 // Monopoles (centre of mass, mass) and node sizes b_J, bottom-up.  FP32 sums
 // relative to a reference point inside the node (first particle for leaves,
 // the cell centre for internal nodes) keep the error a few ulps of the node
@@ -312,7 +332,8 @@ __global__ void __launch_bounds__(256) leaf_moments_kernel(
     const SysBox *__restrict__ box, float G, DevState *ds,
     const int32_t *__restrict__ node_start, const int8_t *__restrict__ node_level,
     const int32_t *__restrict__ node_link, const int32_t *__restrict__ node_count,
-    const int32_t *__restrict__ node_nchild, float4 *nodeA, float4 *nodeB, float2 *mass2) {
+    const int32_t *__restrict__ node_nchild, float4 *nodeA, float4 *nodeB, float2 *mass2,
+    float4 *nodeQ) {
     constexpr int TEAMS = 32 / T;
     const int nn = ds->nnodes;
     const int lane = (int)lane_id(), team = lane / T, tl = lane % T;
@@ -376,19 +397,30 @@ __global__ void __launch_bounds__(256) leaf_moments_kernel(
                 for (int a = 0; a < 3; a++) c[a] = cell.c[a];
             }
             float b2 = 0.0f;
+            float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             for (int ch = 0; ch < nch; ch++) {
                 const int k = ch * T + tl;
                 if (k < cnt) {
                     const float4 p = pos4[first + k];
                     const float dx = p.x - c[0], dy = p.y - c[1], dz = p.z - c[2];
-                    b2 = fmaxf(b2, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    b2 = fmaxf(b2, r2);
+                    if (nodeQ) quad_add(q, p.w, dx, dy, dz, r2);
                 }
             }
 #pragma unroll
             for (int o = T / 2; o > 0; o >>= 1) b2 = fmaxf(b2, __shfl_xor_sync(NB_FULL, b2, o));
-            if (tl == 0 && cnt > 0)
+            if (nodeQ) {
+#pragma unroll
+                for (int o = T / 2; o > 0; o >>= 1)
+#pragma unroll
+                    for (int j = 0; j < 6; j++) q[j] += __shfl_xor_sync(NB_FULL, q[j], o);
+            }
+            if (tl == 0 && cnt > 0) {
                 write_node(id, c[0], c[1], c[2], M, __fsqrt_ru(b2) * kUp, G, first,
                            (cnt << 1) | 1, nodeA, nodeB, mass2);
+                if (nodeQ) write_quad(id, q, nodeQ);
+            }
         }
     }
     if (bad) atomicOr(&ds_status(ds), kStatusBadTree);
@@ -405,7 +437,8 @@ __global__ void __launch_bounds__(256) internal_moments_kernel(
     Layout L, int level, int refit, const uint64_t *__restrict__ keys, const SysBox *__restrict__ box,
     float G, DevState *ds, const int32_t *__restrict__ node_start,
     const int32_t *__restrict__ node_link, int32_t *node_count,
-    const int32_t *__restrict__ node_nchild, float4 *nodeA, float4 *nodeB, float2 *mass2) {
+    const int32_t *__restrict__ node_nchild, float4 *nodeA, float4 *nodeB, float2 *mass2,
+    float4 *nodeQ) {
     const int lo = ds->lvl_off[level], hi = ds->lvl_off[level + 1];
     const int nn = ds->nnodes;
     const int lane = (int)lane_id(), team = lane >> 3, tl = lane & 7;
@@ -464,12 +497,25 @@ __global__ void __launch_bounds__(256) internal_moments_kernel(
                 cp[0] = fmaf(px, inv, cp[0]); cp[1] = fmaf(py, inv, cp[1]); cp[2] = fmaf(pz, inv, cp[2]);
             }
             float rec = 0.0f;
+            float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (tl < nc) {
                 const float dx = A.x - cp[0], dy = A.y - cp[1], dz = A.z - cp[2];
-                rec = __fadd_ru(__fsqrt_ru(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), bc);
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                rec = __fadd_ru(__fsqrt_ru(r2), bc);
+                if (nodeQ) {
+                    const float4 q0 = nodeQ[2 * (c0 + tl)], q1 = nodeQ[2 * (c0 + tl) + 1];
+                    q[0] = q0.x; q[1] = q0.y; q[2] = q0.z; q[3] = q0.w; q[4] = q1.x; q[5] = q1.y;
+                    quad_add(q, A.w, dx, dy, dz, r2);
+                }
             }
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) rec = fmaxf(rec, __shfl_xor_sync(NB_FULL, rec, o));
+            if (nodeQ) {
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+                    for (int j = 0; j < 6; j++) q[j] += __shfl_xor_sync(NB_FULL, q[j], o);
+            }
             if (nc > 0 && tl == 0) {
                 float c2 = 0.0f;
 #pragma unroll
@@ -480,6 +526,7 @@ __global__ void __launch_bounds__(256) internal_moments_kernel(
                 const float bp = (refit ? rec : fminf(rec, __fsqrt_ru(c2))) * kUp;
                 node_count[par] = count;
                 write_node(par, cp[0], cp[1], cp[2], Mp, bp, G, c0, nc << 1, nodeA, nodeB, mass2);
+                if (nodeQ) write_quad(par, q, nodeQ);
             }
         }
     }
@@ -496,7 +543,8 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                 int64_t cap_nodes, int8_t *delta, int8_t *leaflev, void *temp, DevState *ds,
                 int32_t *node_start, int8_t *node_level, int32_t *node_parent,
                 int32_t *node_link, int32_t *node_count, int32_t *node_nchild,
-                float4 *nodeA, float4 *nodeB, float2 *mass2, int32_t *sys_root, int nsm) {
+                float4 *nodeA, float4 *nodeB, float2 *mass2, float4 *nodeQ, int32_t *sys_root,
+                int nsm) {
     const int nblk = (int)((L.n + TB - 1) / TB);
     uint32_t *blockcnt = (uint32_t *)temp;
     if (leaf_cap <= 8)
@@ -513,7 +561,7 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
     sys_root_init_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(L.nsys, sys_root);
     sys_root_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(ds, node_start, d_off, L.nsys, sys_root);
     tree_moments(s, L, keys, pos4, d_box, leaf_cap, G, ds, node_start, node_level, node_link,
-                 node_count, node_nchild, nodeA, nodeB, mass2, nsm, false);
+                 node_count, node_nchild, nodeA, nodeB, mass2, nodeQ, nsm, false);
 }
 
 // Moments of every node of the current tree from pos4: leaves in one launch
@@ -523,23 +571,23 @@ void tree_moments(cudaStream_t s, const Layout &L, const uint64_t *keys, const f
                   const SysBox *d_box, int leaf_cap, float G, DevState *ds,
                   const int32_t *node_start, const int8_t *node_level, const int32_t *node_link,
                   int32_t *node_count, const int32_t *node_nchild, float4 *nodeA, float4 *nodeB,
-                  float2 *mass2, int nsm, bool refit) {
+                  float2 *mass2, float4 *nodeQ, int nsm, bool refit) {
     int64_t mb = (L.n / 4 + 255) / 256;
     if (mb > (int64_t)nsm * 8) mb = (int64_t)nsm * 8;
     if (mb < 1) mb = 1;
     if (leaf_cap <= 4)
         leaf_moments_kernel<4><<<(int)mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start,
                                                        node_level, node_link, node_count,
-                                                       node_nchild, nodeA, nodeB, mass2);
+                                                       node_nchild, nodeA, nodeB, mass2, nodeQ);
     else
         leaf_moments_kernel<8><<<(int)mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start,
                                                        node_level, node_link, node_count,
-                                                       node_nchild, nodeA, nodeB, mass2);
+                                                       node_nchild, nodeA, nodeB, mass2, nodeQ);
     const int ib = nsm * 4;
     for (int l = L.levels - 1; l >= 0; l--)
         internal_moments_kernel<<<ib, 256, 0, s>>>(L, l, refit ? 1 : 0, keys, d_box, G, ds,
                                                    node_start, node_link, node_count, node_nchild,
-                                                   nodeA, nodeB, mass2);
+                                                   nodeA, nodeB, mass2, nodeQ);
 }
 
 // ---------------------------------------------------------------- groups

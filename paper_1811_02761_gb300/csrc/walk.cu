@@ -5,19 +5,29 @@
 
 namespace nb {
 
-template <int IPL>
+template <int IPL, bool QUAD>
 cudaError_t launch_walk_ipl(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm);
-extern template cudaError_t launch_walk_ipl<1>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
-extern template cudaError_t launch_walk_ipl<2>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
-extern template cudaError_t launch_walk_ipl<3>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
-extern template cudaError_t launch_walk_ipl<4>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
+#define NB_WALK_EXTERN(I, Q) \
+    extern template cudaError_t launch_walk_ipl<I, Q>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
+NB_WALK_EXTERN(1, false) NB_WALK_EXTERN(2, false) NB_WALK_EXTERN(3, false) NB_WALK_EXTERN(4, false)
+NB_WALK_EXTERN(1, true) NB_WALK_EXTERN(2, true) NB_WALK_EXTERN(3, true) NB_WALK_EXTERN(4, true)
+#undef NB_WALK_EXTERN
 
 cudaError_t launch_walk(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm) {
+    if (sh.quad) {
+        switch (sh.ipl) {
+            case 1: return launch_walk_ipl<1, true>(s, a, sh, nsm);
+            case 2: return launch_walk_ipl<2, true>(s, a, sh, nsm);
+            case 3: return launch_walk_ipl<3, true>(s, a, sh, nsm);
+            case 4: return launch_walk_ipl<4, true>(s, a, sh, nsm);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (sh.ipl) {
-        case 1: return launch_walk_ipl<1>(s, a, sh, nsm);
-        case 2: return launch_walk_ipl<2>(s, a, sh, nsm);
-        case 3: return launch_walk_ipl<3>(s, a, sh, nsm);
-        case 4: return launch_walk_ipl<4>(s, a, sh, nsm);
+        case 1: return launch_walk_ipl<1, false>(s, a, sh, nsm);
+        case 2: return launch_walk_ipl<2, false>(s, a, sh, nsm);
+        case 3: return launch_walk_ipl<3, false>(s, a, sh, nsm);
+        case 4: return launch_walk_ipl<4, false>(s, a, sh, nsm);
         default: return cudaErrorInvalidValue;
     }
 }

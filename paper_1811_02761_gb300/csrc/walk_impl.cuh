@@ -164,6 +164,124 @@ __device__ __forceinline__ void flush_group(int q, int k0, int ks, float4 *LA, f
     }
 }
 
+// Quadrupole nodes (an extension beyond the paper's monopoles).  The node
+// list holds entries in pairs, five float4 per pair, each component of the
+// two entries side by side: (x, y), (z, M), (Qxx, Qyy), (Qzz, Qxy),
+// (Qxz, Qyz) -- the layout of the packed FP32 instructions, as for the
+// particle list.
+__device__ __forceinline__ void quad_put(float4 *LQ, int e, float4 A, float4 Q0, float4 Q1) {
+    float *p = reinterpret_cast<float *>(LQ + 5 * (e >> 1));
+    const int h = e & 1;
+    p[0 + h] = A.x;
+    p[2 + h] = A.y;
+    p[4 + h] = A.z;
+    p[6 + h] = A.w;
+    p[8 + h] = Q0.x;
+    p[10 + h] = Q0.y;
+    p[12 + h] = Q0.z;
+    p[14 + h] = Q0.w;
+    p[16 + h] = Q1.x;
+    p[18 + h] = Q1.y;
+}
+
+// For each node entry (com, M, Q) and each of the lane's first NQ i-slots,
+// with d = com - r_i softened as r^2 = |d|^2 + eps^2,
+//     a += M d / r^3 - Q d / r^5 + (5/2) (d.Q.d) d / r^7,
+//     phi -= M / r + (d.Q.d) / (2 r^5),
+// the negative gradient of the node's monopole + quadrupole potential,
+// evaluated for two entries per packed instruction.  The lane takes the
+// entry pairs k0, k0 + ks, ... like the particle flush.
+template <int NQ, int IPL, bool PHI, bool COMP, bool SAFE>
+__device__ __forceinline__ void flush_quad_list(float4 *LQ, int nq, float eps2, int k0, int ks,
+                                                ISlots<IPL> &I) {
+    if (nq & 1) {  // pad to a whole pair with a massless, distant entry
+        if (lane_id() == 0)
+            quad_put(LQ, nq, make_float4(1e18f, 1e18f, 1e18f, 0.0f), make_float4(0.f, 0.f, 0.f, 0.f),
+                     make_float4(0.f, 0.f, 0.f, 0.f));
+        __syncwarp();
+    }
+    const int np = (nq + 1) >> 1;
+    const float2 e2 = make_float2(eps2, eps2);
+    const float2 c25 = make_float2(2.5f, 2.5f), neg1 = make_float2(-1.0f, -1.0f);
+    const float2 half = make_float2(0.5f, 0.5f);
+    float2 sx[NQ], sy[NQ], sz[NQ], sp[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        if constexpr (COMP) {
+            sx[q] = sy[q] = sz[q] = sp[q] = make_float2(0.0f, 0.0f);
+        } else {
+            sx[q] = I.run[q][0];
+            sy[q] = I.run[q][1];
+            sz[q] = I.run[q][2];
+            sp[q] = I.run[q][3];
+        }
+    }
+    for (int k = k0; k < np; k += ks) {
+        const float4 F0 = LQ[5 * k], F1 = LQ[5 * k + 1], F2 = LQ[5 * k + 2], F3 = LQ[5 * k + 3],
+                     F4 = LQ[5 * k + 4];
+        const float2 px = make_float2(F0.x, F0.y), py = make_float2(F0.z, F0.w);
+        const float2 pz = make_float2(F1.x, F1.y), pm = make_float2(F1.z, F1.w);
+        const float2 qxx = make_float2(F2.x, F2.y), qyy = make_float2(F2.z, F2.w);
+        const float2 qzz = make_float2(F3.x, F3.y), qxy = make_float2(F3.z, F3.w);
+        const float2 qxz = make_float2(F4.x, F4.y), qyz = make_float2(F4.z, F4.w);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const float2 dx = __fadd2_rn(px, I.nx[q]);
+            const float2 dy = __fadd2_rn(py, I.ny[q]);
+            const float2 dz = __fadd2_rn(pz, I.nz[q]);
+            float2 r2 = __ffma2_rn(dx, dx, e2);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            float2 ri = make_float2(rsqrt_fast(r2.x), rsqrt_fast(r2.y));
+            if constexpr (SAFE) {
+                ri.x = r2.x >= 1.17549435e-38f ? ri.x : 0.0f;
+                ri.y = r2.y >= 1.17549435e-38f ? ri.y : 0.0f;
+            }
+            const float2 ri2 = __fmul2_rn(ri, ri);
+            const float2 ri3 = __fmul2_rn(ri, ri2);
+            const float2 ri5 = __fmul2_rn(ri3, ri2);
+            const float2 gx = __ffma2_rn(qxx, dx, __ffma2_rn(qxy, dy, __fmul2_rn(qxz, dz)));
+            const float2 gy = __ffma2_rn(qxy, dx, __ffma2_rn(qyy, dy, __fmul2_rn(qyz, dz)));
+            const float2 gz = __ffma2_rn(qxz, dx, __ffma2_rn(qyz, dy, __fmul2_rn(qzz, dz)));
+            const float2 dqd = __ffma2_rn(dx, gx, __ffma2_rn(dy, gy, __fmul2_rn(dz, gz)));
+            const float2 c = __ffma2_rn(__fmul2_rn(c25, dqd), __fmul2_rn(ri5, ri2), __fmul2_rn(pm, ri3));
+            const float2 nri5 = __fmul2_rn(ri5, neg1);
+            sx[q] = __ffma2_rn(c, dx, __ffma2_rn(gx, nri5, sx[q]));
+            sy[q] = __ffma2_rn(c, dy, __ffma2_rn(gy, nri5, sy[q]));
+            sz[q] = __ffma2_rn(c, dz, __ffma2_rn(gz, nri5, sz[q]));
+            if constexpr (PHI)
+                sp[q] = __ffma2_rn(__fmul2_rn(half, dqd), nri5, __ffma2_rn(pm, __fmul2_rn(ri, neg1), sp[q]));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        if constexpr (COMP) {
+            const float part[4] = {sx[q].x + sx[q].y, sy[q].x + sy[q].y, sz[q].x + sz[q].y,
+                                   sp[q].x + sp[q].y};
+#pragma unroll
+            for (int c = 0; c < 4; c++) neumaier_add(I.acc[q][c], I.cmp[q][c], part[c]);
+        } else {
+            I.run[q][0] = sx[q];
+            I.run[q][1] = sy[q];
+            I.run[q][2] = sz[q];
+            I.run[q][3] = sp[q];
+        }
+    }
+}
+
+template <int IPL, bool PHI, bool COMP, bool SAFE>
+__device__ __forceinline__ void flush_quad_group(int q, int k0, int ks, float4 *LQ, int nq,
+                                                 float eps2, ISlots<IPL> &I) {
+    if (q <= 1) flush_quad_list<1, IPL, PHI, COMP, SAFE>(LQ, nq, eps2, k0, ks, I);
+    else if constexpr (IPL >= 2) {
+        if (q == 2) flush_quad_list<2, IPL, PHI, COMP, SAFE>(LQ, nq, eps2, k0, ks, I);
+        else if constexpr (IPL >= 3) {
+            if (q == 3) flush_quad_list<3, IPL, PHI, COMP, SAFE>(LQ, nq, eps2, k0, ks, I);
+            else if constexpr (IPL >= 4) flush_quad_list<4, IPL, PHI, COMP, SAFE>(LQ, nq, eps2, k0, ks, I);
+        }
+    }
+}
+
 // Lane tiling of a group of cnt particles: each lane holds q <= IPL of them
 // (the t-th at index row + P t), P = ceil(cnt / q) rows, and the list is cut
 // into s = floor(32 / P) splits; lane L is row L % P of split L / P (lanes
@@ -209,17 +327,21 @@ constexpr int walk_regs() {
     return IPL <= 2 ? NB_WALK_REGS_2 : (IPL == 3 ? NB_WALK_REGS_3 : NB_WALK_REGS_4);
 }
 
-template <int IPL, bool PHI, bool COMP, bool SAFE>
+template <int IPL, bool PHI, bool COMP, bool SAFE, bool QUAD>
 __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geometric) {
     extern __shared__ __align__(16) unsigned char walk_smem[];
     const int D = a.list_depth, S = a.stack_depth;
+    const int DQ = QUAD ? walk_quad_depth(D) : 0;
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
-    // per warp: the paired list (D entries = D/2 pairs in LA and LB), the
-    // stack and kWalkScratch words for the leaf compaction
-    const size_t per_warp = walk_smem_per_warp(D, S);
+    // per warp: the paired list (D entries = D/2 pairs in LA and LB), with
+    // quadrupoles the paired node list (DQ entries, 40 B each), the stack and
+    // kWalkScratch words for the leaf compaction
+    const size_t per_warp = walk_smem_per_warp(D, S, QUAD);
     float4 *LA = reinterpret_cast<float4 *>(walk_smem + w * per_warp);
     float4 *LB = LA + D / 2;
-    uint32_t *stk = reinterpret_cast<uint32_t *>(walk_smem + w * per_warp + (size_t)D * sizeof(float4));
+    float4 *LQ = LA + D;
+    uint32_t *stk = reinterpret_cast<uint32_t *>(walk_smem + w * per_warp + (size_t)D * sizeof(float4) +
+                                                 (size_t)DQ * 40);
     int *scr = reinterpret_cast<int *>(stk + S);
     DevState *ds = a.ds;
     const int ng = ds->ngroups;
@@ -227,7 +349,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
     const int npart = (int)a.n;
     const unsigned lt = lanemask_lt();
     int max_sp = 0;
-    unsigned long long warp_entries = 0, warp_inter = 0;
+    unsigned long long warp_entries = 0, warp_inter = 0, warp_quad = 0;
     bool overflow = false, bad = false;
 
     for (;;) {
@@ -266,8 +388,8 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
         }
 
         if (lane == 0) stk[0] = (uint32_t)root << 3;  // one node: the system's root
-        int sp = 1, nl = 0;
-        long long entries = 0;
+        int sp = 1, nl = 0, nq = 0;
+        long long entries = 0, qentries = 0;
         __syncwarp();
         while (sp > 0) {
             // ---- pop up to 32 nodes (one per lane) from the top ranges
@@ -345,18 +467,32 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
             }
             if (sp > max_sp) max_sp = sp;
 
-            // ---- accepted nodes join the list
+            // ---- accepted nodes join the list (with quadrupoles: the node list)
             const unsigned am = __ballot_sync(NB_FULL, accept);
             const int na = __popc(am);
-            if (nl + na > D) {
-                __syncwarp();
-                flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, LB, nl, eps2, I);
-                entries += nl;
-                nl = 0;
-                __syncwarp();
+            if constexpr (QUAD) {
+                if (nq + na > DQ) {
+                    __syncwarp();
+                    flush_quad_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LQ, nq, eps2, I);
+                    qentries += nq;
+                    nq = 0;
+                    __syncwarp();
+                }
+                if (accept)
+                    quad_put(LQ, nq + __popc(am & lt), A, __ldg(&a.nodeQ[2 * node]),
+                             __ldg(&a.nodeQ[2 * node + 1]));
+                nq += na;
+            } else {
+                if (nl + na > D) {
+                    __syncwarp();
+                    flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, LB, nl, eps2, I);
+                    entries += nl;
+                    nl = 0;
+                    __syncwarp();
+                }
+                if (accept) list_put(LA, LB, nl + __popc(am & lt), A);
+                nl += na;
             }
-            if (accept) list_put(LA, LB, nl + __popc(am & lt), A);
-            nl += na;
 
             // ---- particles of opened leaves join the list, 32 per chunk: the
             // opened leaves are compacted to lanes 0..nlf-1 (through the warp's
@@ -408,6 +544,14 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
             entries += nl;
             nl = 0;
         }
+        if constexpr (QUAD) {
+            if (nq > 0) {
+                __syncwarp();
+                flush_quad_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LQ, nq, eps2, I);
+                qentries += nq;
+                nq = 0;
+            }
+        }
         __syncwarp();
 
         // ---- sum the list splits of every particle onto split 0
@@ -454,9 +598,11 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
                 }
             }
         }
+        entries += qentries;
         if (lane == 0 && a.grp_cost) a.grp_cost[g] = (int32_t)entries;
         warp_entries += (unsigned long long)entries;
         warp_inter += (unsigned long long)entries * (unsigned long long)cnt;
+        warp_quad += (unsigned long long)qentries * (unsigned long long)cnt;
     }
     if (lane == 0) {
         atomicMax(&ds->max_stack, max_sp);
@@ -464,22 +610,24 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
             atomicAdd(&ds->list_entries, warp_entries);
             atomicAdd(&ds->interactions, warp_inter);
         }
+        if (QUAD && warp_quad) atomicAdd(&ds->quad_entries, warp_quad);
         if (overflow) atomicOr(&ds->status, kStatusStackOverflow);
     }
     if (bad) atomicOr(&ds->status, kStatusBadTree);
 }
 
-template <int IPL>
+template <int IPL, bool QUAD>
 cudaError_t launch_walk_ipl(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm) {
     const int threads = 32 * sh.warps_per_block;
-    const size_t smem = (size_t)sh.warps_per_block * walk_smem_per_warp(a.list_depth, a.stack_depth);
+    const size_t smem =
+        (size_t)sh.warps_per_block * walk_smem_per_warp(a.list_depth, a.stack_depth, QUAD);
     void (*k)(WalkArgs, int);
     if (sh.potential) {
-        if (sh.compensated) k = sh.safe ? walk_kernel<IPL, true, true, true> : walk_kernel<IPL, true, true, false>;
-        else k = sh.safe ? walk_kernel<IPL, true, false, true> : walk_kernel<IPL, true, false, false>;
+        if (sh.compensated) k = sh.safe ? walk_kernel<IPL, true, true, true, QUAD> : walk_kernel<IPL, true, true, false, QUAD>;
+        else k = sh.safe ? walk_kernel<IPL, true, false, true, QUAD> : walk_kernel<IPL, true, false, false, QUAD>;
     } else {
-        if (sh.compensated) k = sh.safe ? walk_kernel<IPL, false, true, true> : walk_kernel<IPL, false, true, false>;
-        else k = sh.safe ? walk_kernel<IPL, false, false, true> : walk_kernel<IPL, false, false, false>;
+        if (sh.compensated) k = sh.safe ? walk_kernel<IPL, false, true, true, QUAD> : walk_kernel<IPL, false, true, false, QUAD>;
+        else k = sh.safe ? walk_kernel<IPL, false, false, true, QUAD> : walk_kernel<IPL, false, false, false, QUAD>;
     }
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

@@ -1,7 +1,7 @@
-// walk_ipl1.cu -- instances of the tree walk with up to 1 i-particle per lane
-// (separate translation unit so the instances compile in parallel).
+// walk_ipl1.cu -- instances of the tree walk with up to 1 i-particle per lane,
+// monopole nodes (separate translation unit so the instances compile in parallel).
 #include "walk_impl.cuh"
 
 namespace nb {
-template cudaError_t launch_walk_ipl<1>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
+template cudaError_t launch_walk_ipl<1, false>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
 }  // namespace nb

@@ -35,7 +35,8 @@ class Config(C.Structure):
                 ("ipl", C.c_int32), ("list_depth", C.c_int32), ("stack_depth", C.c_int32),
                 ("warps_per_block", C.c_int32), ("compensated", C.c_int32),
                 ("want_potential", C.c_int32), ("schedule", C.c_int32),
-                ("use_graph", C.c_int32), ("rebuild_interval", C.c_int32)]
+                ("use_graph", C.c_int32), ("rebuild_interval", C.c_int32),
+                ("quadrupole", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -55,7 +56,7 @@ class Stats(C.Structure):
                 ("list_entries", C.c_int64), ("max_stack", C.c_int32), ("levels", C.c_int32),
                 ("kernels", C.c_int64), ("ms_build", C.c_float), ("ms_walk", C.c_float),
                 ("ms_walk_kernel", C.c_float), ("walk_launches", C.c_int32),
-                ("rebuilds", C.c_int32)]
+                ("rebuilds", C.c_int32), ("quad_interactions", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,10 +75,11 @@ EXPORTS = ("nbody_abi_version", "nbody_config_default", "nbody_create", "nbody_d
 MLP_PARAMS, MLP_FEATURES = 1377, 8
 EXPORT_PERM, EXPORT_KEYS, EXPORT_NODE_LEVEL, EXPORT_NODE_START, EXPORT_NODE_COUNT, \
     EXPORT_NODE_PARENT, EXPORT_NODE_A, EXPORT_NODE_B, EXPORT_GROUP_FIRST, EXPORT_GROUP_COUNT, \
-    EXPORT_GROUP_SPHERE, EXPORT_SYS_BOX = range(12)
+    EXPORT_GROUP_SPHERE, EXPORT_SYS_BOX, EXPORT_NODE_Q = range(13)
 _EXPORT_DTYPE = {0: (np.int32, 1), 1: (np.uint64, 1), 2: (np.int8, 1), 3: (np.int32, 1),
                  4: (np.int32, 1), 5: (np.int32, 1), 6: (np.float32, 4), 7: (np.float32, 4),
-                 8: (np.int32, 1), 9: (np.int32, 1), 10: (np.float32, 4), 11: (np.float32, 4)}
+                 8: (np.int32, 1), 9: (np.int32, 1), 10: (np.float32, 4), 11: (np.float32, 4),
+                 12: (np.float32, 8)}
 
 
 def library_path() -> str:

@@ -53,7 +53,7 @@ def gpu_walk(p, cfg, a_old=None, want_phi=False, offsets=None, eps_sys=None):
         out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(4)]
         st = nb.nbody_walk(ctx, None if a_old is None else dev(a_old.astype(np.float32)),
                            out[0], out[1], out[2], out[3] if want_phi else None)
-        exports = {w: nb.nbody_export(ctx, w) for w in range(12)}
+        exports = {w: nb.nbody_export(ctx, w) for w in range(12)}  # all but the quadrupoles
         return [host(o) for o in out], st, exports
     finally:
         nb.nbody_destroy(ctx)
