@@ -281,6 +281,80 @@ def drift(x, v, h):
     lib.oracle_drift(x[0].size, *[_p(q, C.c_double) for q in x], *[_p(_f64(q), C.c_double) for q in v], h)
 
 
+def block_level(amag, eps, eta, dt, levels):
+    """Time-step level of each particle under block time steps (the paper's
+    code integrates with McMillan's block steps, Sect. 1; the step criterion
+    is not given -- READING: dt_i = sqrt(2 eta eps / |a_i|), the level the
+    smallest k in 0..levels with dt / 2^k <= dt_i; |a| = 0 gives level 0).
+    The decision is taken in FP32 with the library's operation order, so equal
+    inputs give equal levels."""
+    a32 = np.atleast_1d(np.asarray(amag, np.float32))
+    eps32 = np.broadcast_to(np.asarray(eps, np.float32), a32.shape)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        dti = np.sqrt(np.float32(2.0) * np.float32(eta) * eps32 / a32).astype(np.float32)
+    k = np.zeros(a32.shape, np.int64)
+    h = np.full(a32.shape, np.float32(dt), np.float32)
+    for _ in range(levels):
+        finer = (k < levels) & (h > dti)
+        h = np.where(finer, h * np.float32(0.5), h).astype(np.float32)
+        k += finer
+    return np.where(a32 > 0, k, 0)
+
+
+def block_kdk(x, v, m, a, G, eps, dt, nsteps, levels, eta, force, trace=None):
+    """Leapfrog kick-drift-kick with block time steps, FP64.
+
+    Level k steps by dt / 2^k; the integer clock ticks in units of dt / 2^levels
+    and a particle on level k is active at ticks that are multiples of
+    2^(levels - k).  At tick 0 every particle takes the opening half kick of
+    its level; at each tick where some particle is active, all positions
+    drift to that tick, the active particles get new accelerations
+    (force(x, index array) -> (ax, ay, az) for those), their closing half
+    kick, a new level (coarser only where the tick is a multiple of the new
+    step) and, unless it is the last tick, the opening half kick of the new
+    step.  x, v, a: tuples of three float64 arrays (copied).  trace (a list,
+    optional) receives (tick, active indices, their levels before the tick).
+    Returns (x, v, a, levels of the last steps, number of force evaluations)."""
+    x = [np.array(q, np.float64) for q in x]
+    v = [np.array(q, np.float64) for q in v]
+    a = [np.array(q, np.float64) for q in a]
+    K = levels
+    amag = np.sqrt(a[0] ** 2 + a[1] ** 2 + a[2] ** 2)
+    lvl = block_level(amag, eps, eta, dt, K)
+    for c in range(3):
+        v[c] += a[c] * (dt / 2.0 ** lvl) * 0.5
+    total, last, nforce = nsteps << K, 0, 0
+    tau = dt / (1 << K)
+    for T in range(1, total + 1):
+        if T % (1 << (K - int(lvl.max()))):
+            continue
+        for c in range(3):
+            x[c] += v[c] * ((T - last) * tau)
+        last = T
+        act = np.flatnonzero(T % (1 << (K - lvl)) == 0)
+        if trace is not None:
+            trace.append((T, act.copy(), lvl[act].copy()))
+        fa = force(x, act)
+        nforce += act.size
+        for c in range(3):
+            a[c][act] = fa[c]
+            v[c][act] += fa[c] * (dt / 2.0 ** lvl[act]) * 0.5
+        if T < total:
+            am = np.sqrt(fa[0] ** 2 + fa[1] ** 2 + fa[2] ** 2)
+            knew = block_level(am, eps, eta, dt, K)
+            old = lvl[act]
+            # a coarser level only where this tick is a multiple of its step
+            while True:
+                bad = (knew < old) & (T % (1 << (K - knew)) != 0)
+                if not bad.any():
+                    break
+                knew = knew + bad
+            lvl[act] = knew
+            for c in range(3):
+                v[c][act] += fa[c] * (dt / 2.0 ** knew) * 0.5
+    return x, v, a, lvl, nforce
+
+
 def diagnostics(x, y, z, vx, vy, vz, m, phi=None):
     """FP64 {E_kin, E_pot, Px, Py, Pz, Lx, Ly, Lz}."""
     lib = _load()

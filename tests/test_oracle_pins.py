@@ -633,6 +633,117 @@ def test_leapfrog_kepler_energy_second_order():
     assert 3.0 < e1 / e2 < 5.0
 
 
+# --------------------------------------------------------------------------- block time steps
+def test_block_level_thresholds():
+    """dt_i = sqrt(2 eta eps / |a|) <= dt / 2^k: with eta = 1/40, eps = 1/64 and
+    dt = 1/256 the level-0 threshold is |a| = 2 eta eps / dt^2 = 51.2 (hand
+    value) and every factor 4 above it adds a level, up to the deepest."""
+    eta, eps, dt, K = 0.025, 1.0 / 64, 1.0 / 256, 5
+    a0 = 2 * eta * eps / dt ** 2
+    assert np.isclose(a0, 51.2)
+    amag = np.array([0.0, a0 * 0.999, a0 * 1.001, 4 * a0 * 0.999, 4 * a0 * 1.001, 16 * a0 * 1.001,
+                     1e9])
+    assert list(oracle.block_level(amag, eps, eta, dt, K)) == [0, 0, 1, 1, 2, 3, 5]
+
+
+def _shared_kdk(x, v, a, m, eps, h, steps):
+    x, v, a = [q.copy() for q in x], [q.copy() for q in v], [q.copy() for q in a]
+    for _ in range(steps):
+        for c in range(3):
+            v[c] += a[c] * (h * 0.5)
+            x[c] += v[c] * h
+        a = list(oracle.direct(*x, m, 1.0, eps, want_phi=False)[:3])
+        for c in range(3):
+            v[c] += a[c] * (h * 0.5)
+    return x, v, a
+
+
+def _direct_force(m, eps):
+    def f(x, idx):
+        return oracle.direct_targets(*x, m, idx, 1.0, eps)[:3]
+    return f
+
+
+@pytest.mark.parametrize("eta,fine", [(1e30, False), (1e-30, True)])
+def test_block_kdk_single_level_is_shared_kdk(eta, fine):
+    """All particles on one level: the block scheme performs exactly the
+    operations of the shared-step leapfrog (step dt, or dt/2^K with 2^K times
+    as many steps), so the states agree bit for bit."""
+    p = ics.plummer(300, 51)
+    m = p["m"].astype(float)
+    x = [p[k].astype(float) for k in ("x", "y", "z")]
+    v = [p[k].astype(float) for k in ("vx", "vy", "vz")]
+    eps, dt, K = 1 / 32, 1 / 64, 3
+    a = list(oracle.direct(*x, m, 1.0, eps, want_phi=False)[:3])
+    bx, bv, ba, lvl, nf = oracle.block_kdk(x, v, m, a, 1.0, eps, dt, 2, K, eta, _direct_force(m, eps))
+    assert np.all(lvl == (K if fine else 0))
+    sx, sv, sa = _shared_kdk(x, v, a, m, eps, dt / 2 ** K if fine else dt, 2 * 2 ** K if fine else 2)
+    for q, r in zip(bx + bv + ba, sx + sv + sa):
+        assert np.array_equal(q, r)
+
+
+def test_block_kdk_every_step_lasts_its_level():
+    """The defining invariant of block steps: a particle's consecutive force
+    evaluations are exactly one step of its level apart (levels change only at
+    the end of a step, and a coarser level only where the clock is a multiple
+    of the new step).  An eccentric binary (levels refine towards pericentre
+    and coarsen after it) exercises both directions."""
+    mb, apo, ecc = 0.5, 0.2, 0.9
+    vapo = np.sqrt(2 * mb / apo * (1 - ecc) / 2)  # apocentre speed of each body, reduced-mass orbit
+    x = [np.array([-apo / 2, apo / 2, 5.0]), np.zeros(3), np.zeros(3)]
+    v = [np.zeros(3), np.array([-vapo / 2 * 2 ** 0.5, vapo / 2 * 2 ** 0.5, 0.3]), np.zeros(3)]
+    m = np.array([mb, mb, 1e-6])
+    eps, dt, K, eta = 1e-4, 1 / 8, 8, 15.0
+    a = list(oracle.direct(*x, m, 1.0, eps, want_phi=False)[:3])
+    tr = []
+    oracle.block_kdk(x, v, m, a, 1.0, eps, dt, 4, K, eta, _direct_force(m, eps), trace=tr)
+    last = {}
+    coarsened = refined = 0
+    for T, act, lv in tr:
+        for i, k in zip(act, lv):
+            assert T % (1 << (K - k)) == 0
+            if i in last:  # the step [T0, T] ran at level k (recorded at its end)
+                T0, k0 = last[i]
+                assert T - T0 == 1 << (K - k)
+                coarsened += k < k0
+                refined += k > k0
+            last[i] = (T, k)
+    assert coarsened > 0 and refined > 0
+
+
+def test_block_kdk_binary_and_distant_particles():
+    """A tight binary (fine levels) beside a loose cluster (coarse levels):
+    the binary's energy is conserved as well as with the fine shared step,
+    and the whole system ends close to the fine shared-step run, with far
+    fewer force evaluations."""
+    g = ics.rng(52)
+    nc = 40
+    cl = g.normal(scale=1.0, size=(nc, 3)) + np.array([30.0, 0.0, 0.0])
+    sep, mb = 0.02, 0.5
+    vb = np.sqrt(mb * 2 / sep) / 2  # circular: each moves at sqrt(G M_tot / r) / 2
+    x = [np.concatenate([[-sep / 2, sep / 2], cl[:, c]]) for c in range(3)]
+    v = [np.concatenate([[0.0, 0.0], np.zeros(nc)]),
+         np.concatenate([[-vb, vb], g.normal(scale=0.05, size=nc)]),
+         np.concatenate([[0.0, 0.0], np.zeros(nc)])]
+    m = np.concatenate([[mb, mb], np.full(nc, 1e-3)])
+    eps, dt, K, eta = 1e-4, 1 / 64, 6, 0.02
+    a = list(oracle.direct(*x, m, 1.0, eps, want_phi=False)[:3])
+    bx, bv, _, lvl, nf = oracle.block_kdk(x, v, m, a, 1.0, eps, dt, 2, K, eta, _direct_force(m, eps))
+    assert lvl[:2].min() >= 4 and lvl[2:].max() <= 2
+    sx, sv, _ = _shared_kdk(x, v, a, m, eps, dt / 2 ** K, 2 * 2 ** K)
+    assert nf < 0.2 * (2 * 2 ** K) * m.size
+
+    def ebin(x_, v_):
+        ke = 0.5 * mb * sum(v_[c][0] ** 2 + v_[c][1] ** 2 for c in range(3))
+        r = np.sqrt(sum((x_[c][0] - x_[c][1]) ** 2 for c in range(3)) + eps ** 2)
+        return ke - mb * mb / r
+    e0 = ebin(x, v)
+    assert abs(ebin(bx, bv) - e0) / abs(e0) < 2 * abs(ebin(sx, sv) - e0) / abs(e0) + 1e-6
+    for c in range(3):
+        assert np.max(np.abs(bx[c][2:] - sx[c][2:])) < 1e-6
+        assert np.max(np.abs(bx[c][:2] - sx[c][:2])) < 1e-3 * sep
+
+
 def test_diagnostics_two_body_closed_form():
     x, y, z = np.array([0.0, 3.0]), np.array([0.0, 4.0]), np.zeros(2)
     vx, vy, vz = np.array([1.0, -0.5]), np.array([0.0, 2.0]), np.array([0.5, 0.0])
