@@ -87,6 +87,10 @@ def parse():
     ap.add_argument("--quadrupole", type=int, default=0, choices=(0, 1),
                     help="galaxy: nodes carry quadrupoles (an extension beyond the paper's "
                          "monopoles); precision: add a quadrupole sweep")
+    ap.add_argument("--block-levels", type=int, default=0,
+                    help="galaxy: block time steps with levels 0..K (step dt/2^k); 0 = shared step")
+    ap.add_argument("--block-eta", type=float, default=0.025)
+    ap.add_argument("--dt", type=float, default=DT, help="galaxy: the (largest) time step")
     ap.add_argument("--rebuild-interval", type=int, default=1,
                     help="galaxy: tree rebuilt every k-th step, refitted between (0: automatic, "
                          "by timing); the headline configuration rebuilds every step")
@@ -103,14 +107,18 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(n, rebuild_interval=1):
+def workload_config(n, rebuild_interval=1, dt=DT, block_levels=0, block_eta=0.025):
     rb = ("tree rebuilt every step" if rebuild_interval == 1 else
           "tree rebuilt when timing says so (refitted between)" if rebuild_interval == 0 else
           f"tree rebuilt every {rebuild_interval} steps (refitted between)")
+    dts = "1/256" if dt == DT else f"{dt:g}"
+    integ = (f"shared-step leapfrog dt={dts}" if block_levels == 0 else
+             f"block-step leapfrog, levels dt/2^k for k=0..{block_levels}, dt={dts}, "
+             f"criterion sqrt(2*{block_eta:g}*eps/|a|)")
     return {
         "workload": f"three-component galaxy N={n} (Hernquist bulge 15% a=0.6, exponential disk "
                     f"10% Rd=5.4 z0=0.6, NFW halo 75% rs=12 cut 10rs), eps=1/64, "
-                    f"delta_acc=2^-9, shared-step leapfrog dt=1/256, {rb}",
+                    f"delta_acc=2^-9, {integ}, {rb}",
         "n": n,
         "flops_per_interaction": FLOPS_PER_INTERACTION,
         "l2": "inputs larger than L2 (particle state ~0.45 GB, tree ~0.4 GB > 129 MB)",
@@ -230,13 +238,15 @@ def run_ours(args, rank, world, local_rank):
     A = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
     stream = torch.cuda.current_stream(dev)
     cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, rebuild_interval=args.rebuild_interval,
-                                  quadrupole=args.quadrupole)
+                                  quadrupole=args.quadrupole, block_levels=args.block_levels,
+                                  block_eta=args.block_eta)
+    dt = args.dt
     ctx = nb.nbody_create(cfg, stream)
     try:
         # accelerations at t = 0 (bootstrap MAC), then warm-up steps
         nb.nbody_build(ctx, *[D(p[k]) for k in ("x", "y", "z")], M)
         nb.nbody_walk(ctx, None, *A)
-        nb.nbody_step(ctx, *X64, *V, M, *A, DT, args.warmup)
+        nb.nbody_step(ctx, *X64, *V, M, *A, dt, args.warmup)
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
@@ -245,7 +255,7 @@ def run_ours(args, rank, world, local_rank):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
         ev0.record(stream)
-        st = nb.nbody_step(ctx, *X64, *V, M, *A, DT, args.steps)
+        st = nb.nbody_step(ctx, *X64, *V, M, *A, dt, args.steps)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         clocks = sampler.stop()
@@ -271,7 +281,7 @@ def run_ours(args, rank, world, local_rank):
         e0.record(stream)
         w0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            s2 = nb.nbody_step(ctx, *hx, *hv, hm, *ha, DT, 1)
+            s2 = nb.nbody_step(ctx, *hx, *hv, hm, *ha, dt, 1)
             e2e_inter += s2.interactions
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -323,7 +333,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": s_per_step * 1e3, "s_per_step": s_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded three-component galaxy; stands in for the paper's M31 model)",
-        "config": dict(workload_config(n, args.rebuild_interval), parallelism=f"replicas x{world}",
+        "config": dict(workload_config(n, args.rebuild_interval, dt, args.block_levels,
+                                       args.block_eta), parallelism=f"replicas x{world}",
                        walk=cfg.as_dict()),
         "interactions_per_step": inter_per_step,
         "whole_step_tflops": whole_tflops,
@@ -334,6 +345,7 @@ def run_ours(args, rank, world, local_rank):
         "nodes": st.n_nodes, "groups": st.n_groups, "max_stack": st.max_stack,
         "rebuilds": int(st.rebuilds),
         "quadrupole": args.quadrupole,
+        "block_levels": args.block_levels, "block_eta": args.block_eta, "dt": dt,
         "quad_interactions_per_step": st.quad_interactions / steps,
         "roofline": {"bound": "alu", "achieved": walk_tflops, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": walk_tflops / peak_tflops, "traffic": traffic,

@@ -103,6 +103,18 @@ typedef struct {
                             M d/r^3 - Q d/r^5 + 5/2 (d.Q.d) d/r^7 (r^2 = |d|^2 +
                             eps^2; an extension beyond the paper's monopoles,
                             same MAC); 0: monopoles (default)                */
+    int32_t block_levels; /* block (hierarchical) time steps in nbody_step(_batched):
+                            0 = one shared step dt (default); K = 1..20: each
+                            particle steps by dt / 2^k on level k <= K, chosen
+                            from dt_i = sqrt(2 block_eta eps / |a_i|) (the paper's
+                            code uses block steps, Sect. 1; this criterion is
+                            a reading); only groups with a particle whose step
+                            ends at a tick are walked.  nsteps counts steps of
+                            dt; the state returned is synchronised.  Not with
+                            use_graph; the stream is synchronised after every
+                            processed tick.                                 */
+    float block_eta;     /* accuracy parameter of the block step criterion
+                            (default 0.025), > 0                             */
 } nbody_config;
 
 typedef struct {

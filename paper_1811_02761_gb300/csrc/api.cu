@@ -65,10 +65,10 @@ struct nbody_ctx {
     // groups
     DevBuf gflag, grp_first, grp_count, grp_sphere, grp_sys, grp_alpha, grp_cost, grp_order;
     // systems
-    DevBuf sys_off, sys_box, sys_boxord, sys_eps2, sys_root;
+    DevBuf sys_off, sys_box, sys_boxord, sys_eps2, sys_eps, sys_root;
     // walk / step
     DevBuf acc_s, aold_s;
-    DevBuf st_buf[2][10];
+    DevBuf st_buf[2][11];
     // learned scheduling
     DevBuf mlp_w, mlp_m1, mlp_m2, mlp_wb, mlp_norm, mlp_gpart, mlp_lpart, mlp_loss;
     DevBuf feat, target, score, okey, okey_alt, oval, oval_alt, pcost_walk;
@@ -104,7 +104,7 @@ struct nbody_ctx {
                          &node_parent, &node_link, &node_count, &node_nchild,
                          &nodeA, &nodeB, &mass2, &nodeQ, &gflag, &grp_first, &grp_count, &grp_sphere,
                          &grp_sys, &grp_alpha, &grp_cost, &grp_order, &sys_off, &sys_box,
-                         &sys_boxord, &sys_eps2, &sys_root, &acc_s, &aold_s, &mlp_w, &mlp_m1,
+                         &sys_boxord, &sys_eps2, &sys_eps, &sys_root, &acc_s, &aold_s, &mlp_w, &mlp_m1,
                          &mlp_m2, &mlp_wb, &mlp_norm, &mlp_gpart, &mlp_lpart, &mlp_loss, &feat,
                          &target, &score, &okey, &okey_alt, &oval, &oval_alt, &pcost_walk};
         for (DevBuf *b : all) owned.push_back(b);
@@ -192,6 +192,8 @@ bool config_ok(const nbody_config *c, std::string &why) {
     if (c->rebuild_interval < 0 || c->rebuild_interval > 1024)
         return bad("rebuild_interval must be in 0..1024");
     if (c->quadrupole != 0 && c->quadrupole != 1) return bad("quadrupole must be 0 or 1");
+    if (c->block_levels < 0 || c->block_levels > 20) return bad("block_levels must be in 0..20");
+    if (!(c->block_eta > 0.0f) || !std::isfinite(c->block_eta)) return bad("block_eta must be finite and > 0");
     size_t smem = (size_t)c->warps_per_block *
                   nb::walk_smem_per_warp(c->list_depth, c->stack_depth, c->quadrupole != 0);
     if (smem > 227 * 1024)
@@ -275,6 +277,7 @@ cudaError_t ensure_capacity(nbody_ctx *c, int64_t n, int nsys, int levels) {
     if (nsys > c->cap_sys) {
         NB_E(ensure(c->sys_off, (size_t)(nsys + 1) * 8)); NB_E(ensure(c->sys_box, (size_t)nsys * sizeof(SysBox)));
         NB_E(ensure(c->sys_boxord, (size_t)nsys * 24)); NB_E(ensure(c->sys_eps2, (size_t)nsys * 4));
+        NB_E(ensure(c->sys_eps, (size_t)nsys * 4));
         NB_E(ensure(c->sys_root, (size_t)nsys * 4));
         c->cap_sys = nsys;
     }
@@ -366,7 +369,7 @@ nbody_status refit_tree_groups(nbody_ctx *c, const Layout &L) {
 // Upload the CSR offsets and per-system eps^2.
 nbody_status upload_systems(nbody_ctx *c, int nsys, const int64_t *offsets, const float *eps_sys) {
     std::vector<int64_t> off(nsys + 1);
-    std::vector<float> e2(nsys);
+    std::vector<float> e2(nsys), e1(nsys);
     if (offsets) {
         std::memcpy(off.data(), offsets, sizeof(int64_t) * (nsys + 1));
     } else {
@@ -374,11 +377,14 @@ nbody_status upload_systems(nbody_ctx *c, int nsys, const int64_t *offsets, cons
     }
     for (int s = 0; s < nsys; s++) {
         float e = eps_sys ? eps_sys[s] : c->cfg.eps;
+        e1[s] = e;
         e2[s] = e * e;
     }
     NB_CUDA(c, cudaMemcpyAsync(c->sys_off.p, off.data(), sizeof(int64_t) * (nsys + 1),
                                cudaMemcpyHostToDevice, c->stream));
     NB_CUDA(c, cudaMemcpyAsync(c->sys_eps2.p, e2.data(), sizeof(float) * nsys,
+                               cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(c->sys_eps.p, e1.data(), sizeof(float) * nsys,
                                cudaMemcpyHostToDevice, c->stream));
     // the copies read pageable host vectors: make sure they have completed
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -600,9 +606,10 @@ nbody_status compute_order(nbody_ctx *c, const float *pcost, const int32_t **ord
 // Walk over the current groups; aold_s (sorted) must hold |a_old|.
 nbody_status run_walk(nbody_ctx *c, bool geometric, bool phi, bool safe, const int32_t *perm,
                       float *ax, float *ay, float *az, float *ph, float4 *acc_sorted,
-                      bool reset_accumulators = true, const float *pcost = nullptr) {
-    const int32_t *order = nullptr;
-    if (!geometric) {
+                      bool reset_accumulators = true, const float *pcost = nullptr,
+                      const int32_t *active_order = nullptr, const int32_t *nactive = nullptr) {
+    const int32_t *order = active_order;
+    if (!geometric && !active_order) {
         nbody_status so = compute_order(c, pcost, &order);
         if (so != NBODY_OK) return so;
     }
@@ -621,6 +628,7 @@ nbody_status run_walk(nbody_ctx *c, bool geometric, bool phi, bool safe, const i
     }
     WalkArgs a = walk_args(c);
     a.order = order;
+    a.nactive = nactive;
     a.perm = perm;
     a.ax = ax;
     a.ay = ay;
@@ -679,6 +687,8 @@ void nbody_config_default(nbody_config *c) {
     c->use_graph = 0;
     c->rebuild_interval = 1;
     c->quadrupole = 0;
+    c->block_levels = 0;
+    c->block_eta = 0.025f;
 }
 
 nbody_status nbody_create(nbody_ctx **out, const nbody_config *cfg, void *cuda_stream) {
@@ -913,6 +923,108 @@ nbody_status nbody_direct(int64_t n, const float *x, const float *y, const float
     return NBODY_OK;
 }
 
+// Block (hierarchical) time steps, nsteps steps of dt with levels 0..K
+// (step dt / 2^k).  The clock ticks in units of dt / 2^K; at tick 0 every
+// particle takes the opening half kick of its level, and at each tick where a
+// particle is active (its level's step ends there) all particles drift to the
+// tick, the tree is rebuilt or refitted (rebuild_interval, per processed
+// tick), the groups holding an active particle are walked, and the active
+// particles take their closing half kick, a new level and -- except at the
+// last tick -- the opening half kick of their next step.  Ticks at which no
+// level ends are skipped (their drifts are merged into the next); the
+// deepest occupied level is read back after every processed tick.
+static nbody_status block_steps(nbody_ctx *ctx, const Layout &L, StepState *S, int &cur,
+                                float4 *acc, float dt, int32_t nsteps, bool safe, int &rebuilds,
+                                std::vector<int> &marks) {
+    if (nsteps == 0) return NBODY_OK;  // no step: the state is returned as given
+    cudaStream_t q = ctx->stream;
+    const int64_t n = L.n;
+    const int K = ctx->cfg.block_levels;
+    const float eta = ctx->cfg.block_eta;
+    int32_t *dmax = &ctx->ds->block_maxlvl, *dact = &ctx->ds->block_nactive;
+    auto read_maxlvl = [&](int *out) -> nbody_status {
+        NB_CUDA(ctx, cudaMemcpyAsync(&ctx->h_ds->block_maxlvl, dmax, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, q));
+        NB_CUDA(ctx, cudaStreamSynchronize(q));
+        *out = ctx->h_ds->block_maxlvl;
+        return (*out >= 0 && *out <= K) ? NBODY_OK
+                                        : fail(ctx, NBODY_ECUDA, "internal error: block level out of range");
+    };
+    NB_CUDA(ctx, cudaMemsetAsync(dmax, 0, sizeof(int32_t), q));
+    launch_block_start(q, n, S[cur], acc, dt, K, eta, P<int64_t>(ctx->sys_off), L.nsys,
+                       P<float>(ctx->sys_eps), dmax);
+    ctx->kernels += 1;
+    int kmax = 0;
+    nbody_status st = read_maxlvl(&kmax);
+    if (st != NBODY_OK) return st;
+    const int64_t total = (int64_t)nsteps << K;
+    const double tau = (double)dt / (double)(int64_t(1) << K);
+    const int interval = ctx->cfg.rebuild_interval;
+    std::vector<float> cycle;
+    int64_t last = 0;
+    int since = 0;
+    bool first = true;
+    for (int64_t T = 1; T <= total; T++) {
+        if (T % (int64_t(1) << (K - kmax))) continue;
+        const float span = (float)((double)(T - last) * tau);
+        last = T;
+        bool rebuild = first || interval == 1;
+        if (!rebuild && interval > 1) rebuild = since >= interval;
+        if (!rebuild && interval == 0)
+            rebuild = since >= 32 || nbody_rebuild_due(cycle.data(), (int32_t)cycle.size()) != 0;
+        if (rebuild) {
+            since = 0;
+            cycle.clear();
+        }
+        first = false;
+        // drift every particle to tick T (no kick: the kick factor is 0)
+        launch_kick_drift(q, n, S[cur], acc, 0.0f, span, rebuild ? nullptr : P<float4>(ctx->pos4));
+        ctx->kernels += 1;
+        cudaEvent_t e0, e1, e2;
+        NB_CUDA(ctx, pool_event(ctx, &e0));
+        NB_CUDA(ctx, cudaEventRecord(e0, q));
+        if (rebuild) {
+            st = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
+            if (st != NBODY_OK) return st;
+            launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur], P<float4>(ctx->pos4));
+            ctx->kernels += 1;
+            cur = 1 - cur;
+            st = build_tree_groups(ctx, L);
+            rebuilds++;
+        } else {
+            st = refit_tree_groups(ctx, L);
+        }
+        if (st != NBODY_OK) return st;
+        NB_CUDA(ctx, pool_event(ctx, &e1));
+        NB_CUDA(ctx, cudaEventRecord(e1, q));
+        NB_CUDA(ctx, cudaMemcpyAsync(ctx->aold_s.p, S[cur].aold, (size_t)n * 4,
+                                     cudaMemcpyDeviceToDevice, q));
+        NB_CUDA(ctx, cudaMemsetAsync(dact, 0, sizeof(int32_t), q));
+        launch_block_active_groups(q, ctx->ds, P<int32_t>(ctx->grp_first), P<int32_t>(ctx->grp_count),
+                                   S[cur].lvl, T, K, P<int32_t>(ctx->grp_order), dact, ctx->nsm);
+        ctx->kernels += 1;
+        st = run_walk(ctx, false, false, safe, nullptr, nullptr, nullptr, nullptr, nullptr, acc,
+                      false, nullptr, P<int32_t>(ctx->grp_order), dact);
+        if (st != NBODY_OK) return st;
+        NB_CUDA(ctx, pool_event(ctx, &e2));
+        NB_CUDA(ctx, cudaEventRecord(e2, q));
+        marks.push_back(ctx->evused - 3);
+        NB_CUDA(ctx, cudaMemsetAsync(dmax, 0, sizeof(int32_t), q));
+        launch_block_kick(q, n, S[cur], acc, T, total, dt, K, eta, P<int64_t>(ctx->sys_off), L.nsys,
+                          P<float>(ctx->sys_eps), dmax);
+        ctx->kernels += 1;
+        st = read_maxlvl(&kmax);
+        if (st != NBODY_OK) return st;
+        since++;
+        if (interval == 0) {
+            float c = 0.0f;
+            NB_CUDA(ctx, cudaEventElapsedTime(&c, e0, e2));
+            cycle.push_back(c);
+        }
+    }
+    return NBODY_OK;
+}
+
 static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offsets,
                               const float *eps_sys, int64_t n, double *x, double *y, double *z,
                               float *vx, float *vy, float *vz, const float *m, float *ax,
@@ -928,6 +1040,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     for (int b = 0; b < 2 && e == cudaSuccess; b++) {
         for (int k = 0; k < 3 && e == cudaSuccess; k++) e = ensure(ctx->st_buf[b][k], (size_t)n * 8);
         for (int k = 3; k < 10 && e == cudaSuccess; k++) e = ensure(ctx->st_buf[b][k], (size_t)n * 4);
+        if (e == cudaSuccess && ctx->cfg.block_levels > 0) e = ensure(ctx->st_buf[b][10], (size_t)n);
     }
     if (e != cudaSuccess) return fail(ctx, NBODY_ENOMEM, std::string("allocation: ") + cudaGetErrorString(e));
     std::vector<int64_t> off1 = {0, n};
@@ -950,6 +1063,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         // schedule that reads it
         S[b].pcost = ctx->cfg.schedule == NBODY_SCHED_LASTCOST ? P<float>(ctx->st_buf[b][9])
                                                                : nullptr;
+        S[b].lvl = ctx->cfg.block_levels > 0 ? P<uint8_t>(ctx->st_buf[b][10]) : nullptr;
     }
     const size_t db = (size_t)n * 8, fb = (size_t)n * 4;
     const void *in[10];
@@ -1026,7 +1140,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     // a cost-ordered queue reads the group count on the host every step, so it
     // runs eagerly; so do steps that may refit instead of rebuilding
     if (ctx->cfg.use_graph && nsteps >= 2 && ctx->cfg.schedule == NBODY_SCHED_MORTON &&
-        ctx->cfg.rebuild_interval == 1) {
+        ctx->cfg.rebuild_interval == 1 && ctx->cfg.block_levels == 0) {
         // Two steps per graph: the sort's ping-pong buffers and the state
         // copies swap roles every step, so after two steps every pointer is
         // back where the capture found it and the graph can be replayed.
@@ -1086,6 +1200,11 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         NB_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->gstream));
         NB_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev[1], 0));
         eager = nsteps % 2;
+    }
+    if (ctx->cfg.block_levels > 0) {
+        st = block_steps(ctx, L, S, cur, acc, dt, nsteps, safe, rebuilds, marks);
+        if (st != NBODY_OK) return st;
+        eager = 0;
     }
     // Rebuild schedule of the eager steps: every rebuild_interval-th step, or
     // (interval 0) when nbody_rebuild_due says the last step raised the mean

@@ -77,6 +77,7 @@ __global__ void permute_state_kernel(int64_t n, const uint32_t *__restrict__ per
         dst.aold[i] = src.aold[j];
         dst.id[i] = src.id[j];
         if (src.pcost) dst.pcost[i] = src.pcost[j];
+        if (src.lvl) dst.lvl[i] = src.lvl[j];
     }
 }
 
@@ -134,6 +135,122 @@ void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *a
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
                         float *ay, float *az) {
     store_state_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, x, y, z, vx, vy, vz, ax, ay, az);
+}
+
+// ---------------------------------------------------------------- block time steps
+// The paper's code integrates with block (hierarchical) time steps (Sect. 1);
+// its step criterion is not given.  Reading: dt_i = sqrt(2 eta eps / |a_i|),
+// level = the smallest k in 0..K with dt / 2^k <= dt_i (|a| = 0: level 0),
+// decided in FP32 in this operation order.
+__device__ __forceinline__ int block_level(float amag, float eps, float eta, float dt, int K) {
+    if (!(amag > 0.0f)) return 0;
+    const float dti = sqrtf(2.0f * eta * eps / amag);
+    int k = 0;
+    float h = dt;
+    while (k < K && h > dti) {
+        h *= 0.5f;
+        k++;
+    }
+    return k;
+}
+
+__device__ __forceinline__ void warp_max_to(int32_t *dst, int v) {
+    v = __reduce_max_sync(NB_FULL, v);
+    if (lane_id() == 0) atomicMax(dst, v);
+}
+
+__global__ void block_start_kernel(int64_t n, StepState st, const float4 *__restrict__ acc, float dt,
+                                   int K, float eta, const int64_t *__restrict__ off, int nsys,
+                                   const float *__restrict__ sys_eps, int32_t *maxlvl) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = b + threadIdx.x;
+        int k = 0;
+        if (i < n) {
+            const float4 a = acc[i];
+            const float am = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+            k = block_level(am, sys_eps[sys_of(off, nsys, i)], eta, dt, K);
+            const float h = ldexpf(dt, -k) * 0.5f;
+            st.vx[i] = fmaf(a.x, h, st.vx[i]);
+            st.vy[i] = fmaf(a.y, h, st.vy[i]);
+            st.vz[i] = fmaf(a.z, h, st.vz[i]);
+            st.lvl[i] = (uint8_t)k;
+        }
+        warp_max_to(maxlvl, k);
+    }
+}
+
+__global__ void block_kick_kernel(int64_t n, StepState st, const float4 *__restrict__ acc, int64_t T,
+                                  int64_t total, float dt, int K, float eta,
+                                  const int64_t *__restrict__ off, int nsys,
+                                  const float *__restrict__ sys_eps, int32_t *maxlvl) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = b + threadIdx.x;
+        int k = 0;
+        if (i < n) {
+            k = st.lvl[i];
+            if ((T & ((int64_t(1) << (K - k)) - 1)) == 0) {  // active at T
+                const float4 a = acc[i];
+                const float am = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+                const float h = ldexpf(dt, -k) * 0.5f;  // closing half kick of the old step
+                float vx = fmaf(a.x, h, st.vx[i]), vy = fmaf(a.y, h, st.vy[i]),
+                      vz = fmaf(a.z, h, st.vz[i]);
+                st.aold[i] = am;
+                if (T < total) {
+                    int kn = block_level(am, sys_eps[sys_of(off, nsys, i)], eta, dt, K);
+                    // a coarser level only where T is a multiple of its step
+                    while (kn < k && (T & ((int64_t(1) << (K - kn)) - 1)) != 0) kn++;
+                    const float hn = ldexpf(dt, -kn) * 0.5f;
+                    vx = fmaf(a.x, hn, vx);
+                    vy = fmaf(a.y, hn, vy);
+                    vz = fmaf(a.z, hn, vz);
+                    k = kn;
+                    st.lvl[i] = (uint8_t)kn;
+                }
+                st.vx[i] = vx;
+                st.vy[i] = vy;
+                st.vz[i] = vz;
+            }
+        }
+        warp_max_to(maxlvl, k);
+    }
+}
+
+void launch_block_start(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float dt,
+                        int K, float eta, const int64_t *off, int nsys, const float *sys_eps,
+                        int32_t *maxlvl) {
+    block_start_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, dt, K, eta, off, nsys, sys_eps, maxlvl);
+}
+
+void launch_block_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, int64_t T,
+                       int64_t total, float dt, int K, float eta, const int64_t *off, int nsys,
+                       const float *sys_eps, int32_t *maxlvl) {
+    block_kick_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, T, total, dt, K, eta, off, nsys,
+                                                  sys_eps, maxlvl);
+}
+
+// Warp per group: the group is listed when one of its members is active.
+__global__ void block_active_groups_kernel(const DevState *__restrict__ ds,
+                                           const int32_t *__restrict__ grp_first,
+                                           const int32_t *__restrict__ grp_count,
+                                           const uint8_t *__restrict__ lvl, int64_t T, int K,
+                                           int32_t *order, int32_t *count) {
+    const int ng = ds->ngroups;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int g = warp; g < ng; g += nw) {
+        const int first = grp_first[g], cnt = grp_count[g];
+        bool act = false;
+        for (int k = (int)lane_id(); k < cnt; k += 32)
+            act |= (T & ((int64_t(1) << (K - lvl[first + k])) - 1)) == 0;
+        if (__any_sync(NB_FULL, act) && lane_id() == 0) order[atomicAdd(count, 1)] = g;
+    }
+}
+
+void launch_block_active_groups(cudaStream_t s, const DevState *ds, const int32_t *grp_first,
+                                const int32_t *grp_count, const uint8_t *lvl, int64_t T, int K,
+                                int32_t *order, int32_t *count, int nsm) {
+    block_active_groups_kernel<<<nsm * 8, 256, 0, s>>>(ds, grp_first, grp_count, lvl, T, K, order,
+                                                       count);
 }
 
 // ---------------------------------------------------------------- diagnostics

@@ -49,6 +49,8 @@ struct DevState {
     unsigned long long interactions;
     unsigned long long quad_entries;  // list entries that were quadrupole nodes
     int32_t lvl_off[kMaxNL + 1];
+    int32_t block_maxlvl;   // block time steps: deepest occupied level
+    int32_t block_nactive;  // block time steps: groups with an active particle
 };
 
 // Error-free transformations in FP32 (Knuth's TwoSum, Dekker's Fast2Sum)
@@ -224,6 +226,7 @@ struct WalkArgs {
     const float *sys_eps2;
     const int32_t *sys_root;
     DevState *ds;
+    const int32_t *nactive;    // non-NULL: walk only order[0 .. *nactive) (block time steps)
     int32_t *grp_cost;         // list entries per group (NULL: not logged)
     int64_t n;                 // particles (bounds of pos4)
     float G;
@@ -288,7 +291,23 @@ struct StepState {
     float *aold;
     uint32_t *id;    // caller index of each sorted particle
     float *pcost;    // cost of each particle's group in the last walk (may be NULL)
+    uint8_t *lvl;    // block time-step level of each particle (may be NULL)
 };
+// Block time steps (levels 0..K, step dt / 2^k).  block_start: every
+// particle's level from |a| and the opening half kick of its step;
+// block_kick at clock tick T (of total): closing half kick, new level and
+// (T < total) the opening half kick for the particles active at T.  Both
+// record the deepest occupied level in *maxlvl (cleared by the caller).
+void launch_block_start(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float dt,
+                        int K, float eta, const int64_t *off, int nsys, const float *sys_eps,
+                        int32_t *maxlvl);
+void launch_block_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, int64_t T,
+                       int64_t total, float dt, int K, float eta, const int64_t *off, int nsys,
+                       const float *sys_eps, int32_t *maxlvl);
+// The groups holding a particle active at tick T, in *count entries of order.
+void launch_block_active_groups(cudaStream_t s, const DevState *ds, const int32_t *grp_first,
+                                const int32_t *grp_count, const uint8_t *lvl, int64_t T, int K,
+                                int32_t *order, int32_t *count, int nsm);
 // pos4 (nullable): also refresh the FP32 walk copy (x, y, z, m) in place.
 void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
                        float dt, float4 *pos4);

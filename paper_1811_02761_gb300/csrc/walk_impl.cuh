@@ -344,7 +344,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
                                                  (size_t)DQ * 40);
     int *scr = reinterpret_cast<int *>(stk + S);
     DevState *ds = a.ds;
-    const int ng = ds->ngroups;
+    const int ng = a.nactive ? *a.nactive : ds->ngroups;
     const int nnodes = ds->nnodes;
     const int npart = (int)a.n;
     const unsigned lt = lanemask_lt();

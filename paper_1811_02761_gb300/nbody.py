@@ -36,7 +36,8 @@ class Config(C.Structure):
                 ("warps_per_block", C.c_int32), ("compensated", C.c_int32),
                 ("want_potential", C.c_int32), ("schedule", C.c_int32),
                 ("use_graph", C.c_int32), ("rebuild_interval", C.c_int32),
-                ("quadrupole", C.c_int32)]
+                ("quadrupole", C.c_int32), ("block_levels", C.c_int32),
+                ("block_eta", C.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
