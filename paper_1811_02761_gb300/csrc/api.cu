@@ -37,6 +37,7 @@ struct GraphKey {
     int32_t nsys;
     float dt;
     bool safe;
+    bool mlp_norm;  // the cost model's input statistics were set at capture
     nbody_config cfg;
     const void *bufs[8];
 };
@@ -567,14 +568,9 @@ nbody_status compute_order(nbody_ctx *c, const float *pcost, const int32_t **ord
         return fail(c, NBODY_EINVAL, "schedule MLP needs parameters (nbody_mlp_set_params)");
     if (sched == NBODY_SCHED_LASTCOST && !pcost)
         return fail(c, NBODY_EINVAL, "schedule LASTCOST needs a previous walk");
-    int64_t ng = 0;
-    nbody_status st = host_ngroups(c, &ng);
-    if (st != NBODY_OK) return st;
-    if (ng < 1) return NBODY_OK;
-    // With no more groups than resident walk warps every group starts at once:
-    // no order can shorten the walk, and Morton order keeps neighbouring
-    // groups (which read the same nodes) together.
-    if (ng <= c->walk_warps) return NBODY_OK;
+    // The group count stays on the device: every kernel below reads it there
+    // and the sort takes it as its key count, so nothing here waits for the
+    // build and the ordering can be captured in a graph.
     cudaError_t e = ensure_mlp_buffers(c);
     if (e != cudaSuccess) return fail(c, NBODY_ENOMEM, "allocation");
     const int32_t *png = &c->ds->ngroups;
@@ -593,8 +589,8 @@ nbody_status compute_order(nbody_ctx *c, const float *pcost, const int32_t **ord
     // score (MLP: features + forward) and order keys; histogram + passes
     c->kernels += (sched == NBODY_SCHED_MLP ? 3 : 2) + 1 + radix_passes(32);
     if (radix_sort(c->stream, P<uint64_t>(c->okey), P<uint32_t>(c->oval), P<uint64_t>(c->okey_alt),
-                   P<uint32_t>(c->oval_alt), ng, 32, c->rs_temp.p, false, &c->ds->status,
-                   c->nsm)) {
+                   P<uint32_t>(c->oval_alt), std::max<int64_t>(c->cap_n, 1), 32, c->rs_temp.p,
+                   false, &c->ds->status, c->nsm, png)) {
         std::swap(c->okey, c->okey_alt);
         std::swap(c->oval, c->oval_alt);
     }
@@ -1137,10 +1133,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     };
 
     int eager = nsteps;
-    // a cost-ordered queue reads the group count on the host every step, so it
-    // runs eagerly; so do steps that may refit instead of rebuilding
-    if (ctx->cfg.use_graph && nsteps >= 2 && ctx->cfg.schedule == NBODY_SCHED_MORTON &&
-        ctx->cfg.rebuild_interval == 1 && ctx->cfg.block_levels == 0) {
+    // steps that may refit instead of rebuilding, and block steps, run eagerly
+    if (ctx->cfg.use_graph && nsteps >= 2 && ctx->cfg.rebuild_interval == 1 &&
+        ctx->cfg.block_levels == 0) {
         // Two steps per graph: the sort's ping-pong buffers and the state
         // copies swap roles every step, so after two steps every pointer is
         // back where the capture found it and the graph can be replayed.
@@ -1150,6 +1145,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         key.nsys = nsys;
         key.dt = dt;
         key.safe = safe;
+        key.mlp_norm = ctx->mlp_norm_set;
         key.cfg = ctx->cfg;
         key.bufs[0] = ctx->keys.p;
         key.bufs[1] = ctx->vals.p;

@@ -153,11 +153,13 @@ void radix_prepare(cudaStream_t s, int64_t n, void *temp);
 // input order); vals must hold 0..n-1 on entry.  hist_done: the histograms in
 // temp are already complete (launch_keys with sort_temp); else the sort
 // clears temp and computes them.  Device-side failures (a look-back wait
-// that ran out, a destination out of range) are or-ed into *status.
+// that ran out, a destination out of range) are or-ed into *status.  dn
+// (nullable): the key count on the device, n then being an upper bound (no
+// host read, so the sort can be captured in a graph).
 // Returns 1 if the result ended in the alt buffers, else 0.
 int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
                uint32_t *vals_alt, int64_t n, int bits, void *temp, bool hist_done,
-               int32_t *status, int nsm);
+               int32_t *status, int nsm, const int32_t *dn = nullptr);
 int radix_passes(int bits);
 // Runs the radix pass kernel on an input whose look-back can never complete
 // and waits for it; the bounded wait records kStatusTimeout in *status.

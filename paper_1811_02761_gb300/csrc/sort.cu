@@ -297,8 +297,9 @@ __device__ __forceinline__ void hist_zero(uint32_t (*h)[RS_BINS], int passes) {
 }
 
 __global__ void __launch_bounds__(256) rs_hist_kernel(const uint64_t *__restrict__ keys, int64_t n,
-                                                      int passes, uint32_t *hist) {
+                                                      const int32_t *dn, int passes, uint32_t *hist) {
     __shared__ uint32_t h[RS_MAXPASS][RS_BINS];
+    if (dn) n = min(n, (int64_t)max(*dn, 0));
     hist_zero(h, passes);
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
          base += (int64_t)gridDim.x * blockDim.x) {
@@ -426,7 +427,7 @@ template <bool FIRST>
 __global__ void __launch_bounds__(RS_THREADS, 2) rs_onesweep_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, int shift, int pass, int ntiles, void *temp,
-    int32_t *status) {
+    int32_t *status, const int32_t *dn) {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     RsShared &S = *reinterpret_cast<RsShared *>(rs_smem);
     uint32_t *counter = (uint32_t *)temp;
@@ -435,14 +436,19 @@ __global__ void __launch_bounds__(RS_THREADS, 2) rs_onesweep_kernel(
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     const int d = threadIdx.x;  // the digit this thread scans and looks back for
 
+    if (dn) {  // the key count lives on the device; n and the grid are bounds
+        n = min(n, (int64_t)max(*dn, 0));
+        ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    }
     if (threadIdx.x == 0) {
         S.tile = (int)atomicAdd(&counter[pass], 1u);
         S.flags = 0;
     }
-    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&S.u.whist[0][0])[i] = 0;
     __syncthreads();
     const int tile = S.tile;
-    if (tile >= ntiles) return;  // block-uniform; the grid has exactly ntiles CTAs
+    if (tile >= ntiles) return;  // block-uniform; the grid has at least ntiles CTAs
+    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&S.u.whist[0][0])[i] = 0;
+    __syncthreads();
     const uint32_t hd = hist[d];
     const int64_t base = (int64_t)tile * RS_TILE;
     const int valid = (int)((n - base) < RS_TILE ? (n - base) : RS_TILE);
@@ -571,7 +577,7 @@ void radix_prepare(cudaStream_t s, int64_t n, void *temp) {
 
 int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
                uint32_t *vals_alt, int64_t n, int bits, void *temp, bool hist_done,
-               int32_t *status, int nsm) {
+               int32_t *status, int nsm, const int32_t *dn) {
     static bool attr_done = false;
     if (!attr_done) {
         cudaFuncSetAttribute(rs_onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -586,7 +592,8 @@ int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_al
         int64_t b = (n + 255) / 256;
         int blocks = (int)(b < (int64_t)nsm * 8 ? b : (int64_t)nsm * 8);
         if (blocks < 1) blocks = 1;
-        rs_hist_kernel<<<blocks, 256, 0, s>>>(keys, n, passes, (uint32_t *)((char *)temp + RS_OFF_HIST));
+        rs_hist_kernel<<<blocks, 256, 0, s>>>(keys, n, dn, passes,
+                                              (uint32_t *)((char *)temp + RS_OFF_HIST));
     }
     const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
     uint64_t *kin = keys, *kout = keys_alt;
@@ -595,10 +602,10 @@ int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_al
         const int shift = p * RS_BITS;
         if (p == 0)
             rs_onesweep_kernel<true><<<ntiles, RS_THREADS, sizeof(RsShared), s>>>(
-                kin, vin, kout, vout, n, shift, p, ntiles, temp, status);
+                kin, vin, kout, vout, n, shift, p, ntiles, temp, status, dn);
         else
             rs_onesweep_kernel<false><<<ntiles, RS_THREADS, sizeof(RsShared), s>>>(
-                kin, vin, kout, vout, n, shift, p, ntiles, temp, status);
+                kin, vin, kout, vout, n, shift, p, ntiles, temp, status, dn);
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
     }
@@ -629,7 +636,7 @@ cudaError_t radix_selftest_wait(cudaStream_t s, int32_t *status) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(temp, &one, sizeof one, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         rs_onesweep_kernel<true><<<1, RS_THREADS, sizeof(RsShared), s>>>(kin, vin, kout, vout, n, 0, 0,
-                                                                         2, temp, status);
+                                                                         2, temp, status, nullptr);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamSynchronize(s);

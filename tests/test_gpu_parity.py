@@ -399,15 +399,20 @@ def test_sort_lookback_wait_is_bounded(plummer8k):
 
 
 # --------------------------------------------------------------------------- CUDA graph
-@pytest.mark.parametrize("nsteps", [4, 5])
-def test_step_graph_equals_eager(nsteps):
-    """The two-step CUDA graph replays exactly the eager launch sequence."""
-    sizes = [3000, 1, 700, 5000]
+@pytest.mark.parametrize("nsteps,schedule", [(4, 0), (5, 0), (4, 1), (5, 2)])
+def test_step_graph_equals_eager(nsteps, schedule):
+    """The two-step CUDA graph replays exactly the eager launch sequence, also
+    with a cost-ordered queue (the ordering reads the group count on the
+    device, so it is captured with the step)."""
+    sizes = [3000, 1, 700, 5000, 20000]
     b = ics.batched(len(sizes), 9, sizes=sizes)
     n = int(b["offsets"][-1])
     res = []
     for graph in (0, 1):
-        ctx = nb.nbody_create(nb.nbody_config_default(delta_acc=DACC, use_graph=graph))
+        ctx = nb.nbody_create(nb.nbody_config_default(delta_acc=DACC, use_graph=graph,
+                                                      group_size=32, ipl=1, schedule=schedule))
+        if schedule == nb.SCHED_MLP:
+            nb.nbody_mlp_set_params(ctx, ics.mlp_init(3))
         try:
             X = [dev(b[k].astype(np.float64)) for k in ("x", "y", "z")]
             V = [dev(b[k]) for k in ("vx", "vy", "vz")]
