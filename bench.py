@@ -46,8 +46,8 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_write.sum) on the N=2^22 galaxy, per particle; the launch at the
 # bench's N is scaled by particles.  It is reported only while the walk source
 # is the one the counters were taken on (sha256 of walk_impl.cuh).
-WALK_TRAFFIC = {"bytes_per_particle": (108.068352e6 + 44.594432e6) / 4194304,
-                "walk_impl_sha256": "1c9fef915d19ae87b6974fe5dfb67df19972272ccf631ea31aceb1e61f650979",
+WALK_TRAFFIC = {"bytes_per_particle": (108.531968e6 + 44.886016e6) / 4194304,
+                "walk_impl_sha256": "7d21c4be15788de7a574ec078a579bf11bcbc0270c6a2692ca4424749344e72d",
                 "capture": "profiles/walk_kernel_galaxy_2e22.md (N=2^22, scaled by particles)"}
 
 

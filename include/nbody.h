@@ -115,6 +115,12 @@ typedef struct {
                             processed tick.                                 */
     float block_eta;     /* accuracy parameter of the block step criterion
                             (default 0.025), > 0                             */
+    int32_t walk_pipeline; /* 1: the walk runs in warp pairs, one warp
+                            traversing the tree and handing interaction lists
+                            through shared memory to one warp evaluating Eq. 1
+                            (monopole walks without the potential; identical
+                            results); needs an even warps_per_block.  0: each
+                            warp traverses and evaluates (default)          */
 } nbody_config;
 
 typedef struct {

@@ -194,6 +194,9 @@ bool config_ok(const nbody_config *c, std::string &why) {
         return bad("rebuild_interval must be in 0..1024");
     if (c->quadrupole != 0 && c->quadrupole != 1) return bad("quadrupole must be 0 or 1");
     if (c->block_levels < 0 || c->block_levels > 20) return bad("block_levels must be in 0..20");
+    if (c->walk_pipeline != 0 && c->walk_pipeline != 1) return bad("walk_pipeline must be 0 or 1");
+    if (c->walk_pipeline && c->warps_per_block % 2)
+        return bad("walk_pipeline needs an even warps_per_block (warp pairs)");
     if (!(c->block_eta > 0.0f) || !std::isfinite(c->block_eta)) return bad("block_eta must be finite and > 0");
     size_t smem = (size_t)c->warps_per_block *
                   nb::walk_smem_per_warp(c->list_depth, c->stack_depth, c->quadrupole != 0);
@@ -474,6 +477,7 @@ WalkShape walk_shape(nbody_ctx *c, bool geometric, bool phi, bool safe) {
     sh.compensated = c->cfg.compensated != 0;
     sh.safe = safe;
     sh.quad = c->cfg.quadrupole != 0;
+    sh.pipeline = c->cfg.walk_pipeline != 0;
     sh.warps_per_block = c->cfg.warps_per_block;
     sh.warps_launched = &c->walk_warps;
     return sh;
@@ -685,6 +689,7 @@ void nbody_config_default(nbody_config *c) {
     c->quadrupole = 0;
     c->block_levels = 0;
     c->block_eta = 0.025f;
+    c->walk_pipeline = 0;
 }
 
 nbody_status nbody_create(nbody_ctx **out, const nbody_config *cfg, void *cuda_stream) {

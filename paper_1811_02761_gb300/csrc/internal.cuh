@@ -247,6 +247,7 @@ struct WalkShape {
     bool compensated;
     bool safe;                  // some eps == 0: guard the self term
     bool quad;                  // accepted nodes add their quadrupole
+    bool pipeline;              // warp pairs: traversal and evaluation (monopole, no potential)
     int warps_per_block;
     int *warps_launched;        // host, nullable: receives the resident walk warps
 };

@@ -13,7 +13,24 @@ NB_WALK_EXTERN(1, false) NB_WALK_EXTERN(2, false) NB_WALK_EXTERN(3, false) NB_WA
 NB_WALK_EXTERN(1, true) NB_WALK_EXTERN(2, true) NB_WALK_EXTERN(3, true) NB_WALK_EXTERN(4, true)
 #undef NB_WALK_EXTERN
 
+template <int IPL>
+cudaError_t launch_walk_pipe_ipl(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm);
+#define NB_PIPE_EXTERN(I) \
+    extern template cudaError_t launch_walk_pipe_ipl<I>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
+NB_PIPE_EXTERN(1) NB_PIPE_EXTERN(2) NB_PIPE_EXTERN(3) NB_PIPE_EXTERN(4)
+#undef NB_PIPE_EXTERN
+
 cudaError_t launch_walk(cudaStream_t s, const WalkArgs &a, const WalkShape &sh, int nsm) {
+    if (sh.pipeline && !sh.quad && !sh.potential) {
+        if (sh.warps_per_block % 2) return cudaErrorInvalidConfiguration;
+        switch (sh.ipl) {
+            case 1: return launch_walk_pipe_ipl<1>(s, a, sh, nsm);
+            case 2: return launch_walk_pipe_ipl<2>(s, a, sh, nsm);
+            case 3: return launch_walk_pipe_ipl<3>(s, a, sh, nsm);
+            case 4: return launch_walk_pipe_ipl<4>(s, a, sh, nsm);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (sh.quad) {
         switch (sh.ipl) {
             case 1: return launch_walk_ipl<1, true>(s, a, sh, nsm);

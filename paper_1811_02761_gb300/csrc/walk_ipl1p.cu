@@ -1,0 +1,8 @@
+// walk_ipl1p.cu -- instances of the warp-specialised tree walk with up to 1
+// i-particle per lane (separate translation unit so the instances compile
+// in parallel).
+#include "walk_pipe.cuh"
+
+namespace nb {
+template cudaError_t launch_walk_pipe_ipl<1>(cudaStream_t, const WalkArgs &, const WalkShape &, int);
+}  // namespace nb

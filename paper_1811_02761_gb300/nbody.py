@@ -37,7 +37,7 @@ class Config(C.Structure):
                 ("want_potential", C.c_int32), ("schedule", C.c_int32),
                 ("use_graph", C.c_int32), ("rebuild_interval", C.c_int32),
                 ("quadrupole", C.c_int32), ("block_levels", C.c_int32),
-                ("block_eta", C.c_float)]
+                ("block_eta", C.c_float), ("walk_pipeline", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
