@@ -55,7 +55,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_addr(bar)), "r"(parity)
@@ -63,7 +63,8 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Wait (all lanes) until the phase with this parity has completed; false if
-// the bounded number of polls ran out.
+// the bounded number of polls ran out.  test_wait never blocks, so the bound
+// is kPipeSpinLimit polls of about 0.1 us each.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     bool done = false;
     if (lane_id() == 0) {
