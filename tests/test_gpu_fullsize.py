@@ -98,3 +98,59 @@ def test_fullsize_sampled_parity(full):
     assert np.median(d) < 5e-6
     # the GPU's groups are the oracle's groups
     assert np.array_equal(ex[nb.nbody.EXPORT_GROUP_FIRST], f.astype(np.int32))
+
+
+def test_fullsize_batched_sampled_parity():
+    """The batched workload at its full size (512 Plummer/Hernquist systems,
+    about 6.9M particles, the benchmark's seed): one forest step exactly as the
+    benchmark launches its steps (one sort, one forest, one persistent walk),
+    then sampled accelerations of 24 seeded systems against each system's
+    FP64 direct sum and its own oracle tree (same a_old, the forest's depth
+    of 18 levels), by the p50/p99 rule."""
+    b = ics.batched(512, 4)
+    off, eps = b["offsets"], b["eps"]
+    n = int(off[-1])
+
+    def D(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    X64 = [D(b[k].astype(np.float64)) for k in ("x", "y", "z")]
+    V = [D(b[k]) for k in ("vx", "vy", "vz")]
+    M = D(b["m"])
+    A = [torch.zeros(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    ctx = nb.nbody_create(nb.nbody_config_default(delta_acc=DACC))
+    try:
+        nb.nbody_build_batched(ctx, off, eps, *[D(b[k]) for k in ("x", "y", "z")], M)
+        nb.nbody_walk(ctx, None, *A)
+        amag = torch.sqrt(A[0] ** 2 + A[1] ** 2 + A[2] ** 2).cpu().numpy()
+        nb.nbody_step_batched(ctx, off, eps, *X64, *V, M, *A, DT, 1)
+        g = [a.cpu().numpy().astype(np.float64) for a in A]
+        pos = [x.float().cpu().numpy().astype(np.float64) for x in X64]
+    finally:
+        nb.nbody_destroy(ctx)
+    m = b["m"].astype(np.float64)
+    levels = (63 - 9) // 3
+    r = ics.rng(4, 78)
+    systems = r.choice(512, 24, replace=False)
+    eg, eo = [], []
+    for s in systems:
+        sl = slice(int(off[s]), int(off[s + 1]))
+        ns = off[s + 1] - off[s]
+        if ns < 2:
+            continue
+        xs = [q[sl] for q in pos]
+        tg = r.choice(ns, min(16, ns), replace=False)
+        bx, by, bz, _ = oracle.direct_targets(*xs, m[sl], tg, 1.0, float(eps[s]))
+        eg.append(oracle.rel_err(g[0][sl][tg], g[1][sl][tg], g[2][sl][tg], bx, by, bz))
+        t = oracle.Tree(*xs, m[sl], levels, 16)
+        f, c = t.groups(64)
+        where = np.empty(ns, np.int64)
+        where[t.order()] = np.arange(ns)
+        sel = np.unique(np.searchsorted(f, where[tg], side="right") - 1)
+        ox, oy, oz, _ = t.walk_groups(sel, oracle.MAC_GROUP_ACC, 1.0, float(eps[s]), DACC, 0.5, 64,
+                                      amag[sl].astype(np.float64))
+        eo.append(oracle.rel_err(ox[tg], oy[tg], oz[tg], bx, by, bz))
+    eg, eo = np.concatenate(eg), np.concatenate(eo)
+    assert eg.size >= 300
+    for q in (50, 99):
+        pg, po = oracle.percentile_nearest_rank(eg, q), oracle.percentile_nearest_rank(eo, q)
+        assert pg <= 1.1 * po + 1e-6, (q, pg, po)
