@@ -564,6 +564,14 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                  node_count, node_nchild, nodeA, nodeB, mass2, nodeQ, nsm, false);
 }
 
+// CTAs per SM of the moment passes (build-time tunable).
+#ifndef NB_LEAF_CTAS_PER_SM
+#define NB_LEAF_CTAS_PER_SM 32
+#endif
+#ifndef NB_INTERNAL_CTAS_PER_SM
+#define NB_INTERNAL_CTAS_PER_SM 16
+#endif
+
 // Moments of every node of the current tree from pos4: leaves in one launch
 // (one warp per 32 nodes), internal nodes one launch per level, deepest
 // first (level `levels` holds leaves only).
@@ -573,7 +581,7 @@ void tree_moments(cudaStream_t s, const Layout &L, const uint64_t *keys, const f
                   int32_t *node_count, const int32_t *node_nchild, float4 *nodeA, float4 *nodeB,
                   float2 *mass2, float4 *nodeQ, int nsm, bool refit) {
     int64_t mb = (L.n / 4 + 255) / 256;
-    if (mb > (int64_t)nsm * 8) mb = (int64_t)nsm * 8;
+    if (mb > (int64_t)nsm * NB_LEAF_CTAS_PER_SM) mb = (int64_t)nsm * NB_LEAF_CTAS_PER_SM;
     if (mb < 1) mb = 1;
     if (leaf_cap <= 4)
         leaf_moments_kernel<4><<<(int)mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start,
@@ -583,7 +591,7 @@ void tree_moments(cudaStream_t s, const Layout &L, const uint64_t *keys, const f
         leaf_moments_kernel<8><<<(int)mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start,
                                                        node_level, node_link, node_count,
                                                        node_nchild, nodeA, nodeB, mass2, nodeQ);
-    const int ib = nsm * 4;
+    const int ib = nsm * NB_INTERNAL_CTAS_PER_SM;
     for (int l = L.levels - 1; l >= 0; l--)
         internal_moments_kernel<<<ib, 256, 0, s>>>(L, l, refit ? 1 : 0, keys, d_box, G, ds,
                                                    node_start, node_link, node_count, node_nchild,
