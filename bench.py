@@ -534,6 +534,28 @@ def batched_schedules(args, off, eps, parts, stream, dev):
             "train_losses_first_last": [losses[0], losses[-1]] if losses else None}
 
 
+def schedule_makespans(cost, pred, workers):
+    """How much any queue order could gain: list scheduling of the groups
+    (time taken as proportional to the logged list entries of each group)
+    onto `workers` walk warps in Morton order, in descending predicted cost
+    and in descending true cost, against the lower bound max(total / workers,
+    largest group).  Locality effects are not modelled."""
+    import heapq
+
+    def makespan(order):
+        h = [0.0] * workers
+        for g in order:
+            heapq.heapreplace(h, h[0] + cost[g])
+        return max(h)
+
+    lb = max(cost.sum() / workers, cost.max())
+    return {"workers": workers, "groups": int(cost.size),
+            "morton_over_bound": makespan(range(cost.size)) / lb,
+            "predicted_order_over_bound": makespan(np.argsort(-pred, kind="stable")) / lb,
+            "true_lpt_over_bound": makespan(np.argsort(-cost, kind="stable")) / lb,
+            "note": "group time taken proportional to its list entries"}
+
+
 # ---------------------------------------------------------------------------- learned schedule
 def run_learned(args, rank, world, local_rank):
     """Galaxy at N = 25 * 2^20: the cost model is trained online on the first
@@ -568,13 +590,15 @@ def run_learned(args, rank, world, local_rank):
         losses = []
         t0 = time.perf_counter()
         for _ in range(args.train_steps):
-            nb.nbody_step(ctx, *X, *V, M, *A, DT, 1)
+            st_train = nb.nbody_step(ctx, *X, *V, M, *A, DT, 1)
             losses.append(nb.nbody_mlp_train(ctx, epochs=args.train_epochs, lr=2e-3, batch=4096))
         train_s = time.perf_counter() - t0
         pred, _ = nb.nbody_mlp_predict(ctx)
         cost = np.empty(pred.size, np.int32)
         nb.nbody_get_group_costs(ctx, cost)
         corr = float(np.corrcoef(pred, np.log2(np.maximum(cost, 1)))[0, 1])
+
+        sched_model = schedule_makespans(cost.astype(np.float64), pred, int(st_train.walk_warps))
         snap = [t.clone() for t in X + V + A]
         runs = args.steps - args.train_steps
         finals = {}
@@ -618,6 +642,7 @@ def run_learned(args, rank, world, local_rank):
         "bitwise_identical_final_states": same,
         "train": {"losses_first_last": [losses[0], losses[-1]], "seconds": train_s,
                   "pred_vs_cost_correlation": corr},
+        "schedule_model": sched_model,
     }
 
 

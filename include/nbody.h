@@ -13,7 +13,13 @@
  *     (Sect. 1) and distant nodes are accepted by the acceleration MAC of Eq. 2
  *       G m_J / d^2 (b_J / d)^2 <= delta_acc |a_i^old|,
  *   - leapfrog kick-drift-kick orbit integration (the paper's code uses a
- *     second-order Runge-Kutta scheme; this library integrates with leapfrog).
+ *     second-order Runge-Kutta scheme; this library integrates with leapfrog),
+ *     with one shared step or block (hierarchical) steps (Sect. 1), the tree
+ *     rebuilt every step or refitted between rebuilds at an interval that can
+ *     be tuned by timing (Sect. 1 and 4.1);
+ *   - optionally, quadrupole moments for the nodes (an extension beyond the
+ *     paper's monopoles), many independent systems in one forest and one
+ *     walk, and a learned cost model that orders the walk's queue.
  *
  * Conventions for every entry point
  *   - Pointers may be device pointers or host pointers (pageable or pinned);
@@ -23,8 +29,9 @@
  *     order; the library's internal Morton order never leaks out.
  *   - Every call returns an nbody_status; no C++ exception crosses the ABI.
  *     Argument errors are detected before any launch.  Device-side errors
- *     (traversal stack overflow) are reported through a device status word
- *     that the call reads after synchronising its stream.
+ *     (traversal stack overflow, an index that failed a bounds check, a
+ *     bounded device wait that ran out) are reported through a device status
+ *     word that the call reads after synchronising its stream.
  *   - All work of a context is enqueued on the stream given at creation
  *     (NULL = the legacy default stream).  A context is not thread-safe.
  *   - Calls that return results synchronise the context's stream before
@@ -140,6 +147,8 @@ typedef struct {
                               tree (the others refitted it)                    */
     int64_t quad_interactions; /* of `interactions`, those with quadrupole
                               nodes (quadrupole = 1)                          */
+    int32_t walk_warps;    /* resident walk warps (queue consumers) of the last
+                              walk launch                                      */
 } nbody_stats;
 
 typedef struct nbody_ctx nbody_ctx;

@@ -868,6 +868,7 @@ nbody_status nbody_walk(nbody_ctx *ctx, const float *a_old, float *ax, float *ay
     ctx->last.interactions = (int64_t)ctx->h_ds->interactions;
     ctx->last.list_entries = (int64_t)ctx->h_ds->list_entries;
     ctx->last.quad_interactions = (int64_t)ctx->h_ds->quad_entries;
+    ctx->last.walk_warps = ctx->walk_warps;
     ctx->last.max_stack = ctx->h_ds->max_stack;
     ctx->last.ms_walk = ms;
     ctx->last.ms_walk_kernel = collect_walk_ms(ctx, &ctx->last.walk_launches);
@@ -1090,9 +1091,15 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     // or refits the current one (moments and group spheres at the drifted
     // positions, which the kick-drift writes to pos4 in place).
     int rebuilds = 0;
+    // Eager steps defer their closing half kick into the next step's
+    // kick-drift pass (pending_kick); graph steps keep it separate so that
+    // every replay starts from the same state.
+    bool pending_kick = false;
     auto one_step = [&](bool timing, bool rebuild) -> nbody_status {
         cudaStream_t q = ctx->stream;
-        launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt, rebuild ? nullptr : P<float4>(ctx->pos4));
+        launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt, rebuild ? nullptr : P<float4>(ctx->pos4),
+                          pending_kick ? 0.5f * dt : 0.0f);
+        pending_kick = false;
         ctx->kernels += 1;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         if (timing) {
@@ -1132,8 +1139,12 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             NB_CUDA(ctx, cudaEventRecord(e2, q));
             marks.push_back(ctx->evused - 3);
         }
-        launch_kick(q, n, S[cur], acc, 0.5f * dt);
-        ctx->kernels += 1;
+        if (ctx->capturing || dt == 0.0f) {
+            launch_kick(q, n, S[cur], acc, 0.5f * dt);
+            ctx->kernels += 1;
+        } else {
+            pending_kick = true;
+        }
         return NBODY_OK;
     };
 
@@ -1236,6 +1247,11 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             cycle.push_back(c);
         }
     }
+    if (pending_kick) {  // the last eager step's closing half kick
+        launch_kick(s, n, S[cur], acc, 0.5f * dt);
+        ctx->kernels += 1;
+        pending_kick = false;
+    }
     // in[] are the device copies (the caller's arrays themselves when on the device)
     launch_store_state(s, n, S[cur], acc, (double *)in[0], (double *)in[1], (double *)in[2],
                        (float *)in[3], (float *)in[4], (float *)in[5], (float *)in[7],
@@ -1265,6 +1281,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     ctx->last.interactions = (int64_t)ctx->h_ds->interactions;
     ctx->last.list_entries = (int64_t)ctx->h_ds->list_entries;
     ctx->last.quad_interactions = (int64_t)ctx->h_ds->quad_entries;
+    ctx->last.walk_warps = ctx->walk_warps;
     ctx->last.max_stack = ctx->h_ds->max_stack;
     ctx->last.ms_build = ms_build;
     ctx->last.ms_walk = ms_walk;

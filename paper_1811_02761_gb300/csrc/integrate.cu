@@ -20,13 +20,27 @@ static inline int grid_for(int64_t n, int threads = 256) {
 #define NB_GRID_LOOP(i, n) \
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// |a| as the next step's a_old (one expression for every kernel that sets it).
+__device__ __forceinline__ float acc_mag(float4 a) {
+    return sqrtf(fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x)));
+}
+
+// hclose != 0: first the closing half kick of the previous step (and its
+// a_old), fused into this pass; the same two roundings as two kernels.
 __global__ void kick_drift_kernel(int64_t n, StepState st, const float4 *__restrict__ acc,
-                                  float hdt, double dt, float4 *pos4) {
+                                  float hclose, float hdt, double dt, float4 *pos4) {
     NB_GRID_LOOP(i, n) {
         float4 a = acc[i];
-        float vx = fmaf(a.x, hdt, st.vx[i]);
-        float vy = fmaf(a.y, hdt, st.vy[i]);
-        float vz = fmaf(a.z, hdt, st.vz[i]);
+        float vx = st.vx[i], vy = st.vy[i], vz = st.vz[i];
+        if (hclose != 0.0f) {
+            vx = fmaf(a.x, hclose, vx);
+            vy = fmaf(a.y, hclose, vy);
+            vz = fmaf(a.z, hclose, vz);
+            st.aold[i] = acc_mag(a);
+        }
+        vx = fmaf(a.x, hdt, vx);
+        vy = fmaf(a.y, hdt, vy);
+        vz = fmaf(a.z, hdt, vz);
         st.vx[i] = vx;
         st.vy[i] = vy;
         st.vz[i] = vz;
@@ -46,13 +60,13 @@ __global__ void kick_kernel(int64_t n, StepState st, const float4 *__restrict__ 
         st.vx[i] = fmaf(a.x, hdt, st.vx[i]);
         st.vy[i] = fmaf(a.y, hdt, st.vy[i]);
         st.vz[i] = fmaf(a.z, hdt, st.vz[i]);
-        st.aold[i] = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+        st.aold[i] = acc_mag(a);
     }
 }
 
 void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
-                       float dt, float4 *pos4) {
-    kick_drift_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, hdt, (double)dt, pos4);
+                       float dt, float4 *pos4, float hclose) {
+    kick_drift_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, hclose, hdt, (double)dt, pos4);
 }
 
 void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt) {
@@ -167,7 +181,7 @@ __global__ void block_start_kernel(int64_t n, StepState st, const float4 *__rest
         int k = 0;
         if (i < n) {
             const float4 a = acc[i];
-            const float am = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+            const float am = acc_mag(a);
             k = block_level(am, sys_eps[sys_of(off, nsys, i)], eta, dt, K);
             const float h = ldexpf(dt, -k) * 0.5f;
             st.vx[i] = fmaf(a.x, h, st.vx[i]);
@@ -190,7 +204,7 @@ __global__ void block_kick_kernel(int64_t n, StepState st, const float4 *__restr
             k = st.lvl[i];
             if ((T & ((int64_t(1) << (K - k)) - 1)) == 0) {  // active at T
                 const float4 a = acc[i];
-                const float am = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+                const float am = acc_mag(a);
                 const float h = ldexpf(dt, -k) * 0.5f;  // closing half kick of the old step
                 float vx = fmaf(a.x, h, st.vx[i]), vy = fmaf(a.y, h, st.vy[i]),
                       vz = fmaf(a.z, h, st.vz[i]);

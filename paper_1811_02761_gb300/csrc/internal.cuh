@@ -312,8 +312,10 @@ void launch_block_active_groups(cudaStream_t s, const DevState *ds, const int32_
                                 const int32_t *grp_count, const uint8_t *lvl, int64_t T, int K,
                                 int32_t *order, int32_t *count, int nsm);
 // pos4 (nullable): also refresh the FP32 walk copy (x, y, z, m) in place.
+// hclose != 0: apply the previous step's closing half kick (v += a hclose,
+// a_old = |a|) first, as the kick kernel would.
 void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
-                       float dt, float4 *pos4);
+                       float dt, float4 *pos4, float hclose = 0.0f);
 void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt);
 void launch_permute_state(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
                           StepState dst, float4 *pos4);

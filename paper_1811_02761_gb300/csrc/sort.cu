@@ -14,6 +14,12 @@
 
 namespace nb {
 
+// CTAs per SM of the grid-strided passes over the particles (cube, keys),
+// build-time tunable.
+#ifndef NB_SCAN_CTAS_PER_SM
+#define NB_SCAN_CTAS_PER_SM 8
+#endif
+
 // ---------------------------------------------------------------- bounding cube
 // Per-system bounding box: each warp keeps running min/max while its chunks
 // stay in one system, the block merges its warps, and one set of atomics per
@@ -162,7 +168,7 @@ void launch_bbox(cudaStream_t s, const Layout &L, const void *x, const void *y, 
     bbox_init_kernel<<<(L.nsys * 6 + 255) / 256, 256, 0, s>>>(L.nsys, d_boxord);
     int64_t warps = (L.n + 255) / 256;
     int blocks = (int)((warps + 7) / 8);
-    int maxb = nsm * 8;
+    int maxb = nsm * NB_SCAN_CTAS_PER_SM;
     if (blocks > maxb) blocks = maxb;
     if (blocks < 1) blocks = 1;
     if (dbl)
@@ -215,7 +221,13 @@ constexpr int RS_BINS = 1 << RS_BITS;
 constexpr int RS_MAXPASS = 8;
 constexpr int RS_THREADS = 512;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_IPT = 8;
+#ifndef NB_RS_IPT
+#define NB_RS_IPT 8  // keys per thread of a radix pass (build-time tunable)
+#endif
+#ifndef NB_RS_MIN_CTAS
+#define NB_RS_MIN_CTAS 2  // resident CTAs per SM the pass kernel is compiled for
+#endif
+constexpr int RS_IPT = NB_RS_IPT;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
 constexpr int RS_SPIN_LIMIT = 1 << 20;
 constexpr int RS_LB = 4;  // look-back words loaded per round trip
@@ -349,7 +361,7 @@ void launch_keys(cudaStream_t s, const Layout &L, const void *x, const void *y, 
                  bool dbl, const int64_t *d_off, const SysBox *d_box, uint64_t *keys,
                  uint32_t *vals, void *sort_temp, int nsm) {
     int64_t b = (L.n + 255) / 256;
-    int blocks = (int)(b < (int64_t)nsm * 8 ? b : (int64_t)nsm * 8);
+    int blocks = (int)(b < (int64_t)nsm * NB_SCAN_CTAS_PER_SM ? b : (int64_t)nsm * NB_SCAN_CTAS_PER_SM);
     if (blocks < 1) blocks = 1;
     const int passes = (L.keybits + RS_BITS - 1) / RS_BITS;
     uint32_t *hist = sort_temp ? (uint32_t *)((char *)sort_temp + RS_OFF_HIST) : nullptr;
@@ -424,7 +436,7 @@ struct RsShared {
 // One pass over the digit at `shift`.  vin is ignored on the first pass
 // (values = input positions).
 template <bool FIRST>
-__global__ void __launch_bounds__(RS_THREADS, 2) rs_onesweep_kernel(
+__global__ void __launch_bounds__(RS_THREADS, NB_RS_MIN_CTAS) rs_onesweep_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, int shift, int pass, int ntiles, void *temp,
     int32_t *status, const int32_t *dn) {

@@ -564,6 +564,10 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                  node_count, node_nchild, nodeA, nodeB, mass2, nodeQ, nsm, false);
 }
 
+// CTAs per SM of the warp-per-group passes (sphere, alpha), build-time tunable.
+#ifndef NB_GROUP_CTAS_PER_SM
+#define NB_GROUP_CTAS_PER_SM 8
+#endif
 // CTAs per SM of the moment passes (build-time tunable).
 #ifndef NB_LEAF_CTAS_PER_SM
 #define NB_LEAF_CTAS_PER_SM 32
@@ -747,7 +751,7 @@ void build_groups(cudaStream_t s, const Layout &L, int group_size, const float4 
     flag_count_kernel<<<nb, FL_T, 0, s>>>(gflag, L.n, bsum);
     launch_scan_sums(s, bsum, nb, &ds->ngroups);
     flag_write_kernel<<<nb, FL_T, 0, s>>>(gflag, L.n, bsum, grp_first);
-    int gb = nsm * 8;
+    int gb = nsm * NB_GROUP_CTAS_PER_SM;
     group_info_kernel<<<gb, 256, 0, s>>>(L, group_size, pos4, d_off, ds, grp_first, grp_count,
                                          grp_sphere, grp_sys);
 }
@@ -757,7 +761,7 @@ void build_groups(cudaStream_t s, const Layout &L, int group_size, const float4 
 void refit_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
                   const int64_t *d_off, DevState *ds, const int32_t *grp_first,
                   int32_t *grp_count, float4 *grp_sphere, int32_t *grp_sys, int nsm) {
-    group_info_kernel<<<nsm * 8, 256, 0, s>>>(L, group_size, pos4, d_off, ds, grp_first, grp_count,
+    group_info_kernel<<<nsm * NB_GROUP_CTAS_PER_SM, 256, 0, s>>>(L, group_size, pos4, d_off, ds, grp_first, grp_count,
                                               grp_sphere, grp_sys);
 }
 
@@ -783,7 +787,7 @@ void launch_group_alpha(cudaStream_t s, int64_t n, const DevState *ds, const int
                         const int32_t *grp_count, const float *aold_sorted, float delta_acc,
                         float *grp_alpha, int nsm) {
     (void)n;
-    group_alpha_kernel<<<nsm * 8, 256, 0, s>>>(ds, grp_first, grp_count, aold_sorted, delta_acc,
+    group_alpha_kernel<<<nsm * NB_GROUP_CTAS_PER_SM, 256, 0, s>>>(ds, grp_first, grp_count, aold_sorted, delta_acc,
                                                 grp_alpha);
 }
 

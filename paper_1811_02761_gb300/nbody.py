@@ -57,7 +57,8 @@ class Stats(C.Structure):
                 ("list_entries", C.c_int64), ("max_stack", C.c_int32), ("levels", C.c_int32),
                 ("kernels", C.c_int64), ("ms_build", C.c_float), ("ms_walk", C.c_float),
                 ("ms_walk_kernel", C.c_float), ("walk_launches", C.c_int32),
-                ("rebuilds", C.c_int32), ("quad_interactions", C.c_int64)]
+                ("rebuilds", C.c_int32), ("quad_interactions", C.c_int64),
+                ("walk_warps", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
