@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--train-epochs", type=int, default=2)
     ap.add_argument("--schedules", action="store_true",
                     help="batched: also train the cost model and time each queue schedule")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batched: also autotune leaf capacity, group size, i-particles per lane, "
+                         "list depth and warps per CTA on the forest and time the tuned step")
     ap.add_argument("--per-system-steps", type=int, default=2,
                     help="batched: steps timed for the one-call-per-system comparison")
     ap.add_argument("--n", type=int, default=1 << 23)
@@ -436,6 +439,8 @@ def run_batched(args, rank, world, local_rank):
     finally:
         nb.nbody_destroy(ctx)
     sched = batched_schedules(args, off, eps, parts, stream, dev) if args.schedules else None
+    tuned = batched_autotune(args, off, eps, parts, stream, dev, elapsed / args.steps) \
+        if args.autotune else None
     t = torch.tensor([elapsed, float(st.interactions)], dtype=torch.float64, device=dev)
     if world > 1:
         tm = t[:1].clone()
@@ -464,9 +469,55 @@ def run_batched(args, rank, world, local_rank):
                                         "and step, eager launches"},
         "speedup_vs_per_system": per_sys / s_per_step,
         "schedules": sched,
+        "autotune": tuned,
         "interactions_per_step": float(st.interactions) / args.steps,
         "gpu_launches": int(st.kernels),
     }
+
+
+def batched_autotune(args, off, eps, parts, stream, dev, default_s_per_step):
+    """The autotuner's grid search (nbody_autotune: build + walk timed with
+    CUDA events per candidate) on the batched forest, then the same graph
+    steps as the default run with the tuned parameters."""
+    import torch
+
+    import paper_1811_02761_gb300 as nb
+
+    def D(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    n = int(off[-1])
+    X32 = [D(parts[k]) for k in ("x", "y", "z")]
+    X = [D(parts[k].astype(np.float64)) for k in ("x", "y", "z")]
+    V = [D(parts[k]) for k in ("vx", "vy", "vz")]
+    M = D(parts["m"])
+    A = [torch.zeros(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    ctx = nb.nbody_create(nb.nbody_config_default(delta_acc=DACC, use_graph=1), stream)
+    try:
+        nb.nbody_build_batched(ctx, off, eps, *X32, M)
+        nb.nbody_walk(ctx, None, *A)
+        amag = torch.sqrt(A[0] ** 2 + A[1] ** 2 + A[2] ** 2).contiguous()
+        w0 = time.perf_counter()
+        best, ms, tried = nb.nbody_autotune(ctx, off, eps, *X32, M, amag)
+        tune_s = time.perf_counter() - w0
+        best.use_graph = 1
+        nb.nbody_set_config(ctx, best)
+        nb.nbody_build_batched(ctx, off, eps, *X32, M)
+        nb.nbody_walk(ctx, None, *A)
+        nb.nbody_step_batched(ctx, off, eps, *X, *V, M, *A, DT, max(args.warmup, 2))
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        nb.nbody_step_batched(ctx, off, eps, *X, *V, M, *A, DT, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        s_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    finally:
+        nb.nbody_destroy(ctx)
+    from paper_1811_02761_gb300.autotune import TUNED_FIELDS
+    return {"tuned": {k: int(getattr(best, k)) for k in TUNED_FIELDS}, "candidates": tried,
+            "search_s": tune_s, "best_build_walk_ms": ms, "s_per_step": s_step,
+            "speedup_vs_default": default_s_per_step / s_step}
 
 
 def batched_schedules(args, off, eps, parts, stream, dev):

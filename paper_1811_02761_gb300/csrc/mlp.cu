@@ -383,14 +383,10 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, const float *feat, const float
                                   const __nv_bfloat16 *wb, const float *norm, float *gpart,
                                   float *lpart, float *grad, float *loss, float *w, float *m1,
                                   float *m2, __nv_bfloat16 *wb_out, float lr, int t, bool update) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(GradSmem));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device's context
+    cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(GradSmem));
+    if (e != cudaSuccess) return e;
     const int nb = (count + kGB - 1) / kGB;
     mlp_grad_kernel<<<nb, kGB, sizeof(GradSmem), s>>>(feat, target, base, stride, count,
                                                       1.0f / (float)count, wb, norm, gpart, lpart);

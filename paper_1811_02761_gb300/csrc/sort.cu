@@ -590,14 +590,11 @@ void radix_prepare(cudaStream_t s, int64_t n, void *temp) {
 int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
                uint32_t *vals_alt, int64_t n, int bits, void *temp, bool hist_done,
                int32_t *status, int nsm, const int32_t *dn) {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(rs_onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(RsShared));
-        cudaFuncSetAttribute(rs_onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(RsShared));
-        attr_done = true;
-    }
+    // per call: the attribute belongs to the current device's context
+    cudaFuncSetAttribute(rs_onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(RsShared));
+    cudaFuncSetAttribute(rs_onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(RsShared));
     const int passes = (bits + RS_BITS - 1) / RS_BITS;
     if (!hist_done) {
         radix_prepare(s, n, temp);
