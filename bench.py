@@ -438,9 +438,10 @@ def run_batched(args, rank, world, local_rank):
         per_sys = (time.perf_counter() - w0) / args.per_system_steps
     finally:
         nb.nbody_destroy(ctx)
-    sched = batched_schedules(args, off, eps, parts, stream, dev) if args.schedules else None
     tuned = batched_autotune(args, off, eps, parts, stream, dev, elapsed / args.steps) \
         if args.autotune else None
+    sched = batched_schedules(args, off, eps, parts, stream, dev,
+                              tuned["tuned"] if tuned else None) if args.schedules else None
     t = torch.tensor([elapsed, float(st.interactions)], dtype=torch.float64, device=dev)
     if world > 1:
         tm = t[:1].clone()
@@ -520,12 +521,11 @@ def batched_autotune(args, off, eps, parts, stream, dev, default_s_per_step):
             "speedup_vs_default": default_s_per_step / s_step}
 
 
-def batched_schedules(args, off, eps, parts, stream, dev):
-    """The batched forest under each queue schedule, eager launches (a
-    cost-ordered queue reads the group count on the host every step): the
-    cost model is trained online on `train_steps` Morton-order steps, then
-    `steps` steps run from the same state per schedule.  Final states must
-    agree bit for bit."""
+def batched_schedules(args, off, eps, parts, stream, dev, tuned=None):
+    """The batched forest under each queue schedule, eager and in the step's
+    CUDA graph (with `tuned`: the autotuner's parameters): the cost model is
+    trained online on `train_steps` Morton-order steps, then `steps` steps run
+    from the same state per schedule.  Final states must agree bit for bit."""
     import torch
 
     import ics
@@ -539,7 +539,10 @@ def batched_schedules(args, off, eps, parts, stream, dev):
     V = [D(parts[k]) for k in ("vx", "vy", "vz")]
     M = D(parts["m"])
     A = [torch.zeros(n, dtype=torch.float32, device=dev) for _ in range(3)]
-    ctx = nb.nbody_create(nb.nbody_config_default(delta_acc=DACC), stream)
+    cfg0 = nb.nbody_config_default(delta_acc=DACC)
+    for k, v in (tuned or {}).items():
+        setattr(cfg0, k, v)
+    ctx = nb.nbody_create(cfg0, stream)
     out, finals = {}, {}
     try:
         nb.nbody_build_batched(ctx, off, eps, *[D(parts[k]) for k in ("x", "y", "z")], M)
@@ -574,7 +577,7 @@ def batched_schedules(args, off, eps, parts, stream, dev):
     finally:
         nb.nbody_destroy(ctx)
     base = out["morton"]["walk_ms_per_step"]
-    return {"runs": out,
+    return {"runs": out, "parameters": "autotuned" if tuned else "defaults",
             "mlp_vs_morton_walk_speedup": base / out["mlp"]["walk_ms_per_step"],
             "mlp_graph_vs_morton_graph_step_speedup":
                 out["morton_graph"]["s_per_step"] / out["mlp_graph"]["s_per_step"],
