@@ -1253,10 +1253,11 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         pending_kick = false;
     }
     // in[] are the device copies (the caller's arrays themselves when on the device)
+    // vals_alt (uint32 [n]) is free between steps: the inverse permutation
     launch_store_state(s, n, S[cur], acc, (double *)in[0], (double *)in[1], (double *)in[2],
                        (float *)in[3], (float *)in[4], (float *)in[5], (float *)in[7],
-                       (float *)in[8], (float *)in[9]);
-    ctx->kernels += 1;
+                       (float *)in[8], (float *)in[9], P<uint32_t>(ctx->vals_alt));
+    ctx->kernels += 2;
     for (int k = 0; k < 10; k++) {
         if (k == 6) continue;
         if (in[k] != arr[k])

@@ -145,10 +145,42 @@ __global__ void store_state_kernel(int64_t n, StepState st, const float4 *__rest
     }
 }
 
+// The same copy as a gather: inv[o] = the sorted index of caller index o,
+// then every output array is written in caller order (coalesced writes; the
+// reads are random but fetch whole sectors, where random writes of 4- and
+// 8-byte values each cost a partial-sector write).
+__global__ void inverse_perm_kernel(int64_t n, const uint32_t *__restrict__ id, uint32_t *inv) {
+    NB_GRID_LOOP(i, n) inv[id[i]] = (uint32_t)i;
+}
+
+__global__ void gather_state_kernel(int64_t n, StepState st, const float4 *__restrict__ acc,
+                                    const uint32_t *__restrict__ inv, double *x, double *y,
+                                    double *z, float *vx, float *vy, float *vz, float *ax,
+                                    float *ay, float *az) {
+    NB_GRID_LOOP(o, n) {
+        const uint32_t i = inv[o];
+        x[o] = st.x[i];
+        y[o] = st.y[i];
+        z[o] = st.z[i];
+        vx[o] = st.vx[i];
+        vy[o] = st.vy[i];
+        vz[o] = st.vz[i];
+        const float4 a = acc[i];
+        ax[o] = a.x;
+        ay[o] = a.y;
+        az[o] = a.z;
+    }
+}
+
 void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
-                        float *ay, float *az) {
-    store_state_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, x, y, z, vx, vy, vz, ax, ay, az);
+                        float *ay, float *az, uint32_t *inv) {
+    if (!inv) {
+        store_state_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, x, y, z, vx, vy, vz, ax, ay, az);
+        return;
+    }
+    inverse_perm_kernel<<<grid_for(n), 256, 0, s>>>(n, st.id, inv);
+    gather_state_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, inv, x, y, z, vx, vy, vz, ax, ay, az);
 }
 
 // ---------------------------------------------------------------- block time steps

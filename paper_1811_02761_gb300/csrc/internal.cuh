@@ -323,9 +323,11 @@ void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double 
                        const double *z, const float *vx, const float *vy, const float *vz,
                        const float *m, const float *ax, const float *ay, const float *az,
                        StepState st, float4 *acc);
+// The state back in caller order; inv (nullable, uint32 [n] scratch): as a
+// gather through the inverse permutation instead of a scatter.
 void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
-                        float *ay, float *az);
+                        float *ay, float *az, uint32_t *inv = nullptr);
 size_t diag_temp_bytes();
 // Message returned by nbody_last_error(NULL, ...) on this thread.
 void set_stateless_error(const std::string &msg);
