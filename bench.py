@@ -577,7 +577,7 @@ def batched_schedules(args, off, eps, parts, stream, dev, tuned=None):
             finals[name] = [t.cpu().numpy() for t in X + V + A]
         if args.autotune and tuned is None:
             # tune under the learned order: the autotuner's timed walks use the
-            # context's schedule, so candidates are judged as they will run
+            # context's schedule, so candidates are timed as they will run
             for t, s0 in zip(X + V + A, snap):
                 t.copy_(s0)
             cfg = nb.nbody_get_config(ctx)
