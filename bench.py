@@ -184,6 +184,29 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------- oracle (CPU)
+def oracle_small_timings():
+    """The FP64 oracle on the N = 2^13 Plummer sphere: the direct sum on all
+    cores and on one core, and the tree build + group walk (all cores)."""
+    import ics
+    import oracle
+    p = ics.plummer(1 << 13, 1)
+    x, y, z, m = (np.asarray(p[k], np.float64) for k in ("x", "y", "z", "m"))
+    out = {"n": 1 << 13}
+    for label, k in (("direct_all_cores_s", 0), ("direct_one_core_s", 1)):
+        oracle.set_threads(k)
+        t0 = time.perf_counter()
+        oracle.direct(x, y, z, m, 1.0, 1.0 / 128, want_phi=False)
+        out[label] = time.perf_counter() - t0
+    oracle.set_threads(0)
+    out["all_cores"] = oracle.threads()
+    t0 = time.perf_counter()
+    t = oracle.Tree(x, y, z, m, 21, 16)
+    ax, ay, az, _, _ = t.walk(oracle.MAC_GROUP_GEO, 1.0, 1.0 / 128, 0.0, 0.5, 64, None,
+                              want_phi=False)
+    out["tree_build_walk_s"] = time.perf_counter() - t0
+    return out
+
+
 def cpu_oracle_sample(p, group_stride, a_old=None):
     """FP64 oracle: full tree build + walk of every group_stride-th group.
     Returns (interactions, walk_seconds, build_seconds, threads, ngroups_walked)."""
@@ -329,7 +352,7 @@ def run_ours(args, rank, world, local_rank):
                          f"({nsel} of {ng} groups, {ni} interactions) of the same N={n} galaxy "
                          f"at its initial positions; oracle tree build {build_s:.2f} s timed "
                          f"separately",
-               "build_s": build_s, "walk_s": walk_s}
+               "build_s": build_s, "walk_s": walk_s, "small": oracle_small_timings()}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,

@@ -80,6 +80,7 @@ def _load():
         lib.oracle_drift.argtypes = [C.c_int64, d, d, d, d, d, d, C.c_double]
         lib.oracle_diagnostics.argtypes = [C.c_int64, d, d, d, d, d, d, d, d, d]
         lib.oracle_threads.restype = C.c_int
+        lib.oracle_set_threads.argtypes = [C.c_int]
         lib.oracle_mlp_params.restype = C.c_int
         lib.oracle_mlp_eval.argtypes = [C.c_int64, d, d, d, d, d, d, d]
         _lib = lib
@@ -96,6 +97,11 @@ def _f64(a):
 
 def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def set_threads(k: int) -> None:
+    """Threads of later oracle calls (k < 1: all cores)."""
+    _load().oracle_set_threads(int(k))
 
 
 def threads() -> int:

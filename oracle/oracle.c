@@ -27,6 +27,16 @@ int oracle_threads(void)
 #endif
 }
 
+/* Threads of the following parallel loops (k < 1: all cores). */
+void oracle_set_threads(int k)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(k >= 1 ? k : omp_get_num_procs());
+#else
+    (void)k;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Eq. 1: one softened pair term, accumulated into s[0..2] (acceleration) and
  * s[3] (potential).  (dx,dy,dz) = r_j - r_i. */

@@ -142,6 +142,8 @@ void oracle_mlp_eval(int64_t n, const double *feat, const double *target, const 
 
 /* Number of threads OpenMP uses (1 without OpenMP). */
 int oracle_threads(void);
+/* Threads of the following parallel loops (k < 1: all cores). */
+void oracle_set_threads(int k);
 
 #ifdef __cplusplus
 }
