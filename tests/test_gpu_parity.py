@@ -428,3 +428,59 @@ def test_step_graph_equals_eager(nsteps, schedule):
     for a, g in zip(res[0][:-2], res[1][:-2]):
         assert np.array_equal(a, g)
     assert res[0][-2:] == res[1][-2:]
+
+
+# --------------------------------------------------------------------------- checkpoint / resume
+def test_resume_from_saved_state_is_bit_identical(tmp_path):
+    """The library keeps no integrator state between nbody_step calls: the
+    caller's arrays (FP64 positions, velocities, accelerations) are the whole
+    state, so saving them and resuming in a new context continues the
+    trajectory bit for bit -- also with the learned queue order, whose
+    parameters round-trip through nbody_mlp_get/set_params."""
+    n = 12000
+    p = ics.plummer(n, 91)
+    for schedule in (nb.SCHED_MORTON, nb.SCHED_MLP):
+        cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, group_size=32, ipl=1,
+                                      schedule=schedule)
+
+        def fresh():
+            ctx = nb.nbody_create(cfg)
+            if schedule == nb.SCHED_MLP:
+                nb.nbody_mlp_set_params(ctx, ics.mlp_init(5))
+            return ctx
+
+        def start():
+            X = [dev(p[k].astype(np.float64)) for k in ("x", "y", "z")]
+            V = [dev(p[k]) for k in ("vx", "vy", "vz")]
+            A = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+            return X, V, A
+
+        M = dev(p["m"])
+        # reference: four steps in one call
+        ctx = fresh()
+        X, V, A = start()
+        nb.nbody_build(ctx, *[dev(p[k]) for k in ("x", "y", "z")], M)
+        nb.nbody_walk(ctx, None, *A)
+        A0 = [a.clone() for a in A]
+        nb.nbody_step(ctx, *X, *V, M, *A, 1.0 / 256, 4)
+        ref = [host(t) for t in X + V + A]
+        nb.nbody_destroy(ctx)
+        # two steps, a checkpoint on disk, a new context, two more steps
+        ctx = fresh()
+        X, V, A = start()
+        for a, a0 in zip(A, A0):
+            a.copy_(a0)
+        nb.nbody_step(ctx, *X, *V, M, *A, 1.0 / 256, 2)
+        params = nb.nbody_mlp_get_params(ctx) if schedule == nb.SCHED_MLP else None
+        ck = tmp_path / f"state{schedule}.npz"
+        np.savez(ck, *[host(t) for t in X + V + A])
+        nb.nbody_destroy(ctx)
+        saved = np.load(ck)
+        T = [dev(saved[f"arr_{k}"]) for k in range(9)]
+        ctx = nb.nbody_create(cfg)
+        if params is not None:
+            nb.nbody_mlp_set_params(ctx, params)
+        nb.nbody_step(ctx, *T[:3], *T[3:6], M, *T[6:9], 1.0 / 256, 2)
+        nb.nbody_destroy(ctx)
+        for r, t in zip(ref, T):
+            assert np.array_equal(r, host(t))
