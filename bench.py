@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--quadrupole", type=int, default=0, choices=(0, 1),
                     help="galaxy: nodes carry quadrupoles (an extension beyond the paper's "
                          "monopoles); precision: add a quadrupole sweep")
+    ap.add_argument("--use-graph", type=int, default=1, choices=(0, 1),
+                    help="galaxy: replay the steps as a two-step CUDA graph (1, default) or "
+                         "launch them eagerly (0)")
     ap.add_argument("--block-levels", type=int, default=0,
                     help="galaxy: block time steps with levels 0..K (step dt/2^k); 0 = shared step")
     ap.add_argument("--block-eta", type=float, default=0.025)
@@ -265,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, rebuild_interval=args.rebuild_interval,
                                   quadrupole=args.quadrupole, block_levels=args.block_levels,
-                                  block_eta=args.block_eta)
+                                  block_eta=args.block_eta, use_graph=args.use_graph)
     dt = args.dt
     ctx = nb.nbody_create(cfg, stream)
     try:
@@ -295,6 +298,17 @@ def run_ours(args, rank, world, local_rank):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dist.all_reduce(it, op=dist.ReduceOp.SUM)
         elapsed_max, inter_all = float(t.item()), float(it.item())
+        walk_ms, walk_launches = st.ms_walk_kernel, st.walk_launches
+        phase_ms, phase_steps = (st.ms_build, st.ms_walk), args.steps
+        if walk_launches == 0:  # graph replay: time the walk kernel in two eager steps
+            c2 = nb.nbody_get_config(ctx)
+            c2.use_graph = 0
+            nb.nbody_set_config(ctx, c2)
+            s3 = nb.nbody_step(ctx, *X64, *V, M, *A, dt, 2)
+            walk_ms, walk_launches = s3.ms_walk_kernel, s3.walk_launches
+            phase_ms, phase_steps = (s3.ms_build, s3.ms_walk), 2
+            c2.use_graph = 1
+            nb.nbody_set_config(ctx, c2)
 
         # end-to-end through the C ABI with pinned host buffers
         hx = [a.cpu().pin_memory() for a in X64]
@@ -328,7 +342,7 @@ def run_ours(args, rank, world, local_rank):
     s_per_step = elapsed_max / steps
     value = inter_all / elapsed_max / 1e9
     inter_per_step = inter / steps
-    walk_avg_s = (st.ms_walk_kernel / max(st.walk_launches, 1)) / 1e3
+    walk_avg_s = (walk_ms / max(walk_launches, 1)) / 1e3
     walk_tflops = FLOPS_PER_INTERACTION * inter_per_step / walk_avg_s / 1e12
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -365,9 +379,12 @@ def run_ours(args, rank, world, local_rank):
         "interactions_per_step": inter_per_step,
         "whole_step_tflops": whole_tflops,
         "whole_step_fp32_peak_frac": whole_tflops / peak_tflops,
-        "walk_ms_per_step": st.ms_walk_kernel / max(st.walk_launches, 1),
-        "build_ms_per_step": st.ms_build / steps,
-        "walk_phase_ms_per_step": st.ms_walk / steps,
+        "walk_ms_per_step": walk_ms / max(walk_launches, 1),
+        "build_ms_per_step": phase_ms[0] / phase_steps,
+        "walk_phase_ms_per_step": phase_ms[1] / phase_steps,
+        "phase_timing": "eager steps (CUDA events per phase)" if phase_steps == steps else
+                        "two extra eager steps after the timed graph replays (CUDA events per "
+                        "phase; graph nodes carry no events)",
         "nodes": st.n_nodes, "groups": st.n_groups, "max_stack": st.max_stack,
         "rebuilds": int(st.rebuilds),
         "quadrupole": args.quadrupole,

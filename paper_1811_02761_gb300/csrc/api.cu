@@ -1091,10 +1091,11 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     // or refits the current one (moments and group spheres at the drifted
     // positions, which the kick-drift writes to pos4 in place).
     int rebuilds = 0;
-    // Eager steps defer their closing half kick into the next step's
-    // kick-drift pass (pending_kick); graph steps keep it separate so that
-    // every replay starts from the same state.
-    bool pending_kick = false;
+    // A step defers its closing half kick into the next step's kick-drift
+    // pass (pending_kick): between eager steps, and between the two steps of
+    // a graph; the graph's last step kicks on its own, so that every replay
+    // starts from the same state.
+    bool pending_kick = false, defer_in_capture = false;
     auto one_step = [&](bool timing, bool rebuild) -> nbody_status {
         cudaStream_t q = ctx->stream;
         launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt, rebuild ? nullptr : P<float4>(ctx->pos4),
@@ -1139,7 +1140,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             NB_CUDA(ctx, cudaEventRecord(e2, q));
             marks.push_back(ctx->evused - 3);
         }
-        if (ctx->capturing || dt == 0.0f) {
+        if ((ctx->capturing && !defer_in_capture) || dt == 0.0f) {
             launch_kick(q, n, S[cur], acc, 0.5f * dt);
             ctx->kernels += 1;
         } else {
@@ -1186,7 +1187,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             cudaError_t ce = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed);
             nbody_status r1 = NBODY_OK, r2 = NBODY_OK;
             if (ce == cudaSuccess) {
+                defer_in_capture = true;
                 r1 = one_step(false, true);
+                defer_in_capture = false;
                 if (r1 == NBODY_OK) r2 = one_step(false, true);
                 cudaError_t ee = cudaStreamEndCapture(ctx->gstream, &graph);
                 if (ce == cudaSuccess) ce = ee;
