@@ -61,7 +61,7 @@ struct nbody_ctx {
     DevBuf keys, keys_alt, vals, vals_alt, pos4, delta, leaflev;
     DevBuf rs_temp, tree_temp, grp_temp, diag_temp, diag_out;
     // nodes
-    DevBuf node_start, node_level, node_parent, node_link, node_count, node_nchild;
+    DevBuf node_start, node_level, node_parent, node_link, node_count, node_nchild, node_arrive;
     DevBuf nodeA, nodeB, mass2, nodeQ;
     // groups
     DevBuf gflag, grp_first, grp_count, grp_sphere, grp_sys, grp_alpha, grp_cost, grp_order;
@@ -102,7 +102,7 @@ struct nbody_ctx {
     nbody_ctx() {
         DevBuf *all[] = {&keys, &keys_alt, &vals, &vals_alt, &pos4, &delta, &leaflev, &rs_temp,
                          &tree_temp, &grp_temp, &diag_temp, &diag_out, &node_start, &node_level,
-                         &node_parent, &node_link, &node_count, &node_nchild,
+                         &node_parent, &node_link, &node_count, &node_nchild, &node_arrive,
                          &nodeA, &nodeB, &mass2, &nodeQ, &gflag, &grp_first, &grp_count, &grp_sphere,
                          &grp_sys, &grp_alpha, &grp_cost, &grp_order, &sys_off, &sys_box,
                          &sys_boxord, &sys_eps2, &sys_eps, &sys_root, &acc_s, &aold_s, &mlp_w, &mlp_m1,
@@ -274,6 +274,7 @@ cudaError_t ensure_capacity(nbody_ctx *c, int64_t n, int nsys, int levels) {
         NB_E(ensure(c->node_start, cn * 4)); NB_E(ensure(c->node_level, cn));
         NB_E(ensure(c->node_parent, cn * 4)); NB_E(ensure(c->node_link, cn * 4));
         NB_E(ensure(c->node_count, cn * 4)); NB_E(ensure(c->node_nchild, cn * 4));
+        NB_E(ensure(c->node_arrive, cn * 4));
         NB_E(ensure(c->nodeA, cn * 16)); NB_E(ensure(c->nodeB, cn * 16));
         NB_E(ensure(c->mass2, cn * 8)); NB_E(ensure(c->nodeQ, cn * 32));
         c->cap_nodes = cn;
@@ -335,7 +336,7 @@ nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
                P<int64_t>(c->sys_off), c->cfg.leaf_cap, c->cfg.G, c->cap_nodes, P<int8_t>(c->delta),
                P<int8_t>(c->leaflev), c->tree_temp.p, c->ds, P<int32_t>(c->node_start),
                P<int8_t>(c->node_level), P<int32_t>(c->node_parent), P<int32_t>(c->node_link),
-               P<int32_t>(c->node_count), P<int32_t>(c->node_nchild),
+               P<int32_t>(c->node_count), P<int32_t>(c->node_nchild), P<int32_t>(c->node_arrive),
                P<float4>(c->nodeA), P<float4>(c->nodeB), P<float2>(c->mass2),
                c->cfg.quadrupole ? P<float4>(c->nodeQ) : nullptr, P<int32_t>(c->sys_root), c->nsm);
     build_groups(s, L, c->cfg.group_size, P<float4>(c->pos4), P<int64_t>(c->sys_off),
@@ -344,9 +345,9 @@ nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
                  P<uint8_t>(c->gflag), c->grp_temp.p, P<int32_t>(c->grp_first),
                  P<int32_t>(c->grp_count), P<float4>(c->grp_sphere), P<int32_t>(c->grp_sys),
                  c->nsm);
-    // tree: leaflevel, level scan, level offsets, nodes, two system-root
-    // kernels, leaf moments, one internal-moments launch per level; groups: 5
-    c->kernels += 6 + 1 + L.levels + 5;
+    // tree: leaflevel, level scan, level offsets, node zeroing, nodes, two
+    // system-root kernels, moments; groups: 5
+    c->kernels += 8 + 5;
     NB_CUDA(c, cudaGetLastError());
     return NBODY_OK;
 }
@@ -358,14 +359,15 @@ nbody_status refit_tree_groups(nbody_ctx *c, const Layout &L) {
     c->costs_valid = false;
     tree_moments(s, L, P<uint64_t>(c->keys), P<float4>(c->pos4), P<SysBox>(c->sys_box),
                  c->cfg.leaf_cap, c->cfg.G, c->ds, P<int32_t>(c->node_start),
-                 P<int8_t>(c->node_level), P<int32_t>(c->node_link), P<int32_t>(c->node_count),
-                 P<int32_t>(c->node_nchild), P<float4>(c->nodeA), P<float4>(c->nodeB),
+                 P<int8_t>(c->node_level), P<int32_t>(c->node_parent), P<int32_t>(c->node_link),
+                 P<int32_t>(c->node_count), P<int32_t>(c->node_nchild), P<int32_t>(c->node_arrive),
+                 P<float4>(c->nodeA), P<float4>(c->nodeB),
                  P<float2>(c->mass2), c->cfg.quadrupole ? P<float4>(c->nodeQ) : nullptr, c->nsm,
                  true);
     refit_groups(s, L, c->cfg.group_size, P<float4>(c->pos4), P<int64_t>(c->sys_off), c->ds,
                  P<int32_t>(c->grp_first), P<int32_t>(c->grp_count), P<float4>(c->grp_sphere),
                  P<int32_t>(c->grp_sys), c->nsm);
-    c->kernels += 1 + L.levels + 1;
+    c->kernels += 1 + 1;
     NB_CUDA(c, cudaGetLastError());
     return NBODY_OK;
 }

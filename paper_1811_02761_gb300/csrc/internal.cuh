@@ -176,16 +176,17 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                 int64_t cap_nodes, int8_t *delta, int8_t *leaflev, void *temp, DevState *ds,
                 int32_t *node_start, int8_t *node_level, int32_t *node_parent,
                 int32_t *node_link, int32_t *node_count, int32_t *node_nchild,
-                float4 *nodeA, float4 *nodeB, float2 *mass2, float4 *nodeQ, int32_t *sys_root,
-                int nsm);
+                int32_t *node_arrive, float4 *nodeA, float4 *nodeB, float2 *mass2, float4 *nodeQ,
+                int32_t *sys_root, int nsm);
 // Node moments of the current tree from pos4 (refit: positions moved since
 // the build; b_J of internal nodes from the child recurrence only).
 // nodeQ (nullable): also the traceless quadrupoles, 2 float4 per node.
 void tree_moments(cudaStream_t s, const Layout &L, const uint64_t *keys, const float4 *pos4,
                   const SysBox *d_box, int leaf_cap, float G, DevState *ds,
-                  const int32_t *node_start, const int8_t *node_level, const int32_t *node_link,
-                  int32_t *node_count, const int32_t *node_nchild, float4 *nodeA, float4 *nodeB,
-                  float2 *mass2, float4 *nodeQ, int nsm, bool refit);
+                  const int32_t *node_start, const int8_t *node_level, const int32_t *node_parent,
+                  const int32_t *node_link, int32_t *node_count, const int32_t *node_nchild,
+                  int32_t *node_arrive, float4 *nodeA, float4 *nodeB, float2 *mass2,
+                  float4 *nodeQ, int nsm, bool refit);
 void refit_groups(cudaStream_t s, const Layout &L, int group_size, const float4 *pos4,
                   const int64_t *d_off, DevState *ds, const int32_t *grp_first,
                   int32_t *grp_count, float4 *grp_sphere, int32_t *grp_sys, int nsm);

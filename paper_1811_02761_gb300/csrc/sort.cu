@@ -230,7 +230,10 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_IPT = NB_RS_IPT;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
 constexpr int RS_SPIN_LIMIT = 1 << 20;
-constexpr int RS_LB = 4;  // look-back words loaded per round trip
+#ifndef NB_RS_LB
+#define NB_RS_LB 4  // look-back words loaded per round trip (build-time tunable)
+#endif
+constexpr int RS_LB = NB_RS_LB;
 constexpr int SCAN_T = 1024;
 constexpr int SCAN_IPT = 4;
 constexpr int SCAN_CH = SCAN_T * SCAN_IPT;

@@ -16,10 +16,10 @@
 // per-particle work in a window of 2*leaf_cap boundaries plus one scan per
 // level -- no level-by-level launches.
 //
-// Monopoles are accumulated bottom-up: all leaves in one launch, then one
-// launch per level for the internal nodes, deepest level first; the stream
-// order between launches stands in for the grid-wide barriers of the
-// paper's calcNode (App. A).
+// Monopoles are accumulated bottom-up in one launch: the leaves from their
+// particles, then each internal node by the thread that finishes its last
+// child (an atomic count per node), so neither a launch per level nor the
+// grid-wide barriers of the paper's calcNode (App. A) are needed.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -141,6 +141,18 @@ __global__ void level_offsets_kernel(int NL, DevState *ds, int64_t cap_nodes) {
     }
     ds->nnodes = off;
     if (off > cap_nodes) atomicOr(&ds->status, kStatusStackOverflow);
+}
+
+// Zeroes the child counts and the moments pass's arrival counters of the
+// nodes about to be made (the node count is on the device).
+__global__ void node_zero_kernel(const DevState *__restrict__ ds, int64_t cap_nodes,
+                                 int32_t *node_nchild, int32_t *node_arrive) {
+    const int64_t nn = min((int64_t)ds->nnodes, cap_nodes);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        node_nchild[i] = 0;
+        node_arrive[i] = 0;
+    }
 }
 
 // Writes every node: start, level, parent, first child / first particle and,
@@ -323,26 +335,121 @@ __device__ __forceinline__ void write_quad(int id, const float q[6], float4 *nod
 // arithmetic only).  b_J is rounded up so it bounds the distance from the
 // FP32 centre of mass to every member.
 //
-// Leaves first, all levels at once: a team of T lanes takes one leaf, lane j
-// loading members j, j + T, ... (coalesced); the sums and the largest member
-// distance are team reductions.
+// One launch for the whole tree, no pass per level.  Leaves: a team of T
+// lanes takes one leaf, lane j loading members j, j + T, ... (coalesced); the
+// sums and the largest member distance are team reductions.  Internal nodes:
+// every finished node counts itself in at its parent (an atomic counter), and
+// the thread whose count completes the parent computes it from the children's
+// records and climbs on.  No thread waits for another.  The counters are
+// zeroed when the nodes are made, and each is reset by the thread that
+// completes its node, so a later pass over the same tree (a refit) starts
+// from zero too; a node that fails its bounds check is still counted in at
+// its parent, which keeps every counter consistent.
+
+// One internal node from its children's records (contiguous, at most 8), by
+// one thread.  Sums run over the children in octant order, relative to the
+// cell centre; the size is
+//   b = min(max_c (|com_c - com| + b_c), distance from com to the farthest
+//           corner of the cell widened by one finest cell),
+// rounded up.  After a refit (positions moved since the build, members may
+// have left the cell) only the child recurrence bounds b.  Children finished
+// by other SMs in this launch are read past L1 (ld.global.cg): a sibling's
+// cache line may already sit in this SM's L1 from before it was written.
+__device__ __forceinline__ bool internal_node(const Layout &L, int p, int c0, int nc, int level,
+                                              uint64_t key, int refit, int nn,
+                                              const SysBox *__restrict__ box, float G,
+                                              int32_t *node_count, float4 *nodeA, float4 *nodeB,
+                                              float2 *mass2, float4 *nodeQ) {
+    if (c0 <= p || nc < 1 || nc > 8 || c0 + nc > nn) return false;
+    const CellF cell = node_cell(L, key, level, box);
+    float2 M = make_float2(0.0f, 0.0f);
+    float px = 0.0f, py = 0.0f, pz = 0.0f;
+    int count = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {  // predicated: every child's loads in flight at once
+        if (k < nc) {
+            const int j = c0 + k;
+            const float4 A = __ldcg(nodeA + j);
+            M = df_add(M, __ldcg(mass2 + j));
+            count += __ldcg(node_count + j);
+            px = fmaf(A.w, A.x - cell.c[0], px);
+            py = fmaf(A.w, A.y - cell.c[1], py);
+            pz = fmaf(A.w, A.z - cell.c[2], pz);
+        }
+    }
+    float cp[3] = {cell.c[0], cell.c[1], cell.c[2]};
+    if (M.x > 0.0f) {
+        const float inv = 1.0f / M.x;
+        cp[0] = fmaf(px, inv, cp[0]); cp[1] = fmaf(py, inv, cp[1]); cp[2] = fmaf(pz, inv, cp[2]);
+    }
+    float rec = 0.0f;
+    float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 8; k++) {  // the children again (L2 hits)
+        if (k >= nc) break;
+        const int j = c0 + k;
+        const float4 A = __ldcg(nodeA + j);
+        const float dx = A.x - cp[0], dy = A.y - cp[1], dz = A.z - cp[2];
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        rec = fmaxf(rec, __fadd_ru(__fsqrt_ru(r2), __ldcg(&nodeB[j].x)));
+        if (nodeQ) {
+            const float4 q0 = __ldcg(nodeQ + 2 * j), q1 = __ldcg(nodeQ + 2 * j + 1);
+            q[0] += q0.x; q[1] += q0.y; q[2] += q0.z; q[3] += q0.w; q[4] += q1.x; q[5] += q1.y;
+            quad_add(q, A.w, dx, dy, dz, r2);
+        }
+    }
+    float c2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float e = fabsf(cp[a] - cell.c[a]) + cell.h;
+        c2 = fmaf(e, e, c2);
+    }
+    const float bp = (refit ? rec : fminf(rec, __fsqrt_ru(c2))) * kUp;
+    node_count[p] = count;
+    write_node(p, cp[0], cp[1], cp[2], M, bp, G, c0, nc << 1, nodeA, nodeB, mass2);
+    if (nodeQ) write_quad(p, q, nodeQ);
+    return true;
+}
+
+// Count a finished node in at its parent `par` (one atomic add with release
+// and acquire semantics: this thread's writes of the node are published by
+// it, and the thread that completes the parent sees every child's records).
+// Returns whether this was the parent's last child.
+__device__ __forceinline__ bool count_in(int par, int nchild_par, int32_t *node_arrive) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;"
+                 : "=r"(old)
+                 : "l"(node_arrive + par)
+                 : "memory");
+    return old + 1 == nchild_par;
+}
+
+#ifndef NB_MOMENTS_MIN_CTAS
+#define NB_MOMENTS_MIN_CTAS 5  // resident 256-thread CTAs per SM the moments pass is compiled for
+#endif
+
 template <int T>
-__global__ void __launch_bounds__(256) leaf_moments_kernel(
-    Layout L, const uint64_t *__restrict__ keys, const float4 *__restrict__ pos4,
+__global__ void __launch_bounds__(256, NB_MOMENTS_MIN_CTAS) moments_kernel(
+    Layout L, int refit, const uint64_t *__restrict__ keys, const float4 *__restrict__ pos4,
     const SysBox *__restrict__ box, float G, DevState *ds,
     const int32_t *__restrict__ node_start, const int8_t *__restrict__ node_level,
-    const int32_t *__restrict__ node_link, const int32_t *__restrict__ node_count,
-    const int32_t *__restrict__ node_nchild, float4 *nodeA, float4 *nodeB, float2 *mass2,
-    float4 *nodeQ) {
+    const int32_t *__restrict__ node_parent, const int32_t *__restrict__ node_link,
+    int32_t *node_count, const int32_t *__restrict__ node_nchild, int32_t *node_arrive,
+    float4 *nodeA, float4 *nodeB, float2 *mass2, float4 *nodeQ) {
     constexpr int TEAMS = 32 / T;
     const int nn = ds->nnodes;
     const int lane = (int)lane_id(), team = lane / T, tl = lane % T;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     bool bad = false;
-    for (int64_t base = wid * 32; base < nn; base += nw * 32) {
+    // deepest chunks first (ids are level-major): the long climbs from deep
+    // leaves start early, and the last leaves to finish sit near the roots
+    const int64_t nchunk = ((int64_t)nn + 31) / 32;
+    for (int64_t ch = wid; ch < nchunk; ch += nw) {
+        const int64_t base = (nchunk - 1 - ch) * 32;
         const int id0 = (int)base + lane;
-        unsigned lm = __ballot_sync(NB_FULL, id0 < nn && node_nchild[id0] == 0);
+        const bool leaf = id0 < nn && node_nchild[id0] == 0;
+        unsigned lm = __ballot_sync(NB_FULL, leaf);
         while (lm) {
             // team t takes the t-th remaining leaf of this chunk
             int mine = -1;
@@ -422,112 +529,35 @@ __global__ void __launch_bounds__(256) leaf_moments_kernel(
                 if (nodeQ) write_quad(id, q, nodeQ);
             }
         }
-    }
-    if (bad) atomicOr(&ds_status(ds), kStatusBadTree);
-}
-
-// Internal nodes of one level, after every deeper level: a team of 8 lanes
-// per node, lane j loading child j (children are contiguous, at most 8).
-// Sums relative to the cell centre; the size is
-//   b = min(max_c (|com_c - com| + b_c), distance from com to the farthest
-//           corner of the cell widened by one finest cell),
-// rounded up.  After a refit (refit != 0: positions moved since the build,
-// members may have left the cell) only the child recurrence bounds b.
-__global__ void __launch_bounds__(256) internal_moments_kernel(
-    Layout L, int level, int refit, const uint64_t *__restrict__ keys, const SysBox *__restrict__ box,
-    float G, DevState *ds, const int32_t *__restrict__ node_start,
-    const int32_t *__restrict__ node_link, int32_t *node_count,
-    const int32_t *__restrict__ node_nchild, float4 *nodeA, float4 *nodeB, float2 *mass2,
-    float4 *nodeQ) {
-    const int lo = ds->lvl_off[level], hi = ds->lvl_off[level + 1];
-    const int nn = ds->nnodes;
-    const int lane = (int)lane_id(), team = lane >> 3, tl = lane & 7;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    bool bad = false;
-    for (int64_t base = lo + wid * 32; base < hi; base += nw * 32) {
-        const int id0 = (int)base + lane;
-        unsigned im = __ballot_sync(NB_FULL, id0 < hi && node_nchild[id0] != 0);
-        while (im) {
-            int mine = -1;
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-                const int b = im ? __ffs(im) - 1 : -1;
-                if (b >= 0) im &= im - 1;
-                if (t == team) mine = b;
+        // internal nodes: the chunk's leaf records are device-visible before
+        // any lane counts a leaf in (the writers' fence, then the warp
+        // barrier).  A climbing thread carries a member key (its leaf's first
+        // particle): every ancestor's cell follows from it and the ancestor's
+        // level, one up per step.
+        __threadfence();
+        __syncwarp();
+        int node = id0, par = -1, level = 0;
+        uint64_t key = 0;
+        if (leaf) {
+            par = node_parent[id0];
+            level = node_level[id0];
+            key = keys[node_start[id0]];
+        }
+        while (par >= 0) {       // a root has none
+            if (par >= node) {   // parents precede their children
+                bad = true;
+                break;
             }
-            const int par = mine >= 0 ? (int)base + mine : -1;
-            int c0 = 0, nc = 0;
-            if (par >= 0) {
-                c0 = node_link[par];
-                nc = node_nchild[par];
-                if (c0 <= par || nc < 1 || nc > 8 || c0 + nc > nn) {
-                    bad = true;
-                    nc = 0;
-                }
-            }
-            CellF cell{{0.f, 0.f, 0.f}, 0.f};
-            if (nc > 0) cell = node_cell(L, keys[node_start[par]], level, box);
-            float2 Mp = make_float2(0.0f, 0.0f);
-            float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
-            float bc = 0.0f;
-            int count = 0;
-            if (tl < nc) {
-                A = nodeA[c0 + tl];
-                bc = nodeB[c0 + tl].x;
-                Mp = mass2[c0 + tl];
-                count = node_count[c0 + tl];
-            }
-            float px = A.w * (A.x - cell.c[0]);
-            float py = A.w * (A.y - cell.c[1]);
-            float pz = A.w * (A.z - cell.c[2]);
-#pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {
-                const float2 Mo = make_float2(__shfl_xor_sync(NB_FULL, Mp.x, o),
-                                              __shfl_xor_sync(NB_FULL, Mp.y, o));
-                Mp = df_add(Mp, Mo);
-                px += __shfl_xor_sync(NB_FULL, px, o);
-                py += __shfl_xor_sync(NB_FULL, py, o);
-                pz += __shfl_xor_sync(NB_FULL, pz, o);
-                count += __shfl_xor_sync(NB_FULL, count, o);
-            }
-            float cp[3] = {cell.c[0], cell.c[1], cell.c[2]};
-            if (Mp.x > 0.0f) {
-                const float inv = 1.0f / Mp.x;
-                cp[0] = fmaf(px, inv, cp[0]); cp[1] = fmaf(py, inv, cp[1]); cp[2] = fmaf(pz, inv, cp[2]);
-            }
-            float rec = 0.0f;
-            float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (tl < nc) {
-                const float dx = A.x - cp[0], dy = A.y - cp[1], dz = A.z - cp[2];
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                rec = __fadd_ru(__fsqrt_ru(r2), bc);
-                if (nodeQ) {
-                    const float4 q0 = nodeQ[2 * (c0 + tl)], q1 = nodeQ[2 * (c0 + tl) + 1];
-                    q[0] = q0.x; q[1] = q0.y; q[2] = q0.z; q[3] = q0.w; q[4] = q1.x; q[5] = q1.y;
-                    quad_add(q, A.w, dx, dy, dz, r2);
-                }
-            }
-#pragma unroll
-            for (int o = 4; o > 0; o >>= 1) rec = fmaxf(rec, __shfl_xor_sync(NB_FULL, rec, o));
-            if (nodeQ) {
-#pragma unroll
-                for (int o = 4; o > 0; o >>= 1)
-#pragma unroll
-                    for (int j = 0; j < 6; j++) q[j] += __shfl_xor_sync(NB_FULL, q[j], o);
-            }
-            if (nc > 0 && tl == 0) {
-                float c2 = 0.0f;
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    const float e = fabsf(cp[a] - cell.c[a]) + cell.h;
-                    c2 = fmaf(e, e, c2);
-                }
-                const float bp = (refit ? rec : fminf(rec, __fsqrt_ru(c2))) * kUp;
-                node_count[par] = count;
-                write_node(par, cp[0], cp[1], cp[2], Mp, bp, G, c0, nc << 1, nodeA, nodeB, mass2);
-                if (nodeQ) write_quad(par, q, nodeQ);
-            }
+            const int c0 = node_link[par], nc = node_nchild[par];
+            if (!count_in(par, nc, node_arrive)) break;
+            const int up = node_parent[par];  // in flight with the children's loads
+            level--;
+            if (!internal_node(L, par, c0, nc, level, key, refit, nn, box, G, node_count, nodeA,
+                               nodeB, mass2, nodeQ))
+                bad = true;  // still counted in above, so the counters stay consistent
+            node_arrive[par] = 0;
+            node = par;
+            par = up;
         }
     }
     if (bad) atomicOr(&ds_status(ds), kStatusBadTree);
@@ -543,8 +573,8 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
                 int64_t cap_nodes, int8_t *delta, int8_t *leaflev, void *temp, DevState *ds,
                 int32_t *node_start, int8_t *node_level, int32_t *node_parent,
                 int32_t *node_link, int32_t *node_count, int32_t *node_nchild,
-                float4 *nodeA, float4 *nodeB, float2 *mass2, float4 *nodeQ, int32_t *sys_root,
-                int nsm) {
+                int32_t *node_arrive, float4 *nodeA, float4 *nodeB, float2 *mass2, float4 *nodeQ,
+                int32_t *sys_root, int nsm) {
     const int nblk = (int)((L.n + TB - 1) / TB);
     uint32_t *blockcnt = (uint32_t *)temp;
     if (leaf_cap <= 8)
@@ -555,51 +585,49 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
         leaflevel_kernel<32><<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
     level_scan_kernel<<<L.levels + 1, 1024, 0, s>>>(blockcnt, nblk, ds);
     level_offsets_kernel<<<1, 32, 0, s>>>(L.levels + 1, ds, cap_nodes);
-    cudaMemsetAsync(node_nchild, 0, (size_t)cap_nodes * sizeof(int32_t), s);
+    node_zero_kernel<<<nsm * 8, 256, 0, s>>>(ds, cap_nodes, node_nchild, node_arrive);
     nodes_kernel<<<nblk, TB, 0, s>>>(L, delta, leaflev, blockcnt, nblk, ds, cap_nodes, node_start,
                                      node_level, node_parent, node_link, node_count, node_nchild);
     sys_root_init_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(L.nsys, sys_root);
     sys_root_kernel<<<(L.nsys + 255) / 256, 256, 0, s>>>(ds, node_start, d_off, L.nsys, sys_root);
-    tree_moments(s, L, keys, pos4, d_box, leaf_cap, G, ds, node_start, node_level, node_link,
-                 node_count, node_nchild, nodeA, nodeB, mass2, nodeQ, nsm, false);
+    tree_moments(s, L, keys, pos4, d_box, leaf_cap, G, ds, node_start, node_level, node_parent,
+                 node_link, node_count, node_nchild, node_arrive, nodeA, nodeB, mass2, nodeQ, nsm,
+                 false);
 }
 
 // CTAs per SM of the warp-per-group passes (sphere, alpha), build-time tunable.
 #ifndef NB_GROUP_CTAS_PER_SM
 #define NB_GROUP_CTAS_PER_SM 8
 #endif
-// CTAs per SM of the moment passes (build-time tunable).
+// CTAs per SM of the moments pass (build-time tunable).
 #ifndef NB_LEAF_CTAS_PER_SM
 #define NB_LEAF_CTAS_PER_SM 32
 #endif
-#ifndef NB_INTERNAL_CTAS_PER_SM
-#define NB_INTERNAL_CTAS_PER_SM 16
-#endif
 
-// Moments of every node of the current tree from pos4: leaves in one launch
-// (one warp per 32 nodes), internal nodes one launch per level, deepest
-// first (level `levels` holds leaves only).
+// Moments of every node of the current tree from pos4 in one launch (one warp
+// per 32 consecutive nodes for the leaves; internal nodes climb from the
+// leaves).  The arrival counters must be zero: the build zeroes them and a
+// completed pass leaves them zero.
 void tree_moments(cudaStream_t s, const Layout &L, const uint64_t *keys, const float4 *pos4,
                   const SysBox *d_box, int leaf_cap, float G, DevState *ds,
-                  const int32_t *node_start, const int8_t *node_level, const int32_t *node_link,
-                  int32_t *node_count, const int32_t *node_nchild, float4 *nodeA, float4 *nodeB,
-                  float2 *mass2, float4 *nodeQ, int nsm, bool refit) {
+                  const int32_t *node_start, const int8_t *node_level, const int32_t *node_parent,
+                  const int32_t *node_link, int32_t *node_count, const int32_t *node_nchild,
+                  int32_t *node_arrive, float4 *nodeA, float4 *nodeB, float2 *mass2,
+                  float4 *nodeQ, int nsm, bool refit) {
     int64_t mb = (L.n / 4 + 255) / 256;
     if (mb > (int64_t)nsm * NB_LEAF_CTAS_PER_SM) mb = (int64_t)nsm * NB_LEAF_CTAS_PER_SM;
     if (mb < 1) mb = 1;
+    const int rf = refit ? 1 : 0;
     if (leaf_cap <= 4)
-        leaf_moments_kernel<4><<<(int)mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start,
-                                                       node_level, node_link, node_count,
-                                                       node_nchild, nodeA, nodeB, mass2, nodeQ);
+        moments_kernel<4><<<(int)mb, 256, 0, s>>>(L, rf, keys, pos4, d_box, G, ds, node_start,
+                                                  node_level, node_parent, node_link, node_count,
+                                                  node_nchild, node_arrive, nodeA, nodeB, mass2,
+                                                  nodeQ);
     else
-        leaf_moments_kernel<8><<<(int)mb, 256, 0, s>>>(L, keys, pos4, d_box, G, ds, node_start,
-                                                       node_level, node_link, node_count,
-                                                       node_nchild, nodeA, nodeB, mass2, nodeQ);
-    const int ib = nsm * NB_INTERNAL_CTAS_PER_SM;
-    for (int l = L.levels - 1; l >= 0; l--)
-        internal_moments_kernel<<<ib, 256, 0, s>>>(L, l, refit ? 1 : 0, keys, d_box, G, ds,
-                                                   node_start, node_link, node_count, node_nchild,
-                                                   nodeA, nodeB, mass2, nodeQ);
+        moments_kernel<8><<<(int)mb, 256, 0, s>>>(L, rf, keys, pos4, d_box, G, ds, node_start,
+                                                  node_level, node_parent, node_link, node_count,
+                                                  node_nchild, node_arrive, nodeA, nodeB, mass2,
+                                                  nodeQ);
 }
 
 // ---------------------------------------------------------------- groups
