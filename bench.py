@@ -402,8 +402,9 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": n * (3 * 8 + 7 * 4),
                 "d2h_bytes_per_step": n * (3 * 8 + 6 * 4),
                 "steps": args.e2e_steps,
-                "note": "nbody_step(nsteps=1) per step on pinned host arrays; the library "
-                        "copies state in and out every call"},
+                "note": "nbody_step(nsteps=1) per step on pinned host arrays: every call reads "
+                        "the state from host memory and writes it back (the state load and the "
+                        "closing gather use the page-locked arrays in place)"},
         "clocks": clocks,
         "gpu_launches": int(st.kernels),
     }

@@ -24,7 +24,9 @@
  * Conventions for every entry point
  *   - Pointers may be device pointers or host pointers (pageable or pinned);
  *     the library inspects each with cudaPointerGetAttributes and stages host
- *     data through its own device buffers.  Device pointers are used in place.
+ *     data through its own device buffers.  Device pointers are used in place,
+ *     and so are page-locked host arrays of nbody_step(_batched), whose state
+ *     is read once by one kernel and written back once by another.
  *   - Arrays are structure-of-arrays, length n, in the caller's particle
  *     order; the library's internal Morton order never leaks out.
  *   - Every call returns an nbody_status; no C++ exception crosses the ABI.

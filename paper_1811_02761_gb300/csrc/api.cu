@@ -240,6 +240,35 @@ cudaError_t stage_out(nbody_ctx *c, int slot, void *p, size_t bytes, void **out)
     return e;
 }
 
+// An array the step's kernels touch exactly once (read in, or written back):
+// device pointers pass through, page-locked host memory is passed as its
+// device mapping (the kernel reads or writes it across the host link in one
+// coalesced pass, with no staging copy), and other host memory is staged as
+// in stage_in.  *direct tells whether no copy-back is needed.
+cudaError_t stage_once(nbody_ctx *c, int slot, const void *p, size_t bytes, const void **out,
+                       bool *direct) {
+    *direct = true;
+    if (!p) {
+        *out = nullptr;
+        return cudaSuccess;
+    }
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        *out = p;
+        return cudaSuccess;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        *out = at.devicePointer;
+        return cudaSuccess;
+    }
+    *direct = false;
+    return stage_in(c, slot, p, bytes, out);
+}
+
 cudaError_t stage_out_finish(nbody_ctx *c, void *host, const void *dev, size_t bytes) {
     if (!host || host == dev) return cudaSuccess;
     return cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream);
@@ -1073,7 +1102,11 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     const void *in[10];
     void *arr[10] = {x, y, z, vx, vy, vz, (void *)m, ax, ay, az};
     size_t sz[10] = {db, db, db, fb, fb, fb, fb, fb, fb, fb};
-    for (int k = 0; k < 10; k++) NB_CUDA(ctx, stage_in(ctx, k, arr[k], sz[k], &in[k]));
+    // load_state reads each input once and the closing gather writes each
+    // output once: page-locked host arrays are used in place
+    bool direct[10];
+    for (int k = 0; k < 10; k++)
+        NB_CUDA(ctx, stage_once(ctx, k, arr[k], sz[k], &in[k], &direct[k]));
     float4 *acc = P<float4>(ctx->acc_s);
     ctx->kernels = 0;
     ctx->wev_used = 0;
@@ -1264,9 +1297,8 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
                        (float *)in[8], (float *)in[9], P<uint32_t>(ctx->vals_alt));
     ctx->kernels += 2;
     for (int k = 0; k < 10; k++) {
-        if (k == 6) continue;
-        if (in[k] != arr[k])
-            NB_CUDA(ctx, cudaMemcpyAsync(arr[k], in[k], sz[k], cudaMemcpyDeviceToHost, s));
+        if (k == 6 || direct[k]) continue;
+        NB_CUDA(ctx, cudaMemcpyAsync(arr[k], in[k], sz[k], cudaMemcpyDeviceToHost, s));
     }
     st = read_status(ctx);
     float ms_build = 0.0f, ms_walk = 0.0f;

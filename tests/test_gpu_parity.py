@@ -484,3 +484,37 @@ def test_resume_from_saved_state_is_bit_identical(tmp_path):
         nb.nbody_destroy(ctx)
         for r, t in zip(ref, T):
             assert np.array_equal(r, host(t))
+
+
+def test_step_on_host_arrays_matches_device_arrays():
+    """nbody_step on page-locked host tensors (read and written in place by the
+    state load and the closing gather) and on pageable numpy arrays (staged
+    through device copies) leaves the same state, bit for bit, as the same
+    steps on device tensors."""
+    n = 20000
+    p = ics.plummer(n, 17)
+    cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC)
+
+    def run(kind):
+        ctx = nb.nbody_create(cfg)
+        A = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+        nb.nbody_build(ctx, *[dev(p[k]) for k in ("x", "y", "z")], dev(p["m"]))
+        nb.nbody_walk(ctx, None, *A)
+        arrs = [p[k].astype(np.float64) for k in ("x", "y", "z")]
+        arrs += [p[k].copy() for k in ("vx", "vy", "vz")] + [host(a) for a in A]
+        m = np.ascontiguousarray(p["m"])
+        if kind == "device":
+            T, mt = [dev(a) for a in arrs], dev(m)
+        elif kind == "pinned":
+            T = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in arrs]
+            mt = torch.from_numpy(m).pin_memory()
+        else:
+            T, mt = [np.ascontiguousarray(a) for a in arrs], m
+        nb.nbody_step(ctx, *T[:3], *T[3:6], mt, *T[6:9], 1.0 / 256, 3)
+        nb.nbody_destroy(ctx)
+        return [t.cpu().numpy() if isinstance(t, torch.Tensor) else t for t in T]
+
+    ref = run("device")
+    for kind in ("pinned", "pageable"):
+        for r, g in zip(ref, run(kind)):
+            assert np.array_equal(r, g), kind
