@@ -30,8 +30,10 @@ __device__ __forceinline__ float acc_mag(float4 a) {
 __global__ void kick_drift_kernel(int64_t n, StepState st, const float4 *__restrict__ acc,
                                   float hclose, float hdt, double dt, float4 *pos4) {
     NB_GRID_LOOP(i, n) {
-        float4 a = acc[i];
+        const float4 a = acc[i];
         float vx = st.vx[i], vy = st.vy[i], vz = st.vz[i];
+        const double x0 = st.x[i], y0 = st.y[i], z0 = st.z[i];
+        const float m = pos4 ? st.m[i] : 0.0f;
         if (hclose != 0.0f) {
             vx = fmaf(a.x, hclose, vx);
             vy = fmaf(a.y, hclose, vy);
@@ -44,22 +46,23 @@ __global__ void kick_drift_kernel(int64_t n, StepState st, const float4 *__restr
         st.vx[i] = vx;
         st.vy[i] = vy;
         st.vz[i] = vz;
-        const double x = st.x[i] + (double)vx * dt;
-        const double y = st.y[i] + (double)vy * dt;
-        const double z = st.z[i] + (double)vz * dt;
+        const double x = x0 + (double)vx * dt;
+        const double y = y0 + (double)vy * dt;
+        const double z = z0 + (double)vz * dt;
         st.x[i] = x;
         st.y[i] = y;
         st.z[i] = z;
-        if (pos4) pos4[i] = make_float4((float)x, (float)y, (float)z, st.m[i]);
+        if (pos4) pos4[i] = make_float4((float)x, (float)y, (float)z, m);
     }
 }
 
 __global__ void kick_kernel(int64_t n, StepState st, const float4 *__restrict__ acc, float hdt) {
     NB_GRID_LOOP(i, n) {
-        float4 a = acc[i];
-        st.vx[i] = fmaf(a.x, hdt, st.vx[i]);
-        st.vy[i] = fmaf(a.y, hdt, st.vy[i]);
-        st.vz[i] = fmaf(a.z, hdt, st.vz[i]);
+        const float4 a = acc[i];
+        const float vx = st.vx[i], vy = st.vy[i], vz = st.vz[i];
+        st.vx[i] = fmaf(a.x, hdt, vx);
+        st.vy[i] = fmaf(a.y, hdt, vy);
+        st.vz[i] = fmaf(a.z, hdt, vz);
         st.aold[i] = acc_mag(a);
     }
 }
@@ -74,30 +77,40 @@ void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, flo
 }
 
 // Gather the state into the new Morton order and refresh the FP32 walk copy.
-__global__ void permute_state_kernel(int64_t n, const uint32_t *__restrict__ perm, StepState src,
-                                     StepState dst, float4 *__restrict__ pos4) {
-    NB_GRID_LOOP(i, n) {
-        uint32_t j = perm[i];
-        double px = src.x[j], py = src.y[j], pz = src.z[j];
-        float mj = src.m[j];
-        dst.x[i] = px;
-        dst.y[i] = py;
-        dst.z[i] = pz;
-        pos4[i] = make_float4((float)px, (float)py, (float)pz, mj);
-        dst.vx[i] = src.vx[j];
-        dst.vy[i] = src.vy[j];
-        dst.vz[i] = src.vz[j];
-        dst.m[i] = mj;
-        dst.aold[i] = src.aold[j];
-        dst.id[i] = src.id[j];
-        if (src.pcost) dst.pcost[i] = src.pcost[j];
-        if (src.lvl) dst.lvl[i] = src.lvl[j];
-    }
+// In these per-particle kernels every load is issued before the first store:
+// the compiler may not move a load above a store to memory it cannot prove
+// distinct, so interleaving them would serialise the thread's round trips.
+__global__ void __launch_bounds__(256) permute_state_kernel(int64_t n,
+                                                            const uint32_t *__restrict__ perm,
+                                                            StepState src, StepState dst,
+                                                            float4 *__restrict__ pos4) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    const double px = src.x[j], py = src.y[j], pz = src.z[j];
+    const float vx = src.vx[j], vy = src.vy[j], vz = src.vz[j];
+    const float m = src.m[j], ao = src.aold[j];
+    const uint32_t id = src.id[j];
+    const float pc = src.pcost ? src.pcost[j] : 0.0f;
+    const uint8_t lv = src.lvl ? src.lvl[j] : (uint8_t)0;
+    dst.x[i] = px;
+    dst.y[i] = py;
+    dst.z[i] = pz;
+    pos4[i] = make_float4((float)px, (float)py, (float)pz, m);
+    dst.vx[i] = vx;
+    dst.vy[i] = vy;
+    dst.vz[i] = vz;
+    dst.m[i] = m;
+    dst.aold[i] = ao;
+    dst.id[i] = id;
+    if (src.pcost) dst.pcost[i] = pc;
+    if (src.lvl) dst.lvl[i] = lv;
 }
 
 void launch_permute_state(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
                           StepState dst, float4 *pos4) {
-    permute_state_kernel<<<grid_for(n), 256, 0, s>>>(n, perm, src, dst, pos4);
+    const int64_t b = (n + 255) / 256;
+    permute_state_kernel<<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(n, perm, src, dst, pos4);
 }
 
 __global__ void load_state_kernel(int64_t n, const double *x, const double *y, const double *z,
@@ -105,14 +118,16 @@ __global__ void load_state_kernel(int64_t n, const double *x, const double *y, c
                                   const float *m, const float *ax, const float *ay,
                                   const float *az, StepState st, float4 *acc) {
     NB_GRID_LOOP(i, n) {
-        st.x[i] = x[i];
-        st.y[i] = y[i];
-        st.z[i] = z[i];
-        st.vx[i] = vx[i];
-        st.vy[i] = vy[i];
-        st.vz[i] = vz[i];
-        st.m[i] = m[i];
-        float a0 = ax[i], a1 = ay[i], a2 = az[i];
+        const double px = x[i], py = y[i], pz = z[i];
+        const float qx = vx[i], qy = vy[i], qz = vz[i], mi = m[i];
+        const float a0 = ax[i], a1 = ay[i], a2 = az[i];
+        st.x[i] = px;
+        st.y[i] = py;
+        st.z[i] = pz;
+        st.vx[i] = qx;
+        st.vy[i] = qy;
+        st.vz[i] = qz;
+        st.m[i] = mi;
         acc[i] = make_float4(a0, a1, a2, 0.0f);
         st.aold[i] = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
         st.id[i] = (uint32_t)i;
@@ -131,14 +146,16 @@ __global__ void store_state_kernel(int64_t n, StepState st, const float4 *__rest
                                    double *x, double *y, double *z, float *vx, float *vy,
                                    float *vz, float *ax, float *ay, float *az) {
     NB_GRID_LOOP(i, n) {
-        uint32_t o = st.id[i];
-        x[o] = st.x[i];
-        y[o] = st.y[i];
-        z[o] = st.z[i];
-        vx[o] = st.vx[i];
-        vy[o] = st.vy[i];
-        vz[o] = st.vz[i];
-        float4 a = acc[i];
+        const uint32_t o = st.id[i];
+        const double px = st.x[i], py = st.y[i], pz = st.z[i];
+        const float qx = st.vx[i], qy = st.vy[i], qz = st.vz[i];
+        const float4 a = acc[i];
+        x[o] = px;
+        y[o] = py;
+        z[o] = pz;
+        vx[o] = qx;
+        vy[o] = qy;
+        vz[o] = qz;
         ax[o] = a.x;
         ay[o] = a.y;
         az[o] = a.z;
@@ -159,13 +176,15 @@ __global__ void gather_state_kernel(int64_t n, StepState st, const float4 *__res
                                     float *ay, float *az) {
     NB_GRID_LOOP(o, n) {
         const uint32_t i = inv[o];
-        x[o] = st.x[i];
-        y[o] = st.y[i];
-        z[o] = st.z[i];
-        vx[o] = st.vx[i];
-        vy[o] = st.vy[i];
-        vz[o] = st.vz[i];
+        const double px = st.x[i], py = st.y[i], pz = st.z[i];
+        const float qx = st.vx[i], qy = st.vy[i], qz = st.vz[i];
         const float4 a = acc[i];
+        x[o] = px;
+        y[o] = py;
+        z[o] = pz;
+        vx[o] = qx;
+        vy[o] = qy;
+        vz[o] = qz;
         ax[o] = a.x;
         ay[o] = a.y;
         az[o] = a.z;

@@ -140,3 +140,43 @@ def test_step_with_rebuild_interval(interval, want):
         assert oracle.percentile_nearest_rank(ei, q) <= 1.5 * oracle.percentile_nearest_rank(e1, q) + 1e-6
     # the trajectories stay close (forces differ only by tree error)
     assert np.max(np.abs(Xi[0] - X1[0])) < 1e-4
+
+
+def test_repeated_refits_and_builds_are_reproducible():
+    """The moments pass counts every finished node in at its parent and leaves
+    the counters at zero: refits to other positions and back reproduce the
+    node records bit for bit, a second build reproduces the first, and a refit
+    at the build positions keeps the build's masses, centres and quadrupoles
+    (b_J then comes from the child recurrence alone, never below the build's)."""
+    n = 30000
+    p = ics.galaxy(n, 33)
+    m = dev(p["m"])
+    P0 = [dev(p[k]) for k in ("x", "y", "z")]
+    P1 = [dev(a) for a in moved(p, 5, 0.02)]
+    E = nb.nbody
+    what = (E.EXPORT_NODE_A, E.EXPORT_NODE_B, E.EXPORT_NODE_Q, E.EXPORT_NODE_COUNT)
+    ctx = nb.nbody_create(nb.nbody_config_default(eps=EPS, delta_acc=DACC, quadrupole=1))
+    try:
+        def records():
+            return [nb.nbody_export(ctx, w).copy() for w in what]
+
+        nb.nbody_build(ctx, *P0, m)
+        b0 = records()
+        nb.nbody_refit(ctx, *P1, m)
+        r1 = records()
+        nb.nbody_refit(ctx, *P0, m)
+        r0 = records()
+        nb.nbody_refit(ctx, *P1, m)
+        r1b = records()
+        nb.nbody_build(ctx, *P0, m)
+        b0b = records()
+    finally:
+        nb.nbody_destroy(ctx)
+    for a, b in zip(r1, r1b):
+        assert np.array_equal(a, b)
+    for a, b in zip(b0, b0b):
+        assert np.array_equal(a, b)
+    assert np.array_equal(b0[0], r0[0]) and np.array_equal(b0[2], r0[2])
+    assert np.array_equal(b0[3], r0[3])
+    assert np.all(r0[1][:, 0] >= b0[1][:, 0])
+    assert not np.array_equal(r1[0], b0[0])
