@@ -40,6 +40,7 @@ METRIC = "s/step & Ginteractions/s at N=2^23, % GB300 FP32 peak, at stated force
 UNIT = "Ginteractions/s"
 FLOPS_PER_INTERACTION = 22  # 3 sub, 3 FMA (r^2+eps^2), rsqrt = 4, 3 mul, 3 FMA
 EPS, DACC, DT = 1.0 / 64, 2.0 ** -9, 1.0 / 256
+PHASE_STEPS = 8  # eager steps that time the phases when the timed steps replay a graph
 FP32_LANES_PER_SM = 128
 
 # DRAM traffic of walk_kernel from one ncu capture (dram__bytes_read.sum +
@@ -300,13 +301,13 @@ def run_ours(args, rank, world, local_rank):
         elapsed_max, inter_all = float(t.item()), float(it.item())
         walk_ms, walk_launches = st.ms_walk_kernel, st.walk_launches
         phase_ms, phase_steps = (st.ms_build, st.ms_walk), args.steps
-        if walk_launches == 0:  # graph replay: time the walk kernel in two eager steps
+        if walk_launches == 0:  # graph replay: time the phases in eager steps
             c2 = nb.nbody_get_config(ctx)
             c2.use_graph = 0
             nb.nbody_set_config(ctx, c2)
-            s3 = nb.nbody_step(ctx, *X64, *V, M, *A, dt, 2)
+            s3 = nb.nbody_step(ctx, *X64, *V, M, *A, dt, PHASE_STEPS)
             walk_ms, walk_launches = s3.ms_walk_kernel, s3.walk_launches
-            phase_ms, phase_steps = (s3.ms_build, s3.ms_walk), 2
+            phase_ms, phase_steps = (s3.ms_build, s3.ms_walk), PHASE_STEPS
             c2.use_graph = 1
             nb.nbody_set_config(ctx, c2)
 
@@ -383,8 +384,9 @@ def run_ours(args, rank, world, local_rank):
         "build_ms_per_step": phase_ms[0] / phase_steps,
         "walk_phase_ms_per_step": phase_ms[1] / phase_steps,
         "phase_timing": "eager steps (CUDA events per phase)" if phase_steps == steps else
-                        "two extra eager steps after the timed graph replays (CUDA events per "
-                        "phase; graph nodes carry no events)",
+                        f"{PHASE_STEPS} extra eager steps after the timed graph replays (CUDA "
+                        "events per phase; graph nodes carry no events; the first step of the "
+                        "call also gathers the state from the caller's order)",
         "nodes": st.n_nodes, "groups": st.n_groups, "max_stack": st.max_stack,
         "rebuilds": int(st.rebuilds),
         "quadrupole": args.quadrupole,

@@ -336,7 +336,8 @@ __device__ __forceinline__ void write_quad(int id, const float q[6], float4 *nod
 // FP32 centre of mass to every member.
 //
 // One launch for the whole tree, no pass per level.  Leaves: a team of T
-// lanes takes one leaf, lane j loading members j, j + T, ... (coalesced); the
+// lanes takes one leaf (T = 1 up to leaf capacity 16: a lane per leaf, its
+// member loads issued in batches), lane j loading members j, j + T, ...; the
 // sums and the largest member distance are team reductions.  Internal nodes:
 // every finished node counts itself in at its parent (an atomic counter), and
 // the thread whose count completes the parent computes it from the children's
@@ -428,6 +429,9 @@ __device__ __forceinline__ bool count_in(int par, int nchild_par, int32_t *node_
 #define NB_MOMENTS_MIN_CTAS 5  // resident 256-thread CTAs per SM the moments pass is compiled for
 #endif
 
+// Members loaded per batch by each lane of a leaf team (independent loads in
+// flight together).
+constexpr int kLeafUnroll = 4;
 template <int T>
 __global__ void __launch_bounds__(256, NB_MOMENTS_MIN_CTAS) moments_kernel(
     Layout L, int refit, const uint64_t *__restrict__ keys, const float4 *__restrict__ pos4,
@@ -475,6 +479,7 @@ __global__ void __launch_bounds__(256, NB_MOMENTS_MIN_CTAS) moments_kernel(
             const float4 r0 = cnt > 0 ? pos4[first] : make_float4(0.f, 0.f, 0.f, 0.f);
             float2 M = make_float2(0.0f, 0.0f);
             float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll kLeafUnroll
             for (int ch = 0; ch < nch; ch++) {
                 const int k = ch * T + tl;
                 if (k < cnt) {
@@ -505,6 +510,7 @@ __global__ void __launch_bounds__(256, NB_MOMENTS_MIN_CTAS) moments_kernel(
             }
             float b2 = 0.0f;
             float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll kLeafUnroll
             for (int ch = 0; ch < nch; ch++) {
                 const int k = ch * T + tl;
                 if (k < cnt) {
@@ -618,8 +624,10 @@ void tree_moments(cudaStream_t s, const Layout &L, const uint64_t *keys, const f
     if (mb > (int64_t)nsm * NB_LEAF_CTAS_PER_SM) mb = (int64_t)nsm * NB_LEAF_CTAS_PER_SM;
     if (mb < 1) mb = 1;
     const int rf = refit ? 1 : 0;
-    if (leaf_cap <= 4)
-        moments_kernel<4><<<(int)mb, 256, 0, s>>>(L, rf, keys, pos4, d_box, G, ds, node_start,
+    // one lane per leaf up to leaf capacity 16 (each lane's member loads in
+    // batches; measured fastest), teams of 8 lanes for larger leaves
+    if (leaf_cap <= 16)
+        moments_kernel<1><<<(int)mb, 256, 0, s>>>(L, rf, keys, pos4, d_box, G, ds, node_start,
                                                   node_level, node_parent, node_link, node_count,
                                                   node_nchild, node_arrive, nodeA, nodeB, mass2,
                                                   nodeQ);
