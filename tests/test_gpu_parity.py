@@ -518,3 +518,36 @@ def test_step_on_host_arrays_matches_device_arrays():
     for kind in ("pinned", "pageable"):
         for r, g in zip(ref, run(kind)):
             assert np.array_equal(r, g), kind
+
+
+def test_batched_step_on_host_arrays_matches_device_arrays():
+    """The same for nbody_step_batched over a forest of uneven systems."""
+    sizes = [3000, 1, 700, 5000]
+    b = ics.batched(len(sizes), 13, sizes=sizes)
+    n = int(b["offsets"][-1])
+    cfg = nb.nbody_config_default(delta_acc=DACC)
+
+    def run(kind):
+        arrs = [b[k].astype(np.float64) for k in ("x", "y", "z")]
+        arrs += [b[k].copy() for k in ("vx", "vy", "vz")] + [np.zeros(n, np.float32)] * 3
+        m = np.ascontiguousarray(b["m"])
+        if kind == "device":
+            T, mt = [dev(a) for a in arrs], dev(m)
+        elif kind == "pinned":
+            T = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in arrs]
+            mt = torch.from_numpy(m).pin_memory()
+        else:
+            T, mt = [np.array(a) for a in arrs], m
+        ctx = nb.nbody_create(cfg)
+        try:
+            for _ in range(2):
+                nb.nbody_step_batched(ctx, b["offsets"], b["eps"], *T[:3], *T[3:6], mt, *T[6:9],
+                                      1.0 / 256, 2)
+        finally:
+            nb.nbody_destroy(ctx)
+        return [t.cpu().numpy() if isinstance(t, torch.Tensor) else t for t in T]
+
+    ref = run("device")
+    for kind in ("pinned", "pageable"):
+        for r, g in zip(ref, run(kind)):
+            assert np.array_equal(r, g), kind
