@@ -109,22 +109,35 @@ __global__ void __launch_bounds__(TB) leaflevel_kernel(Layout L, int cap,
 
 // One block per level: exclusive scan of that level's block counts; the
 // level's node count goes to lvl_off[l + 1] (turned into offsets below).
-__global__ void __launch_bounds__(1024) level_scan_kernel(uint32_t *blockcnt, int nblk,
+// Each thread scans LS_IPT consecutive counts, so a level of 32768 blocks
+// takes four block-wide scans.
+constexpr int LS_T = 1024, LS_IPT = 8;
+__global__ void __launch_bounds__(LS_T) level_scan_kernel(uint32_t *blockcnt, int nblk,
                                                           DevState *ds) {
     __shared__ uint32_t sh[32];
     const int l = blockIdx.x;
+    const int w = threadIdx.x >> 5;
     uint32_t carry = 0;
     uint32_t *row = blockcnt + (int64_t)l * nblk;
-    for (int base = 0; base < nblk; base += 1024) {
-        int i = base + threadIdx.x;
-        uint32_t v = i < nblk ? row[i] : 0u;
-        uint32_t incl = (uint32_t)warp_incl_scan((int)v);
-        if (lane_id() == 31) sh[threadIdx.x >> 5] = incl;
+    for (int base = 0; base < nblk; base += LS_T * LS_IPT) {
+        const int i0 = base + threadIdx.x * LS_IPT;
+        uint32_t v[LS_IPT], t = 0;
+#pragma unroll
+        for (int k = 0; k < LS_IPT; k++) {
+            v[k] = i0 + k < nblk ? row[i0 + k] : 0u;
+            t += v[k];
+        }
+        const uint32_t incl = (uint32_t)warp_incl_scan((int)t);
+        if (lane_id() == 31) sh[w] = incl;
         __syncthreads();
         if (threadIdx.x < 32) sh[threadIdx.x] = (uint32_t)warp_incl_scan((int)sh[threadIdx.x]);
         __syncthreads();
-        uint32_t ex = incl - v + ((threadIdx.x >> 5) ? sh[(threadIdx.x >> 5) - 1] : 0u);
-        if (i < nblk) row[i] = carry + ex;
+        uint32_t ex = carry + incl - t + (w ? sh[w - 1] : 0u);
+#pragma unroll
+        for (int k = 0; k < LS_IPT; k++) {
+            if (i0 + k < nblk) row[i0 + k] = ex;
+            ex += v[k];
+        }
         carry += sh[31];
         __syncthreads();
     }
@@ -589,7 +602,7 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
         leaflevel_kernel<16><<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
     else
         leaflevel_kernel<32><<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
-    level_scan_kernel<<<L.levels + 1, 1024, 0, s>>>(blockcnt, nblk, ds);
+    level_scan_kernel<<<L.levels + 1, LS_T, 0, s>>>(blockcnt, nblk, ds);
     level_offsets_kernel<<<1, 32, 0, s>>>(L.levels + 1, ds, cap_nodes);
     node_zero_kernel<<<nsm * 8, 256, 0, s>>>(ds, cap_nodes, node_nchild, node_arrive);
     nodes_kernel<<<nblk, TB, 0, s>>>(L, delta, leaflev, blockcnt, nblk, ds, cap_nodes, node_start,
