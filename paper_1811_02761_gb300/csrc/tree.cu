@@ -745,36 +745,45 @@ __global__ void __launch_bounds__(256) group_info_kernel(Layout L, int G,
                                                          const int32_t *__restrict__ grp_first,
                                                          int32_t *grp_count, float4 *grp_sphere,
                                                          int32_t *grp_sys) {
+    // a half-warp per group, two groups per warp at a time: both groups'
+    // member loads are in flight together (min, max and the largest distance
+    // do not depend on the order of the reduction)
     const int ng = ds->ngroups;
-    const unsigned lane = lane_id();
+    const unsigned lane = lane_id(), sl = lane & 15u;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int g = warp; g < ng; g += nw) {
-        int first = grp_first[g];
-        int end = (g + 1 < ng) ? grp_first[g + 1] : (int)L.n;
-        int cnt = end - first;
+    for (int g0 = 2 * warp; g0 < ng; g0 += 2 * nw) {
+        const int g = g0 + (int)(lane >> 4);
+        int first = 0, cnt = 0;
+        if (g < ng) {
+            first = grp_first[g];
+            const int end = (g + 1 < ng) ? grp_first[g + 1] : (int)L.n;
+            cnt = end - first;
+        }
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int k = lane; k < cnt; k += 32) {
+#pragma unroll 4
+        for (int k = (int)sl; k < cnt; k += 16) {
             float4 p = pos4[first + k];
             lo[0] = fminf(lo[0], p.x); hi[0] = fmaxf(hi[0], p.x);
             lo[1] = fminf(lo[1], p.y); hi[1] = fmaxf(hi[1], p.y);
             lo[2] = fminf(lo[2], p.z); hi[2] = fmaxf(hi[2], p.z);
         }
         for (int a = 0; a < 3; a++)
-            for (int o = 16; o; o >>= 1) {
+            for (int o = 8; o; o >>= 1) {
                 lo[a] = fminf(lo[a], __shfl_xor_sync(NB_FULL, lo[a], o));
                 hi[a] = fmaxf(hi[a], __shfl_xor_sync(NB_FULL, hi[a], o));
             }
         float c[3];
         for (int a = 0; a < 3; a++) c[a] = 0.5f * (lo[a] + hi[a]);
         float r2 = 0.0f;
-        for (int k = lane; k < cnt; k += 32) {
+#pragma unroll 4
+        for (int k = (int)sl; k < cnt; k += 16) {
             float4 p = pos4[first + k];
             float dx = p.x - c[0], dy = p.y - c[1], dz = p.z - c[2];
             r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
         }
-        for (int o = 16; o; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(NB_FULL, r2, o));
-        if (lane == 0) {
+        for (int o = 8; o; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(NB_FULL, r2, o));
+        if (sl == 0 && g < ng) {
             // rounded up so the sphere encloses every member despite FP32 error
             float r = __fsqrt_ru(r2) * (1.0f + 0x1p-20f);
             grp_count[g] = cnt;
@@ -819,16 +828,23 @@ __global__ void group_alpha_kernel(const DevState *__restrict__ ds,
                                    const int32_t *__restrict__ grp_first,
                                    const int32_t *__restrict__ grp_count,
                                    const float *__restrict__ aold, float dacc, float *grp_alpha) {
+    // a half-warp per group, two groups per warp at a time (as group_info)
     const int ng = ds->ngroups;
-    const unsigned lane = lane_id();
+    const unsigned lane = lane_id(), sl = lane & 15u;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int g = warp; g < ng; g += nw) {
-        int first = grp_first[g], cnt = grp_count[g];
+    for (int g0 = 2 * warp; g0 < ng; g0 += 2 * nw) {
+        const int g = g0 + (int)(lane >> 4);
+        int first = 0, cnt = 0;
+        if (g < ng) {
+            first = grp_first[g];
+            cnt = grp_count[g];
+        }
         float m = INFINITY;
-        for (int k = lane; k < cnt; k += 32) m = fminf(m, aold[first + k]);
-        for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(NB_FULL, m, o));
-        if (lane == 0) grp_alpha[g] = dacc * m;
+#pragma unroll 4
+        for (int k = (int)sl; k < cnt; k += 16) m = fminf(m, aold[first + k]);
+        for (int o = 8; o; o >>= 1) m = fminf(m, __shfl_xor_sync(NB_FULL, m, o));
+        if (sl == 0 && g < ng) grp_alpha[g] = dacc * m;
     }
 }
 
