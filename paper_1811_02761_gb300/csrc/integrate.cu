@@ -142,30 +142,11 @@ void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double 
     load_state_kernel<<<grid_for(n), 256, 0, s>>>(n, x, y, z, vx, vy, vz, m, ax, ay, az, st, acc);
 }
 
-__global__ void store_state_kernel(int64_t n, StepState st, const float4 *__restrict__ acc,
-                                   double *x, double *y, double *z, float *vx, float *vy,
-                                   float *vz, float *ax, float *ay, float *az) {
-    NB_GRID_LOOP(i, n) {
-        const uint32_t o = st.id[i];
-        const double px = st.x[i], py = st.y[i], pz = st.z[i];
-        const float qx = st.vx[i], qy = st.vy[i], qz = st.vz[i];
-        const float4 a = acc[i];
-        x[o] = px;
-        y[o] = py;
-        z[o] = pz;
-        vx[o] = qx;
-        vy[o] = qy;
-        vz[o] = qz;
-        ax[o] = a.x;
-        ay[o] = a.y;
-        az[o] = a.z;
-    }
-}
-
-// The same copy as a gather: inv[o] = the sorted index of caller index o,
-// then every output array is written in caller order (coalesced writes; the
-// reads are random but fetch whole sectors, where random writes of 4- and
-// 8-byte values each cost a partial-sector write).
+// The state back in the caller's order, as a gather: inv[o] = the sorted index
+// of caller index o, then every output array is written in caller order
+// (coalesced writes; the reads are random but fetch whole sectors, where a
+// scatter's random writes of 4- and 8-byte values would each cost a
+// partial-sector write).
 __global__ void inverse_perm_kernel(int64_t n, const uint32_t *__restrict__ id, uint32_t *inv) {
     NB_GRID_LOOP(i, n) inv[id[i]] = (uint32_t)i;
 }
@@ -194,10 +175,6 @@ __global__ void gather_state_kernel(int64_t n, StepState st, const float4 *__res
 void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
                         float *ay, float *az, uint32_t *inv) {
-    if (!inv) {
-        store_state_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, x, y, z, vx, vy, vz, ax, ay, az);
-        return;
-    }
     inverse_perm_kernel<<<grid_for(n), 256, 0, s>>>(n, st.id, inv);
     gather_state_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, inv, x, y, z, vx, vy, vz, ax, ay, az);
 }

@@ -324,8 +324,8 @@ void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double 
                        const double *z, const float *vx, const float *vy, const float *vz,
                        const float *m, const float *ax, const float *ay, const float *az,
                        StepState st, float4 *acc);
-// The state back in caller order; inv (nullable, uint32 [n] scratch): as a
-// gather through the inverse permutation instead of a scatter.
+// The state back in caller order, as a gather through the inverse
+// permutation; inv: uint32 [n] scratch.
 void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
                         float *ay, float *az, uint32_t *inv = nullptr);

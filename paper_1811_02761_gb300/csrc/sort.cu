@@ -235,8 +235,6 @@ constexpr int RS_SPIN_LIMIT = 1 << 20;
 #endif
 constexpr int RS_LB = NB_RS_LB;
 constexpr int SCAN_T = 1024;
-constexpr int SCAN_IPT = 4;
-constexpr int SCAN_CH = SCAN_T * SCAN_IPT;
 static_assert(RS_BINS == RS_THREADS, "one digit per thread");
 
 // Look-back word of one (tile, digit): bits 63..60 = pass + 1 (a word left by
@@ -376,28 +374,6 @@ void launch_keys(cudaStream_t s, const Layout &L, const void *x, const void *y, 
         keys_kernel<float><<<blocks, 256, 0, s>>>(L, (const float *)x, (const float *)y,
                                                   (const float *)z, d_off, d_box, keys, vals,
                                                   hist, passes);
-}
-
-// In-place exclusive scan of a[0..len) in chunks of SCAN_CH; chunk totals go
-// to sums[] (scanned later by scan_sums_kernel).
-__global__ void __launch_bounds__(SCAN_T) scan_chunks_kernel(uint32_t *a, int64_t len,
-                                                             uint32_t *sums) {
-    __shared__ uint32_t sh[SCAN_T / 32];
-    const int64_t base = (int64_t)blockIdx.x * SCAN_CH + threadIdx.x * SCAN_IPT;
-    uint32_t v[SCAN_IPT], t = 0;
-#pragma unroll
-    for (int k = 0; k < SCAN_IPT; k++) {
-        v[k] = (base + k < len) ? a[base + k] : 0u;
-        t += v[k];
-    }
-    uint32_t total;
-    uint32_t ex = block_excl_scan<SCAN_T>(t, sh, &total);
-#pragma unroll
-    for (int k = 0; k < SCAN_IPT; k++) {
-        if (base + k < len) a[base + k] = ex;
-        ex += v[k];
-    }
-    if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
 // Single-block exclusive scan of sums[0..nb) in place; the grand total goes
