@@ -43,13 +43,15 @@ EPS, DACC, DT = 1.0 / 64, 2.0 ** -9, 1.0 / 256
 PHASE_STEPS = 8  # eager steps that time the phases when the timed steps replay a graph
 FP32_LANES_PER_SM = 128
 
-# DRAM traffic of walk_kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the N=2^22 galaxy, per particle; the launch at the
-# bench's N is scaled by particles.  It is reported only while the walk source
-# is the one the counters were taken on (sha256 of walk_impl.cuh).
-WALK_TRAFFIC = {"bytes_per_particle": (108.531968e6 + 44.886016e6) / 4194304,
+# DRAM traffic of walk_kernel from one single-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the N=2^23 galaxy's
+# warm-up-step walk, per particle; at another N the launch is scaled by
+# particles.  It is reported only while the walk source is the one the
+# counters were taken on (sha256 of walk_impl.cuh).
+WALK_TRAFFIC = {"bytes_per_particle": (230.80e6 + 111.21e6) / 8388608,
+                "n_captured": 8388608,
                 "walk_impl_sha256": "7d21c4be15788de7a574ec078a579bf11bcbc0270c6a2692ca4424749344e72d",
-                "capture": "profiles/walk_kernel_galaxy_2e22.md (N=2^22, scaled by particles)"}
+                "capture": "profiles/walk_kernel_traffic_galaxy_2e23.md"}
 
 
 def walk_traffic(n):
@@ -61,7 +63,10 @@ def walk_traffic(n):
         return None, "walk source not found"
     if sha != WALK_TRAFFIC["walk_impl_sha256"]:
         return None, "walk kernel changed since the ncu capture"
-    return WALK_TRAFFIC["bytes_per_particle"] * n, WALK_TRAFFIC["capture"]
+    note = WALK_TRAFFIC["capture"]
+    if n != WALK_TRAFFIC["n_captured"]:
+        note += f" (N={WALK_TRAFFIC['n_captured']}, scaled by particles)"
+    return WALK_TRAFFIC["bytes_per_particle"] * n, note
 
 
 def parse():
