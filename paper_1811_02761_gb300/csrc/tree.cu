@@ -439,7 +439,7 @@ __device__ __forceinline__ bool count_in(int par, int nchild_par, int32_t *node_
 }
 
 #ifndef NB_MOMENTS_MIN_CTAS
-#define NB_MOMENTS_MIN_CTAS 5  // resident 256-thread CTAs per SM the moments pass is compiled for
+#define NB_MOMENTS_MIN_CTAS 6  // resident 256-thread CTAs per SM the moments pass is compiled for
 #endif
 
 // Members loaded per batch by each lane of a leaf team (independent loads in
@@ -620,7 +620,7 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
 #endif
 // CTAs per SM of the moments pass (build-time tunable).
 #ifndef NB_LEAF_CTAS_PER_SM
-#define NB_LEAF_CTAS_PER_SM 32
+#define NB_LEAF_CTAS_PER_SM 64
 #endif
 
 // Moments of every node of the current tree from pos4 in one launch (one warp
