@@ -133,8 +133,18 @@ def workload_config(n, rebuild_interval=1, dt=DT, block_levels=0, block_eta=0.02
                     f"delta_acc=2^-9, {integ}, {rb}",
         "n": n,
         "flops_per_interaction": FLOPS_PER_INTERACTION,
-        "l2": "inputs larger than L2 (particle state ~0.45 GB, tree ~0.4 GB > 129 MB)",
+        "l2": l2_note(n),
     }
+
+
+def l2_note(n):
+    """Whether one step's inputs exceed the 129 MB L2 (about 0.45 GB of particle state
+    and 0.4 GB of tree at N = 2^23, in proportion to N)."""
+    state, tree = 0.45 * n / (1 << 23), 0.4 * n / (1 << 23)
+    if state + tree > 0.129:
+        return f"inputs larger than L2 (particle state ~{state:.2g} GB, tree ~{tree:.2g} GB > 129 MB)"
+    return (f"inputs smaller than L2 (~{1e3 * (state + tree):.2g} MB < 129 MB); "
+            "L2 not flushed between steps")
 
 
 # ---------------------------------------------------------------------------- clocks
