@@ -393,8 +393,9 @@ nbody_status nbody_export(nbody_ctx *ctx, int32_t what, void *dst, int64_t cap, 
 /* Self-tests of the library's failure paths (no counterpart in the paper).
  * NBODY_SELFTEST_SORT_WAIT: runs one radix-sort pass kernel on a two-tile
  * input whose first tile is never processed, so the second tile's look-back
- * (the decoupled look-back of the one-sweep sort, the library's only device
- * wait) finds nothing to wait for; the wait is bounded (2^20 polls) and the
+ * (the decoupled look-back of the one-sweep sort, the default path's only
+ * device wait; the opt-in warp-pair walk's hand-offs are the other, bounded
+ * the same way) finds nothing to wait for; the wait is bounded (2^20 polls) and the
  * kernel records a timeout and finishes.  Returns the status the device
  * reported: NBODY_ETIMEOUT when the bound works.  Allocates and frees its own
  * buffers (about 200 KB) and synchronises cuda_stream (NULL = default
