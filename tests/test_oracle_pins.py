@@ -416,6 +416,50 @@ def test_tree_distant_cluster_is_its_monopole():
     assert np.allclose([ax[k], ay[k], az[k]], want, rtol=1e-12)
 
 
+def _eq1(src, ms, tgt, G):
+    """Eq. 1 with eps = 0 written out for a handful of sources (test-side)."""
+    d = np.asarray(src, float) - np.asarray(tgt, float)
+    r = np.sqrt((d * d).sum(1))
+    keep = r > 0
+    return G * (np.asarray(ms)[keep, None] * d[keep] / r[keep, None] ** 3).sum(0)
+
+
+@pytest.mark.parametrize("case", GOLD["mac_threshold"]["cases"], ids=lambda c: c["name"])
+def test_mac_threshold_hand_cases(case):
+    """Eq. 2 at its boundary: hand-derived node/target pairs for which both
+    sides are exact in FP64 decide accept on equality, reject one ulp below,
+    the powers of b_J (2) and d (4), the factor G, the strict d > b_J and the
+    group-mode distance |com - c_g| - r_g (tests/golden/closed_forms.json)."""
+    anchors = [[0.0, 0.0, 0.0], [64.0, 64.0, 64.0]]
+    ma = 2.0 ** -40
+    cl, tg = case["cluster"], case["targets"]
+    pos = np.array(anchors + cl + tg, float)
+    m = np.array([ma, ma] + [0.25] * len(cl) + [0.25] * len(tg))
+    nt = len(tg)
+    t = oracle.Tree(pos[:, 0], pos[:, 1], pos[:, 2], m, 21, 2)
+    nd = t.nodes()
+    # the cluster is one leaf with the exact centre of mass and b_J
+    com = np.mean(np.array(cl, float), 0)
+    bJ = np.sqrt(((np.array(cl, float) - com) ** 2).sum(1)).max()
+    hit = [k for k in range(t.nnodes) if nd["nchild"][k] == 0 and nd["count"][k] == 2 and
+           nd["cx"][k] == com[0] and nd["cy"][k] == com[1] and nd["cz"][k] == com[2]]
+    assert len(hit) == 1 and nd["b"][hit[0]] == bJ and nd["M"][hit[0]] == 0.5
+    aold = np.ones(pos.shape[0])
+    aold[-nt:] = case["a_old"]
+    mode = oracle.MAC_GROUP_ACC if case["mode"] == "group" else oracle.MAC_PARTICLE_ACC
+    gs = case.get("group_size", 1)
+    ax, ay, az, _, nint = t.walk(mode, case["G"], 0.0, case["dacc"], 0.5, gs, aold, want_phi=False)
+    assert list(nint[-nt:]) == case["ninter"]
+    # the accepted cluster adds its monopole, an opened one its members
+    for j in range(nt):
+        i = pos.shape[0] - nt + j
+        others = [p for k, p in enumerate(tg) if k != j]
+        src = anchors + others + ([list(com)] if case["accept"] else cl)
+        ms = [ma, ma] + [0.25] * len(others) + ([0.5] if case["accept"] else [0.25] * len(cl))
+        want = _eq1(src, ms, tg[j], case["G"])
+        assert np.allclose([ax[i], ay[i], az[i]], want, rtol=1e-12, atol=1e-15)
+
+
 # --------------------------------------------------------------------------- quadrupoles
 def _far_cluster_walk(cl, mc, eps, quad, target=(0.0, 0.0, 0.0), leaf_cap=1):
     """Walk for one light target far from a cluster; returns its acceleration
