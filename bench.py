@@ -432,7 +432,8 @@ def run_ours(args, rank, world, local_rank):
 def run_batched(args, rank, world, local_rank):
     """512 independent systems: one forest + one persistent walk per step
     (CUDA graph of two steps) against one nbody_step call per system.  With N
-    ranks every rank takes whole systems (round robin by size), no collective."""
+    ranks every rank takes whole systems, placed by predicted walk cost, and
+    no collective touches the data path."""
     import torch
     import torch.distributed as dist
 
@@ -441,9 +442,18 @@ def run_batched(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    from paper_1811_02761_gb300.sharding import local_csr, partition_systems
+    from paper_1811_02761_gb300.sharding import (local_csr, partition_systems, rank_loads,
+                                                  system_costs)
     full = ics.batched(args.nsys, 4)
-    mine = partition_systems(np.diff(full["offsets"]), world)[rank]
+    placement, cost = "single rank: every system", None
+    if world > 1:
+        # predicted cost per system: its interactions in one walk of the whole
+        # forest (every rank computes the same numbers, so the placement needs
+        # no communication), then longest-processing-time placement by cost
+        cost = batched_system_costs(full, dev)
+        placement = "whole systems by predicted walk cost (interactions of a probe walk), LPT"
+    parts_all = partition_systems(np.diff(full["offsets"]), world, cost)
+    mine = parts_all[rank]
     off, idx = local_csr(full["offsets"], mine)
     parts = {k: full[k][idx] for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
     sizes = np.diff(off)
@@ -523,6 +533,9 @@ def run_batched(args, rank, world, local_rank):
                                f"CUDA graph of two steps",
                    "systems_this_rank": int(len(sizes)), "n_this_rank": n,
                    "parallelism": f"whole systems per rank x{world}",
+                   "placement": placement,
+                   "predicted_cost_per_rank": (rank_loads(parts_all, cost).tolist()
+                                               if cost is not None else None),
                    "l2": "inputs larger than L2 (~8M particles)"},
         "per_system_launches": {"s_per_step": per_sys,
                                 "note": "one nbody_step call (build + walk + kicks) per system "
@@ -533,6 +546,36 @@ def run_batched(args, rank, world, local_rank):
         "interactions_per_step": float(st.interactions) / args.steps,
         "gpu_launches": int(st.kernels),
     }
+
+
+def batched_system_costs(full, dev):
+    """Interactions of every system in one acceleration-MAC walk of the whole
+    forest (bootstrap walk for |a_old| first), from the walk's per-group log."""
+    import torch
+
+    import paper_1811_02761_gb300 as nb
+    from paper_1811_02761_gb300.sharding import system_costs
+
+    def D(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    n = int(full["offsets"][-1])
+    A = [torch.zeros(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    ctx = nb.nbody_create(nb.nbody_config_default(delta_acc=DACC), torch.cuda.current_stream(dev))
+    try:
+        nb.nbody_build_batched(ctx, full["offsets"], full["eps"],
+                               *[D(full[k]) for k in ("x", "y", "z")], D(full["m"]))
+        nb.nbody_walk(ctx, None, *A)
+        amag = torch.sqrt(A[0] ** 2 + A[1] ** 2 + A[2] ** 2)
+        nb.nbody_walk(ctx, amag, *A)
+        first = nb.nbody_export(ctx, nb.EXPORT_GROUP_FIRST)
+        count = nb.nbody_export(ctx, nb.EXPORT_GROUP_COUNT)
+        costs = torch.zeros(first.size, dtype=torch.int32, device=dev)
+        ng = nb.nbody_get_group_costs(ctx, costs)
+        entries = costs[:ng].cpu().numpy()
+    finally:
+        nb.nbody_destroy(ctx)
+    return system_costs(full["offsets"], first[:ng], count[:ng], entries)
 
 
 def batched_autotune(args, off, eps, parts, stream, dev, default_s_per_step):
