@@ -3,8 +3,11 @@ the launch configuration bench.py times, on sampled outputs the oracle can
 compute one by one:
   * GPU tree accelerations vs FP64 direct summation on 384 seeded targets;
   * the same targets through the FP64 oracle tree (walking only the groups
-    that hold them) -- p50/p99 of the GPU within 1.1x the oracle's + 1e-6,
-    and per-particle agreement with the oracle tree;
+    that hold them) -- p50/p99 of the GPU within 1.1x the oracle's + 1e-6;
+  * group by group over those groups: the GPU's list lengths equal the
+    oracle's except where a MAC decision sits within FP32 rounding of its
+    threshold, and every member of a group with an equal list agrees with
+    the oracle tree per particle to FP32 rounding (p50, p99 and max);
   * tree invariants that hold at any size (node count, leaf coverage).
 """
 import numpy as np
@@ -12,6 +15,7 @@ import pytest
 
 import ics
 import oracle
+from _walk_parity import compare_groups, group_entries, group_spheres, visited_margin
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +58,9 @@ def full():
                                                    nb.nbody.EXPORT_NODE_B,
                                                    nb.nbody.EXPORT_GROUP_FIRST,
                                                    nb.nbody.EXPORT_GROUP_COUNT)}
+        costs = torch.zeros(int(st.n_groups), dtype=torch.int32, device="cuda")
+        ng = nb.nbody_get_group_costs(ctx, costs)
+        ex["costs"] = costs.cpu().numpy()[:ng]
     finally:
         nb.nbody_destroy(ctx)
     return pos, p["m"].astype(np.float64), g, w, amag, st, ex
@@ -87,8 +94,8 @@ def test_fullsize_sampled_parity(full):
     pos = np.empty(N, np.int64)
     pos[t.order()] = np.arange(N)
     sel = np.unique(np.searchsorted(f, pos[tg], side="right") - 1)
-    ox, oy, oz, _ = t.walk_groups(sel, oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, 64,
-                                  amag.astype(np.float64))
+    ox, oy, oz, nint = t.walk_groups(sel, oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, 64,
+                                     amag.astype(np.float64))
     eo = oracle.rel_err(ox[tg], oy[tg], oz[tg], bx, by, bz)
     for q in (50, 99):
         pg = oracle.percentile_nearest_rank(eg, q)
@@ -98,6 +105,25 @@ def test_fullsize_sampled_parity(full):
     assert np.median(d) < 5e-6
     # the GPU's groups are the oracle's groups
     assert np.array_equal(ex[nb.nbody.EXPORT_GROUP_FIRST], f.astype(np.int32))
+    assert np.array_equal(ex[nb.nbody.EXPORT_GROUP_COUNT], c.astype(np.int32))
+    # group by group over the walked groups: the list lengths of the plain
+    # walk at these positions are the oracle's except at near-threshold MAC
+    # decisions, and its accelerations agree per particle up to FP32 rounding
+    order = t.order()
+    ora = group_entries(nint, order, f[sel])
+    cen, rad, amin = group_spheres(x, y, z, order, f[sel], c[sel], amag.astype(np.float64))
+    nodes = t.nodes()
+    flipped, margins = compare_groups(
+        ex["costs"][sel], ora, flipped_budget=max(3, sel.size // 100),
+        explain=lambda k: visited_margin(nodes, cen[k], rad[k], DACC * amin[k], 1.0))
+    keep = np.setdiff1d(np.arange(sel.size), flipped)
+    members = np.concatenate([order[f[gi]:f[gi] + c[gi]] for gi in sel[keep]])
+    dw = oracle.rel_err(w[0][members], w[1][members], w[2][members],
+                        ox[members], oy[members], oz[members])
+    print(f"walked groups {sel.size}, flipped {flipped.size} (margins {margins}); same-list "
+          f"particles {members.size}: p50 {np.median(dw):.2e} p99 {np.percentile(dw, 99):.2e} "
+          f"max {dw.max():.2e}")
+    assert np.median(dw) < 1e-6 and np.percentile(dw, 99) < 5e-6 and dw.max() < 1e-4
 
 
 def test_fullsize_batched_sampled_parity():

@@ -4,13 +4,19 @@ Integer work (keys, sort, tree structure, groups) must match bit for bit;
 floating-point results within the tolerances stated in each test:
   * GPU direct vs FP64 direct: max relative error <= 1e-5 (compensated);
   * GPU tree error percentiles (p50, p99) vs FP64 direct within 1.1x the
-    oracle tree's percentiles + 1e-6 (same MAC reading, group mode).
+    oracle tree's percentiles + 1e-6 (same MAC reading, group mode);
+  * the walk against the oracle's walk of the same tree, group by group:
+    equal interaction-list lengths except for a few groups, each explained
+    by a MAC decision within 1e-5 (relative) of its threshold, and per-
+    particle agreement to FP32 rounding (p50 < 1e-6, p99 < 5e-6, max < 1e-4)
+    for every member of a group with an equal list.
 """
 import numpy as np
 import pytest
 
 import ics
 import oracle
+from _walk_parity import compare_groups, group_entries, group_spheres, visited_margin
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +60,9 @@ def gpu_walk(p, cfg, a_old=None, want_phi=False, offsets=None, eps_sys=None):
         st = nb.nbody_walk(ctx, None if a_old is None else dev(a_old.astype(np.float32)),
                            out[0], out[1], out[2], out[3] if want_phi else None)
         exports = {w: nb.nbody_export(ctx, w) for w in range(12)}  # all but the quadrupoles
+        costs = torch.zeros(max(int(st.n_groups), 1), dtype=torch.int32, device="cuda")
+        ng = nb.nbody_get_group_costs(ctx, costs)
+        exports["costs"] = host(costs)[:ng]
         return [host(o) for o in out], st, exports
     finally:
         nb.nbody_destroy(ctx)
@@ -131,11 +140,20 @@ def test_tree_structure_and_moments(gen, n, cap):
     for c, k in ((0, "cx"), (1, "cy"), (2, "cz")):
         scale = np.maximum(np.abs(on[k][idx]), on["b"][idx] + 1e-3)
         assert np.all(np.abs(A[:, c] - on[k][idx]) <= 2e-6 * scale)
-    # b_J on the GPU bounds member distances from the FP32 centre of mass, so it
-    # may differ from the FP64 oracle's by a few FP32 ulps of the coordinates
+    # b_J is an upper bound (Eq. 2's node size; the MAC's d > b_J must never
+    # accept a node that can hold the target): the GPU's b_J covers, with no
+    # slack, the exact (FP64) largest distance of the node's members from the
+    # GPU's own FP32 centre of mass, and exceeds the oracle's b_J by rounding only
+    perm = ex[nb.nbody.EXPORT_PERM].astype(np.int64)
+    P = np.stack([p[k][perm].astype(np.float64) for k in ("x", "y", "z")], 1)
+    rows = np.repeat(np.arange(lev.size), cnt)
+    mem = np.concatenate([np.arange(a, a + c) for a, c in zip(start, cnt)])
+    dist = np.sqrt(((P[mem] - A[rows, :3].astype(np.float64)) ** 2).sum(1))
+    exact = np.zeros(lev.size)
+    np.maximum.at(exact, rows, dist)
+    assert np.all(B[:, 0].astype(np.float64) >= exact), np.min(B[:, 0] - exact)
     b_o = on["b"][idx]
     ulp = np.spacing(np.max(np.abs(A[:, :3]), axis=1).astype(np.float32)).astype(np.float64)
-    assert np.all(B[:, 0] >= b_o * (1 - 1e-6) - 2 * ulp)
     assert np.all(B[:, 0] <= b_o * (1 + 1e-5) + 8 * ulp)
 
 
@@ -161,7 +179,7 @@ def test_walk_error_vs_oracle_tree(plummer8k, ipl, G):
     amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
     aold32 = amag.astype(np.float32)
     cfg = nb.nbody_config_default(eps=EPS, delta_acc=DACC, ipl=ipl, group_size=G)
-    (gx, gy, gz, _), st, _ = gpu_walk(p, cfg, a_old=aold32)
+    (gx, gy, gz, _), st, ex = gpu_walk(p, cfg, a_old=aold32)
     t = oracle.Tree(*f64(p), levels=21, leaf_cap=16)
     ox, oy, oz, _, nint = t.walk(oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, G,
                                  aold32.astype(np.float64))
@@ -171,10 +189,38 @@ def test_walk_error_vs_oracle_tree(plummer8k, ipl, G):
     o50, o99 = _pcts(eo)
     assert g50 <= 1.1 * o50 + 1e-6, (g50, o50)
     assert g99 <= 1.1 * o99 + 1e-6, (g99, o99)
-    # same tree, same groups, same MAC: per-particle agreement with the oracle tree
-    d = oracle.rel_err(gx.astype(float), gy.astype(float), gz.astype(float), ox, oy, oz)
-    assert np.median(d) < 5e-6
+    # same tree, same groups, same MAC: group by group, the list lengths are
+    # the oracle's except where a MAC decision is within FP32 rounding of its
+    # threshold, and the accelerations agree per particle up to FP32 rounding
+    check_walk_against_oracle_tree(p, t, ex, nint, aold32, G, (gx, gy, gz), (ox, oy, oz))
     assert abs(st.interactions - nint.sum()) <= 0.01 * nint.sum()
+
+
+def check_walk_against_oracle_tree(p, t, ex, nint, aold32, G, gpu_acc, ora_acc, dacc=DACC,
+                                   grav=1.0):
+    """Per-group list lengths and per-particle accelerations of a GPU walk
+    against the oracle's walk of the same tree (group mode, same a_old)."""
+    first = ex[nb.nbody.EXPORT_GROUP_FIRST].astype(np.int64)
+    count = ex[nb.nbody.EXPORT_GROUP_COUNT].astype(np.int64)
+    f, c = t.groups(G)
+    assert np.array_equal(first, f) and np.array_equal(count, c)
+    order = t.order()
+    ora = group_entries(nint, order, first)
+    x, y, z, _ = f64(p)
+    cen, rad, amin = group_spheres(x, y, z, order, first, count, aold32.astype(np.float64))
+    nodes = t.nodes()
+    flipped, margins = compare_groups(
+        ex["costs"], ora, flipped_budget=max(3, first.size // 200),
+        explain=lambda g: visited_margin(nodes, cen[g], rad[g], dacc * amin[g], grav))
+    d = oracle.rel_err(*[a.astype(float) for a in gpu_acc], *ora_acc)
+    same = np.ones(d.size, bool)
+    for g in flipped:
+        same[order[first[g]:first[g] + count[g]]] = False
+    ds = d[same]
+    print(f"groups {first.size}, flipped {flipped.size} (margins {margins}); "
+          f"same-list particles: p50 {np.median(ds):.2e} p99 {np.percentile(ds, 99):.2e} "
+          f"max {ds.max():.2e}; all: max {d.max():.2e}")
+    assert np.median(ds) < 1e-6 and np.percentile(ds, 99) < 5e-6 and ds.max() < 1e-4
 
 
 def test_walk_bootstrap_without_a_old(plummer8k):
@@ -240,15 +286,15 @@ def test_walk_small_and_ragged_n(n):
     ax, ay, az, _ = oracle.direct(x, y, z, m, 1.0, 0.05)
     amag = np.sqrt(ax ** 2 + ay ** 2 + az ** 2)
     cfg = nb.nbody_config_default(eps=0.05, delta_acc=DACC)
-    (gx, gy, gz, _), _, _ = gpu_walk(p, cfg, a_old=amag)
+    a32 = amag.astype(np.float32)
+    (gx, gy, gz, _), _, ex = gpu_walk(p, cfg, a_old=a32)
     if n == 1:
         assert gx[0] == 0 and gy[0] == 0 and gz[0] == 0
         return
     t = oracle.Tree(x, y, z, m, 21, 16)
-    ox, oy, oz, _, _ = t.walk(oracle.MAC_GROUP_ACC, 1.0, 0.05, DACC, 0.5, 64,
-                              amag.astype(np.float32).astype(float))
-    d = oracle.rel_err(gx.astype(float), gy.astype(float), gz.astype(float), ox, oy, oz)
-    assert np.median(d) < 1e-5 and np.percentile(d, 99) < 1e-2
+    ox, oy, oz, _, nint = t.walk(oracle.MAC_GROUP_ACC, 1.0, 0.05, DACC, 0.5, 64,
+                                 a32.astype(float))
+    check_walk_against_oracle_tree(p, t, ex, nint, a32, 64, (gx, gy, gz), (ox, oy, oz))
 
 
 def test_walk_coincident_particles():
@@ -306,11 +352,19 @@ def test_batched_forest_matches_per_system_oracle():
             continue
         t = oracle.Tree(*[b[k][sl].astype(float) for k in ("x", "y", "z", "m")], levels=levels,
                         leaf_cap=16)
-        ox, oy, oz, _, _ = t.walk(oracle.MAC_GROUP_ACC, 1.0, float(eps[s]), DACC, 0.5, 64,
-                                  aold[sl].astype(np.float32).astype(float), want_phi=False)
-        d = oracle.rel_err(gx[sl].astype(float), gy[sl].astype(float), gz[sl].astype(float),
-                           ox, oy, oz)
-        assert np.median(d) < 5e-6, (s, np.median(d))
+        a32 = aold[sl].astype(np.float32)
+        ox, oy, oz, _, nint = t.walk(oracle.MAC_GROUP_ACC, 1.0, float(eps[s]), DACC, 0.5, 64,
+                                     a32.astype(float), want_phi=False)
+        # this system's groups of the forest (sorted order keeps each system in
+        # its own index range), renumbered from the system's first particle
+        gf = ex[nb.nbody.EXPORT_GROUP_FIRST].astype(np.int64)
+        mine = (gf >= off[s]) & (gf < off[s + 1])
+        sub = {nb.nbody.EXPORT_GROUP_FIRST: gf[mine] - off[s],
+               nb.nbody.EXPORT_GROUP_COUNT: ex[nb.nbody.EXPORT_GROUP_COUNT][mine],
+               "costs": ex["costs"][mine]}
+        ps = {k: b[k][sl] for k in ("x", "y", "z", "m")}
+        check_walk_against_oracle_tree(ps, t, sub, nint, a32, 64,
+                                       (gx[sl], gy[sl], gz[sl]), (ox, oy, oz))
 
 
 # --------------------------------------------------------------------------- step, diagnostics
@@ -341,7 +395,7 @@ def test_step_one_kdk_vs_oracle():
     amag = np.sqrt(sum(a.astype(float) ** 2 for a in a0)).astype(np.float32).astype(float)
     ox, oy, oz, _, _ = t.walk(oracle.MAC_GROUP_ACC, 1.0, EPS, DACC, 0.5, 64, amag, want_phi=False)
     d = oracle.rel_err(ga[0].astype(float), ga[1].astype(float), ga[2].astype(float), ox, oy, oz)
-    assert np.median(d) < 5e-6
+    assert np.median(d) < 5e-6 and np.percentile(d, 99) < 1e-4, (np.median(d), np.percentile(d, 99))
     v1 = [v + a * dt / 2 for v, a in zip(vh, (ox, oy, oz))]
     assert np.max(np.abs(gv[0] - v1[0])) < 1e-5 * np.max(np.abs(v1[0]))
 
