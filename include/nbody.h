@@ -272,8 +272,13 @@ nbody_status nbody_diagnostics(nbody_ctx *ctx, int64_t n, const double *x, const
  * (1024 x 8 + 8 doubles, 65.6 KB per GPU, held until the process exits) that
  * every call shares: calls that overlap on the GPU race on it.  The first
  * call on a device looks up the array's device address; make that first call
- * before any stream capture.  n must be in 1..2^31-1 (larger n: EINVAL).
- * Errors: EINVAL (bad n, NULL or host input array), ECUDA. */
+ * before any stream capture.  That address is cached for the life of the
+ * device's CUDA context: do not use the library across a cudaDeviceReset.
+ * n must be in 1..2^31-1 (larger n: EINVAL).  Inputs must be device (or
+ * managed) memory of the current device; out may be host memory or device
+ * memory of the current device.
+ * Errors: EINVAL (bad n, NULL input, host input, or an array on another
+ * GPU), ECUDA. */
 nbody_status nbody_diagnostics_noalloc(int64_t n, const double *x, const double *y,
                                        const double *z, const float *vx, const float *vy,
                                        const float *vz, const float *m, const float *phi,

@@ -17,7 +17,10 @@
 //     different host threads) race on the array and may return mixed results.
 // On the first call on a device (with that device current) the library looks
 // up the array's device address with cudaGetSymbolAddress and caches it; make
-// that first call before any stream capture.
+// that first call before any stream capture.  The cached address belongs to
+// the device's current CUDA context: after a cudaDeviceReset the array may
+// sit elsewhere, so the library must not be used across a reset (nor must any
+// nbody_ctx, whose device memory a reset frees).
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -42,13 +45,18 @@ nbody_status fail(nbody_status st, const std::string &msg) {
     return st;
 }
 
-bool on_device(const void *p) {
+// True for memory the current device dev can read in place: its own device
+// memory, or managed memory.  Device memory of another GPU is refused (the
+// kernel runs on dev and would read it across the peer link, or fault when
+// peer access is off).
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes at;
     if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 // Device address of the scratch array on the current device (looked up once
@@ -80,12 +88,22 @@ extern "C" nbody_status nbody_diagnostics_noalloc(int64_t n, const double *x, co
         return fail(NBODY_EINVAL, "nbody_diagnostics_noalloc: n must be in 1..2^31-1");
     if (!x || !y || !z || !vx || !vy || !vz || !m || !out)
         return fail(NBODY_EINVAL, "nbody_diagnostics_noalloc: NULL array");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NBODY_ECUDA, "nbody_diagnostics_noalloc: no current CUDA device");
+    }
     const void *in[8] = {x, y, z, vx, vy, vz, m, phi};
     for (int k = 0; k < 8; k++)
-        if (in[k] && !on_device(in[k]))
+        if (in[k] && !on_device(in[k], dev))
             return fail(NBODY_EINVAL,
-                        "nbody_diagnostics_noalloc: input arrays must be device pointers "
-                        "(staging host arrays would need an allocation)");
+                        "nbody_diagnostics_noalloc: input arrays must be device pointers of the "
+                        "current device (staging host arrays would need an allocation)");
+    cudaPointerAttributes oat;
+    if (cudaPointerGetAttributes(&oat, out) != cudaSuccess) cudaGetLastError();
+    else if (oat.type == cudaMemoryTypeDevice && oat.device != dev)
+        return fail(NBODY_EINVAL,
+                    "nbody_diagnostics_noalloc: out is device memory of another GPU");
     // the diagnostics kernel grid-strides over at most kNoallocBlocks blocks,
     // so the partial sums of every n fit the array
     if (nb::diag_temp_bytes() > (size_t)kNoallocBlocks * 8 * sizeof(double))
@@ -95,7 +113,7 @@ extern "C" nbody_status nbody_diagnostics_noalloc(int64_t n, const double *x, co
     if (e != cudaSuccess)
         return fail(NBODY_ECUDA, std::string("nbody_diagnostics_noalloc: ") + cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const bool out_dev = on_device(out);
+    const bool out_dev = on_device(out, dev);
     double *result = out_dev ? out : scratch + kNoallocBlocks * 8;
     nb::launch_diagnostics(s, n, x, y, z, vx, vy, vz, m, phi, scratch, result);
     e = cudaGetLastError();

@@ -65,3 +65,14 @@ def test_noalloc_diagnostics_rejects_host_inputs():
     with pytest.raises(nb.NbodyError) as e:
         nb.nbody_diagnostics_noalloc(*host)
     assert e.value.status == nb.NBODY_EINVAL
+
+
+def test_noalloc_diagnostics_rejects_arrays_of_another_gpu():
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    cols = _state(100, 24)
+    other = [c.to("cuda:1") for c in cols]
+    with torch.cuda.device(0):
+        with pytest.raises(nb.NbodyError) as e:
+            nb.nbody_diagnostics_noalloc(*other)
+    assert e.value.status == nb.NBODY_EINVAL
