@@ -9,9 +9,10 @@
 //     group is tiled over the lanes as q particles per lane times s splits
 //     of the list, so that few lanes idle in the flush (lane_tile below);
 //   * traversal: a per-warp stack in shared memory whose entries are child
-//     ranges (first node, count <= 8).  Each round the warp pops up to 32
-//     nodes (one per lane), evaluates the MAC of Eq. 2 against the group's
-//     bounding sphere, and compacts the outcomes with ballot/popc:
+//     ranges (first node, count <= 8).  Each round the warp pops the top four
+//     ranges (up to 32 nodes, one per lane), evaluates the MAC of Eq. 2
+//     against the group's bounding sphere, and compacts the outcomes with
+//     ballot/popc:
 //       accepted node       -> its pseudo particle (com, M) joins the list,
 //       opened internal node -> its child range is pushed,
 //       opened leaf          -> its particles join the list;
@@ -392,40 +393,21 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
         long long entries = 0, qentries = 0;
         __syncwarp();
         while (sp > 0) {
-            // ---- pop up to 32 nodes (one per lane) from the top ranges
-            const int take = sp < 32 ? sp : 32;
+            // ---- pop the top four child ranges (<= 8 nodes each): lane L takes
+            // node L % 8 of range L / 8.  Opened internal nodes have close to 8
+            // children, so the lanes stay nearly full without a scan of the
+            // range sizes (a scan costs a chain of dependent shuffles per round).
+            const int take = sp < 4 ? sp : 4;
+            const int rr = (int)(lane >> 3), jj = (int)(lane & 7);
             uint32_t e = 0;
-            int ne = 0;
-            if ((int)lane < take) {
-                e = stk[sp - 1 - lane];
-                ne = (int)(e & 7u) + 1;
-            }
-            const int incl = warp_incl_scan(ne);
-            const int excl = incl - ne;
-            const bool cons = (int)lane < take && excl < 32;
-            const unsigned cm = __ballot_sync(NB_FULL, cons);
-            const int ncons = __popc(cm);
-            const int last = ncons - 1;
-            const int last_incl = __shfl_sync(NB_FULL, incl, last);
-            const uint32_t last_e = __shfl_sync(NB_FULL, e, last);
-            const int last_ex = __shfl_sync(NB_FULL, excl, last);
-            const int nn = last_incl < 32 ? last_incl : 32;
-            const unsigned smap = __reduce_or_sync(NB_FULL, cons ? (1u << excl) : 0u);
-            const int owner = __popc(smap & (0xffffffffu >> (31 - lane))) - 1;
-            const uint32_t oe = __shfl_sync(NB_FULL, e, owner);
-            const int oex = __shfl_sync(NB_FULL, excl, owner);
-            const int node = (int)(oe >> 3) + ((int)lane - oex);
+            if (rr < take) e = stk[sp - 1 - rr];
+            const int node = (int)(e >> 3) + jj;
+            const bool slot = rr < take && jj <= (int)(e & 7u);
             const bool in_range = node >= 0 && node < nnodes;
-            if ((int)lane < nn && !in_range) bad = true;
-            const bool has = (int)lane < nn && in_range;
-            sp -= ncons;
+            if (slot && !in_range) bad = true;
+            const bool has = slot && in_range;
+            sp -= take;
             __syncwarp();
-            if (last_incl > 32) {  // put back the unconsumed tail of the last range
-                if (lane == 0)
-                    stk[sp] = ((last_e >> 3) + (uint32_t)(32 - last_ex)) << 3 |
-                              (uint32_t)(last_incl - 32 - 1);
-                sp += 1;
-            }
 
             // ---- MAC (Eq. 2) against the group's bounding sphere
             float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = make_float4(0.f, 0.f, 0.f, 0.f);

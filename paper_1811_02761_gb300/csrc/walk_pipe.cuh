@@ -2,12 +2,12 @@
 // handled by a pair of warps, a traversal warp and an evaluation warp, that
 // pass interaction lists through two shared-memory buffers.
 //
-// The traversal warp runs the same traversal as walk_kernel (pop up to 32
-// nodes, MAC of Eq. 2 against the group's sphere, ballot/popc compaction of
-// accepted nodes, opened nodes and opened leaves) and publishes a buffer
-// whenever walk_kernel would flush its list; the evaluation warp holds the
-// group's i-particles and evaluates Eq. 1 over each published buffer with the
-// same packed-FP32 flush.  Lists, flush boundaries and the order of every sum
+// The traversal warp runs the same traversal as walk_kernel (pop four child
+// ranges of up to 8 nodes, MAC of Eq. 2 against the group's sphere,
+// ballot/popc compaction of accepted nodes, opened nodes and opened leaves)
+// and publishes a buffer whenever walk_kernel would flush its list; the
+// evaluation warp holds the group's i-particles and evaluates Eq. 1 over each
+// published buffer with the same packed-FP32 flush.  Lists, flush boundaries and the order of every sum
 // are those of walk_kernel, so the results are identical bit for bit; what
 // changes is that the traversal (integer, shared-memory and load work) and
 // the evaluation (FP32 FMA work) of different groups run in different warps
@@ -167,40 +167,21 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
             bool alive = true;
             __syncwarp();
             while (sp > 0 && alive) {
-                // ---- pop up to 32 nodes (one per lane) from the top ranges
-                const int take = sp < 32 ? sp : 32;
+                // ---- pop the top four child ranges (<= 8 nodes each): lane L takes
+                // node L % 8 of range L / 8.  Opened internal nodes have close to 8
+                // children, so the lanes stay nearly full without a scan of the
+                // range sizes (a scan costs a chain of dependent shuffles per round).
+                const int take = sp < 4 ? sp : 4;
+                const int rr = (int)(lane >> 3), jj = (int)(lane & 7);
                 uint32_t e = 0;
-                int ne = 0;
-                if ((int)lane < take) {
-                    e = stk[sp - 1 - lane];
-                    ne = (int)(e & 7u) + 1;
-                }
-                const int incl = warp_incl_scan(ne);
-                const int excl = incl - ne;
-                const bool cons = (int)lane < take && excl < 32;
-                const unsigned cm = __ballot_sync(NB_FULL, cons);
-                const int ncons = __popc(cm);
-                const int last = ncons - 1;
-                const int last_incl = __shfl_sync(NB_FULL, incl, last);
-                const uint32_t last_e = __shfl_sync(NB_FULL, e, last);
-                const int last_ex = __shfl_sync(NB_FULL, excl, last);
-                const int nn = last_incl < 32 ? last_incl : 32;
-                const unsigned smap = __reduce_or_sync(NB_FULL, cons ? (1u << excl) : 0u);
-                const int owner = __popc(smap & (0xffffffffu >> (31 - lane))) - 1;
-                const uint32_t oe = __shfl_sync(NB_FULL, e, owner);
-                const int oex = __shfl_sync(NB_FULL, excl, owner);
-                const int node = (int)(oe >> 3) + ((int)lane - oex);
+                if (rr < take) e = stk[sp - 1 - rr];
+                const int node = (int)(e >> 3) + jj;
+                const bool slot = rr < take && jj <= (int)(e & 7u);
                 const bool in_range = node >= 0 && node < nnodes;
-                if ((int)lane < nn && !in_range) bad = true;
-                const bool has = (int)lane < nn && in_range;
-                sp -= ncons;
+                if (slot && !in_range) bad = true;
+                const bool has = slot && in_range;
+                sp -= take;
                 __syncwarp();
-                if (last_incl > 32) {
-                    if (lane == 0)
-                        stk[sp] = ((last_e >> 3) + (uint32_t)(32 - last_ex)) << 3 |
-                                  (uint32_t)(last_incl - 32 - 1);
-                    sp += 1;
-                }
 
                 // ---- MAC (Eq. 2) against the group's bounding sphere
                 float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = make_float4(0.f, 0.f, 0.f, 0.f);
