@@ -108,7 +108,8 @@ def parse():
                          "by timing); the headline configuration rebuilds every step")
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=4)
-    ap.add_argument("--error-sample", type=int, default=256)
+    ap.add_argument("--error-sample", type=int, default=4096,
+                    help="seeded particles whose accelerations are checked against the FP64 direct sum")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-sample", type=int, default=1 << 16)
     ap.add_argument("--sweep-max", type=int, default=20)
@@ -252,11 +253,13 @@ def oracle_force_error(final, sample, seed):
     import oracle
     xs, ms, ga = final
     tg = np.random.default_rng(seed).choice(ms.size, sample, replace=False)
+    t0 = time.perf_counter()
     bx, by, bz, _ = oracle.direct_targets(*xs, ms, tg, 1.0, EPS)
     e = oracle.rel_err(*[a[tg].astype(np.float64) for a in ga], bx, by, bz)
     return {"p50": oracle.percentile_nearest_rank(e, 50),
             "p99": oracle.percentile_nearest_rank(e, 99), "max": float(e.max()),
-            "sample": int(sample), "vs": "FP64 direct summation at the final positions"}
+            "sample": int(sample), "vs": "FP64 direct summation at the final positions",
+            "oracle_s": time.perf_counter() - t0, "cores": oracle.threads()}
 
 
 def run_ours(args, rank, world, local_rank):
