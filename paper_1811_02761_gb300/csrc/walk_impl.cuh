@@ -41,20 +41,19 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
 }
 
 // The interaction list of a warp holds entries in pairs, structure-of-arrays
-// within the pair: LA[k] = (x_2k, x_2k+1, y_2k, y_2k+1) and LB[k] = (z_2k,
-// z_2k+1, m_2k, m_2k+1).  Two LDS.128 broadcasts then give every lane two
+// within the pair, the two halves of a pair side by side: L[2k] = (x_2k,
+// x_2k+1, y_2k, y_2k+1) and L[2k+1] = (z_2k, z_2k+1, m_2k, m_2k+1).  Two
+// LDS.128 broadcasts from one address register then give every lane two
 // entries laid out for Blackwell's packed FP32 instructions (FFMA2/FADD2/
 // FMUL2), which evaluate Eq. 1 for both entries against one i-particle in one
 // instruction each -- half the issue slots of scalar code, which is what
 // bounds this loop.
-__device__ __forceinline__ void list_put(float4 *LA, float4 *LB, int e, float4 v) {
-    float *pa = reinterpret_cast<float *>(LA + (e >> 1));
-    float *pb = reinterpret_cast<float *>(LB + (e >> 1));
-    const int h = e & 1;
-    pa[h] = v.x;
-    pa[2 + h] = v.y;
-    pb[h] = v.z;
-    pb[2 + h] = v.w;
+__device__ __forceinline__ void list_put(float4 *L, int e, float4 v) {
+    float *p = reinterpret_cast<float *>(L + 2 * (e >> 1)) + (e & 1);
+    p[0] = v.x;
+    p[2] = v.y;
+    p[4] = v.z;
+    p[6] = v.w;
 }
 
 // Unroll depth of the flush loop over entry pairs (build-time tunable).
@@ -82,10 +81,10 @@ struct ISlots {
 // COMP each flush forms packed partial sums that are folded into the running
 // sums at its end with Neumaier compensation.
 template <int NQ, int IPL, bool PHI, bool COMP, bool SAFE>
-__device__ __forceinline__ void flush_list(float4 *LA, float4 *LB, int nl, float eps2, int k0,
-                                           int ks, ISlots<IPL> &I) {
+__device__ __forceinline__ void flush_list(float4 *L, int nl, float eps2, int k0, int ks,
+                                           ISlots<IPL> &I) {
     if (nl & 1) {  // pad to a whole pair with a massless, distant entry
-        if (lane_id() == 0) list_put(LA, LB, nl, make_float4(1e18f, 1e18f, 1e18f, 0.0f));
+        if (lane_id() == 0) list_put(L, nl, make_float4(1e18f, 1e18f, 1e18f, 0.0f));
         __syncwarp();
     }
     const int np = (nl + 1) >> 1;
@@ -103,9 +102,12 @@ __device__ __forceinline__ void flush_list(float4 *LA, float4 *LB, int nl, float
             sp[q] = I.run[q][3];
         }
     }
+    // this lane's pairs k0, k0 + ks, ... < np (idle lanes: k0 >= np)
+    const float4 *pe = L + 2 * np;
+    const int step = 2 * ks;
 #pragma unroll kFlushUnroll
-    for (int k = k0; k < np; k += ks) {
-        const float4 A = LA[k], B = LB[k];
+    for (const float4 *pk = L + 2 * min(k0, np); pk < pe; pk += step) {
+        const float4 A = pk[0], B = pk[1];
         const float2 px = make_float2(A.x, A.y), py = make_float2(A.z, A.w);
         const float2 pz = make_float2(B.x, B.y), pm = make_float2(B.z, B.w);
 #pragma unroll
@@ -146,22 +148,22 @@ __device__ __forceinline__ void flush_list(float4 *LA, float4 *LB, int nl, float
 }
 
 template <int IPL, bool PHI, bool COMP, bool SAFE>
-__device__ __forceinline__ void flush_group(int q, int k0, int ks, float4 *LA, float4 *LB, int nl,
-                                            float eps2, ISlots<IPL> &I) {
+__device__ __forceinline__ void flush_group(int q, int k0, int ks, float4 *L, int nl, float eps2,
+                                            ISlots<IPL> &I) {
     if constexpr (IPL == 1) {
-        flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        flush_list<1, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
     } else if constexpr (IPL == 2) {
-        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
-        else flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
+        else flush_list<2, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
     } else if constexpr (IPL == 3) {
-        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
-        else if (q == 2) flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
-        else flush_list<3, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
+        else if (q == 2) flush_list<2, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
+        else flush_list<3, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
     } else {
-        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
-        else if (q == 2) flush_list<2, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
-        else if (q == 3) flush_list<3, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
-        else flush_list<4, IPL, PHI, COMP, SAFE>(LA, LB, nl, eps2, k0, ks, I);
+        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
+        else if (q == 2) flush_list<2, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
+        else if (q == 3) flush_list<3, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
+        else flush_list<4, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
     }
 }
 
@@ -334,12 +336,11 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
     const int D = a.list_depth, S = a.stack_depth;
     const int DQ = QUAD ? walk_quad_depth(D) : 0;
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
-    // per warp: the paired list (D entries = D/2 pairs in LA and LB), with
+    // per warp: the paired list (D entries = D/2 pairs in LA), with
     // quadrupoles the paired node list (DQ entries, 40 B each), the stack and
     // kWalkScratch words for the leaf compaction
     const size_t per_warp = walk_smem_per_warp(D, S, QUAD);
     float4 *LA = reinterpret_cast<float4 *>(walk_smem + w * per_warp);
-    float4 *LB = LA + D / 2;
     float4 *LQ = LA + D;
     uint32_t *stk = reinterpret_cast<uint32_t *>(walk_smem + w * per_warp + (size_t)D * sizeof(float4) +
                                                  (size_t)DQ * 40);
@@ -410,11 +411,9 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
             __syncwarp();
 
             // ---- MAC (Eq. 2) against the group's bounding sphere
-            float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (has) {
-                A = __ldg(&a.nodeA[node]);
-                B = __ldg(&a.nodeB[node]);
-            }
+            // every lane loads (a lane without a node reads node 0): no branch
+            const int nd = has ? node : 0;
+            const float4 A = __ldg(&a.nodeA[nd]), B = __ldg(&a.nodeB[nd]);
             const float dx = A.x - sph.x, dy = A.y - sph.y, dz = A.z - sph.z;
             const float d = sqrt_fast(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) - sph.w;
             bool accept;
@@ -467,12 +466,12 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
             } else {
                 if (nl + na > D) {
                     __syncwarp();
-                    flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, LB, nl, eps2, I);
+                    flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, nl, eps2, I);
                     entries += nl;
                     nl = 0;
                     __syncwarp();
                 }
-                if (accept) list_put(LA, LB, nl + __popc(am & lt), A);
+                if (accept) list_put(LA, nl + __popc(am & lt), A);
                 nl += na;
             }
 
@@ -499,7 +498,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
                     const int c = (total - base) < 32 ? (total - base) : 32;
                     if (nl + c > D) {
                         __syncwarp();
-                        flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, LB, nl, eps2, I);
+                        flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, nl, eps2, I);
                         entries += nl;
                         nl = 0;
                         __syncwarp();
@@ -514,7 +513,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
                     const int k = before + __popc(smap & (0xffffffffu >> (31 - lane))) - 1;
                     const int of = __shfl_sync(NB_FULL, lf, k & 31);
                     const int oex = __shfl_sync(NB_FULL, lexcl, k & 31);
-                    if ((int)lane < c) list_put(LA, LB, nl + lane, __ldg(&a.pos4[of + base + (int)lane - oex]));
+                    if ((int)lane < c) list_put(LA, nl + lane, __ldg(&a.pos4[of + base + (int)lane - oex]));
                     nl += c;
                 }
             }
@@ -522,7 +521,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
         }
         if (nl > 0) {
             __syncwarp();
-            flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, LB, nl, eps2, I);
+            flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, nl, eps2, I);
             entries += nl;
             nl = 0;
         }

@@ -149,7 +149,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
             const int root = a.sys_root[sys];
             if (cnt > 32 * IPL) bad = true;
             if (!acquire(b)) break;
-            float4 *LA = buf + (size_t)b * D, *LB = LA + D / 2;
+            float4 *LA = buf + (size_t)b * D;
             int flags = kPipeFirst;
             auto hand_over = [&](int nl) -> bool {
                 publish(b, PipeHdr{g, first, cnt, nl, flags, eps2, {0, 0}});
@@ -157,7 +157,6 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
                 b ^= 1;
                 if (!acquire(b)) return false;
                 LA = buf + (size_t)b * D;
-                LB = LA + D / 2;
                 return true;
             };
 
@@ -232,7 +231,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
                     }
                     nl = 0;
                 }
-                if (accept) list_put(LA, LB, nl + __popc(am & lt), A);
+                if (accept) list_put(LA, nl + __popc(am & lt), A);
                 nl += na;
 
                 // ---- particles of opened leaves join the list, 32 per chunk
@@ -267,7 +266,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
                         const int of = __shfl_sync(NB_FULL, lf, k & 31);
                         const int oex2 = __shfl_sync(NB_FULL, lexcl, k & 31);
                         if ((int)lane < c)
-                            list_put(LA, LB, nl + lane, __ldg(&a.pos4[of + base_ + (int)lane - oex2]));
+                            list_put(LA, nl + lane, __ldg(&a.pos4[of + base_ + (int)lane - oex2]));
                         nl += c;
                     }
                 }
@@ -329,8 +328,8 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
                     }
                 }
             }
-            float4 *LA = buf + (size_t)b * D, *LB = LA + D / 2;
-            if (h.nl > 0) flush_group<IPL, false, COMP, SAFE>(tile.q, k0, tile.s, LA, LB, h.nl, eps2, I);
+            float4 *LA = buf + (size_t)b * D;
+            if (h.nl > 0) flush_group<IPL, false, COMP, SAFE>(tile.q, k0, tile.s, LA, h.nl, eps2, I);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[b]);
             seen[b]++;
