@@ -44,7 +44,11 @@ __device__ __forceinline__ uint32_t level_mask(int d, int L) {
 }
 
 // delta, leaf level and per-level node counts of each block of TB particles.
+// A CTA takes VB consecutive blocks (VB * TB particles, one per thread and
+// block): the keys of all of them and of the window around them are loaded
+// together, so one load latency covers VB blocks.
 constexpr int kMaxCap = 32;
+constexpr int VB = 4;
 // CAPT: a power of two >= cap, the unrolled length of the window loops.
 template <int CAPT>
 __global__ void __launch_bounds__(TB) leaflevel_kernel(Layout L, int cap,
@@ -52,58 +56,66 @@ __global__ void __launch_bounds__(TB) leaflevel_kernel(Layout L, int cap,
                                                        int8_t *__restrict__ delta,
                                                        int8_t *__restrict__ leaflev,
                                                        uint32_t *__restrict__ blockcnt, int nblk) {
-    __shared__ uint64_t sk[TB + 2 * kMaxCap + 1];
-    __shared__ int sd[TB + 2 * kMaxCap];
-    __shared__ uint32_t wc[kMaxNL][TB / 32];
+    __shared__ uint64_t sk[VB * TB + 2 * kMaxCap + 1];
+    __shared__ int sd[VB * TB + 2 * kMaxCap];
+    __shared__ uint32_t wc[VB][kMaxNL][TB / 32];
     const int64_t n = L.n;
-    const int64_t lo = (int64_t)blockIdx.x * TB - cap;  // global boundary index of sd[0]
-    for (int t = threadIdx.x; t < TB + 2 * cap + 1; t += TB) {
+    const int64_t blk0 = (int64_t)blockIdx.x * VB;
+    const int64_t lo = blk0 * TB - cap;  // global boundary index of sd[0]
+    for (int t = threadIdx.x; t < VB * TB + 2 * cap + 1; t += TB) {
         int64_t g = lo - 1 + t;
         sk[t] = (g >= 0 && g < n) ? keys[g] : 0ull;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < TB + 2 * cap; t += TB) {
+    // boundaries outside (0, n) read as -1 ("no shared level"), so the window
+    // loops need no range checks: a pair with an end beyond the range
+    // repeats one that ends at 0 or n
+    for (int t = threadIdx.x; t < VB * TB + 2 * cap; t += TB) {
         int64_t g = lo + t;
         sd[t] = (g <= 0 || g >= n) ? -1 : delta_of(sk[t], sk[t + 1], 3 * L.levels, L.levels);
     }
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    uint32_t mask = 0;
-    if (i < n) {
-        const int ti = threadIdx.x + cap;
-        int R = 127, best = 127;
-        // R = min delta over boundaries i+1..i+k; a run [i-cap+k, right) with
-        // right <= i-cap+k+cap is cut at level max(delta_left, R) + 1.
-#pragma unroll
-        for (int k = 1; k <= CAPT; k++) {
-            if (k <= cap) {
-                if (i + k <= n) R = min(R, sd[ti + k]);
-                if (i - cap + k >= 0) best = min(best, max(sd[ti - cap + k], R));
-            }
-        }
-        int Li = min(L.levels, best + 1);
-        int di = sd[ti];
-        delta[i] = (int8_t)di;
-        leaflev[i] = (int8_t)Li;
-        if (i == n - 1) delta[n] = -1;
-        mask = level_mask(di, Li);
-    }
     const int NL = L.levels + 1;
     const unsigned w = threadIdx.x >> 5;
-    // per-warp node counts, visiting only the levels some lane starts a node at
-    if (lane_id() < (unsigned)NL) wc[lane_id()][w] = 0u;
-    __syncwarp();
-    const unsigned any = __reduce_or_sync(NB_FULL, mask);
-    for (unsigned m = any; m; m &= m - 1) {
-        const int l = __ffs(m) - 1;
-        const unsigned b = __ballot_sync(NB_FULL, (mask >> l) & 1u);
-        if (lane_id() == 0) wc[l][w] = (uint32_t)__popc(b);
+    for (int v = 0; v < VB; v++) {
+        const int64_t i = (blk0 + v) * TB + threadIdx.x;
+        uint32_t mask = 0;
+        if (i < n) {
+            const int ti = v * TB + threadIdx.x + cap;
+            int R = 127, best = 127;
+            // R = min delta over boundaries i+1..i+k; a run [i-cap+k, right)
+            // with right <= i-cap+k+cap is cut at level max(delta_left, R) + 1.
+#pragma unroll
+            for (int k = 1; k <= CAPT; k++) {
+                if (k <= cap) {
+                    R = min(R, sd[ti + k]);
+                    best = min(best, max(sd[ti - cap + k], R));
+                }
+            }
+            int Li = min(L.levels, best + 1);
+            int di = sd[ti];
+            delta[i] = (int8_t)di;
+            leaflev[i] = (int8_t)Li;
+            if (i == n - 1) delta[n] = -1;
+            mask = level_mask(di, Li);
+        }
+        // per-warp node counts, visiting only the levels some lane starts a node at
+        if (lane_id() < (unsigned)NL) wc[v][lane_id()][w] = 0u;
+        __syncwarp();
+        const unsigned any = __reduce_or_sync(NB_FULL, mask);
+        for (unsigned m = any; m; m &= m - 1) {
+            const int l = __ffs(m) - 1;
+            const unsigned b = __ballot_sync(NB_FULL, (mask >> l) & 1u);
+            if (lane_id() == 0) wc[v][l][w] = (uint32_t)__popc(b);
+        }
     }
     __syncthreads();
-    if (threadIdx.x < NL) {
-        uint32_t t = 0;
-        for (int q = 0; q < TB / 32; q++) t += wc[threadIdx.x][q];
-        blockcnt[(int64_t)threadIdx.x * nblk + blockIdx.x] = t;
+    for (int t = threadIdx.x; t < VB * NL; t += TB) {
+        const int v = t / NL, l = t % NL;
+        if (blk0 + v >= nblk) continue;
+        uint32_t c = 0;
+        for (int q = 0; q < TB / 32; q++) c += wc[v][l][q];
+        blockcnt[(int64_t)l * nblk + blk0 + v] = c;
     }
 }
 
@@ -428,14 +440,14 @@ __device__ __forceinline__ bool internal_node(const Layout &L, int p, int c0, in
 // Count a finished node in at its parent `par` (one atomic add with release
 // and acquire semantics: this thread's writes of the node are published by
 // it, and the thread that completes the parent sees every child's records).
-// Returns whether this was the parent's last child.
-__device__ __forceinline__ bool count_in(int par, int nchild_par, int32_t *node_arrive) {
+// Returns how many of the parent's children have now arrived.
+__device__ __forceinline__ int count_in(int par, int32_t *node_arrive) {
     int old;
     asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;"
                  : "=r"(old)
                  : "l"(node_arrive + par)
                  : "memory");
-    return old + 1 == nchild_par;
+    return old + 1;
 }
 
 #ifndef NB_MOMENTS_MIN_CTAS
@@ -465,22 +477,38 @@ __global__ void __launch_bounds__(256, NB_MOMENTS_MIN_CTAS) moments_kernel(
     for (int64_t ch = wid; ch < nchunk; ch += nw) {
         const int64_t base = (nchunk - 1 - ch) * 32;
         const int id0 = (int)base + lane;
-        const bool leaf = id0 < nn && node_nchild[id0] == 0;
+        // every field this lane's node needs, in one round trip
+        const bool inb = id0 < nn;
+        const int nch0 = inb ? node_nchild[id0] : -1;
+        const int link0 = inb ? node_link[id0] : 0;
+        const int cnt0 = inb ? node_count[id0] : 0;
+        const int par0 = inb ? node_parent[id0] : -1;
+        const int lev0 = inb ? (int)node_level[id0] : 0;
+        const int st0 = inb ? node_start[id0] : 0;
+        const bool leaf = nch0 == 0;
+        // the climb needs a member key: load it now, beside the members
+        const uint64_t key0 = leaf ? keys[st0] : 0ull;
         unsigned lm = __ballot_sync(NB_FULL, leaf);
         while (lm) {
-            // team t takes the t-th remaining leaf of this chunk
+            // one lane per leaf: each lane takes its own node (its fields are
+            // loaded); teams: team t takes the t-th remaining leaf
             int mine = -1;
+            if constexpr (T == 1) {
+                mine = leaf ? lane : -1;
+                lm = 0;
+            } else {
 #pragma unroll
-            for (int t = 0; t < TEAMS; t++) {
-                const int b = lm ? __ffs(lm) - 1 : -1;
-                if (b >= 0) lm &= lm - 1;
-                if (t == team) mine = b;
+                for (int t = 0; t < TEAMS; t++) {
+                    const int b = lm ? __ffs(lm) - 1 : -1;
+                    if (b >= 0) lm &= lm - 1;
+                    if (t == team) mine = b;
+                }
             }
             const int id = mine >= 0 ? (int)base + mine : -1;
             int first = 0, cnt = 0;
             if (id >= 0) {
-                first = node_link[id];
-                cnt = node_count[id];
+                first = T == 1 ? link0 : node_link[id];
+                cnt = T == 1 ? cnt0 : node_count[id];
                 if (first < 0 || cnt < 1 || (int64_t)first + cnt > L.n) {
                     bad = true;
                     cnt = 0;
@@ -558,18 +586,20 @@ __global__ void __launch_bounds__(256, NB_MOMENTS_MIN_CTAS) moments_kernel(
         int node = id0, par = -1, level = 0;
         uint64_t key = 0;
         if (leaf) {
-            par = node_parent[id0];
-            level = node_level[id0];
-            key = keys[node_start[id0]];
+            par = par0;
+            level = lev0;
+            key = key0;
         }
         while (par >= 0) {       // a root has none
             if (par >= node) {   // parents precede their children
                 bad = true;
                 break;
             }
+            // the parent's fields load beside the count-in atomic; the thread
+            // that brings the last child computes the parent
             const int c0 = node_link[par], nc = node_nchild[par];
-            if (!count_in(par, nc, node_arrive)) break;
-            const int up = node_parent[par];  // in flight with the children's loads
+            const int up = node_parent[par];
+            if (count_in(par, node_arrive) != nc) break;
             level--;
             if (!internal_node(L, par, c0, nc, level, key, refit, nn, box, G, node_count, nodeA,
                                nodeB, mass2, nodeQ))
@@ -597,11 +627,11 @@ void build_tree(cudaStream_t s, const Layout &L, const uint64_t *keys, const flo
     const int nblk = (int)((L.n + TB - 1) / TB);
     uint32_t *blockcnt = (uint32_t *)temp;
     if (leaf_cap <= 8)
-        leaflevel_kernel<8><<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
+        leaflevel_kernel<8><<<(nblk + VB - 1) / VB, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
     else if (leaf_cap <= 16)
-        leaflevel_kernel<16><<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
+        leaflevel_kernel<16><<<(nblk + VB - 1) / VB, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
     else
-        leaflevel_kernel<32><<<nblk, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
+        leaflevel_kernel<32><<<(nblk + VB - 1) / VB, TB, 0, s>>>(L, leaf_cap, keys, delta, leaflev, blockcnt, nblk);
     level_scan_kernel<<<L.levels + 1, LS_T, 0, s>>>(blockcnt, nblk, ds);
     level_offsets_kernel<<<1, 32, 0, s>>>(L.levels + 1, ds, cap_nodes);
     node_zero_kernel<<<nsm * 8, 256, 0, s>>>(ds, cap_nodes, node_nchild, node_arrive);
