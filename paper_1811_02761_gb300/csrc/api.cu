@@ -334,16 +334,24 @@ Layout make_layout(int64_t n, int nsys) {
 // Keys, sort and tree of n particles whose positions are x, y, z (FP32, or
 // FP64 when dbl); pos4 must be filled by the caller-specific gather given
 // the permutation in vals (fill_pos4 == true: gather from x, y, z, m here).
+// box_done: the cube's min/max words already hold these positions (the
+// fused kick-drift pass); only the cube is finished here.
 nbody_status build_core(nbody_ctx *c, const Layout &L, const void *x, const void *y,
-                        const void *z, bool dbl, const float *m, bool fill_pos4) {
+                        const void *z, bool dbl, const float *m, bool fill_pos4,
+                        bool box_done = false) {
     cudaStream_t s = c->stream;
-    launch_bbox(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<uint32_t>(c->sys_boxord),
-                P<SysBox>(c->sys_box), c->nsm);
-    c->kernels += 3;
+    if (box_done) {
+        launch_bbox_finalize(s, L, P<uint32_t>(c->sys_boxord), P<SysBox>(c->sys_box));
+        c->kernels += 1;
+    } else {
+        launch_bbox(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<uint32_t>(c->sys_boxord),
+                    P<SysBox>(c->sys_box), c->nsm);
+        c->kernels += 3;
+    }
     radix_prepare(s, L.n, c->rs_temp.p);
     launch_keys(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<SysBox>(c->sys_box),
                 P<uint64_t>(c->keys), P<uint32_t>(c->vals), c->rs_temp.p, c->nsm);
-    c->kernels += 1 + radix_passes(L.keybits);
+    c->kernels += 2 + radix_passes(L.keybits);  // keys, digit starts, passes
     if (radix_sort(s, P<uint64_t>(c->keys), P<uint32_t>(c->vals), P<uint64_t>(c->keys_alt),
                    P<uint32_t>(c->vals_alt), L.n, L.keybits, c->rs_temp.p, true, &c->ds->status,
                    c->nsm)) {
@@ -621,8 +629,8 @@ nbody_status compute_order(nbody_ctx *c, const float *pcost, const int32_t **ord
     }
     launch_order_keys(c->stream, png, P<float>(c->score), P<int32_t>(c->grp_count),
                       P<uint64_t>(c->okey), P<uint32_t>(c->oval), c->nsm);
-    // score (MLP: features + forward) and order keys; histogram + passes
-    c->kernels += (sched == NBODY_SCHED_MLP ? 3 : 2) + 1 + radix_passes(32);
+    // score (MLP: features + forward) and order keys; histogram, digit starts, passes
+    c->kernels += (sched == NBODY_SCHED_MLP ? 3 : 2) + 2 + radix_passes(32);
     if (radix_sort(c->stream, P<uint64_t>(c->okey), P<uint32_t>(c->oval), P<uint64_t>(c->okey_alt),
                    P<uint32_t>(c->oval_alt), std::max<int64_t>(c->cap_n, 1), 32, c->rs_temp.p,
                    false, &c->ds->status, c->nsm, png)) {
@@ -1133,8 +1141,16 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     bool pending_kick = false, defer_in_capture = false;
     auto one_step = [&](bool timing, bool rebuild) -> nbody_status {
         cudaStream_t q = ctx->stream;
+        // one system: the cube of the drifted positions comes out of the
+        // kick-drift pass itself
+        const bool fuse_box = rebuild && nsys == 1;
+        if (fuse_box) {
+            launch_bbox_init(q, L, P<uint32_t>(ctx->sys_boxord));
+            ctx->kernels += 1;
+        }
         launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt, rebuild ? nullptr : P<float4>(ctx->pos4),
-                          pending_kick ? 0.5f * dt : 0.0f);
+                          pending_kick ? 0.5f * dt : 0.0f,
+                          fuse_box ? P<uint32_t>(ctx->sys_boxord) : nullptr);
         pending_kick = false;
         ctx->kernels += 1;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -1144,7 +1160,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         }
         nbody_status r;
         if (rebuild) {
-            r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
+            r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false, fuse_box);
             if (r != NBODY_OK) return r;
             launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
                                  P<float4>(ctx->pos4));

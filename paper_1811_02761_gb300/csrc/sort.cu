@@ -163,9 +163,17 @@ __global__ void bbox_finalize_kernel(int nsys, int levels, const uint32_t *boxor
     }
 }
 
+void launch_bbox_init(cudaStream_t s, const Layout &L, uint32_t *d_boxord) {
+    bbox_init_kernel<<<(L.nsys * 6 + 255) / 256, 256, 0, s>>>(L.nsys, d_boxord);
+}
+
+void launch_bbox_finalize(cudaStream_t s, const Layout &L, const uint32_t *d_boxord, SysBox *d_box) {
+    bbox_finalize_kernel<<<(L.nsys + 127) / 128, 128, 0, s>>>(L.nsys, L.levels, d_boxord, d_box);
+}
+
 void launch_bbox(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
                  bool dbl, const int64_t *d_off, uint32_t *d_boxord, SysBox *d_box, int nsm) {
-    bbox_init_kernel<<<(L.nsys * 6 + 255) / 256, 256, 0, s>>>(L.nsys, d_boxord);
+    launch_bbox_init(s, L, d_boxord);
     int64_t warps = (L.n + 255) / 256;
     int blocks = (int)((warps + 7) / 8);
     int maxb = nsm * NB_SCAN_CTAS_PER_SM;
@@ -177,7 +185,7 @@ void launch_bbox(cudaStream_t s, const Layout &L, const void *x, const void *y, 
     else
         bbox_kernel<float><<<blocks, 256, 0, s>>>(L.n, (const float *)x, (const float *)y,
                                                   (const float *)z, d_off, L.nsys, d_boxord);
-    bbox_finalize_kernel<<<(L.nsys + 127) / 128, 128, 0, s>>>(L.nsys, L.levels, d_boxord, d_box);
+    launch_bbox_finalize(s, L, d_boxord, d_box);
 }
 
 // ---------------------------------------------------------------- Morton keys
@@ -243,9 +251,12 @@ static_assert(RS_BINS == RS_THREADS, "one digit per thread");
 constexpr unsigned long long RS_INCL = 1ull << 59;
 constexpr unsigned long long RS_CNT = RS_INCL - 1;
 
-// Temporary layout: tile counters, digit histograms, look-back words.
+// Temporary layout: tile counters, digit histograms, their exclusive
+// prefixes (where each digit's keys start in the output, per pass), look-back
+// words.
 constexpr size_t RS_OFF_HIST = 256;
-constexpr size_t RS_OFF_STATUS = RS_OFF_HIST + (size_t)RS_MAXPASS * RS_BINS * sizeof(uint32_t);
+constexpr size_t RS_OFF_GSTART = RS_OFF_HIST + (size_t)RS_MAXPASS * RS_BINS * sizeof(uint32_t);
+constexpr size_t RS_OFF_STATUS = RS_OFF_GSTART + (size_t)RS_MAXPASS * RS_BINS * sizeof(uint32_t);
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -397,6 +408,15 @@ void launch_scan_sums(cudaStream_t s, uint32_t *sums, int nb, int32_t *total_out
     scan_sums_kernel<<<1, SCAN_T, 0, s>>>(sums, nb, total_out);
 }
 
+// Where each digit's keys start in a pass's output: the exclusive prefix of
+// that pass's histogram (one block per pass; the same for every tile).
+__global__ void __launch_bounds__(RS_BINS) rs_gstart_kernel(const uint32_t *__restrict__ hist,
+                                                          uint32_t *__restrict__ gstart) {
+    __shared__ uint32_t sh[RS_BINS / 32];
+    const int p = blockIdx.x, d = threadIdx.x;
+    gstart[p * RS_BINS + d] = block_excl_scan<RS_BINS>(hist[p * RS_BINS + d], sh, nullptr);
+}
+
 struct RsShared {
     union {
         uint32_t whist[RS_WARPS][RS_BINS];  // per-warp digit counts, then offsets
@@ -422,7 +442,7 @@ __global__ void __launch_bounds__(RS_THREADS, NB_RS_MIN_CTAS) rs_onesweep_kernel
     extern __shared__ __align__(16) unsigned char rs_smem[];
     RsShared &S = *reinterpret_cast<RsShared *>(rs_smem);
     uint32_t *counter = (uint32_t *)temp;
-    const uint32_t *hist = (const uint32_t *)((char *)temp + RS_OFF_HIST) + pass * RS_BINS;
+    const uint32_t *gstart_p = (const uint32_t *)((char *)temp + RS_OFF_GSTART) + pass * RS_BINS;
     unsigned long long *look = (unsigned long long *)((char *)temp + RS_OFF_STATUS);
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     const int d = threadIdx.x;  // the digit this thread scans and looks back for
@@ -440,7 +460,7 @@ __global__ void __launch_bounds__(RS_THREADS, NB_RS_MIN_CTAS) rs_onesweep_kernel
     if (tile >= ntiles) return;  // block-uniform; the grid has at least ntiles CTAs
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&S.u.whist[0][0])[i] = 0;
     __syncthreads();
-    const uint32_t hd = hist[d];
+    const uint32_t gstart = gstart_p[d];
     const int64_t base = (int64_t)tile * RS_TILE;
     const int valid = (int)((n - base) < RS_TILE ? (n - base) : RS_TILE);
 
@@ -480,19 +500,33 @@ __global__ void __launch_bounds__(RS_THREADS, NB_RS_MIN_CTAS) rs_onesweep_kernel
         tot += c;
     }
     const uint32_t lex = block_excl_scan<RS_THREADS>(tot, S.wsum, nullptr);
-    const uint32_t gstart = block_excl_scan<RS_THREADS>(hd, S.wsum, nullptr);
     S.loff[d] = lex;
 
-    // decoupled look-back for digit d
+    // publish this tile's digit counts (an aggregate; tile 0's are already
+    // its inclusive prefix) before staging, so the tiles after it can walk
+    // past it while this one stages its keys
     const unsigned long long tag = (unsigned long long)(pass + 1) << 60;
     const unsigned long long mine =
         tot - (d == RS_BINS - 1 ? (uint32_t)(RS_TILE - valid) : 0u);  // keys past n excluded
     unsigned long long *slot = look + (size_t)tile * RS_BINS + d;
+    st_relaxed_u64(slot, tile == 0 ? (tag | RS_INCL | mine) : (tag | mine));
+    __syncthreads();
+
+    // stage the tile in digit order (needs only this tile's offsets)
+    uint32_t pos[RS_IPT];
+#pragma unroll
+    for (int k = 0; k < RS_IPT; k++) pos[k] = S.loff[dg[k]] + S.u.whist[w][dg[k]] + rk[k];
+    __syncthreads();  // the staging area overlays the per-warp counts
+#pragma unroll
+    for (int k = 0; k < RS_IPT; k++) {
+        S.u.st.k[pos[k]] = key[k];
+        S.u.st.v[pos[k]] = val[k];
+    }
+
+    // decoupled look-back for digit d: how many keys of digit d the tiles
+    // before this one hold
     unsigned long long excl = 0;
-    if (tile == 0) {
-        st_relaxed_u64(slot, tag | RS_INCL | mine);
-    } else {
-        st_relaxed_u64(slot, tag | mine);
+    if (tile > 0) {
         // walk back RS_LB words per round trip: the words of tiles j, j-1,
         // ... are loaded together and consumed in order until an inclusive
         // prefix; a word not yet published is polled again (bounded)
@@ -529,16 +563,6 @@ __global__ void __launch_bounds__(RS_THREADS, NB_RS_MIN_CTAS) rs_onesweep_kernel
         st_relaxed_u64(slot, tag | RS_INCL | (excl + mine));
     }
     S.goff[d] = (uint32_t)((unsigned long long)gstart + excl) - lex;
-    __syncthreads();
-    uint32_t pos[RS_IPT];
-#pragma unroll
-    for (int k = 0; k < RS_IPT; k++) pos[k] = S.loff[dg[k]] + S.u.whist[w][dg[k]] + rk[k];
-    __syncthreads();  // the staging area overlays the per-warp counts
-#pragma unroll
-    for (int k = 0; k < RS_IPT; k++) {
-        S.u.st.k[pos[k]] = key[k];
-        S.u.st.v[pos[k]] = val[k];
-    }
     __syncthreads();
     bool bad = false;
     for (int p = threadIdx.x; p < valid; p += RS_THREADS) {
@@ -583,6 +607,8 @@ int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_al
         rs_hist_kernel<<<blocks, 256, 0, s>>>(keys, n, dn, passes,
                                               (uint32_t *)((char *)temp + RS_OFF_HIST));
     }
+    rs_gstart_kernel<<<passes, RS_BINS, 0, s>>>((const uint32_t *)((char *)temp + RS_OFF_HIST),
+                                                (uint32_t *)((char *)temp + RS_OFF_GSTART));
     const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
     uint64_t *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
