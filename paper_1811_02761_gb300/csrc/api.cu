@@ -334,20 +334,12 @@ Layout make_layout(int64_t n, int nsys) {
 // Keys, sort and tree of n particles whose positions are x, y, z (FP32, or
 // FP64 when dbl); pos4 must be filled by the caller-specific gather given
 // the permutation in vals (fill_pos4 == true: gather from x, y, z, m here).
-// box_done: the cube's min/max words already hold these positions (the
-// fused kick-drift pass); only the cube is finished here.
 nbody_status build_core(nbody_ctx *c, const Layout &L, const void *x, const void *y,
-                        const void *z, bool dbl, const float *m, bool fill_pos4,
-                        bool box_done = false) {
+                        const void *z, bool dbl, const float *m, bool fill_pos4) {
     cudaStream_t s = c->stream;
-    if (box_done) {
-        launch_bbox_finalize(s, L, P<uint32_t>(c->sys_boxord), P<SysBox>(c->sys_box));
-        c->kernels += 1;
-    } else {
-        launch_bbox(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<uint32_t>(c->sys_boxord),
-                    P<SysBox>(c->sys_box), c->nsm);
-        c->kernels += 3;
-    }
+    launch_bbox(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<uint32_t>(c->sys_boxord),
+                P<SysBox>(c->sys_box), c->nsm);
+    c->kernels += 3;
     radix_prepare(s, L.n, c->rs_temp.p);
     launch_keys(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<SysBox>(c->sys_box),
                 P<uint64_t>(c->keys), P<uint32_t>(c->vals), c->rs_temp.p, c->nsm);
@@ -1141,16 +1133,8 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     bool pending_kick = false, defer_in_capture = false;
     auto one_step = [&](bool timing, bool rebuild) -> nbody_status {
         cudaStream_t q = ctx->stream;
-        // one system: the cube of the drifted positions comes out of the
-        // kick-drift pass itself
-        const bool fuse_box = rebuild && nsys == 1;
-        if (fuse_box) {
-            launch_bbox_init(q, L, P<uint32_t>(ctx->sys_boxord));
-            ctx->kernels += 1;
-        }
         launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt, rebuild ? nullptr : P<float4>(ctx->pos4),
-                          pending_kick ? 0.5f * dt : 0.0f,
-                          fuse_box ? P<uint32_t>(ctx->sys_boxord) : nullptr);
+                          pending_kick ? 0.5f * dt : 0.0f);
         pending_kick = false;
         ctx->kernels += 1;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -1160,7 +1144,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         }
         nbody_status r;
         if (rebuild) {
-            r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false, fuse_box);
+            r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
             if (r != NBODY_OK) return r;
             launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
                                  P<float4>(ctx->pos4));

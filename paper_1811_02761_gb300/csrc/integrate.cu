@@ -27,16 +27,8 @@ __device__ __forceinline__ float acc_mag(float4 a) {
 
 // hclose != 0: first the closing half kick of the previous step (and its
 // a_old), fused into this pass; the same two roundings as two kernels.
-// BOX: also the bounding box of the drifted positions of a single system, as
-// the cube kernel would compute it (per-axis min/max of the FP32-rounded
-// positions), merged per block and published with one set of atomics per
-// block into boxord (initialised by the caller).
-template <bool BOX>
-__global__ void __launch_bounds__(256) kick_drift_kernel(int64_t n, StepState st,
-                                                         const float4 *__restrict__ acc,
-                                                         float hclose, float hdt, double dt,
-                                                         float4 *pos4, uint32_t *boxord) {
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+__global__ void kick_drift_kernel(int64_t n, StepState st, const float4 *__restrict__ acc,
+                                  float hclose, float hdt, double dt, float4 *pos4) {
     NB_GRID_LOOP(i, n) {
         const float4 a = acc[i];
         float vx = st.vx[i], vy = st.vy[i], vz = st.vz[i];
@@ -61,49 +53,6 @@ __global__ void __launch_bounds__(256) kick_drift_kernel(int64_t n, StepState st
         st.y[i] = y;
         st.z[i] = z;
         if (pos4) pos4[i] = make_float4((float)x, (float)y, (float)z, m);
-        if constexpr (BOX) {
-            const float f[3] = {(float)x, (float)y, (float)z};
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                lo[c] = fminf(lo[c], f[c]);
-                hi[c] = fmaxf(hi[c], f[c]);
-            }
-        }
-    }
-    if constexpr (BOX) {
-        __shared__ float sh[8][6];
-#pragma unroll
-        for (int c = 0; c < 3; c++)
-            for (int o = 16; o; o >>= 1) {
-                lo[c] = fminf(lo[c], __shfl_xor_sync(NB_FULL, lo[c], o));
-                hi[c] = fmaxf(hi[c], __shfl_xor_sync(NB_FULL, hi[c], o));
-            }
-        const int w = threadIdx.x >> 5;
-        if (lane_id() == 0)
-            for (int c = 0; c < 3; c++) {
-                sh[w][c] = lo[c];
-                sh[w][3 + c] = hi[c];
-            }
-        __syncthreads();
-        if (threadIdx.x < 6) {
-            const int c = threadIdx.x;
-            float v = sh[0][c];
-            for (int q = 1; q < (int)(blockDim.x >> 5); q++)
-                v = c < 3 ? fminf(v, sh[q][c]) : fmaxf(v, sh[q][c]);
-            if (c < 3) atomicMin(&boxord[c], f2ord(v));
-            else atomicMax(&boxord[c], f2ord(v));
-        }
-    }
-}
-
-void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
-                       float dt, float4 *pos4, float hclose, uint32_t *boxord) {
-    if (boxord) {
-        kick_drift_kernel<true><<<grid_for(n), 256, 0, s>>>(n, st, acc, hclose, hdt, (double)dt, pos4,
-                                                           boxord);
-    } else {
-        kick_drift_kernel<false><<<grid_for(n), 256, 0, s>>>(n, st, acc, hclose, hdt, (double)dt,
-                                                            pos4, nullptr);
     }
 }
 
@@ -118,6 +67,10 @@ __global__ void kick_kernel(int64_t n, StepState st, const float4 *__restrict__ 
     }
 }
 
+void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
+                       float dt, float4 *pos4, float hclose) {
+    kick_drift_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, hclose, hdt, (double)dt, pos4);
+}
 
 void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt) {
     kick_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, hdt);

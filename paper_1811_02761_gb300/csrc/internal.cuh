@@ -140,10 +140,6 @@ __device__ __forceinline__ int sys_of(const int64_t *off, int nsys, int64_t i) {
 // sort.cu
 void launch_bbox(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
                  bool dbl, const int64_t *d_off, uint32_t *d_boxord, SysBox *d_box, int nsm);
-// The cube's two ends around a min/max pass done elsewhere (the fused
-// kick-drift): reset the min/max words, then turn them into the cube.
-void launch_bbox_init(cudaStream_t s, const Layout &L, uint32_t *d_boxord);
-void launch_bbox_finalize(cudaStream_t s, const Layout &L, const uint32_t *d_boxord, SysBox *d_box);
 // Morton keys (vals = 0..n-1).  With sort_temp (cleared by radix_prepare),
 // the kernel also accumulates the radix sort's digit histograms, and the
 // sort is then called with hist_done = true.
@@ -318,11 +314,9 @@ void launch_block_active_groups(cudaStream_t s, const DevState *ds, const int32_
                                 int32_t *order, int32_t *count, int nsm);
 // pos4 (nullable): also refresh the FP32 walk copy (x, y, z, m) in place.
 // hclose != 0: apply the previous step's closing half kick (v += a hclose,
-// a_old = |a|) first, as the kick kernel would.  boxord (nullable, one
-// system): also fold the drifted positions into the cube's min/max words
-// (initialised by launch_bbox_init), in place of the cube kernel's pass.
+// a_old = |a|) first, as the kick kernel would.
 void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt,
-                       float dt, float4 *pos4, float hclose = 0.0f, uint32_t *boxord = nullptr);
+                       float dt, float4 *pos4, float hclose = 0.0f);
 void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt);
 void launch_permute_state(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
                           StepState dst, float4 *pos4);

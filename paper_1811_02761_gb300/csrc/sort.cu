@@ -163,17 +163,9 @@ __global__ void bbox_finalize_kernel(int nsys, int levels, const uint32_t *boxor
     }
 }
 
-void launch_bbox_init(cudaStream_t s, const Layout &L, uint32_t *d_boxord) {
-    bbox_init_kernel<<<(L.nsys * 6 + 255) / 256, 256, 0, s>>>(L.nsys, d_boxord);
-}
-
-void launch_bbox_finalize(cudaStream_t s, const Layout &L, const uint32_t *d_boxord, SysBox *d_box) {
-    bbox_finalize_kernel<<<(L.nsys + 127) / 128, 128, 0, s>>>(L.nsys, L.levels, d_boxord, d_box);
-}
-
 void launch_bbox(cudaStream_t s, const Layout &L, const void *x, const void *y, const void *z,
                  bool dbl, const int64_t *d_off, uint32_t *d_boxord, SysBox *d_box, int nsm) {
-    launch_bbox_init(s, L, d_boxord);
+    bbox_init_kernel<<<(L.nsys * 6 + 255) / 256, 256, 0, s>>>(L.nsys, d_boxord);
     int64_t warps = (L.n + 255) / 256;
     int blocks = (int)((warps + 7) / 8);
     int maxb = nsm * NB_SCAN_CTAS_PER_SM;
@@ -185,7 +177,7 @@ void launch_bbox(cudaStream_t s, const Layout &L, const void *x, const void *y, 
     else
         bbox_kernel<float><<<blocks, 256, 0, s>>>(L.n, (const float *)x, (const float *)y,
                                                   (const float *)z, d_off, L.nsys, d_boxord);
-    launch_bbox_finalize(s, L, d_boxord, d_box);
+    bbox_finalize_kernel<<<(L.nsys + 127) / 128, 128, 0, s>>>(L.nsys, L.levels, d_boxord, d_box);
 }
 
 // ---------------------------------------------------------------- Morton keys
