@@ -319,7 +319,8 @@ def run_ours(args, rank, world, local_rank):
         elapsed_max, inter_all = float(t.item()), float(it.item())
         walk_ms, walk_launches = st.ms_walk_kernel, st.walk_launches
         phase_ms, phase_steps = (st.ms_build, st.ms_walk), args.steps
-        if walk_launches == 0:  # graph replay: time the phases in eager steps
+        if walk_launches < args.steps:  # graph replays (all but the call's first step):
+            # time the phases in eager steps
             c2 = nb.nbody_get_config(ctx)
             c2.use_graph = 0
             nb.nbody_set_config(ctx, c2)

@@ -395,6 +395,26 @@ typedef enum {
  * EINVAL, ECUDA. */
 nbody_status nbody_export(nbody_ctx *ctx, int32_t what, void *dst, int64_t cap, int64_t *count);
 
+/* Stable sort of 64-bit keys: the ordering step of the tree build (Sect.
+ * 4.1, particles sorted along the Morton curve), callable on its own so that
+ * both of the build's sort paths can be checked on any key set.
+ * keys: DEVICE uint64 [n], read only.  keys_out: DEVICE uint64 [n], the keys
+ * in ascending order.  perm_out: DEVICE int32 [n], perm_out[k] = the input
+ * index of keys_out[k]; equal keys keep their input order.
+ * method: NBODY_SORT_RADIX, the one-sweep LSD radix sort over all 64 bits
+ * (a build from the caller's order), or NBODY_SORT_NEAR_ORDER, the bucket
+ * sort of the builds inside a step (splitters from one key per 1984, a
+ * scatter into buckets, a shared-memory merge sort per bucket): fastest on
+ * nearly sorted keys, the same result for any input, and the radix sort for
+ * n > 16384 * 1984.  Runs on the context's stream with its sort buffers
+ * (grown as needed) and synchronises it; the tree of the last build is
+ * invalidated.  1 <= n < 2^31.  Errors: EINVAL (n, method, a pointer that is
+ * NULL or not memory of the context's device), ENOMEM, ECUDA, ETIMEOUT. */
+#define NBODY_SORT_RADIX 0
+#define NBODY_SORT_NEAR_ORDER 1
+nbody_status nbody_sort_keys(nbody_ctx *ctx, int32_t method, const uint64_t *keys, int64_t n,
+                             uint64_t *keys_out, int32_t *perm_out);
+
 /* Self-tests of the library's failure paths (no counterpart in the paper).
  * NBODY_SELFTEST_SORT_WAIT: runs one radix-sort pass kernel on a two-tile
  * input whose first tile is never processed, so the second tile's look-back

@@ -287,7 +287,7 @@ cudaError_t ensure_capacity(nbody_ctx *c, int64_t n, int nsys, int levels) {
         NB_E(ensure(c->keys, n * 8)); NB_E(ensure(c->keys_alt, n * 8));
         NB_E(ensure(c->vals, n * 4)); NB_E(ensure(c->vals_alt, n * 4));
         NB_E(ensure(c->pos4, n * 16)); NB_E(ensure(c->delta, n + 1)); NB_E(ensure(c->leaflev, n));
-        NB_E(ensure(c->rs_temp, radix_temp_bytes(n)));
+        NB_E(ensure(c->rs_temp, std::max(radix_temp_bytes(n), nosort_temp_bytes(n))));
         NB_E(ensure(c->tree_temp, tree_temp_bytes(n, kMaxLevels)));
         NB_E(ensure(c->grp_temp, (size_t)((n + 4095) / 4096 + 64) * 4));
         NB_E(ensure(c->gflag, n));
@@ -334,21 +334,35 @@ Layout make_layout(int64_t n, int nsys) {
 // Keys, sort and tree of n particles whose positions are x, y, z (FP32, or
 // FP64 when dbl); pos4 must be filled by the caller-specific gather given
 // the permutation in vals (fill_pos4 == true: gather from x, y, z, m here).
+// near_order: the positions are in the order of the previous build (the
+// particles have moved since), so their keys are nearly sorted: the near-order
+// sort moves every key twice where the radix sort moves it seven times.
 nbody_status build_core(nbody_ctx *c, const Layout &L, const void *x, const void *y,
-                        const void *z, bool dbl, const float *m, bool fill_pos4) {
+                        const void *z, bool dbl, const float *m, bool fill_pos4,
+                        bool near_order = false) {
     cudaStream_t s = c->stream;
     launch_bbox(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<uint32_t>(c->sys_boxord),
                 P<SysBox>(c->sys_box), c->nsm);
     c->kernels += 3;
-    radix_prepare(s, L.n, c->rs_temp.p);
-    launch_keys(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<SysBox>(c->sys_box),
-                P<uint64_t>(c->keys), P<uint32_t>(c->vals), c->rs_temp.p, c->nsm);
-    c->kernels += 2 + radix_passes(L.keybits);  // keys, digit starts, passes
-    if (radix_sort(s, P<uint64_t>(c->keys), P<uint32_t>(c->vals), P<uint64_t>(c->keys_alt),
-                   P<uint32_t>(c->vals_alt), L.n, L.keybits, c->rs_temp.p, true, &c->ds->status,
-                   c->nsm)) {
+    if (near_order && nosort_fits(L.n)) {
+        launch_keys(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<SysBox>(c->sys_box),
+                    P<uint64_t>(c->keys), P<uint32_t>(c->vals), nullptr, c->nsm);
+        nosort(s, P<uint64_t>(c->keys), P<uint64_t>(c->keys_alt), P<uint32_t>(c->vals),
+               P<uint32_t>(c->vals_alt), L.n, c->rs_temp.p, &c->ds->status);
+        c->kernels += 1 + nosort_kernels();
         std::swap(c->keys, c->keys_alt);
         std::swap(c->vals, c->vals_alt);
+    } else {
+        radix_prepare(s, L.n, c->rs_temp.p);
+        launch_keys(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<SysBox>(c->sys_box),
+                    P<uint64_t>(c->keys), P<uint32_t>(c->vals), c->rs_temp.p, c->nsm);
+        c->kernels += 2 + radix_passes(L.keybits);  // keys, digit starts, passes
+        if (radix_sort(s, P<uint64_t>(c->keys), P<uint32_t>(c->vals), P<uint64_t>(c->keys_alt),
+                       P<uint32_t>(c->vals_alt), L.n, L.keybits, c->rs_temp.p, true,
+                       &c->ds->status, c->nsm)) {
+            std::swap(c->keys, c->keys_alt);
+            std::swap(c->vals, c->vals_alt);
+        }
     }
     if (fill_pos4) {
         launch_gather_pos4(s, L.n, P<uint32_t>(c->vals), x, y, z, dbl, m, P<float4>(c->pos4));
@@ -1009,6 +1023,8 @@ static nbody_status block_steps(nbody_ctx *ctx, const Layout &L, StepState *S, i
             since = 0;
             cycle.clear();
         }
+        // the first rebuild sorts the caller's order; later ones the last build's
+        const bool near_order = !first;
         first = false;
         // drift every particle to tick T (no kick: the kick factor is 0)
         launch_kick_drift(q, n, S[cur], acc, 0.0f, span, rebuild ? nullptr : P<float4>(ctx->pos4));
@@ -1017,7 +1033,8 @@ static nbody_status block_steps(nbody_ctx *ctx, const Layout &L, StepState *S, i
         NB_CUDA(ctx, pool_event(ctx, &e0));
         NB_CUDA(ctx, cudaEventRecord(e0, q));
         if (rebuild) {
-            st = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
+            st = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false,
+                            near_order);
             if (st != NBODY_OK) return st;
             launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur], P<float4>(ctx->pos4));
             ctx->kernels += 1;
@@ -1131,7 +1148,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     // a graph; the graph's last step kicks on its own, so that every replay
     // starts from the same state.
     bool pending_kick = false, defer_in_capture = false;
-    auto one_step = [&](bool timing, bool rebuild) -> nbody_status {
+    // near_order: the state is in the Morton order of this call's previous
+    // build (every step but the call's first, whose state is in caller order)
+    auto one_step = [&](bool timing, bool rebuild, bool near_order) -> nbody_status {
         cudaStream_t q = ctx->stream;
         launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt, rebuild ? nullptr : P<float4>(ctx->pos4),
                           pending_kick ? 0.5f * dt : 0.0f);
@@ -1144,7 +1163,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         }
         nbody_status r;
         if (rebuild) {
-            r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false);
+            r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false, near_order);
             if (r != NBODY_OK) return r;
             launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
                                  P<float4>(ctx->pos4));
@@ -1185,9 +1204,21 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     };
 
     int eager = nsteps;
+    bool sorted_state = false;  // the state is in the Morton order of a build of this call
     // steps that may refit instead of rebuilding, and block steps, run eagerly
-    if (ctx->cfg.use_graph && nsteps >= 2 && ctx->cfg.rebuild_interval == 1 &&
+    if (ctx->cfg.use_graph && nsteps >= 3 && ctx->cfg.rebuild_interval == 1 &&
         ctx->cfg.block_levels == 0) {
+        // The call's first step sorts the state from the caller's order: it
+        // runs eagerly, and the graph's steps all find the state in the order
+        // of the build before them.
+        st = one_step(true, true, false);
+        if (st != NBODY_OK) return st;
+        if (pending_kick) {
+            launch_kick(s, n, S[cur], acc, 0.5f * dt);
+            ctx->kernels += 1;
+            pending_kick = false;
+        }
+        sorted_state = true;
         // Two steps per graph: the sort's ping-pong buffers and the state
         // copies swap roles every step, so after two steps every pointer is
         // back where the capture found it and the graph can be replayed.
@@ -1223,9 +1254,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             nbody_status r1 = NBODY_OK, r2 = NBODY_OK;
             if (ce == cudaSuccess) {
                 defer_in_capture = true;
-                r1 = one_step(false, true);
+                r1 = one_step(false, true, true);
                 defer_in_capture = false;
-                if (r1 == NBODY_OK) r2 = one_step(false, true);
+                if (r1 == NBODY_OK) r2 = one_step(false, true, true);
                 cudaError_t ee = cudaStreamEndCapture(ctx->gstream, &graph);
                 if (ce == cudaSuccess) ce = ee;
             }
@@ -1242,14 +1273,14 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         }
         NB_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
         NB_CUDA(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev[0], 0));
-        for (int it = 0; it + 1 < nsteps; it += 2) {
+        for (int it = 1; it + 1 < nsteps; it += 2) {
             NB_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->gstream));
             ctx->kernels += ctx->gkernels;
             rebuilds += 2;
         }
         NB_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->gstream));
         NB_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev[1], 0));
-        eager = nsteps % 2;
+        eager = (nsteps - 1) % 2;
     }
     if (ctx->cfg.block_levels > 0) {
         st = block_steps(ctx, L, S, cur, acc, dt, nsteps, safe, rebuilds, marks);
@@ -1274,8 +1305,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             since = 0;
             cycle.clear();
         }
-        st = one_step(true, rebuild);
+        st = one_step(true, rebuild, sorted_state);
         if (st != NBODY_OK) return st;
+        if (rebuild) sorted_state = true;
         since++;
         if (interval == 0) {
             const int k = marks.back();
@@ -1720,6 +1752,39 @@ nbody_status nbody_mlp_eval(int64_t n, const float *features, const float *targe
     cudaFree(buf);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "nbody_mlp_eval");
     return NBODY_OK;
+}
+
+nbody_status nbody_sort_keys(nbody_ctx *ctx, int32_t method, const uint64_t *keys, int64_t n,
+                             uint64_t *keys_out, int32_t *perm_out) {
+    if (!ctx) return fail(nullptr, NBODY_EINVAL, "ctx is NULL");
+    if (n < 1 || n >= ((int64_t)1 << 31)) return fail(ctx, NBODY_EINVAL, "n must be in 1..2^31-1");
+    if (method != NBODY_SORT_RADIX && method != NBODY_SORT_NEAR_ORDER)
+        return fail(ctx, NBODY_EINVAL, "unknown sort method");
+    int dev = 0;
+    NB_CUDA(ctx, cudaGetDevice(&dev));
+    if (!on_device(keys, dev) || !on_device(keys_out, dev) || !on_device(perm_out, dev))
+        return fail(ctx, NBODY_EINVAL, "keys, keys_out and perm_out must be memory of the "
+                                       "context's device");
+    cudaError_t e = ensure_capacity(ctx, n, 1, make_layout(n, 1).levels);
+    if (e != cudaSuccess) return fail(ctx, NBODY_ENOMEM, std::string("allocation: ") + cudaGetErrorString(e));
+    ctx->built = false;
+    cudaStream_t s = ctx->stream;
+    NB_CUDA(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevState), s));
+    NB_CUDA(ctx, cudaMemcpyAsync(ctx->keys.p, keys, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    bool alt = true;
+    if (method == NBODY_SORT_NEAR_ORDER && nosort_fits(n))
+        nosort(s, P<uint64_t>(ctx->keys), P<uint64_t>(ctx->keys_alt), P<uint32_t>(ctx->vals),
+               P<uint32_t>(ctx->vals_alt), n, ctx->rs_temp.p, &ctx->ds->status);
+    else
+        alt = radix_sort(s, P<uint64_t>(ctx->keys), P<uint32_t>(ctx->vals),
+                         P<uint64_t>(ctx->keys_alt), P<uint32_t>(ctx->vals_alt), n, 64,
+                         ctx->rs_temp.p, false, &ctx->ds->status, ctx->nsm) != 0;
+    NB_CUDA(ctx, cudaGetLastError());
+    NB_CUDA(ctx, cudaMemcpyAsync(keys_out, alt ? ctx->keys_alt.p : ctx->keys.p, (size_t)n * 8,
+                                 cudaMemcpyDeviceToDevice, s));
+    NB_CUDA(ctx, cudaMemcpyAsync(perm_out, alt ? ctx->vals_alt.p : ctx->vals.p, (size_t)n * 4,
+                                 cudaMemcpyDeviceToDevice, s));
+    return read_status(ctx);
 }
 
 nbody_status nbody_selftest(int32_t which, void *cuda_stream) {

@@ -29,6 +29,24 @@
 
 #include "internal.cuh"
 
+namespace nb {
+
+// True for memory the current device dev can read in place: its own device
+// memory, or managed memory.  Device memory of another GPU is refused (the
+// kernel runs on dev and would read it across the peer link, or fault when
+// peer access is off).
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+}  // namespace nb
+
 namespace {
 
 // Partial sums of up to kNoallocBlocks blocks (8 doubles each) + the result.
@@ -43,20 +61,6 @@ double *g_scratch_ptr[kMaxDevices] = {nullptr};
 nbody_status fail(nbody_status st, const std::string &msg) {
     nb::set_stateless_error(msg);  // read back by nbody_last_error(NULL, ...)
     return st;
-}
-
-// True for memory the current device dev can read in place: its own device
-// memory, or managed memory.  Device memory of another GPU is refused (the
-// kernel runs on dev and would read it across the peer link, or fault when
-// peer access is off).
-bool on_device(const void *p, int dev) {
-    cudaPointerAttributes at;
-    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    if (at.type == cudaMemoryTypeManaged) return true;
-    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 // Device address of the scratch array on the current device (looked up once
@@ -95,7 +99,7 @@ extern "C" nbody_status nbody_diagnostics_noalloc(int64_t n, const double *x, co
     }
     const void *in[8] = {x, y, z, vx, vy, vz, m, phi};
     for (int k = 0; k < 8; k++)
-        if (in[k] && !on_device(in[k], dev))
+        if (in[k] && !nb::on_device(in[k], dev))
             return fail(NBODY_EINVAL,
                         "nbody_diagnostics_noalloc: input arrays must be device pointers of the "
                         "current device (staging host arrays would need an allocation)");
@@ -113,7 +117,7 @@ extern "C" nbody_status nbody_diagnostics_noalloc(int64_t n, const double *x, co
     if (e != cudaSuccess)
         return fail(NBODY_ECUDA, std::string("nbody_diagnostics_noalloc: ") + cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const bool out_dev = on_device(out, dev);
+    const bool out_dev = nb::on_device(out, dev);
     double *result = out_dev ? out : scratch + kNoallocBlocks * 8;
     nb::launch_diagnostics(s, n, x, y, z, vx, vy, vz, m, phi, scratch, result);
     e = cudaGetLastError();

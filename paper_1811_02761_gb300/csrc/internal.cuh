@@ -161,6 +161,21 @@ int radix_sort(cudaStream_t s, uint64_t *keys, uint32_t *vals, uint64_t *keys_al
                uint32_t *vals_alt, int64_t n, int bits, void *temp, bool hist_done,
                int32_t *status, int nsm, const int32_t *dn = nullptr);
 int radix_passes(int bits);
+// Sort of keys that are nearly in order already (the previous build's order
+// with new keys, as inside a time step): splitters from one key per tile,
+// buckets, a scatter and a shared-memory sort per bucket (nosort.cu).
+// keys (overwritten: scratch) -> kout (sorted keys), vout (the index of each
+// sorted key in the input); vscr: uint32 [n] scratch.  The result equals
+// the stable sort of the keys for any input order.  Device-side failures are
+// or-ed into *status.
+bool nosort_fits(int64_t n);
+size_t nosort_temp_bytes(int64_t n);
+void nosort(cudaStream_t s, uint64_t *keys, uint64_t *kout, uint32_t *vscr, uint32_t *vout,
+            int64_t n, void *temp, int32_t *status);
+int nosort_kernels();
+// True for memory the current device dev can read in place (its own device
+// memory, or managed memory); diag_noalloc.cu.
+bool on_device(const void *p, int dev);
 // Runs the radix pass kernel on an input whose look-back can never complete
 // and waits for it; the bounded wait records kStatusTimeout in *status.
 cudaError_t radix_selftest_wait(cudaStream_t s, int32_t *status);

@@ -73,7 +73,7 @@ EXPORTS = ("nbody_abi_version", "nbody_config_default", "nbody_create", "nbody_d
            "nbody_diagnostics_noalloc", "nbody_tune_space_default", "nbody_autotune",
            "nbody_mlp_set_params", "nbody_mlp_get_params", "nbody_mlp_train",
            "nbody_mlp_predict", "nbody_mlp_eval", "nbody_selftest",
-           "nbody_refit", "nbody_rebuild_due")
+           "nbody_refit", "nbody_rebuild_due", "nbody_sort_keys")
 MLP_PARAMS, MLP_FEATURES = 1377, 8
 EXPORT_PERM, EXPORT_KEYS, EXPORT_NODE_LEVEL, EXPORT_NODE_START, EXPORT_NODE_COUNT, \
     EXPORT_NODE_PARENT, EXPORT_NODE_A, EXPORT_NODE_B, EXPORT_GROUP_FIRST, EXPORT_GROUP_COUNT, \
@@ -129,6 +129,7 @@ def load(build_if_missing: bool = True):
             "nbody_autotune": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(TuneSpace),
                                     C.POINTER(Config), C.POINTER(f32), C.POINTER(i32)]),
             "nbody_selftest": (st, [i32, vp]),
+            "nbody_sort_keys": (st, [vp, i32, vp, i64, vp, vp]),
             "nbody_refit": (st, [vp, vp, vp, vp, vp]),
             "nbody_rebuild_due": (i32, [C.POINTER(f32), i32]),
             "nbody_last_error": (st, [vp, C.c_char_p, C.c_size_t]),
@@ -440,6 +441,21 @@ def nbody_rebuild_due(cost_ms) -> bool:
 
 
 SELFTEST_SORT_WAIT = 1
+SORT_RADIX, SORT_NEAR_ORDER = 0, 1
+
+
+def nbody_sort_keys(ctx, method, keys, keys_out, perm_out) -> None:
+    """Stable sort of 64-bit keys on the context's device (the tree build's
+    ordering step): keys, keys_out int64 CUDA tensors [n] holding the key
+    bits (compared as unsigned), perm_out int32 [n] (input index of each
+    sorted key).  method: SORT_RADIX or SORT_NEAR_ORDER."""
+    lib = load()
+    n = _size(keys)
+    _check(lib, ctx, lib.nbody_sort_keys(ctx, int(method), _ptr(keys, "int64", None, "keys"), n,
+                                         _ptr(keys_out, "int64", n, "keys_out"),
+                                         _ptr(perm_out, "int32", n, "perm_out")))
+
+
 
 
 def nbody_selftest(which, stream=None) -> int:
