@@ -5,9 +5,10 @@
 //   * persistent grid, one warp per i-group, groups popped from a device queue
 //     (one atomicAdd per group); the queue order is Morton order or a cost
 //     order chosen by the scheduler;
-//   * each lane holds up to IPL i-particles (group <= 32*IPL particles); a
-//     group is tiled over the lanes as q particles per lane times s splits
-//     of the list, so that few lanes idle in the flush (lane_tile below);
+//   * each lane holds up to IPL i-particles (group <= 32*IPL particles) in
+//     slots; slot j covers a power-of-two share of the group and cuts the
+//     list into 32 / u_j splits, so that few lanes idle in the flush
+//     (bin_tile below);
 //   * traversal: a per-warp stack in shared memory whose entries are child
 //     ranges (first node, count <= 8).  Each round the warp pops the top four
 //     ranges (up to 32 nodes, one per lane), evaluates the MAC of Eq. 2
@@ -80,7 +81,7 @@ struct ISlots {
 // below).  Plain sums accumulate straight into the packed running sums; with
 // COMP each flush forms packed partial sums that are folded into the running
 // sums at its end with Neumaier compensation.
-template <int NQ, int IPL, bool PHI, bool COMP, bool SAFE>
+template <int J0, int NQ, int IPL, bool PHI, bool COMP, bool SAFE>
 __device__ __forceinline__ void flush_list(float4 *L, int nl, float eps2, int k0, int ks,
                                            ISlots<IPL> &I) {
     if (nl & 1) {  // pad to a whole pair with a massless, distant entry
@@ -96,10 +97,10 @@ __device__ __forceinline__ void flush_list(float4 *L, int nl, float eps2, int k0
         if constexpr (COMP) {
             sx[q] = sy[q] = sz[q] = sp[q] = make_float2(0.0f, 0.0f);
         } else {
-            sx[q] = I.run[q][0];
-            sy[q] = I.run[q][1];
-            sz[q] = I.run[q][2];
-            sp[q] = I.run[q][3];
+            sx[q] = I.run[J0 + q][0];
+            sy[q] = I.run[J0 + q][1];
+            sz[q] = I.run[J0 + q][2];
+            sp[q] = I.run[J0 + q][3];
         }
     }
     // this lane's pairs k0, k0 + ks, ... < np (idle lanes: k0 >= np)
@@ -112,9 +113,9 @@ __device__ __forceinline__ void flush_list(float4 *L, int nl, float eps2, int k0
         const float2 pz = make_float2(B.x, B.y), pm = make_float2(B.z, B.w);
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            const float2 dx = __fadd2_rn(px, I.nx[q]);
-            const float2 dy = __fadd2_rn(py, I.ny[q]);
-            const float2 dz = __fadd2_rn(pz, I.nz[q]);
+            const float2 dx = __fadd2_rn(px, I.nx[J0 + q]);
+            const float2 dy = __fadd2_rn(py, I.ny[J0 + q]);
+            const float2 dz = __fadd2_rn(pz, I.nz[J0 + q]);
             float2 r2 = __ffma2_rn(dx, dx, e2);
             r2 = __ffma2_rn(dy, dy, r2);
             r2 = __ffma2_rn(dz, dz, r2);
@@ -137,33 +138,13 @@ __device__ __forceinline__ void flush_list(float4 *L, int nl, float eps2, int k0
             const float part[4] = {sx[q].x + sx[q].y, sy[q].x + sy[q].y, sz[q].x + sz[q].y,
                                    sp[q].x + sp[q].y};
 #pragma unroll
-            for (int c = 0; c < 4; c++) neumaier_add(I.acc[q][c], I.cmp[q][c], part[c]);
+            for (int c = 0; c < 4; c++) neumaier_add(I.acc[J0 + q][c], I.cmp[J0 + q][c], part[c]);
         } else {
-            I.run[q][0] = sx[q];
-            I.run[q][1] = sy[q];
-            I.run[q][2] = sz[q];
-            I.run[q][3] = sp[q];
+            I.run[J0 + q][0] = sx[q];
+            I.run[J0 + q][1] = sy[q];
+            I.run[J0 + q][2] = sz[q];
+            I.run[J0 + q][3] = sp[q];
         }
-    }
-}
-
-template <int IPL, bool PHI, bool COMP, bool SAFE>
-__device__ __forceinline__ void flush_group(int q, int k0, int ks, float4 *L, int nl, float eps2,
-                                            ISlots<IPL> &I) {
-    if constexpr (IPL == 1) {
-        flush_list<1, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
-    } else if constexpr (IPL == 2) {
-        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
-        else flush_list<2, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
-    } else if constexpr (IPL == 3) {
-        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
-        else if (q == 2) flush_list<2, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
-        else flush_list<3, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
-    } else {
-        if (q <= 1) flush_list<1, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
-        else if (q == 2) flush_list<2, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
-        else if (q == 3) flush_list<3, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
-        else flush_list<4, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);
     }
 }
 
@@ -194,7 +175,7 @@ __device__ __forceinline__ void quad_put(float4 *LQ, int e, float4 A, float4 Q0,
 // the negative gradient of the node's monopole + quadrupole potential,
 // evaluated for two entries per packed instruction.  The lane takes the
 // entry pairs k0, k0 + ks, ... like the particle flush.
-template <int NQ, int IPL, bool PHI, bool COMP, bool SAFE>
+template <int J0, int NQ, int IPL, bool PHI, bool COMP, bool SAFE>
 __device__ __forceinline__ void flush_quad_list(float4 *LQ, int nq, float eps2, int k0, int ks,
                                                 ISlots<IPL> &I) {
     if (nq & 1) {  // pad to a whole pair with a massless, distant entry
@@ -213,10 +194,10 @@ __device__ __forceinline__ void flush_quad_list(float4 *LQ, int nq, float eps2, 
         if constexpr (COMP) {
             sx[q] = sy[q] = sz[q] = sp[q] = make_float2(0.0f, 0.0f);
         } else {
-            sx[q] = I.run[q][0];
-            sy[q] = I.run[q][1];
-            sz[q] = I.run[q][2];
-            sp[q] = I.run[q][3];
+            sx[q] = I.run[J0 + q][0];
+            sy[q] = I.run[J0 + q][1];
+            sz[q] = I.run[J0 + q][2];
+            sp[q] = I.run[J0 + q][3];
         }
     }
     for (int k = k0; k < np; k += ks) {
@@ -229,9 +210,9 @@ __device__ __forceinline__ void flush_quad_list(float4 *LQ, int nq, float eps2, 
         const float2 qxz = make_float2(F4.x, F4.y), qyz = make_float2(F4.z, F4.w);
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            const float2 dx = __fadd2_rn(px, I.nx[q]);
-            const float2 dy = __fadd2_rn(py, I.ny[q]);
-            const float2 dz = __fadd2_rn(pz, I.nz[q]);
+            const float2 dx = __fadd2_rn(px, I.nx[J0 + q]);
+            const float2 dy = __fadd2_rn(py, I.ny[J0 + q]);
+            const float2 dz = __fadd2_rn(pz, I.nz[J0 + q]);
             float2 r2 = __ffma2_rn(dx, dx, e2);
             r2 = __ffma2_rn(dy, dy, r2);
             r2 = __ffma2_rn(dz, dz, r2);
@@ -262,55 +243,167 @@ __device__ __forceinline__ void flush_quad_list(float4 *LQ, int nq, float eps2, 
             const float part[4] = {sx[q].x + sx[q].y, sy[q].x + sy[q].y, sz[q].x + sz[q].y,
                                    sp[q].x + sp[q].y};
 #pragma unroll
-            for (int c = 0; c < 4; c++) neumaier_add(I.acc[q][c], I.cmp[q][c], part[c]);
+            for (int c = 0; c < 4; c++) neumaier_add(I.acc[J0 + q][c], I.cmp[J0 + q][c], part[c]);
         } else {
-            I.run[q][0] = sx[q];
-            I.run[q][1] = sy[q];
-            I.run[q][2] = sz[q];
-            I.run[q][3] = sp[q];
+            I.run[J0 + q][0] = sx[q];
+            I.run[J0 + q][1] = sy[q];
+            I.run[J0 + q][2] = sz[q];
+            I.run[J0 + q][3] = sp[q];
         }
     }
 }
 
-template <int IPL, bool PHI, bool COMP, bool SAFE>
-__device__ __forceinline__ void flush_quad_group(int q, int k0, int ks, float4 *LQ, int nq,
-                                                 float eps2, ISlots<IPL> &I) {
-    if (q <= 1) flush_quad_list<1, IPL, PHI, COMP, SAFE>(LQ, nq, eps2, k0, ks, I);
-    else if constexpr (IPL >= 2) {
-        if (q == 2) flush_quad_list<2, IPL, PHI, COMP, SAFE>(LQ, nq, eps2, k0, ks, I);
-        else if constexpr (IPL >= 3) {
-            if (q == 3) flush_quad_list<3, IPL, PHI, COMP, SAFE>(LQ, nq, eps2, k0, ks, I);
-            else if constexpr (IPL >= 4) flush_quad_list<4, IPL, PHI, COMP, SAFE>(LQ, nq, eps2, k0, ks, I);
-        }
-    }
-}
-
-// Lane tiling of a group of cnt particles: each lane holds q <= IPL of them
-// (the t-th at index row + P t), P = ceil(cnt / q) rows, and the list is cut
-// into s = floor(32 / P) splits; lane L is row L % P of split L / P (lanes
-// with L / P >= s stay idle) and takes the entry pairs split, split + s, ...
-// The q with the least work per lane, q / s, is chosen (the smallest such q).
-// Against one slot layout of ceil(cnt / 32) particles per lane this recovers
-// most of the lanes a group smaller than a multiple of 32 leaves empty; the
-// splits are summed once per group.
-struct LaneTile {
-    int q, P, s;
+// Binary lane tiling: slot j of every lane covers u_j = 2^lg[j] <= 32
+// particles of the group (lane L holds particle base_j + L % u_j) and takes
+// every s_j-th entry pair of the list, s_j = 32 / u_j, starting at pair
+// L / u_j; the s_j lanes of a particle are summed at the end of the group.
+// The u_j are the fewest powers of two, at most IPL of them, whose sum covers
+// cnt (the top bits of cnt, the rest rounded up to a power of two, equal
+// neighbours merged), so a lane's share of the work is sum_j u_j / 32 times
+// the list for cnt / 32 ideally -- e.g. 50 = 32 + 16 + 2 costs 1.5625 lists
+// per lane where one layout of 25 rows of two particles costs 2.  Runs of
+// slots with equal u share one flush loop.
+template <int IPL>
+struct BinTile {
+    int q;
+    int lg[IPL];
 };
 template <int IPL>
-__device__ __forceinline__ LaneTile lane_tile(int cnt) {
-    LaneTile t{IPL, 32, 1};
-    bool found = false;
+__device__ __forceinline__ BinTile<IPL> bin_tile(int cnt) {
+    BinTile<IPL> t;
+    t.q = 0;
+    int rem = cnt;
 #pragma unroll
-    for (int q = 1; q <= IPL; q++) {
-        const int P = (cnt + q - 1) / q;
-        if (P > 32) continue;
-        const int s = 32 / P;
-        if (!found || q * t.s < t.q * s) {
-            t = LaneTile{q, P, s};
-            found = true;
+    for (int j = 0; j < IPL; j++) {
+        int lg = 0;
+        if (rem > 0) {
+            lg = (j + 1 < IPL) ? 31 - __clz(rem) : (rem > 1 ? 32 - __clz(rem - 1) : 0);
+            lg = lg < 5 ? lg : 5;
+            rem -= 1 << lg;
+            t.q = j + 1;
+        }
+        t.lg[j] = lg;
+    }
+#pragma unroll
+    for (int j = IPL - 1; j >= 1; j--) {
+        if (j == t.q - 1 && t.lg[j] == t.lg[j - 1] && t.lg[j] < 5) {
+            t.lg[j - 1] += 1;
+            t.lg[j] = 0;
+            t.q = j;
         }
     }
     return t;
+}
+
+template <int J, int IPL, bool PHI, bool COMP, bool SAFE, bool QUADL>
+__device__ __forceinline__ void flush_bin(const BinTile<IPL> &t, float4 *L, int nl, float eps2,
+                                          ISlots<IPL> &I) {
+    if constexpr (J < IPL) {
+        if (J >= t.q) return;
+        const int lg = t.lg[J];
+        const int k0 = (int)lane_id() >> lg, ks = 32 >> lg;
+        int run = 1;
+#pragma unroll
+        for (int j = J + 1; j < IPL; j++)
+            if (run == j - J && j < t.q && t.lg[j] == lg) run++;
+#define NB_FLUSH(R)                                                                       \
+    do {                                                                                  \
+        if constexpr (QUADL) flush_quad_list<J, R, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I); \
+        else flush_list<J, R, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);             \
+    } while (0)
+        if constexpr (J + 3 < IPL) {
+            if (run >= 4) { NB_FLUSH(4); return; }
+        }
+        if constexpr (J + 2 < IPL) {
+            if (run == 3) { NB_FLUSH(3); flush_bin<J + 3, IPL, PHI, COMP, SAFE, QUADL>(t, L, nl, eps2, I); return; }
+        }
+        if constexpr (J + 1 < IPL) {
+            if (run == 2) { NB_FLUSH(2); flush_bin<J + 2, IPL, PHI, COMP, SAFE, QUADL>(t, L, nl, eps2, I); return; }
+        }
+        NB_FLUSH(1);
+        flush_bin<J + 1, IPL, PHI, COMP, SAFE, QUADL>(t, L, nl, eps2, I);
+#undef NB_FLUSH
+    }
+}
+
+// A group's i-particles into the lanes' slots (the members slot j covers;
+// past the group's end, massless copies of the sphere centre) and zeroed sums.
+template <int IPL>
+__device__ __forceinline__ void load_slots(const BinTile<IPL> &tile, const float4 *__restrict__ pos4,
+                                           int first, int cnt, float4 sph, ISlots<IPL> &I) {
+    const int lane = (int)lane_id();
+    int base = 0;
+#pragma unroll
+    for (int q = 0; q < IPL; q++) {
+        const int u = 1 << tile.lg[q];
+        const int k = base + (lane & (u - 1));
+        const float4 p = (q < tile.q && k < cnt) ? pos4[first + k]
+                                                : make_float4(sph.x, sph.y, sph.z, 0.0f);
+        base += q < tile.q ? u : 0;
+        I.nx[q] = make_float2(-p.x, -p.x);
+        I.ny[q] = make_float2(-p.y, -p.y);
+        I.nz[q] = make_float2(-p.z, -p.z);
+        I.mi[q] = p.w;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            I.acc[q][c] = I.cmp[q][c] = 0.0f;
+            I.run[q][c] = make_float2(0.0f, 0.0f);
+        }
+    }
+}
+
+// End of a group: the s_j lanes of every particle of slot j are summed (a
+// butterfly over the lane bits above its row; compensated: in split order
+// onto split 0), then the results are written (G applied once; the
+// potential's self term removed).
+template <int IPL, bool PHI, bool COMP, bool SAFE>
+__device__ __forceinline__ void finish_group(const BinTile<IPL> &tile, int first, int cnt,
+                                             float eps2, const WalkArgs &a, ISlots<IPL> &I) {
+    const int lane = (int)lane_id();
+    const float G = a.G;
+    const float self = SAFE ? 0.0f : rsqrt_fast(eps2);
+    int base = 0;
+#pragma unroll
+    for (int q = 0; q < IPL; q++) {
+        if (q < tile.q) {  // warp-uniform
+            const int lg = tile.lg[q], u = 1 << lg;
+            const int row = lane & (u - 1), split = lane >> lg;
+            float r[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                if (c == 3 && !PHI) {
+                    r[c] = 0.0f;
+                    continue;
+                }
+                if constexpr (COMP) {
+                    for (int t = 1; t < (32 >> lg); t++) {
+                        const float v = __shfl_sync(NB_FULL, I.acc[q][c] + I.cmp[q][c], row + (t << lg));
+                        if (split == 0) neumaier_add(I.acc[q][c], I.cmp[q][c], v);
+                    }
+                    r[c] = I.acc[q][c] + I.cmp[q][c];
+                } else {
+                    float v = I.run[q][c].x + I.run[q][c].y;
+                    for (int m = 16; m >= u; m >>= 1) v += __shfl_xor_sync(NB_FULL, v, m);
+                    r[c] = v;
+                }
+            }
+            const int k = base + row;
+            if (split == 0 && k < cnt) {
+                const float ph = PHI ? G * (r[3] + I.mi[q] * self) : 0.0f;
+                const int i = first + k;
+                if (a.perm) {
+                    const int o = a.perm[i];
+                    a.ax[o] = G * r[0];
+                    a.ay[o] = G * r[1];
+                    a.az[o] = G * r[2];
+                    if (PHI && a.phi) a.phi[o] = ph;
+                } else {
+                    a.acc_sorted[i] = make_float4(G * r[0], G * r[1], G * r[2], ph);
+                }
+            }
+            base += u;
+        }
+    }
 }
 
 // Register budget of the walk kernel per thread: 64 (32 resident warps per
@@ -368,26 +461,10 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
         const int root = a.sys_root[sys];
 
         if (cnt > 32 * IPL) bad = true;  // larger than the group size allows
-        const LaneTile tile = lane_tile<IPL>(cnt);
-        const int row = (int)lane % tile.P, split = (int)lane / tile.P;
-        const int k0 = split < tile.s ? split : (1 << 30);  // idle lanes take no pairs
+        const BinTile<IPL> tile = bin_tile<IPL>(cnt);
 
         ISlots<IPL> I;
-#pragma unroll
-        for (int q = 0; q < IPL; q++) {
-            const int k = row + tile.P * q;
-            float4 p = (q < tile.q && k < cnt) ? a.pos4[first + k]
-                                              : make_float4(sph.x, sph.y, sph.z, 0.0f);
-            I.nx[q] = make_float2(-p.x, -p.x);
-            I.ny[q] = make_float2(-p.y, -p.y);
-            I.nz[q] = make_float2(-p.z, -p.z);
-            I.mi[q] = p.w;
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                I.acc[q][c] = I.cmp[q][c] = 0.0f;
-                I.run[q][c] = make_float2(0.0f, 0.0f);
-            }
-        }
+        load_slots<IPL>(tile, a.pos4, first, cnt, sph, I);
 
         if (lane == 0) stk[0] = (uint32_t)root << 3;  // one node: the system's root
         int sp = 1, nl = 0, nq = 0;
@@ -454,7 +531,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
             if constexpr (QUAD) {
                 if (nq + na > DQ) {
                     __syncwarp();
-                    flush_quad_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LQ, nq, eps2, I);
+                    flush_bin<0, IPL, PHI, COMP, SAFE, true>(tile, LQ, nq, eps2, I);
                     qentries += nq;
                     nq = 0;
                     __syncwarp();
@@ -466,7 +543,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
             } else {
                 if (nl + na > D) {
                     __syncwarp();
-                    flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, nl, eps2, I);
+                    flush_bin<0, IPL, PHI, COMP, SAFE, false>(tile, LA, nl, eps2, I);
                     entries += nl;
                     nl = 0;
                     __syncwarp();
@@ -498,7 +575,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
                     const int c = (total - base) < 32 ? (total - base) : 32;
                     if (nl + c > D) {
                         __syncwarp();
-                        flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, nl, eps2, I);
+                        flush_bin<0, IPL, PHI, COMP, SAFE, false>(tile, LA, nl, eps2, I);
                         entries += nl;
                         nl = 0;
                         __syncwarp();
@@ -521,64 +598,21 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
         }
         if (nl > 0) {
             __syncwarp();
-            flush_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LA, nl, eps2, I);
+            flush_bin<0, IPL, PHI, COMP, SAFE, false>(tile, LA, nl, eps2, I);
             entries += nl;
             nl = 0;
         }
         if constexpr (QUAD) {
             if (nq > 0) {
                 __syncwarp();
-                flush_quad_group<IPL, PHI, COMP, SAFE>(tile.q, k0, tile.s, LQ, nq, eps2, I);
+                flush_bin<0, IPL, PHI, COMP, SAFE, true>(tile, LQ, nq, eps2, I);
                 qentries += nq;
                 nq = 0;
             }
         }
         __syncwarp();
 
-        // ---- sum the list splits of every particle onto split 0
-        for (int t = 1; t < tile.s; t++) {
-            const int src = row + tile.P * t;
-#pragma unroll
-            for (int q = 0; q < IPL; q++) {
-                if (q < tile.q) {  // warp-uniform
-#pragma unroll
-                    for (int c = 0; c < (PHI ? 4 : 3); c++) {
-                        const float mine = COMP ? I.acc[q][c] + I.cmp[q][c]
-                                                : I.run[q][c].x + I.run[q][c].y;
-                        const float v = __shfl_sync(NB_FULL, mine, src);
-                        if (split == 0) {
-                            if constexpr (COMP) neumaier_add(I.acc[q][c], I.cmp[q][c], v);
-                            else I.run[q][c].x += v;
-                        }
-                    }
-                }
-            }
-        }
-
-        // ---- results (G applied once; the potential's self term removed)
-        const float G = a.G;
-        const float self = SAFE ? 0.0f : rsqrt_fast(eps2);
-#pragma unroll
-        for (int q = 0; q < IPL; q++) {
-            const int k = row + tile.P * q;
-            if (split == 0 && q < tile.q && k < cnt) {
-                float r[4];
-#pragma unroll
-                for (int c = 0; c < 4; c++)
-                    r[c] = COMP ? I.acc[q][c] + I.cmp[q][c] : I.run[q][c].x + I.run[q][c].y;
-                const float ph = PHI ? G * (r[3] + I.mi[q] * self) : 0.0f;
-                const int i = first + k;
-                if (a.perm) {
-                    const int o = a.perm[i];
-                    a.ax[o] = G * r[0];
-                    a.ay[o] = G * r[1];
-                    a.az[o] = G * r[2];
-                    if (PHI && a.phi) a.phi[o] = ph;
-                } else {
-                    a.acc_sorted[i] = make_float4(G * r[0], G * r[1], G * r[2], ph);
-                }
-            }
-        }
+        finish_group<IPL, PHI, COMP, SAFE>(tile, first, cnt, eps2, a, I);
         entries += qentries;
         if (lane == 0 && a.grp_cost) a.grp_cost[g] = (int32_t)entries;
         warp_entries += (unsigned long long)entries;

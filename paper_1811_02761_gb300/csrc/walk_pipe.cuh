@@ -293,8 +293,8 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
         int b = 0;
         uint32_t seen[2] = {0u, 0u};
         ISlots<IPL> I;
-        LaneTile tile{1, 32, 1};
-        int row = 0, split = 0, k0 = 0, first = 0, cnt = 0;
+        BinTile<IPL> tile = bin_tile<IPL>(1);
+        int first = 0, cnt = 0;
         float eps2 = 0.0f;
         for (;;) {
             if (!mbar_wait(&full[b], seen[b] & 1u)) {
@@ -307,74 +307,16 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
                 first = h.first;
                 cnt = h.cnt;
                 eps2 = h.eps2;
-                tile = lane_tile<IPL>(cnt);
-                row = (int)lane % tile.P;
-                split = (int)lane / tile.P;
-                k0 = split < tile.s ? split : (1 << 30);
-                const float4 sph = a.grp_sphere[h.g];
-#pragma unroll
-                for (int q = 0; q < IPL; q++) {
-                    const int k = row + tile.P * q;
-                    float4 p = (q < tile.q && k < cnt) ? a.pos4[first + k]
-                                                      : make_float4(sph.x, sph.y, sph.z, 0.0f);
-                    I.nx[q] = make_float2(-p.x, -p.x);
-                    I.ny[q] = make_float2(-p.y, -p.y);
-                    I.nz[q] = make_float2(-p.z, -p.z);
-                    I.mi[q] = p.w;
-#pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        I.acc[q][c] = I.cmp[q][c] = 0.0f;
-                        I.run[q][c] = make_float2(0.0f, 0.0f);
-                    }
-                }
+                tile = bin_tile<IPL>(cnt);
+                load_slots<IPL>(tile, a.pos4, first, cnt, a.grp_sphere[h.g], I);
             }
             float4 *LA = buf + (size_t)b * D;
-            if (h.nl > 0) flush_group<IPL, false, COMP, SAFE>(tile.q, k0, tile.s, LA, h.nl, eps2, I);
+            if (h.nl > 0) flush_bin<0, IPL, false, COMP, SAFE, false>(tile, LA, h.nl, eps2, I);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[b]);
             seen[b]++;
             b ^= 1;
-            if (h.flags & kPipeLast) {
-                // ---- sum the list splits of every particle onto split 0
-                for (int t = 1; t < tile.s; t++) {
-                    const int src = row + tile.P * t;
-#pragma unroll
-                    for (int q = 0; q < IPL; q++) {
-                        if (q < tile.q) {
-#pragma unroll
-                            for (int c = 0; c < 3; c++) {
-                                const float mine = COMP ? I.acc[q][c] + I.cmp[q][c]
-                                                        : I.run[q][c].x + I.run[q][c].y;
-                                const float v = __shfl_sync(NB_FULL, mine, src);
-                                if (split == 0) {
-                                    if constexpr (COMP) neumaier_add(I.acc[q][c], I.cmp[q][c], v);
-                                    else I.run[q][c].x += v;
-                                }
-                            }
-                        }
-                    }
-                }
-                const float G = a.G;
-#pragma unroll
-                for (int q = 0; q < IPL; q++) {
-                    const int k = row + tile.P * q;
-                    if (split == 0 && q < tile.q && k < cnt) {
-                        float r[3];
-#pragma unroll
-                        for (int c = 0; c < 3; c++)
-                            r[c] = COMP ? I.acc[q][c] + I.cmp[q][c] : I.run[q][c].x + I.run[q][c].y;
-                        const int i = first + k;
-                        if (a.perm) {
-                            const int o = a.perm[i];
-                            a.ax[o] = G * r[0];
-                            a.ay[o] = G * r[1];
-                            a.az[o] = G * r[2];
-                        } else {
-                            a.acc_sorted[i] = make_float4(G * r[0], G * r[1], G * r[2], 0.0f);
-                        }
-                    }
-                }
-            }
+            if (h.flags & kPipeLast) finish_group<IPL, false, COMP, SAFE>(tile, first, cnt, eps2, a, I);
         }
     }
     if (lane == 0 && timeout) atomicOr(&ds->status, kStatusTimeout);
