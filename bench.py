@@ -48,9 +48,9 @@ FP32_LANES_PER_SM = 128
 # warm-up-step walk, per particle; at another N the launch is scaled by
 # particles.  It is reported only while the walk source is the one the
 # counters were taken on (sha256 of walk_impl.cuh).
-WALK_TRAFFIC = {"bytes_per_particle": (230.475e6 + 111.109e6) / 8388608,
+WALK_TRAFFIC = {"bytes_per_particle": (230.797e6 + 110.955e6) / 8388608,
                 "n_captured": 8388608,
-                "walk_impl_sha256": "6b23cd84dbb4ed031bb123b736f8242206d9f4ae857963b275a0f88953a43bd3",
+                "walk_impl_sha256": "fcd23ced0cf44168e8e1d37eb9c664876ccf7ab0d58c70dfcd19fe721c959c8d",
                 "capture": "profiles/walk_kernel_traffic_galaxy_2e23.md"}
 
 

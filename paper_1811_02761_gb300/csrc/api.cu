@@ -70,6 +70,7 @@ struct nbody_ctx {
     // walk / step
     DevBuf acc_s, aold_s;
     DevBuf st_buf[2][11];
+    DevBuf recs;  // 64-byte particle records of a call's full permutations
     // learned scheduling
     DevBuf mlp_w, mlp_m1, mlp_m2, mlp_wb, mlp_norm, mlp_gpart, mlp_lpart, mlp_loss;
     DevBuf feat, target, score, okey, okey_alt, oval, oval_alt, pcost_walk;
@@ -107,7 +108,7 @@ struct nbody_ctx {
                          &grp_sys, &grp_alpha, &grp_cost, &grp_order, &sys_off, &sys_box,
                          &sys_boxord, &sys_eps2, &sys_eps, &sys_root, &acc_s, &aold_s, &mlp_w, &mlp_m1,
                          &mlp_m2, &mlp_wb, &mlp_norm, &mlp_gpart, &mlp_lpart, &mlp_loss, &feat,
-                         &target, &score, &okey, &okey_alt, &oval, &oval_alt, &pcost_walk};
+                         &target, &score, &okey, &okey_alt, &oval, &oval_alt, &pcost_walk, &recs};
         for (DevBuf *b : all) owned.push_back(b);
         for (auto &a : st_buf)
             for (auto &b : a) owned.push_back(&b);
@@ -1036,8 +1037,14 @@ static nbody_status block_steps(nbody_ctx *ctx, const Layout &L, StepState *S, i
             st = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false,
                             near_order);
             if (st != NBODY_OK) return st;
-            launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur], P<float4>(ctx->pos4));
-            ctx->kernels += 1;
+            if (near_order) {
+                launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur], P<float4>(ctx->pos4));
+                ctx->kernels += 1;
+            } else {
+                launch_permute_state_recs(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
+                                          P<float4>(ctx->pos4), ctx->recs.p);
+                ctx->kernels += 2;
+            }
             cur = 1 - cur;
             st = build_tree_groups(ctx, L);
             rebuilds++;
@@ -1092,6 +1099,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         for (int k = 3; k < 10 && e == cudaSuccess; k++) e = ensure(ctx->st_buf[b][k], (size_t)n * 4);
         if (e == cudaSuccess && ctx->cfg.block_levels > 0) e = ensure(ctx->st_buf[b][10], (size_t)n);
     }
+    if (e == cudaSuccess) e = ensure(ctx->recs, (size_t)n * 64);
     if (e != cudaSuccess) return fail(ctx, NBODY_ENOMEM, std::string("allocation: ") + cudaGetErrorString(e));
     std::vector<int64_t> off1 = {0, n};
     nbody_status st = upload_systems(ctx, nsys, offsets ? offsets : off1.data(), eps_sys);
@@ -1165,8 +1173,14 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         if (rebuild) {
             r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false, near_order);
             if (r != NBODY_OK) return r;
-            launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
-                                 P<float4>(ctx->pos4));
+            if (near_order) {
+                launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
+                                     P<float4>(ctx->pos4));
+            } else {  // the caller's order: a far-from-identity permutation
+                launch_permute_state_recs(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
+                                          P<float4>(ctx->pos4), ctx->recs.p);
+                ctx->kernels += 1;
+            }
             ctx->kernels += 1;
             cur = 1 - cur;
             r = build_tree_groups(ctx, L);
@@ -1323,10 +1337,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         pending_kick = false;
     }
     // in[] are the device copies (the caller's arrays themselves when on the device)
-    // vals_alt (uint32 [n]) is free between steps: the inverse permutation
     launch_store_state(s, n, S[cur], acc, (double *)in[0], (double *)in[1], (double *)in[2],
                        (float *)in[3], (float *)in[4], (float *)in[5], (float *)in[7],
-                       (float *)in[8], (float *)in[9], P<uint32_t>(ctx->vals_alt));
+                       (float *)in[8], (float *)in[9], ctx->recs.p);
     ctx->kernels += 2;
     for (int k = 0; k < 10; k++) {
         if (k == 6 || direct[k]) continue;

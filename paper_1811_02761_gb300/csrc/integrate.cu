@@ -113,6 +113,93 @@ void launch_permute_state(cudaStream_t s, int64_t n, const uint32_t *perm, StepS
     permute_state_kernel<<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(n, perm, src, dst, pos4);
 }
 
+// 64-byte particle records for the two full permutations of a call (the
+// first sort, from the caller's order, and the return to it).  Gathering
+// field by field reads one sector for every 4- or 8-byte value; a record
+// moves a particle's whole state in one aligned 64-byte line.
+union StateRec {
+    struct {
+        double x, y, z;
+        float vx, vy, vz, m, aold;
+        uint32_t id;
+        float pcost;
+        uint32_t lvl;
+    } f;
+    uint4 q[4];
+};
+static_assert(sizeof(StateRec) == 64, "one 64-byte line per particle");
+
+__device__ __forceinline__ void rec_store(uint4 *rec, int64_t i, const StateRec &r) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) rec[4 * i + k] = r.q[k];
+}
+__device__ __forceinline__ StateRec rec_load(const uint4 *__restrict__ rec, int64_t i) {
+    StateRec r;
+#pragma unroll
+    for (int k = 0; k < 4; k++) r.q[k] = rec[4 * i + k];
+    return r;
+}
+
+__global__ void __launch_bounds__(256) pack_state_kernel(int64_t n, StepState st, uint4 *rec) {
+    NB_GRID_LOOP(i, n) {
+        StateRec r;
+        r.f.x = st.x[i];
+        r.f.y = st.y[i];
+        r.f.z = st.z[i];
+        r.f.vx = st.vx[i];
+        r.f.vy = st.vy[i];
+        r.f.vz = st.vz[i];
+        r.f.m = st.m[i];
+        r.f.aold = st.aold[i];
+        r.f.id = st.id[i];
+        r.f.pcost = st.pcost ? st.pcost[i] : 0.0f;
+        r.f.lvl = st.lvl ? st.lvl[i] : 0u;
+        r.q[3].z = r.q[3].w = 0u;
+        rec_store(rec, i, r);
+    }
+}
+
+// Each load instruction of a warp fetches eight whole records (four lanes
+// per 64-byte line); the records reach their threads through shared memory.
+__global__ void __launch_bounds__(256) permute_recs_kernel(int64_t n,
+                                                           const uint32_t *__restrict__ perm,
+                                                           const uint4 *__restrict__ rec,
+                                                           StepState dst, float4 *__restrict__ pos4) {
+    __shared__ uint4 srec[256 * 4];
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t src = i < n ? (int64_t)perm[i] : -1;
+    const int lane = (int)(threadIdx.x & 31), w0 = (int)(threadIdx.x & ~31u);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int c = 32 * k + lane, j = c >> 2, part = c & 3;  // record j of the warp, piece part
+        const int64_t sj = __shfl_sync(NB_FULL, src, j);
+        if (sj >= 0) srec[4 * (w0 + j) + part] = rec[4 * sj + part];
+    }
+    __syncwarp();
+    if (i >= n) return;
+    StateRec r;
+#pragma unroll
+    for (int k = 0; k < 4; k++) r.q[k] = srec[4 * threadIdx.x + k];
+    dst.x[i] = r.f.x;
+    dst.y[i] = r.f.y;
+    dst.z[i] = r.f.z;
+    pos4[i] = make_float4((float)r.f.x, (float)r.f.y, (float)r.f.z, r.f.m);
+    dst.vx[i] = r.f.vx;
+    dst.vy[i] = r.f.vy;
+    dst.vz[i] = r.f.vz;
+    dst.m[i] = r.f.m;
+    dst.aold[i] = r.f.aold;
+    dst.id[i] = r.f.id;
+    if (dst.pcost) dst.pcost[i] = r.f.pcost;
+    if (dst.lvl) dst.lvl[i] = (uint8_t)r.f.lvl;
+}
+
+void launch_permute_state_recs(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
+                               StepState dst, float4 *pos4, void *rec) {
+    pack_state_kernel<<<grid_for(n), 256, 0, s>>>(n, src, (uint4 *)rec);
+    permute_recs_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(n, perm, (const uint4 *)rec, dst, pos4);
+}
+
 __global__ void load_state_kernel(int64_t n, const double *x, const double *y, const double *z,
                                   const float *vx, const float *vy, const float *vz,
                                   const float *m, const float *ax, const float *ay,
@@ -142,41 +229,81 @@ void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double 
     load_state_kernel<<<grid_for(n), 256, 0, s>>>(n, x, y, z, vx, vy, vz, m, ax, ay, az, st, acc);
 }
 
-// The state back in the caller's order, as a gather: inv[o] = the sorted index
-// of caller index o, then every output array is written in caller order
-// (coalesced writes; the reads are random but fetch whole sectors, where a
-// scatter's random writes of 4- and 8-byte values would each cost a
-// partial-sector write).
-__global__ void inverse_perm_kernel(int64_t n, const uint32_t *__restrict__ id, uint32_t *inv) {
-    NB_GRID_LOOP(i, n) inv[id[i]] = (uint32_t)i;
+// The state back in the caller's order: every sorted particle's output
+// record (x, y, z, v, a) goes to its caller index as one whole 64-byte line
+// (a random write of full sectors, no read-modify-write), then the records
+// are unpacked into the caller's arrays with coalesced writes.
+union OutRec {
+    struct {
+        double x, y, z;
+        float vx, vy, vz, ax, ay, az;
+    } f;
+    uint4 q[4];
+};
+static_assert(sizeof(OutRec) == 64, "one 64-byte line per particle");
+
+// One thread per sorted particle builds its record in shared memory; then
+// each store instruction of a warp writes eight whole records (four lanes
+// per 64-byte line) instead of one 16-byte piece of 32 different lines.
+__global__ void __launch_bounds__(256) scatter_out_kernel(int64_t n, StepState st,
+                                                          const float4 *__restrict__ acc,
+                                                          uint4 *rec) {
+    __shared__ uint4 srec[256 * 4];
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    OutRec r;
+    r.q[0] = r.q[1] = r.q[2] = r.q[3] = make_uint4(0u, 0u, 0u, 0u);
+    int64_t o = -1;
+    if (i < n) {
+        const float4 a = acc[i];
+        r.f.x = st.x[i];
+        r.f.y = st.y[i];
+        r.f.z = st.z[i];
+        r.f.vx = st.vx[i];
+        r.f.vy = st.vy[i];
+        r.f.vz = st.vz[i];
+        r.f.ax = a.x;
+        r.f.ay = a.y;
+        r.f.az = a.z;
+        o = st.id[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) srec[4 * threadIdx.x + k] = r.q[k];
+    __syncwarp();
+    const int lane = (int)(threadIdx.x & 31), w0 = (int)(threadIdx.x & ~31u);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int c = 32 * k + lane, j = c >> 2, part = c & 3;  // record j of the warp, piece part
+        const int64_t oj = __shfl_sync(NB_FULL, o, j);
+        if (oj >= 0) rec[4 * oj + part] = srec[4 * (w0 + j) + part];
+    }
 }
 
-__global__ void gather_state_kernel(int64_t n, StepState st, const float4 *__restrict__ acc,
-                                    const uint32_t *__restrict__ inv, double *x, double *y,
-                                    double *z, float *vx, float *vy, float *vz, float *ax,
-                                    float *ay, float *az) {
+__global__ void __launch_bounds__(256) unpack_out_kernel(int64_t n, const uint4 *__restrict__ rec,
+                                                         double *x, double *y, double *z,
+                                                         float *vx, float *vy, float *vz,
+                                                         float *ax, float *ay, float *az) {
     NB_GRID_LOOP(o, n) {
-        const uint32_t i = inv[o];
-        const double px = st.x[i], py = st.y[i], pz = st.z[i];
-        const float qx = st.vx[i], qy = st.vy[i], qz = st.vz[i];
-        const float4 a = acc[i];
-        x[o] = px;
-        y[o] = py;
-        z[o] = pz;
-        vx[o] = qx;
-        vy[o] = qy;
-        vz[o] = qz;
-        ax[o] = a.x;
-        ay[o] = a.y;
-        az[o] = a.z;
+        OutRec r;
+#pragma unroll
+        for (int k = 0; k < 4; k++) r.q[k] = rec[4 * o + k];
+        x[o] = r.f.x;
+        y[o] = r.f.y;
+        z[o] = r.f.z;
+        vx[o] = r.f.vx;
+        vy[o] = r.f.vy;
+        vz[o] = r.f.vz;
+        ax[o] = r.f.ax;
+        ay[o] = r.f.ay;
+        az[o] = r.f.az;
     }
 }
 
 void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
-                        float *ay, float *az, uint32_t *inv) {
-    inverse_perm_kernel<<<grid_for(n), 256, 0, s>>>(n, st.id, inv);
-    gather_state_kernel<<<grid_for(n), 256, 0, s>>>(n, st, acc, inv, x, y, z, vx, vy, vz, ax, ay, az);
+                        float *ay, float *az, void *rec) {
+    scatter_out_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(n, st, acc, (uint4 *)rec);
+    unpack_out_kernel<<<grid_for(n), 256, 0, s>>>(n, (const uint4 *)rec, x, y, z, vx, vy, vz, ax,
+                                                  ay, az);
 }
 
 // ---------------------------------------------------------------- block time steps

@@ -339,11 +339,15 @@ void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double 
                        const double *z, const float *vx, const float *vy, const float *vz,
                        const float *m, const float *ax, const float *ay, const float *az,
                        StepState st, float4 *acc);
-// The state back in caller order, as a gather through the inverse
-// permutation; inv: uint32 [n] scratch.
+// The same permutation through 64-byte particle records (rec: 64 n bytes of
+// scratch): for a far-from-identity perm (the first sort of a call).
+void launch_permute_state_recs(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
+                               StepState dst, float4 *pos4, void *rec);
+// The state back in caller order (x, y, z, v, a), through 64-byte records
+// scattered to the caller indices (rec: 64 n bytes of scratch).
 void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
-                        float *ay, float *az, uint32_t *inv = nullptr);
+                        float *ay, float *az, void *rec);
 size_t diag_temp_bytes();
 // Message returned by nbody_last_error(NULL, ...) on this thread.
 void set_stateless_error(const std::string &msg);

@@ -388,16 +388,23 @@ __device__ __forceinline__ bool internal_node(const Layout &L, int p, int c0, in
                                               float2 *mass2, float4 *nodeQ) {
     if (c0 <= p || nc < 1 || nc > 8 || c0 + nc > nn) return false;
     const CellF cell = node_cell(L, key, level, box);
+    // every field of every child in one round trip; the positions and sizes
+    // stay in registers for the size bound
+    float CX[8], CY[8], CZ[8], CB[8];
     float2 M = make_float2(0.0f, 0.0f);
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     int count = 0;
 #pragma unroll
-    for (int k = 0; k < 8; k++) {  // predicated: every child's loads in flight at once
+    for (int k = 0; k < 8; k++) {
+        const int j = k < nc ? c0 + k : c0;
+        const float4 A = __ldcg(nodeA + j);
+        const float2 mk = __ldcg(mass2 + j);
+        const int ck = __ldcg(node_count + j);
+        CB[k] = __ldcg(&nodeB[j].x);
+        CX[k] = A.x; CY[k] = A.y; CZ[k] = A.z;
         if (k < nc) {
-            const int j = c0 + k;
-            const float4 A = __ldcg(nodeA + j);
-            M = df_add(M, __ldcg(mass2 + j));
-            count += __ldcg(node_count + j);
+            M = df_add(M, mk);
+            count += ck;
             px = fmaf(A.w, A.x - cell.c[0], px);
             py = fmaf(A.w, A.y - cell.c[1], py);
             pz = fmaf(A.w, A.z - cell.c[2], pz);
@@ -411,14 +418,21 @@ __device__ __forceinline__ bool internal_node(const Layout &L, int p, int c0, in
     float rec = 0.0f;
     float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < 8; k++) {  // the children again (L2 hits)
-        if (k >= nc) break;
-        const int j = c0 + k;
-        const float4 A = __ldcg(nodeA + j);
-        const float dx = A.x - cp[0], dy = A.y - cp[1], dz = A.z - cp[2];
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        rec = fmaxf(rec, __fadd_ru(__fsqrt_ru(r2), __ldcg(&nodeB[j].x)));
-        if (nodeQ) {
+    for (int k = 0; k < 8; k++) {
+        if (k < nc) {
+            const float dx = CX[k] - cp[0], dy = CY[k] - cp[1], dz = CZ[k] - cp[2];
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            rec = fmaxf(rec, __fadd_ru(__fsqrt_ru(r2), CB[k]));
+        }
+    }
+    if (nodeQ) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (k >= nc) break;
+            const int j = c0 + k;
+            const float4 A = __ldcg(nodeA + j);
+            const float dx = A.x - cp[0], dy = A.y - cp[1], dz = A.z - cp[2];
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             const float4 q0 = __ldcg(nodeQ + 2 * j), q1 = __ldcg(nodeQ + 2 * j + 1);
             q[0] += q0.x; q[1] += q0.y; q[2] += q0.z; q[3] += q0.w; q[4] += q1.x; q[5] += q1.y;
             quad_add(q, A.w, dx, dy, dz, r2);
@@ -451,7 +465,7 @@ __device__ __forceinline__ int count_in(int par, int32_t *node_arrive) {
 }
 
 #ifndef NB_MOMENTS_MIN_CTAS
-#define NB_MOMENTS_MIN_CTAS 6  // resident 256-thread CTAs per SM the moments pass is compiled for
+#define NB_MOMENTS_MIN_CTAS 4  // resident 256-thread CTAs per SM the moments pass is compiled for
 #endif
 
 // Members loaded per batch by each lane of a leaf team (independent loads in
