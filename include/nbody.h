@@ -81,14 +81,18 @@ typedef struct {
     int32_t leaf_cap;    /* max particles in a leaf, 1..32 (default 16)             */
     int32_t group_size;  /* max particles sharing one list, leaf_cap..32*ipl (64)   */
     int32_t ipl;         /* most i-particles a lane of a walking warp holds, 1..4;
-                            a group is tiled over the lanes as q <= ipl particles
-                            per lane times 32 / ceil(size / q) list splits (3)    */
+                            slot j of a lane covers 2^k members of a group and
+                            cuts the list 32 / 2^k ways, the 2^k the fewest powers
+                            of two covering the group (3)                         */
     int32_t list_depth;  /* interaction-list entries per warp, 64..1024, multiple
                             of 32 (default 256)                                    */
     int32_t stack_depth; /* traversal stack entries per warp, 64..4096 (256)        */
     int32_t warps_per_block; /* walk warps per CTA, 1..16 (default 4)             */
     int32_t compensated; /* 1: per-flush partial sums added with Neumaier
-                            compensation; 0: plain FP32 sums (default 0)          */
+                            compensation; 0: plain FP32 sums; 2 (default): automatic,
+                            compensated where the MAC is tight (delta_acc <= 2^-18,
+                            where plain FP32 sums start to add measurably to the
+                            force error)                                           */
     int32_t want_potential; /* 1: also accumulate phi (default 0)                 */
     int32_t schedule;    /* nbody_schedule (default NBODY_SCHED_MORTON)             */
     int32_t use_graph;   /* 1: nbody_step(_batched) replays a CUDA graph of two

@@ -152,3 +152,37 @@ def test_energy_history_matches_oracle_leapfrog():
         # P wanders by about the force error (the tree force is not exactly
         # antisymmetric); both runs wander alike
         assert np.linalg.norm(gg[2:5] - go[2:5]) <= 2e-5
+
+
+def test_automatic_compensation_follows_the_mac():
+    """compensated = 2 (the default) sums plain at a loose MAC and with
+    compensation where the MAC is tight (delta_acc <= 2^-18): its forces equal
+    the explicit setting's bit for bit on each side of the threshold, and the
+    two settings differ there."""
+    n = 1 << 13
+    p = ics.plummer(n, 5)
+    ctx = nb.nbody_create(nb.nbody_config_default(eps=EPS))
+    assert nb.nbody_get_config(ctx).compensated == 2
+    out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    try:
+        nb.nbody_build(ctx, *[dev(p[k]) for k in ("x", "y", "z", "m")])
+        nb.nbody_walk(ctx, None, *out)
+        amag = torch.sqrt(out[0] ** 2 + out[1] ** 2 + out[2] ** 2).contiguous()
+        forces = {}
+        for k in (9, 18):
+            for comp in (0, 1, 2):
+                cfg = nb.nbody_get_config(ctx)
+                cfg.delta_acc, cfg.compensated, cfg.stack_depth = 2.0 ** -k, comp, 1024
+                nb.nbody_set_config(ctx, cfg)
+                nb.nbody_walk(ctx, amag, *out)
+                forces[k, comp] = np.stack([o.cpu().numpy() for o in out])
+        cfg = nb.nbody_get_config(ctx)
+        cfg.compensated = 3
+        with pytest.raises(nb.NbodyError) as e:
+            nb.nbody_set_config(ctx, cfg)
+        assert e.value.status == nb.NBODY_EINVAL
+    finally:
+        nb.nbody_destroy(ctx)
+    assert np.array_equal(forces[9, 2], forces[9, 0])
+    assert np.array_equal(forces[18, 2], forces[18, 1])
+    assert not np.array_equal(forces[18, 0], forces[18, 1])
