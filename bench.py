@@ -48,9 +48,9 @@ FP32_LANES_PER_SM = 128
 # warm-up-step walk, per particle; at another N the launch is scaled by
 # particles.  It is reported only while the walk source is the one the
 # counters were taken on (sha256 of walk_impl.cuh).
-WALK_TRAFFIC = {"bytes_per_particle": (230.797e6 + 110.955e6) / 8388608,
+WALK_TRAFFIC = {"bytes_per_particle": (230.617e6 + 110.988e6) / 8388608,
                 "n_captured": 8388608,
-                "walk_impl_sha256": "fcd23ced0cf44168e8e1d37eb9c664876ccf7ab0d58c70dfcd19fe721c959c8d",
+                "walk_impl_sha256": "f45061adc710b78f6f6a1da075f2fc1840aeb28aed1bfb5370e2eeb20542bb67",
                 "capture": "profiles/walk_kernel_traffic_galaxy_2e23.md"}
 
 

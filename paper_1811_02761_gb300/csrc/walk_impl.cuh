@@ -6,9 +6,9 @@
 //     (one atomicAdd per group); the queue order is Morton order or a cost
 //     order chosen by the scheduler;
 //   * each lane holds up to IPL i-particles (group <= 32*IPL particles) in
-//     slots; slot j covers a power-of-two share of the group and cuts the
-//     list into 32 / u_j splits, so that few lanes idle in the flush
-//     (bin_tile below);
+//     slots; the slots form runs, each a number of rows of the group times
+//     a number of list splits, chosen per group size from a table so that
+//     the flush issues the fewest instructions (lane_tiling below);
 //   * traversal: a per-warp stack in shared memory whose entries are child
 //     ranges (first node, count <= 8).  Each round the warp pops the top four
 //     ranges (up to 32 nodes, one per lane), evaluates the MAC of Eq. 2
@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
+#include "walk_tiling.cuh"
 
 namespace nb {
 
@@ -253,93 +254,96 @@ __device__ __forceinline__ void flush_quad_list(float4 *LQ, int nq, float eps2, 
     }
 }
 
-// Binary lane tiling: slot j of every lane covers u_j = 2^lg[j] <= 32
-// particles of the group (lane L holds particle base_j + L % u_j) and takes
-// every s_j-th entry pair of the list, s_j = 32 / u_j, starting at pair
-// L / u_j; the s_j lanes of a particle are summed at the end of the group.
-// The u_j are the fewest powers of two, at most IPL of them, whose sum covers
-// cnt (the top bits of cnt, the rest rounded up to a power of two, equal
-// neighbours merged), so a lane's share of the work is sum_j u_j / 32 times
-// the list for cnt / 32 ideally -- e.g. 50 = 32 + 16 + 2 costs 1.5625 lists
-// per lane where one layout of 25 rows of two particles costs 2.  Runs of
-// slots with equal u share one flush loop.
-template <int IPL>
-struct BinTile {
-    int q;
-    int lg[IPL];
+// Lane tiling of a group of cnt particles (walk_tiling.cuh, written by
+// gen_tiling.py): the slots of a lane form runs; run k has r_k slots, P_k
+// rows and s_k = floor(32 / P_k) splits.  Lane L is row L % P_k of split
+// L / P_k (idle in run k when L / P_k >= s_k), its t-th slot of the run holds
+// particle base_k + row + P_k t, and it takes every s_k-th entry pair of the
+// list from pair L / P_k on.  One flush loop serves a run.  The table picks,
+// for every cnt, the runs with the fewest issued instructions per list entry
+// (the loop's loads and control once per pair, the arithmetic once per slot).
+struct Tiling {
+    uint64_t code;  // the table entry: number of runs, then (r, P, s) per run
+    int k0[3];      // this lane's first entry pair in each run (idle: 1 << 30)
 };
+__device__ __forceinline__ int run_field(uint64_t code, int k, int shift, int bits) {
+    return (int)((code >> (2 + 16 * k + shift)) & ((1u << bits) - 1u));
+}
+__device__ __forceinline__ int run_r(uint64_t code, int k) { return run_field(code, k, 0, 4); }
+__device__ __forceinline__ int run_P(uint64_t code, int k) { return run_field(code, k, 4, 6); }
+__device__ __forceinline__ int run_s(uint64_t code, int k) { return run_field(code, k, 10, 6); }
+
 template <int IPL>
-__device__ __forceinline__ BinTile<IPL> bin_tile(int cnt) {
-    BinTile<IPL> t;
-    t.q = 0;
-    int rem = cnt;
+__device__ __forceinline__ Tiling lane_tiling(int cnt) {
+    // a group larger than the slots allow (flagged by the caller) still gets
+    // a well-formed layout: the largest one
+    const int c = cnt < 1 ? 1 : (cnt > 32 * IPL ? 32 * IPL : cnt);
+    Tiling t;
+    t.code = __ldg(&kTiling[IPL - 1][c]);
+    const int nr = (int)(t.code & 3u), lane = (int)lane_id();
 #pragma unroll
-    for (int j = 0; j < IPL; j++) {
-        int lg = 0;
-        if (rem > 0) {
-            lg = (j + 1 < IPL) ? 31 - __clz(rem) : (rem > 1 ? 32 - __clz(rem - 1) : 0);
-            lg = lg < 5 ? lg : 5;
-            rem -= 1 << lg;
-            t.q = j + 1;
-        }
-        t.lg[j] = lg;
-    }
-#pragma unroll
-    for (int j = IPL - 1; j >= 1; j--) {
-        if (j == t.q - 1 && t.lg[j] == t.lg[j - 1] && t.lg[j] < 5) {
-            t.lg[j - 1] += 1;
-            t.lg[j] = 0;
-            t.q = j;
-        }
+    for (int k = 0; k < 3; k++) {
+        const int P = k < nr ? run_P(t.code, k) : 32, s = k < nr ? run_s(t.code, k) : 1;
+        const int split = lane / P;
+        t.k0[k] = (k < nr && split < s) ? split : (1 << 30);
     }
     return t;
 }
 
-template <int J, int IPL, bool PHI, bool COMP, bool SAFE, bool QUADL>
-__device__ __forceinline__ void flush_bin(const BinTile<IPL> &t, float4 *L, int nl, float eps2,
-                                          ISlots<IPL> &I) {
-    if constexpr (J < IPL) {
-        if (J >= t.q) return;
-        const int lg = t.lg[J];
-        const int k0 = (int)lane_id() >> lg, ks = 32 >> lg;
-        int run = 1;
-#pragma unroll
-        for (int j = J + 1; j < IPL; j++)
-            if (run == j - J && j < t.q && t.lg[j] == lg) run++;
-#define NB_FLUSH(R)                                                                       \
-    do {                                                                                  \
+// The flush loops of the runs from slot J on (run K).
+template <int J, int K, int IPL, bool PHI, bool COMP, bool SAFE, bool QUADL>
+__device__ __forceinline__ void flush_runs(const Tiling &t, float4 *L, int nl, float eps2,
+                                           ISlots<IPL> &I) {
+    if constexpr (J < IPL && K < 3) {
+        if (K >= (int)(t.code & 3u)) return;
+        const int r = run_r(t.code, K), ks = run_s(t.code, K), k0 = t.k0[K];
+#define NB_FLUSH(R)                                                                            \
+    do {                                                                                       \
         if constexpr (QUADL) flush_quad_list<J, R, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I); \
-        else flush_list<J, R, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);             \
+        else flush_list<J, R, IPL, PHI, COMP, SAFE>(L, nl, eps2, k0, ks, I);                  \
     } while (0)
-        if constexpr (J + 3 < IPL) {
-            if (run >= 4) { NB_FLUSH(4); return; }
+        if constexpr (J + 4 <= IPL) {
+            if (r == 4) { NB_FLUSH(4); return; }
         }
-        if constexpr (J + 2 < IPL) {
-            if (run == 3) { NB_FLUSH(3); flush_bin<J + 3, IPL, PHI, COMP, SAFE, QUADL>(t, L, nl, eps2, I); return; }
+        if constexpr (J + 3 <= IPL) {
+            if (r == 3) { NB_FLUSH(3); flush_runs<J + 3, K + 1, IPL, PHI, COMP, SAFE, QUADL>(t, L, nl, eps2, I); return; }
         }
-        if constexpr (J + 1 < IPL) {
-            if (run == 2) { NB_FLUSH(2); flush_bin<J + 2, IPL, PHI, COMP, SAFE, QUADL>(t, L, nl, eps2, I); return; }
+        if constexpr (J + 2 <= IPL) {
+            if (r == 2) { NB_FLUSH(2); flush_runs<J + 2, K + 1, IPL, PHI, COMP, SAFE, QUADL>(t, L, nl, eps2, I); return; }
         }
         NB_FLUSH(1);
-        flush_bin<J + 1, IPL, PHI, COMP, SAFE, QUADL>(t, L, nl, eps2, I);
+        flush_runs<J + 1, K + 1, IPL, PHI, COMP, SAFE, QUADL>(t, L, nl, eps2, I);
 #undef NB_FLUSH
     }
 }
 
-// A group's i-particles into the lanes' slots (the members slot j covers;
-// past the group's end, massless copies of the sphere centre) and zeroed sums.
+// Run k, slot t within it, of the lane's slot j (j < the slots in use).
+__device__ __forceinline__ void slot_run(uint64_t code, int j, int &k, int &t) {
+    const int r0 = run_r(code, 0), r1 = run_r(code, 1);
+    k = j < r0 ? 0 : (j < r0 + r1 ? 1 : 2);
+    t = j - (k == 0 ? 0 : (k == 1 ? r0 : r0 + r1));
+}
+__device__ __forceinline__ int slots_used(uint64_t code) {
+    const int nr = (int)(code & 3u);
+    return (nr > 0 ? run_r(code, 0) : 0) + (nr > 1 ? run_r(code, 1) : 0) + (nr > 2 ? run_r(code, 2) : 0);
+}
+
+// A group's i-particles into the lanes' slots (past the group's end, or on an
+// idle row: massless copies of the sphere centre) and zeroed sums.
 template <int IPL>
-__device__ __forceinline__ void load_slots(const BinTile<IPL> &tile, const float4 *__restrict__ pos4,
+__device__ __forceinline__ void load_slots(const Tiling &tile, const float4 *__restrict__ pos4,
                                            int first, int cnt, float4 sph, ISlots<IPL> &I) {
-    const int lane = (int)lane_id();
-    int base = 0;
+    const int lane = (int)lane_id(), used = slots_used(tile.code);
 #pragma unroll
     for (int q = 0; q < IPL; q++) {
-        const int u = 1 << tile.lg[q];
-        const int k = base + (lane & (u - 1));
-        const float4 p = (q < tile.q && k < cnt) ? pos4[first + k]
-                                                : make_float4(sph.x, sph.y, sph.z, 0.0f);
-        base += q < tile.q ? u : 0;
+        int k = 0, t = 0;
+        slot_run(tile.code, q, k, t);
+        const int P = run_P(tile.code, k);
+        const int base = k == 0 ? 0 : run_r(tile.code, 0) * run_P(tile.code, 0) +
+                                          (k == 2 ? run_r(tile.code, 1) * run_P(tile.code, 1) : 0);
+        const int idx = base + lane % P + P * t;
+        const float4 p = (q < used && idx < cnt) ? pos4[first + idx]
+                                                 : make_float4(sph.x, sph.y, sph.z, 0.0f);
         I.nx[q] = make_float2(-p.x, -p.x);
         I.ny[q] = make_float2(-p.y, -p.y);
         I.nz[q] = make_float2(-p.z, -p.z);
@@ -352,22 +356,24 @@ __device__ __forceinline__ void load_slots(const BinTile<IPL> &tile, const float
     }
 }
 
-// End of a group: the s_j lanes of every particle of slot j are summed (a
-// butterfly over the lane bits above its row; compensated: in split order
-// onto split 0), then the results are written (G applied once; the
-// potential's self term removed).
+// End of a group: the s_k splits of every row are summed onto split 0 in
+// split order (with compensation: Neumaier), then the results are written (G
+// applied once; the potential's self term removed).
 template <int IPL, bool PHI, bool COMP, bool SAFE>
-__device__ __forceinline__ void finish_group(const BinTile<IPL> &tile, int first, int cnt,
-                                             float eps2, const WalkArgs &a, ISlots<IPL> &I) {
-    const int lane = (int)lane_id();
+__device__ __forceinline__ void finish_group(const Tiling &tile, int first, int cnt, float eps2,
+                                             const WalkArgs &a, ISlots<IPL> &I) {
+    const int lane = (int)lane_id(), used = slots_used(tile.code);
     const float G = a.G;
     const float self = SAFE ? 0.0f : rsqrt_fast(eps2);
-    int base = 0;
 #pragma unroll
     for (int q = 0; q < IPL; q++) {
-        if (q < tile.q) {  // warp-uniform
-            const int lg = tile.lg[q], u = 1 << lg;
-            const int row = lane & (u - 1), split = lane >> lg;
+        if (q < used) {  // warp-uniform
+            int k = 0, t = 0;
+            slot_run(tile.code, q, k, t);
+            const int P = run_P(tile.code, k), s = run_s(tile.code, k);
+            const int base = k == 0 ? 0 : run_r(tile.code, 0) * run_P(tile.code, 0) +
+                                              (k == 2 ? run_r(tile.code, 1) * run_P(tile.code, 1) : 0);
+            const int row = lane % P, split = lane / P;
             float r[4];
 #pragma unroll
             for (int c = 0; c < 4; c++) {
@@ -376,21 +382,22 @@ __device__ __forceinline__ void finish_group(const BinTile<IPL> &tile, int first
                     continue;
                 }
                 if constexpr (COMP) {
-                    for (int t = 1; t < (32 >> lg); t++) {
-                        const float v = __shfl_sync(NB_FULL, I.acc[q][c] + I.cmp[q][c], row + (t << lg));
+                    for (int u = 1; u < s; u++) {
+                        const float v = __shfl_sync(NB_FULL, I.acc[q][c] + I.cmp[q][c], row + P * u);
                         if (split == 0) neumaier_add(I.acc[q][c], I.cmp[q][c], v);
                     }
                     r[c] = I.acc[q][c] + I.cmp[q][c];
                 } else {
                     float v = I.run[q][c].x + I.run[q][c].y;
-                    for (int m = 16; m >= u; m >>= 1) v += __shfl_xor_sync(NB_FULL, v, m);
-                    r[c] = v;
+                    float sum = v;
+                    for (int u = 1; u < s; u++) sum += __shfl_sync(NB_FULL, v, row + P * u);
+                    r[c] = sum;
                 }
             }
-            const int k = base + row;
-            if (split == 0 && k < cnt) {
+            const int idx = base + row + P * t;
+            if (split == 0 && idx < cnt) {
                 const float ph = PHI ? G * (r[3] + I.mi[q] * self) : 0.0f;
-                const int i = first + k;
+                const int i = first + idx;
                 if (a.perm) {
                     const int o = a.perm[i];
                     a.ax[o] = G * r[0];
@@ -401,7 +408,6 @@ __device__ __forceinline__ void finish_group(const BinTile<IPL> &tile, int first
                     a.acc_sorted[i] = make_float4(G * r[0], G * r[1], G * r[2], ph);
                 }
             }
-            base += u;
         }
     }
 }
@@ -461,7 +467,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
         const int root = a.sys_root[sys];
 
         if (cnt > 32 * IPL) bad = true;  // larger than the group size allows
-        const BinTile<IPL> tile = bin_tile<IPL>(cnt);
+        const Tiling tile = lane_tiling<IPL>(cnt);
 
         ISlots<IPL> I;
         load_slots<IPL>(tile, a.pos4, first, cnt, sph, I);
@@ -531,7 +537,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
             if constexpr (QUAD) {
                 if (nq + na > DQ) {
                     __syncwarp();
-                    flush_bin<0, IPL, PHI, COMP, SAFE, true>(tile, LQ, nq, eps2, I);
+                    flush_runs<0, 0, IPL, PHI, COMP, SAFE, true>(tile, LQ, nq, eps2, I);
                     qentries += nq;
                     nq = 0;
                     __syncwarp();
@@ -543,7 +549,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
             } else {
                 if (nl + na > D) {
                     __syncwarp();
-                    flush_bin<0, IPL, PHI, COMP, SAFE, false>(tile, LA, nl, eps2, I);
+                    flush_runs<0, 0, IPL, PHI, COMP, SAFE, false>(tile, LA, nl, eps2, I);
                     entries += nl;
                     nl = 0;
                     __syncwarp();
@@ -575,7 +581,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
                     const int c = (total - base) < 32 ? (total - base) : 32;
                     if (nl + c > D) {
                         __syncwarp();
-                        flush_bin<0, IPL, PHI, COMP, SAFE, false>(tile, LA, nl, eps2, I);
+                        flush_runs<0, 0, IPL, PHI, COMP, SAFE, false>(tile, LA, nl, eps2, I);
                         entries += nl;
                         nl = 0;
                         __syncwarp();
@@ -598,14 +604,14 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_kernel(WalkArgs a, int geomet
         }
         if (nl > 0) {
             __syncwarp();
-            flush_bin<0, IPL, PHI, COMP, SAFE, false>(tile, LA, nl, eps2, I);
+            flush_runs<0, 0, IPL, PHI, COMP, SAFE, false>(tile, LA, nl, eps2, I);
             entries += nl;
             nl = 0;
         }
         if constexpr (QUAD) {
             if (nq > 0) {
                 __syncwarp();
-                flush_bin<0, IPL, PHI, COMP, SAFE, true>(tile, LQ, nq, eps2, I);
+                flush_runs<0, 0, IPL, PHI, COMP, SAFE, true>(tile, LQ, nq, eps2, I);
                 qentries += nq;
                 nq = 0;
             }

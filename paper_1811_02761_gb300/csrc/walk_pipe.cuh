@@ -293,7 +293,7 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
         int b = 0;
         uint32_t seen[2] = {0u, 0u};
         ISlots<IPL> I;
-        BinTile<IPL> tile = bin_tile<IPL>(1);
+        Tiling tile = lane_tiling<IPL>(1);
         int first = 0, cnt = 0;
         float eps2 = 0.0f;
         for (;;) {
@@ -307,11 +307,11 @@ __global__ void __maxnreg__(walk_regs<IPL>()) walk_pipe_kernel(WalkArgs a, int g
                 first = h.first;
                 cnt = h.cnt;
                 eps2 = h.eps2;
-                tile = bin_tile<IPL>(cnt);
+                tile = lane_tiling<IPL>(cnt);
                 load_slots<IPL>(tile, a.pos4, first, cnt, a.grp_sphere[h.g], I);
             }
             float4 *LA = buf + (size_t)b * D;
-            if (h.nl > 0) flush_bin<0, IPL, false, COMP, SAFE, false>(tile, LA, h.nl, eps2, I);
+            if (h.nl > 0) flush_runs<0, 0, IPL, false, COMP, SAFE, false>(tile, LA, h.nl, eps2, I);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[b]);
             seen[b]++;
