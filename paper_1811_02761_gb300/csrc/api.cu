@@ -71,6 +71,12 @@ struct nbody_ctx {
     DevBuf acc_s, aold_s;
     DevBuf st_buf[2][11];
     DevBuf recs;  // 64-byte particle records of a call's full permutations
+    // the Morton order (caller indices) at the end of the last step call: the
+    // next call's first sort starts from it (hint_n: its particle count, 0 =
+    // none)
+    DevBuf last_ids;
+    int64_t hint_n = 0;
+    int32_t hint_nsys = 0;
     // learned scheduling
     DevBuf mlp_w, mlp_m1, mlp_m2, mlp_wb, mlp_norm, mlp_gpart, mlp_lpart, mlp_loss;
     DevBuf feat, target, score, okey, okey_alt, oval, oval_alt, pcost_walk;
@@ -108,7 +114,7 @@ struct nbody_ctx {
                          &grp_sys, &grp_alpha, &grp_cost, &grp_order, &sys_off, &sys_box,
                          &sys_boxord, &sys_eps2, &sys_eps, &sys_root, &acc_s, &aold_s, &mlp_w, &mlp_m1,
                          &mlp_m2, &mlp_wb, &mlp_norm, &mlp_gpart, &mlp_lpart, &mlp_loss, &feat,
-                         &target, &score, &okey, &okey_alt, &oval, &oval_alt, &pcost_walk, &recs};
+                         &target, &score, &okey, &okey_alt, &oval, &oval_alt, &pcost_walk, &recs, &last_ids};
         for (DevBuf *b : all) owned.push_back(b);
         for (auto &a : st_buf)
             for (auto &b : a) owned.push_back(&b);
@@ -339,9 +345,14 @@ Layout make_layout(int64_t n, int nsys) {
 // near_order: the positions are in the order of the previous build (the
 // particles have moved since), so their keys are nearly sorted: the near-order
 // sort moves every key twice where the radix sort moves it seven times.
+// hint (nullable, not near_order): a permutation of 0..n-1 that nearly sorts
+// the keys (the Morton order of this context's last step call, as caller
+// indices): the keys are gathered into that order and sorted by the
+// near-order sort by (key, caller index), the same result as the radix sort
+// of the caller's order.
 nbody_status build_core(nbody_ctx *c, const Layout &L, const void *x, const void *y,
                         const void *z, bool dbl, const float *m, bool fill_pos4,
-                        bool near_order = false) {
+                        bool near_order = false, const uint32_t *hint = nullptr) {
     cudaStream_t s = c->stream;
     launch_bbox(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<uint32_t>(c->sys_boxord),
                 P<SysBox>(c->sys_box), c->nsm);
@@ -354,6 +365,16 @@ nbody_status build_core(nbody_ctx *c, const Layout &L, const void *x, const void
         c->kernels += 1 + nosort_kernels();
         std::swap(c->keys, c->keys_alt);
         std::swap(c->vals, c->vals_alt);
+    } else if (hint && nosort_fits(L.n)) {
+        launch_keys(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<SysBox>(c->sys_box),
+                    P<uint64_t>(c->keys), P<uint32_t>(c->vals), nullptr, c->nsm);
+        nosort_hint_gather(s, L.n, P<uint64_t>(c->keys), hint, P<uint64_t>(c->keys_alt),
+                           P<uint32_t>(c->vals_alt));
+        // values: the caller indices; vals_alt is read by the scatter before
+        // the bucket pass uses it as scratch
+        nosort(s, P<uint64_t>(c->keys_alt), P<uint64_t>(c->keys), P<uint32_t>(c->vals_alt),
+               P<uint32_t>(c->vals), L.n, c->rs_temp.p, &c->ds->status, P<uint32_t>(c->vals_alt));
+        c->kernels += 2 + nosort_kernels();
     } else {
         radix_prepare(s, L.n, c->rs_temp.p);
         launch_keys(s, L, x, y, z, dbl, P<int64_t>(c->sys_off), P<SysBox>(c->sys_box),
@@ -372,6 +393,15 @@ nbody_status build_core(nbody_ctx *c, const Layout &L, const void *x, const void
     }
     NB_CUDA(c, cudaGetLastError());
     return NBODY_OK;
+}
+
+// The hint for a call's first sort: the Morton order (as caller indices) that
+// the context's last step call ended in, when it had the same particle count
+// and systems.
+const uint32_t *first_sort_hint(const nbody_ctx *c, const Layout &L) {
+    return (c->hint_n == L.n && c->hint_nsys == L.nsys && c->last_ids.p)
+               ? static_cast<const uint32_t *>(c->last_ids.p)
+               : nullptr;
 }
 
 nbody_status build_tree_groups(nbody_ctx *c, const Layout &L) {
@@ -1045,7 +1075,7 @@ static nbody_status block_steps(nbody_ctx *ctx, const Layout &L, StepState *S, i
         NB_CUDA(ctx, cudaEventRecord(e0, q));
         if (rebuild) {
             st = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false,
-                            near_order);
+                            near_order, near_order ? nullptr : first_sort_hint(ctx, L));
             if (st != NBODY_OK) return st;
             if (near_order) {
                 launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur], P<float4>(ctx->pos4));
@@ -1181,7 +1211,8 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         }
         nbody_status r;
         if (rebuild) {
-            r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false, near_order);
+            r = build_core(ctx, L, S[cur].x, S[cur].y, S[cur].z, true, S[cur].m, false, near_order,
+                           near_order ? nullptr : first_sort_hint(ctx, L));
             if (r != NBODY_OK) return r;
             if (near_order) {
                 launch_permute_state(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
@@ -1346,6 +1377,11 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
         ctx->kernels += 1;
         pending_kick = false;
     }
+    // the Morton order this call ends in starts the next call's first sort
+    NB_CUDA(ctx, ensure(ctx->last_ids, (size_t)n * 4));
+    NB_CUDA(ctx, cudaMemcpyAsync(ctx->last_ids.p, S[cur].id, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    ctx->hint_n = n;
+    ctx->hint_nsys = nsys;
     // in[] are the device copies (the caller's arrays themselves when on the device)
     launch_store_state(s, n, S[cur], acc, (double *)in[0], (double *)in[1], (double *)in[2],
                        (float *)in[3], (float *)in[4], (float *)in[5], (float *)in[7],

@@ -164,14 +164,21 @@ int radix_passes(int bits);
 // Sort of keys that are nearly in order already (the previous build's order
 // with new keys, as inside a time step): splitters from one key per tile,
 // buckets, a scatter and a shared-memory sort per bucket (nosort.cu).
-// keys (overwritten: scratch) -> kout (sorted keys), vout (the index of each
-// sorted key in the input); vscr: uint32 [n] scratch.  The result equals
-// the stable sort of the keys for any input order.  Device-side failures are
-// or-ed into *status.
+// keys (overwritten: scratch) -> kout (sorted keys), vout (the value of each
+// sorted key: its index in the input, or vin[index] when vin is given);
+// vscr: uint32 [n] scratch (may be vin: read before vscr is written).  The
+// result is the sort by (key, value): with the indices as values, the stable
+// sort of the keys for any input order; with vin a permutation, the stable
+// sort of the keys in the order vin names.  Device-side failures are or-ed
+// into *status.
 bool nosort_fits(int64_t n);
 size_t nosort_temp_bytes(int64_t n);
 void nosort(cudaStream_t s, uint64_t *keys, uint64_t *kout, uint32_t *vscr, uint32_t *vout,
-            int64_t n, void *temp, int32_t *status);
+            int64_t n, void *temp, int32_t *status, const uint32_t *vin = nullptr);
+// kout[k] = keys[hint[k]], vout[k] = hint[k]: keys put in a hinted order
+// (a permutation of 0..n-1) before the near-order sort.
+void nosort_hint_gather(cudaStream_t s, int64_t n, const uint64_t *keys, const uint32_t *hint,
+                        uint64_t *kout, uint32_t *vout);
 int nosort_kernels();
 // True for memory the current device dev can read in place (its own device
 // memory, or managed memory); diag_noalloc.cu.

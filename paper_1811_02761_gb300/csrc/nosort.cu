@@ -273,7 +273,9 @@ __global__ void __launch_bounds__(NS_THREADS) ns_scatter_kernel(const uint64_t *
                                                                 const uint64_t *__restrict__ spl,
                                                                 const uint32_t *__restrict__ start,
                                                                 uint32_t *fill, uint64_t *kout,
-                                                                uint32_t *vout, int32_t *status) {
+                                                                uint32_t *vout,
+                                                                const uint32_t *__restrict__ vin,
+                                                                int32_t *status) {
     __shared__ uint32_t band[3], base[3];
     const int t = blockIdx.x;
     if (threadIdx.x < 3) band[threadIdx.x] = 0;
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(NS_THREADS) ns_scatter_kernel(const uint64_t *
         const uint32_t s0 = start[b], s1 = start[b + 1];
         if (slot < s1 - s0) {
             kout[s0 + slot] = key[u];
-            vout[s0 + slot] = (uint32_t)i;
+            vout[s0 + slot] = vin ? vin[i] : (uint32_t)i;
         } else {
             bad = true;
         }
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(NSS_THREADS, 4) ns_bucket_kernel(const uint32_
 }
 
 void nosort(cudaStream_t s, uint64_t *keys, uint64_t *kout, uint32_t *vscr, uint32_t *vout,
-            int64_t n, void *temp, int32_t *status) {
+            int64_t n, void *temp, int32_t *status, const uint32_t *vin) {
     const int nb = (int)ns_nb(n);
     NsTemp T = ns_temp(temp, n);
     cudaMemsetAsync(T.rank, 0, (size_t)nb * 12, s);  // ranks, counts, fill
@@ -454,8 +456,28 @@ void nosort(cudaStream_t s, uint64_t *keys, uint64_t *kout, uint32_t *vscr, uint
     cudaMemcpyAsync(T.start, T.cnt, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s);
     launch_scan_sums(s, T.start, nb, reinterpret_cast<int32_t *>(T.start + nb));
     ns_scatter_kernel<<<nb, NS_THREADS, 0, s>>>(keys, n, nb, T.spl, T.start, T.fill, kout, vout,
-                                                status);
+                                                vin, status);
     ns_bucket_kernel<<<nb, NSS_THREADS, 0, s>>>(T.start, kout, vout, keys, vscr);
+}
+
+// Keys in a hinted order: kout[k] = keys[hint[k]], vout[k] = hint[k] (hint: a
+// permutation of 0..n-1, e.g. the Morton order of the previous build).
+__global__ void __launch_bounds__(256) ns_hint_gather_kernel(int64_t n, const uint64_t *__restrict__ keys,
+                                                             const uint32_t *__restrict__ hint,
+                                                             uint64_t *kout, uint32_t *vout) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = hint[k];
+        kout[k] = j < n ? keys[j] : ~0ull;
+        vout[k] = j;
+    }
+}
+
+void nosort_hint_gather(cudaStream_t s, int64_t n, const uint64_t *keys, const uint32_t *hint,
+                        uint64_t *kout, uint32_t *vout) {
+    int64_t b = (n + 255) / 256;
+    if (b > 65535 * 8) b = 65535 * 8;
+    ns_hint_gather_kernel<<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(n, keys, hint, kout, vout);
 }
 
 int nosort_kernels() { return 6; }  // rank, place, count, scan, scatter, bucket sort
