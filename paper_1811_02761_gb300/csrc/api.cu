@@ -1177,10 +1177,13 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     ctx->wev_used = 0;
     ctx->evused = 0;
     NB_CUDA(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevState), s));
+    // the first step's opening kick and drift are applied by the state load
+    // (shared steps; block steps start with their own kicks)
+    bool loaded_kd = nsteps >= 1 && ctx->cfg.block_levels == 0;
     launch_load_state(s, n, (const double *)in[0], (const double *)in[1], (const double *)in[2],
                       (const float *)in[3], (const float *)in[4], (const float *)in[5],
                       (const float *)in[6], (const float *)in[7], (const float *)in[8],
-                      (const float *)in[9], S[0], acc);
+                      (const float *)in[9], S[0], acc, loaded_kd, 0.5f * dt, dt);
     ctx->kernels += 1;
     int cur = 0;
     std::vector<int> marks;  // per eager step: event indices (build start, build end, walk end)
@@ -1200,10 +1203,14 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     // build (every step but the call's first, whose state is in caller order)
     auto one_step = [&](bool timing, bool rebuild, bool near_order) -> nbody_status {
         cudaStream_t q = ctx->stream;
-        launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt, rebuild ? nullptr : P<float4>(ctx->pos4),
-                          pending_kick ? 0.5f * dt : 0.0f);
+        if (loaded_kd) {  // done by the state load (the call's first step)
+            loaded_kd = false;
+        } else {
+            launch_kick_drift(q, n, S[cur], acc, 0.5f * dt, dt,
+                              rebuild ? nullptr : P<float4>(ctx->pos4), pending_kick ? 0.5f * dt : 0.0f);
+            ctx->kernels += 1;
+        }
         pending_kick = false;
-        ctx->kernels += 1;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         if (timing) {
             NB_CUDA(ctx, pool_event(ctx, &e0));
@@ -1372,11 +1379,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             cycle.push_back(c);
         }
     }
-    if (pending_kick) {  // the last eager step's closing half kick
-        launch_kick(s, n, S[cur], acc, 0.5f * dt);
-        ctx->kernels += 1;
-        pending_kick = false;
-    }
+    // the last eager step's closing half kick is applied on the way out
+    const float hclose = pending_kick ? 0.5f * dt : 0.0f;
+    pending_kick = false;
     // the Morton order this call ends in starts the next call's first sort
     NB_CUDA(ctx, ensure(ctx->last_ids, (size_t)n * 4));
     NB_CUDA(ctx, cudaMemcpyAsync(ctx->last_ids.p, S[cur].id, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
@@ -1385,7 +1390,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     // in[] are the device copies (the caller's arrays themselves when on the device)
     launch_store_state(s, n, S[cur], acc, (double *)in[0], (double *)in[1], (double *)in[2],
                        (float *)in[3], (float *)in[4], (float *)in[5], (float *)in[7],
-                       (float *)in[8], (float *)in[9], ctx->recs.p);
+                       (float *)in[8], (float *)in[9], ctx->recs.p, hclose);
     ctx->kernels += 2;
     for (int k = 0; k < 10; k++) {
         if (k == 6 || direct[k]) continue;

@@ -200,14 +200,26 @@ void launch_permute_state_recs(cudaStream_t s, int64_t n, const uint32_t *perm, 
     permute_recs_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(n, perm, (const uint4 *)rec, dst, pos4);
 }
 
+// kd != 0: the first step's opening half kick (hdt) and drift (dt) applied
+// on the way in, with the kick-drift pass's arithmetic.
 __global__ void load_state_kernel(int64_t n, const double *x, const double *y, const double *z,
                                   const float *vx, const float *vy, const float *vz,
                                   const float *m, const float *ax, const float *ay,
-                                  const float *az, StepState st, float4 *acc) {
+                                  const float *az, StepState st, float4 *acc, int kd, float hdt,
+                                  double dt) {
     NB_GRID_LOOP(i, n) {
-        const double px = x[i], py = y[i], pz = z[i];
-        const float qx = vx[i], qy = vy[i], qz = vz[i], mi = m[i];
+        double px = x[i], py = y[i], pz = z[i];
+        float qx = vx[i], qy = vy[i], qz = vz[i];
+        const float mi = m[i];
         const float a0 = ax[i], a1 = ay[i], a2 = az[i];
+        if (kd) {
+            qx = fmaf(a0, hdt, qx);
+            qy = fmaf(a1, hdt, qy);
+            qz = fmaf(a2, hdt, qz);
+            px = px + (double)qx * dt;
+            py = py + (double)qy * dt;
+            pz = pz + (double)qz * dt;
+        }
         st.x[i] = px;
         st.y[i] = py;
         st.z[i] = pz;
@@ -225,8 +237,9 @@ __global__ void load_state_kernel(int64_t n, const double *x, const double *y, c
 void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double *y,
                        const double *z, const float *vx, const float *vy, const float *vz,
                        const float *m, const float *ax, const float *ay, const float *az,
-                       StepState st, float4 *acc) {
-    load_state_kernel<<<grid_for(n), 256, 0, s>>>(n, x, y, z, vx, vy, vz, m, ax, ay, az, st, acc);
+                       StepState st, float4 *acc, bool kick_drift, float hdt, float dt) {
+    load_state_kernel<<<grid_for(n), 256, 0, s>>>(n, x, y, z, vx, vy, vz, m, ax, ay, az, st, acc,
+                                                  kick_drift ? 1 : 0, hdt, (double)dt);
 }
 
 // The state back in the caller's order: every sorted particle's output
@@ -247,7 +260,7 @@ static_assert(sizeof(OutRec) == 64, "one 64-byte line per particle");
 // per 64-byte line) instead of one 16-byte piece of 32 different lines.
 __global__ void __launch_bounds__(256) scatter_out_kernel(int64_t n, StepState st,
                                                           const float4 *__restrict__ acc,
-                                                          uint4 *rec) {
+                                                          uint4 *rec, float hkick) {
     __shared__ uint4 srec[256 * 4];
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     OutRec r;
@@ -258,9 +271,9 @@ __global__ void __launch_bounds__(256) scatter_out_kernel(int64_t n, StepState s
         r.f.x = st.x[i];
         r.f.y = st.y[i];
         r.f.z = st.z[i];
-        r.f.vx = st.vx[i];
-        r.f.vy = st.vy[i];
-        r.f.vz = st.vz[i];
+        r.f.vx = hkick != 0.0f ? fmaf(a.x, hkick, st.vx[i]) : st.vx[i];
+        r.f.vy = hkick != 0.0f ? fmaf(a.y, hkick, st.vy[i]) : st.vy[i];
+        r.f.vz = hkick != 0.0f ? fmaf(a.z, hkick, st.vz[i]) : st.vz[i];
         r.f.ax = a.x;
         r.f.ay = a.y;
         r.f.az = a.z;
@@ -300,8 +313,8 @@ __global__ void __launch_bounds__(256) unpack_out_kernel(int64_t n, const uint4 
 
 void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
-                        float *ay, float *az, void *rec) {
-    scatter_out_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(n, st, acc, (uint4 *)rec);
+                        float *ay, float *az, void *rec, float hkick) {
+    scatter_out_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(n, st, acc, (uint4 *)rec, hkick);
     unpack_out_kernel<<<grid_for(n), 256, 0, s>>>(n, (const uint4 *)rec, x, y, z, vx, vy, vz, ax,
                                                   ay, az);
 }

@@ -342,19 +342,24 @@ void launch_kick_drift(cudaStream_t s, int64_t n, StepState st, const float4 *ac
 void launch_kick(cudaStream_t s, int64_t n, StepState st, const float4 *acc, float hdt);
 void launch_permute_state(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
                           StepState dst, float4 *pos4);
+// kick_drift: also the first step's opening half kick (v += a hdt) and drift
+// (x += v dt), with the kick-drift pass's arithmetic.
 void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double *y,
                        const double *z, const float *vx, const float *vy, const float *vz,
                        const float *m, const float *ax, const float *ay, const float *az,
-                       StepState st, float4 *acc);
+                       StepState st, float4 *acc, bool kick_drift = false, float hdt = 0.0f,
+                       float dt = 0.0f);
 // The same permutation through 64-byte particle records (rec: 64 n bytes of
 // scratch): for a far-from-identity perm (the first sort of a call).
 void launch_permute_state_recs(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
                                StepState dst, float4 *pos4, void *rec);
 // The state back in caller order (x, y, z, v, a), through 64-byte records
-// scattered to the caller indices (rec: 64 n bytes of scratch).
+// scattered to the caller indices (rec: 64 n bytes of scratch); hkick != 0:
+// the velocities get the last step's closing half kick on the way out (the
+// device state itself is left without it).
 void launch_store_state(cudaStream_t s, int64_t n, StepState st, const float4 *acc, double *x,
                         double *y, double *z, float *vx, float *vy, float *vz, float *ax,
-                        float *ay, float *az, void *rec);
+                        float *ay, float *az, void *rec, float hkick = 0.0f);
 size_t diag_temp_bytes();
 // Message returned by nbody_last_error(NULL, ...) on this thread.
 void set_stateless_error(const std::string &msg);
