@@ -1183,7 +1183,11 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     launch_load_state(s, n, (const double *)in[0], (const double *)in[1], (const double *)in[2],
                       (const float *)in[3], (const float *)in[4], (const float *)in[5],
                       (const float *)in[6], (const float *)in[7], (const float *)in[8],
-                      (const float *)in[9], S[0], acc, loaded_kd, 0.5f * dt, dt);
+                      (const float *)in[9], S[0], acc, loaded_kd, 0.5f * dt, dt,
+                      loaded_kd ? ctx->recs.p : nullptr);
+    // with the first kick-drift fused, the load also writes the records the
+    // first step's sort gathers (its state exists only as records and x, y, z)
+    bool loaded_recs = loaded_kd;
     ctx->kernels += 1;
     int cur = 0;
     std::vector<int> marks;  // per eager step: event indices (build start, build end, walk end)
@@ -1226,9 +1230,10 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
                                      P<float4>(ctx->pos4));
             } else {  // the caller's order: a far-from-identity permutation
                 launch_permute_state_recs(q, n, P<uint32_t>(ctx->vals), S[cur], S[1 - cur],
-                                          P<float4>(ctx->pos4), ctx->recs.p);
-                ctx->kernels += 1;
+                                          P<float4>(ctx->pos4), ctx->recs.p, loaded_recs);
+                ctx->kernels += loaded_recs ? 0 : 1;
             }
+            loaded_recs = false;
             ctx->kernels += 1;
             cur = 1 - cur;
             r = build_tree_groups(ctx, L);

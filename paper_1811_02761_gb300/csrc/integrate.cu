@@ -195,8 +195,8 @@ __global__ void __launch_bounds__(256) permute_recs_kernel(int64_t n,
 }
 
 void launch_permute_state_recs(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
-                               StepState dst, float4 *pos4, void *rec) {
-    pack_state_kernel<<<grid_for(n), 256, 0, s>>>(n, src, (uint4 *)rec);
+                               StepState dst, float4 *pos4, void *rec, bool packed) {
+    if (!packed) pack_state_kernel<<<grid_for(n), 256, 0, s>>>(n, src, (uint4 *)rec);
     permute_recs_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(n, perm, (const uint4 *)rec, dst, pos4);
 }
 
@@ -206,7 +206,7 @@ __global__ void load_state_kernel(int64_t n, const double *x, const double *y, c
                                   const float *vx, const float *vy, const float *vz,
                                   const float *m, const float *ax, const float *ay,
                                   const float *az, StepState st, float4 *acc, int kd, float hdt,
-                                  double dt) {
+                                  double dt, uint4 *rec) {
     NB_GRID_LOOP(i, n) {
         double px = x[i], py = y[i], pz = z[i];
         float qx = vx[i], qy = vy[i], qz = vz[i];
@@ -223,23 +223,43 @@ __global__ void load_state_kernel(int64_t n, const double *x, const double *y, c
         st.x[i] = px;
         st.y[i] = py;
         st.z[i] = pz;
-        st.vx[i] = qx;
-        st.vy[i] = qy;
-        st.vz[i] = qz;
-        st.m[i] = mi;
         acc[i] = make_float4(a0, a1, a2, 0.0f);
-        st.aold[i] = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
-        st.id[i] = (uint32_t)i;
-        if (st.pcost) st.pcost[i] = 1.0f;
+        const float ao = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+        if (rec) {  // the rest of the state only as the record the first sort gathers
+            StateRec r;
+            r.f.x = px;
+            r.f.y = py;
+            r.f.z = pz;
+            r.f.vx = qx;
+            r.f.vy = qy;
+            r.f.vz = qz;
+            r.f.m = mi;
+            r.f.aold = ao;
+            r.f.id = (uint32_t)i;
+            r.f.pcost = 1.0f;
+            r.f.lvl = 0u;
+            r.q[3].z = r.q[3].w = 0u;
+            rec_store(rec, i, r);
+        } else {
+            st.vx[i] = qx;
+            st.vy[i] = qy;
+            st.vz[i] = qz;
+            st.m[i] = mi;
+            st.aold[i] = ao;
+            st.id[i] = (uint32_t)i;
+            if (st.pcost) st.pcost[i] = 1.0f;
+        }
     }
 }
 
 void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double *y,
                        const double *z, const float *vx, const float *vy, const float *vz,
                        const float *m, const float *ax, const float *ay, const float *az,
-                       StepState st, float4 *acc, bool kick_drift, float hdt, float dt) {
+                       StepState st, float4 *acc, bool kick_drift, float hdt, float dt,
+                       void *rec) {
     load_state_kernel<<<grid_for(n), 256, 0, s>>>(n, x, y, z, vx, vy, vz, m, ax, ay, az, st, acc,
-                                                  kick_drift ? 1 : 0, hdt, (double)dt);
+                                                  kick_drift ? 1 : 0, hdt, (double)dt,
+                                                  (uint4 *)rec);
 }
 
 // The state back in the caller's order: every sorted particle's output

@@ -348,11 +348,15 @@ void launch_load_state(cudaStream_t s, int64_t n, const double *x, const double 
                        const double *z, const float *vx, const float *vy, const float *vz,
                        const float *m, const float *ax, const float *ay, const float *az,
                        StepState st, float4 *acc, bool kick_drift = false, float hdt = 0.0f,
-                       float dt = 0.0f);
+                       float dt = 0.0f, void *rec = nullptr);
+// (rec != nullptr: only x, y, z, acc go to the SoA state; the rest of each
+// particle, with x, y, z, is written as its 64-byte record into rec, ready
+// for launch_permute_state_recs(..., packed = true).)
 // The same permutation through 64-byte particle records (rec: 64 n bytes of
 // scratch): for a far-from-identity perm (the first sort of a call).
+// packed: rec already holds src's records (written by the state load).
 void launch_permute_state_recs(cudaStream_t s, int64_t n, const uint32_t *perm, StepState src,
-                               StepState dst, float4 *pos4, void *rec);
+                               StepState dst, float4 *pos4, void *rec, bool packed = false);
 // The state back in caller order (x, y, z, v, a), through 64-byte records
 // scattered to the caller indices (rec: 64 n bytes of scratch); hkick != 0:
 // the velocities get the last step's closing half kick on the way out (the
