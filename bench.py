@@ -317,15 +317,16 @@ def run_ours(args, rank, world, local_rank):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dist.all_reduce(it, op=dist.ReduceOp.SUM)
         elapsed_max, inter_all = float(t.item()), float(it.item())
+        # the walk kernel's CUDA-event time inside the timed call: its eager
+        # steps and, with the graph, the last replay's two walks (event nodes)
         walk_ms, walk_launches = st.ms_walk_kernel, st.walk_launches
         phase_ms, phase_steps = (st.ms_build, st.ms_walk), args.steps
-        if walk_launches < args.steps:  # graph replays (all but the call's first step):
-            # time the phases in eager steps
+        if walk_launches < args.steps:  # graph replays carry no phase events:
+            # time the build and walk phases in eager steps
             c2 = nb.nbody_get_config(ctx)
             c2.use_graph = 0
             nb.nbody_set_config(ctx, c2)
             s3 = nb.nbody_step(ctx, *X64, *V, M, *A, dt, PHASE_STEPS)
-            walk_ms, walk_launches = s3.ms_walk_kernel, s3.walk_launches
             phase_ms, phase_steps = (s3.ms_build, s3.ms_walk), PHASE_STEPS
             c2.use_graph = 1
             nb.nbody_set_config(ctx, c2)
@@ -400,6 +401,9 @@ def run_ours(args, rank, world, local_rank):
         "whole_step_tflops": whole_tflops,
         "whole_step_fp32_peak_frac": whole_tflops / peak_tflops,
         "walk_ms_per_step": walk_ms / max(walk_launches, 1),
+        "walk_timing": f"CUDA events around {walk_launches} walk launches inside the timed call "
+                       f"(its eager steps and the last graph replay's two walks, event nodes of "
+                       f"the graph)",
         "build_ms_per_step": phase_ms[0] / phase_steps,
         "walk_phase_ms_per_step": phase_ms[1] / phase_steps,
         "phase_timing": "eager steps (CUDA events per phase)" if phase_steps == steps else

@@ -147,7 +147,10 @@ typedef struct {
     int64_t kernels;       /* kernels this library launched in the last call  */
     float ms_build;        /* device time of the build phase(s) (CUDA events)  */
     float ms_walk;         /* device time of the walk phase(s) (CUDA events)   */
-    float ms_walk_kernel;  /* device time of the walk kernel launches alone    */
+    float ms_walk_kernel;  /* device time of the walk kernel launches alone: the
+                              eager steps' launches and, when nbody_step
+                              replayed a CUDA graph, the last replay's two
+                              (event nodes in the graph)                      */
     int32_t walk_launches; /* walk kernel launches behind ms_walk_kernel       */
     int32_t rebuilds;      /* steps of the last nbody_step call that rebuilt the
                               tree (the others refitted it)                    */

@@ -89,6 +89,10 @@ struct nbody_ctx {
 
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> wev;  // (start, end) pairs around walk-kernel launches
+    // (start, end) pairs around the two walks of the step graph, recorded by
+    // event nodes at every replay: the last replay's walk times
+    cudaEvent_t gwev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int gwev_used = 0, gwev_pairs = 0;  // pairs recorded while capturing / in the graph
     int wev_used = 0;
     std::vector<cudaEvent_t> evpool;  // phase boundaries of asynchronous multi-step calls
     int evused = 0;
@@ -721,12 +725,19 @@ nbody_status run_walk(nbody_ctx *c, bool geometric, bool phi, bool safe, const i
     a.az = az;
     a.phi = ph;
     a.acc_sorted = acc_sorted;
+    // inside a graph capture: event nodes (recorded at every replay)
+    const bool gtime = c->capturing && c->gwev_used + 2 <= 4 && c->gwev[c->gwev_used];
     if (!c->capturing) NB_CUDA(c, cudaEventRecord(c->wev[c->wev_used], c->stream));
+    if (gtime) NB_CUDA(c, cudaEventRecordWithFlags(c->gwev[c->gwev_used], c->stream, cudaEventRecordExternal));
     cudaError_t e = launch_walk(c->stream, a, walk_shape(c, geometric, phi, safe), c->nsm);
     if (e != cudaSuccess) return cuda_fail(c, e, "walk launch");
     if (!c->capturing) {
         NB_CUDA(c, cudaEventRecord(c->wev[c->wev_used + 1], c->stream));
         c->wev_used += 2;
+    }
+    if (gtime) {
+        NB_CUDA(c, cudaEventRecordWithFlags(c->gwev[c->gwev_used + 1], c->stream, cudaEventRecordExternal));
+        c->gwev_used += 2;
     }
     c->kernels += 1;
     if (!geometric) c->costs_valid = true;
@@ -816,6 +827,8 @@ nbody_status nbody_destroy(nbody_ctx *ctx) {
     for (auto &ev : ctx->ev)
         if (ev) cudaEventDestroy(ev);
     for (auto ev : ctx->wev) cudaEventDestroy(ev);
+    for (auto ev : ctx->gwev)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     for (auto ev : ctx->evpool) cudaEventDestroy(ev);
@@ -1271,6 +1284,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     };
 
     int eager = nsteps;
+    int graph_replays = 0;
     bool sorted_state = false;  // the state is in the Morton order of a build of this call
     // steps that may refit instead of rebuilding, and block steps, run eagerly
     if (ctx->cfg.use_graph && nsteps >= 3 && ctx->cfg.rebuild_interval == 1 &&
@@ -1312,6 +1326,9 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
                 cudaGraphExecDestroy(ctx->gexec);
                 ctx->gexec = nullptr;
             }
+            for (auto &ev : ctx->gwev)
+                if (!ev) NB_CUDA(ctx, cudaEventCreate(&ev));
+            ctx->gwev_used = 0;
             cudaStream_t saved = ctx->stream;
             ctx->stream = ctx->gstream;
             ctx->capturing = true;
@@ -1335,6 +1352,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             if (graph) cudaGraphDestroy(graph);
             if (ce != cudaSuccess) return cuda_fail(ctx, ce, "step graph capture");
             ctx->gkernels = ctx->kernels - k0;
+            ctx->gwev_pairs = ctx->gwev_used / 2;
             ctx->kernels = k0;
             ctx->gkey = key;
         }
@@ -1344,6 +1362,7 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
             NB_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->gstream));
             ctx->kernels += ctx->gkernels;
             rebuilds += 2;
+            graph_replays++;
         }
         NB_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->gstream));
         NB_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev[1], 0));
@@ -1425,6 +1444,17 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     ctx->last.ms_build = ms_build;
     ctx->last.ms_walk = ms_walk;
     ctx->last.ms_walk_kernel = collect_walk_ms(ctx, &ctx->last.walk_launches);
+    if (graph_replays > 0) {  // the walks of the last graph replay (its event nodes)
+        for (int k = 0; k < ctx->gwev_pairs; k++) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, ctx->gwev[2 * k], ctx->gwev[2 * k + 1]) == cudaSuccess) {
+                ctx->last.ms_walk_kernel += ms;
+                ctx->last.walk_launches += 1;
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
     ctx->last.kernels = ctx->kernels;
     ctx->last.rebuilds = rebuilds;
     if (stats) *stats = ctx->last;
