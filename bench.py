@@ -321,7 +321,10 @@ def run_ours(args, rank, world, local_rank):
         # steps and, with the graph, the last replay's two walks (event nodes)
         walk_ms, walk_launches = st.ms_walk_kernel, st.walk_launches
         phase_ms, phase_steps = (st.ms_build, st.ms_walk), args.steps
-        if walk_launches < args.steps:  # graph replays carry no phase events:
+        wcfg = nb.nbody_get_config(ctx)
+        graph_used = (wcfg.use_graph and args.steps >= 3 and wcfg.rebuild_interval == 1
+                      and wcfg.block_levels == 0)  # the library's condition for replays
+        if graph_used:  # graph replays carry no phase events:
             # time the build and walk phases in eager steps
             c2 = nb.nbody_get_config(ctx)
             c2.use_graph = 0
@@ -406,7 +409,7 @@ def run_ours(args, rank, world, local_rank):
                        f"the graph)",
         "build_ms_per_step": phase_ms[0] / phase_steps,
         "walk_phase_ms_per_step": phase_ms[1] / phase_steps,
-        "phase_timing": "eager steps (CUDA events per phase)" if phase_steps == steps else
+        "phase_timing": "eager steps (CUDA events per phase)" if not graph_used else
                         f"{PHASE_STEPS} extra eager steps after the timed graph replays (CUDA "
                         "events per phase; graph nodes carry no events; the first step of the "
                         "call also gathers the state from the caller's order)",
