@@ -6,9 +6,10 @@
 // 1.1 % of neighbours are out of order).  A global LSD radix sort ignores
 // that and moves every key through seven passes.  This sort moves every key
 // twice:
-//   1. splitters: the key at the start of every tile of NS_T keys, ranked
-//      among all of them by (key, tile) and placed at their rank; bucket b
-//      holds the keys in [spl[b], spl[b+1]);
+//   1. splitters: the element (key, value) at the start of every tile of
+//      NS_T keys, ranked among all of them and placed at their rank; bucket
+//      b holds the elements from splitter b up to (not including) splitter
+//      b + 1 in the order by (key, value), so equal keys spread over buckets;
 //   2. count: each tile finds the bucket of each of its keys -- almost always
 //      its own or a neighbour's, checked first; a binary search otherwise --
 //      and counts them;
@@ -42,27 +43,28 @@ constexpr int NS_VPAD = NS_CAP + NS_CAP / 32;    // padded shared index slots
 constexpr int NS_MAX_BUCKETS = 16384;
 constexpr int NS_RANK_X = 256, NS_RANK_Y = 256;  // samples per rank block: own, compared
 
-// Temporary layout: splitters u64 [nb], sample ranks u32 [nb], counts u32
-// [nb], fill u32 [nb], starts u32 [nb + 1] (ranks, counts and fill are
-// cleared with one memset).
+// Temporary layout: splitter keys u64 [nb] and values u32 [nb], sample ranks
+// u32 [nb], counts u32 [nb], fill u32 [nb], starts u32 [nb + 1] (ranks,
+// counts and fill are cleared with one memset).
 static size_t ns_nb(int64_t n) { return (size_t)((n + NS_T - 1) / NS_T); }
 
 bool nosort_fits(int64_t n) { return n >= 1 && ns_nb(n) <= NS_MAX_BUCKETS; }
 
 size_t nosort_temp_bytes(int64_t n) {
     const size_t nb = ns_nb(n);
-    return nb * 8 + nb * 12 + (nb + 1) * 4 + 64;
+    return nb * 8 + nb * 16 + (nb + 1) * 4 + 64;
 }
 
 struct NsTemp {
     uint64_t *spl;
-    uint32_t *rank, *cnt, *fill, *start;
+    uint32_t *splv, *rank, *cnt, *fill, *start;
 };
 static NsTemp ns_temp(void *temp, int64_t n) {
     const size_t nb = ns_nb(n);
     NsTemp t;
     t.spl = (uint64_t *)temp;
-    t.rank = (uint32_t *)(t.spl + nb);
+    t.splv = (uint32_t *)(t.spl + nb);
+    t.rank = t.splv + nb;
     t.cnt = t.rank + nb;
     t.fill = t.cnt + nb;
     t.start = t.fill + nb;
@@ -209,18 +211,29 @@ __device__ void block_sort_chunk(uint64_t *k, uint32_t *v, int m, uint64_t *sk, 
     if (!sort_chunk_impl<false>(k, v, m, sk, sv)) sort_chunk_impl<true>(k, v, m, sk, sv);
 }
 
-// Bucket of a key: the largest b with spl[b] <= key.  Tile t's keys almost
-// always belong to bucket t or a neighbour, which are checked first.
-__device__ __forceinline__ int ns_bucket(const uint64_t *__restrict__ spl, int nb, int t,
-                                         uint64_t key) {
-    auto upper = [&](int b) { return b + 1 < nb ? spl[b + 1] : ~0ull; };
-    if (spl[t] <= key && (key < upper(t) || t + 1 == nb)) return t;
-    if (t > 0 && spl[t - 1] <= key && key < spl[t]) return t - 1;
-    if (t + 1 < nb && spl[t + 1] <= key && (t + 2 == nb || key < spl[t + 2])) return t + 1;
-    int lo = 0, hi = nb;  // spl[lo] <= key (spl[0] = 0), and key < spl[hi] (spl[nb] = inf)
+// Bucket of an element (key, value): the largest b whose splitter (spl[b],
+// splv[b]) is not above it in the order by (key, value).  Splitting by pairs
+// spreads equal keys over buckets by value, so no bucket grows with the
+// number of equal keys.  Tile t's elements almost always belong to bucket t
+// or a neighbour, which are checked first.
+__device__ __forceinline__ bool ns_le(const uint64_t *__restrict__ spl,
+                                      const uint32_t *__restrict__ splv, int b, uint64_t key,
+                                      uint32_t val) {
+    const uint64_t k = spl[b];
+    return k < key || (k == key && splv[b] <= val);
+}
+__device__ __forceinline__ int ns_bucket(const uint64_t *__restrict__ spl,
+                                         const uint32_t *__restrict__ splv, int nb, int t,
+                                         uint64_t key, uint32_t val) {
+    // in bucket b: splitter b at or below, splitter b + 1 (if any) above
+    auto in = [&](int b) { return ns_le(spl, splv, b, key, val) && (b + 1 == nb || !ns_le(spl, splv, b + 1, key, val)); };
+    if (in(t)) return t;
+    if (t > 0 && in(t - 1)) return t - 1;
+    if (t + 1 < nb && in(t + 1)) return t + 1;
+    int lo = 0, hi = nb;  // splitter lo at or below (splitter 0 = (0, 0)), hi above (nb: none)
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (spl[mid] <= key) lo = mid; else hi = mid;
+        if (ns_le(spl, splv, mid, key, val)) lo = mid; else hi = mid;
     }
     return lo;
 }
@@ -240,6 +253,8 @@ __device__ __forceinline__ void band_ballots(int d, bool valid, unsigned (&m)[3]
 __global__ void __launch_bounds__(NS_THREADS) ns_count_kernel(const uint64_t *__restrict__ keys,
                                                               int64_t n, int nb,
                                                               const uint64_t *__restrict__ spl,
+                                                              const uint32_t *__restrict__ splv,
+                                                              const uint32_t *__restrict__ vin,
                                                               uint32_t *cnt) {
     __shared__ uint32_t band[3];
     const int t = blockIdx.x;
@@ -250,7 +265,7 @@ __global__ void __launch_bounds__(NS_THREADS) ns_count_kernel(const uint64_t *__
     for (int u = 0; u < NS_IPT; u++) {
         const int64_t i = (int64_t)t * NS_T + u * NS_THREADS + threadIdx.x;
         const bool valid = i < end;
-        const int b = valid ? ns_bucket(spl, nb, t, keys[i]) : t;
+        const int b = valid ? ns_bucket(spl, splv, nb, t, keys[i], vin ? vin[i] : (uint32_t)i) : t;
         const int d = b - t;
         if (valid && (d < -1 || d > 1)) atomicAdd(&cnt[b], 1u);
         unsigned m[3];
@@ -268,9 +283,10 @@ __global__ void __launch_bounds__(NS_THREADS) ns_count_kernel(const uint64_t *__
 // reserves one run of slots per neighbouring bucket, far keys take single
 // slots.  A slot outside the bucket (impossible unless the counts were
 // wrong) is skipped and recorded.
-__global__ void __launch_bounds__(NS_THREADS) ns_scatter_kernel(const uint64_t *__restrict__ keys,
+__global__ void __launch_bounds__(NS_THREADS, 3) ns_scatter_kernel(const uint64_t *__restrict__ keys,
                                                                 int64_t n, int nb,
                                                                 const uint64_t *__restrict__ spl,
+                                                                const uint32_t *__restrict__ splv,
                                                                 const uint32_t *__restrict__ start,
                                                                 uint32_t *fill, uint64_t *kout,
                                                                 uint32_t *vout,
@@ -294,7 +310,7 @@ __global__ void __launch_bounds__(NS_THREADS) ns_scatter_kernel(const uint64_t *
     for (int u = 0; u < NS_IPT; u++) {
         const int64_t i = (int64_t)t * NS_T + u * NS_THREADS + threadIdx.x;
         const bool valid = i < end;
-        bk[u] = valid ? ns_bucket(spl, nb, t, key[u]) : -1;
+        bk[u] = valid ? ns_bucket(spl, splv, nb, t, key[u], vin ? vin[i] : (uint32_t)i) : -1;
         const int d = valid ? bk[u] - t : -5;
         unsigned m[3];
         band_ballots(d, valid, m);
@@ -397,36 +413,47 @@ __device__ void sort_range(uint64_t *k, uint32_t *v, int64_t m, uint64_t *kscr, 
     }
 }
 
-// 1a. Splitter ranks: sample i is the first key of tile i; its rank is the
-// number of samples j before it in the order by (key, j).  Block (x, y)
-// counts, for its NS_RANK_X samples, the smaller ones among samples
-// [NS_RANK_Y y, NS_RANK_Y (y + 1)).
+// 1a. Splitter ranks: sample i is the first element (key, value) of tile i;
+// its rank is the number of samples below it in the order by (key, value)
+// (values are distinct).  Block (x, y) counts, for its NS_RANK_X samples,
+// the smaller ones among samples [NS_RANK_Y y, NS_RANK_Y (y + 1)).
 __global__ void __launch_bounds__(NS_RANK_X) ns_rank_kernel(const uint64_t *__restrict__ keys,
+                                                            const uint32_t *__restrict__ vin,
                                                             int nb, uint32_t *rank) {
     __shared__ uint64_t sk_s[NS_RANK_Y];
+    __shared__ uint32_t sv_s[NS_RANK_Y];
     const int j0 = blockIdx.y * NS_RANK_Y;
     const int cnt = nb - j0 < NS_RANK_Y ? nb - j0 : NS_RANK_Y;
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) sk_s[j] = keys[(int64_t)(j0 + j) * NS_T];
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const int64_t e = (int64_t)(j0 + j) * NS_T;
+        sk_s[j] = keys[e];
+        sv_s[j] = vin ? vin[e] : (uint32_t)e;
+    }
     __syncthreads();
     const int i = blockIdx.x * NS_RANK_X + threadIdx.x;
     if (i >= nb) return;
-    const uint64_t ki = keys[(int64_t)i * NS_T];
+    const int64_t ei = (int64_t)i * NS_T;
+    const uint64_t ki = keys[ei];
+    const uint32_t vi = vin ? vin[ei] : (uint32_t)ei;
     uint32_t c = 0;
     for (int j = 0; j < cnt; j++) {
         const uint64_t kj = sk_s[j];
-        c += (kj < ki || (kj == ki && j0 + j < i)) ? 1u : 0u;
+        c += (kj < ki || (kj == ki && sv_s[j] < vi)) ? 1u : 0u;
     }
     if (c) atomicAdd(&rank[i], c);
 }
 
-// 1b. Each sample goes to its rank; the smallest becomes 0, so that every
-// key has a bucket.
-__global__ void ns_place_kernel(const uint64_t *__restrict__ keys, int nb,
-                                const uint32_t *__restrict__ rank, uint64_t *spl) {
+// 1b. Each sample goes to its rank; the smallest becomes (0, 0), so that
+// every element has a bucket.
+__global__ void ns_place_kernel(const uint64_t *__restrict__ keys,
+                                const uint32_t *__restrict__ vin, int nb,
+                                const uint32_t *__restrict__ rank, uint64_t *spl, uint32_t *splv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     const uint32_t r = rank[i];
-    spl[r] = r == 0 ? 0ull : keys[(int64_t)i * NS_T];
+    const int64_t e = (int64_t)i * NS_T;
+    spl[r] = r == 0 ? 0ull : keys[e];
+    splv[r] = r == 0 ? 0u : (vin ? vin[e] : (uint32_t)e);
 }
 
 // 5. Sort of each bucket by (key, index), in place in (kout, vout); (kscr,
@@ -450,13 +477,13 @@ void nosort(cudaStream_t s, uint64_t *keys, uint64_t *kout, uint32_t *vscr, uint
     NsTemp T = ns_temp(temp, n);
     cudaMemsetAsync(T.rank, 0, (size_t)nb * 12, s);  // ranks, counts, fill
     ns_rank_kernel<<<dim3((nb + NS_RANK_X - 1) / NS_RANK_X, (nb + NS_RANK_Y - 1) / NS_RANK_Y),
-                     NS_RANK_X, 0, s>>>(keys, nb, T.rank);
-    ns_place_kernel<<<(nb + 255) / 256, 256, 0, s>>>(keys, nb, T.rank, T.spl);
-    ns_count_kernel<<<nb, NS_THREADS, 0, s>>>(keys, n, nb, T.spl, T.cnt);
+                     NS_RANK_X, 0, s>>>(keys, vin, nb, T.rank);
+    ns_place_kernel<<<(nb + 255) / 256, 256, 0, s>>>(keys, vin, nb, T.rank, T.spl, T.splv);
+    ns_count_kernel<<<nb, NS_THREADS, 0, s>>>(keys, n, nb, T.spl, T.splv, vin, T.cnt);
     cudaMemcpyAsync(T.start, T.cnt, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s);
     launch_scan_sums(s, T.start, nb, reinterpret_cast<int32_t *>(T.start + nb));
-    ns_scatter_kernel<<<nb, NS_THREADS, 0, s>>>(keys, n, nb, T.spl, T.start, T.fill, kout, vout,
-                                                vin, status);
+    ns_scatter_kernel<<<nb, NS_THREADS, 0, s>>>(keys, n, nb, T.spl, T.splv, T.start, T.fill, kout,
+                                                vout, vin, status);
     ns_bucket_kernel<<<nb, NSS_THREADS, 0, s>>>(T.start, kout, vout, keys, vscr);
 }
 

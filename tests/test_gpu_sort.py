@@ -6,10 +6,11 @@ builds inside a step, whose keys are nearly in order already, use the bucket
 sort (splitters, scatter, a shared-memory merge sort per bucket).  Both must
 give exactly the oracle's stable order, for every input: random keys over
 the whole 64-bit range (0 and 2^64 - 1 included), the sizes around the
-bucket sort's tile (1984) and shared-memory capacity (2048), heavy and total
-ties (buckets far above the capacity, merged in global memory), reversed and
-nearly sorted keys, and the galaxy's own keys after a drift in the order of
-the build before it.
+bucket sort's tile (1984) and shared-memory capacity (2048), random keys
+whose uneven buckets exceed the capacity (merged in global memory), heavy and
+total ties (the buckets are cut by key and index, so ties spread over them),
+reversed and nearly sorted keys, and the galaxy's own keys after a drift in
+the order of the build before it.
 """
 import numpy as np
 import pytest
@@ -93,8 +94,11 @@ def test_heavy_ties(ctx, method):
 
 
 @pytest.mark.parametrize("method", METHODS)
-def test_all_keys_equal(ctx, method):
-    _check(ctx, method, np.full(50000, 0x123456789ABCDEF, dtype=np.uint64))
+@pytest.mark.parametrize("n", [50000, 1 << 21])
+def test_all_keys_equal(ctx, method, n):
+    """Buckets are cut by (key, index), so 2^21 equal keys still make
+    buckets of one tile each instead of one bucket of everything."""
+    _check(ctx, method, np.full(n, 0x123456789ABCDEF, dtype=np.uint64))
 
 
 @pytest.mark.parametrize("method", METHODS)
