@@ -242,8 +242,11 @@ nbody_status nbody_direct(int64_t n, const float *x, const float *y, const float
  * x, y, z: FP64 [n]; vx, vy, vz: FP32 [n]; m: FP32 [n];
  * ax, ay, az: FP32 [n], on entry the acceleration at the entry positions (from
  * nbody_walk), on return the acceleration at the final positions.  All arrays
- * are updated in place, in caller order.  Errors: EINVAL, ENOMEM, EOVERFLOW,
- * ECUDA. */
+ * are updated in place, in caller order.  Sorting is the stable sort of the
+ * Morton keys in caller order (Sect. 4.1); inside a call each rebuild starts
+ * from the previous build's order, and a call's first rebuild from the order
+ * the context's last call of the same n ended in -- which makes it faster,
+ * never different.  Errors: EINVAL, ENOMEM, EOVERFLOW, ECUDA. */
 nbody_status nbody_step(nbody_ctx *ctx, int64_t n, double *x, double *y, double *z,
                         float *vx, float *vy, float *vz, const float *m,
                         float *ax, float *ay, float *az, float dt, int32_t nsteps,
