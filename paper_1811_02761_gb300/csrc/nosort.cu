@@ -14,16 +14,18 @@
 //      its own or a neighbour's, checked first; a binary search otherwise --
 //      and counts them;
 //   3. the buckets' starts (a scan of the counts);
-//   4. scatter: every key and its index go to a slot of their bucket;
+//   4. scatter: every key and its value go to a slot of their bucket;
 //   5. each bucket is sorted in shared memory (a block merge sort), or, when
 //      it holds more than NS_CAP keys, sorted in chunks that are then merged
 //      pairwise in global memory.
-// The result is the sort by (key, index), which is unique with distinct
-// indices: it is the stable sort of the keys, whatever order the scatter's
-// atomics fill a bucket in.  A chunk is first sorted by key alone (half the
-// shared-memory reads); if two of its keys are equal it is sorted again by
-// (key, index).  Any input order gives the right result; a far-from-sorted
-// one only makes the buckets uneven and the count and scatter slower.
+// The value of an element is its index, or the caller's value for it (vin, a
+// permutation).  The result is the sort by (key, value), which is unique with
+// distinct values: with indices, the stable sort of the keys, whatever order
+// the scatter's atomics fill a bucket in.  A chunk is first sorted by key
+// alone (half the shared-memory reads); if two of its keys are equal it is
+// sorted again by (key, value).  Any input order gives the right result; a
+// far-from-sorted one only makes the buckets uneven and the count and
+// scatter slower.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -75,7 +77,7 @@ __device__ __forceinline__ bool pair_less(uint64_t ka, uint32_t va, uint64_t kb,
     return ka < kb || (ka == kb && va < vb);
 }
 
-// The order of the bucket sort: by key alone (PAIR false), or by (key, index).
+// The order of the bucket sort: by key alone (PAIR false), or by (key, value).
 template <bool PAIR>
 __device__ __forceinline__ bool ns_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb) {
     if constexpr (PAIR) return pair_less(ka, va, kb, vb);
@@ -205,7 +207,7 @@ __device__ bool sort_chunk_impl(uint64_t *k, uint32_t *v, int m, uint64_t *sk, u
     return true;
 }
 
-// Sorts m <= NS_CAP pairs in place by (key, index): by key alone when the
+// Sorts m <= NS_CAP pairs in place by (key, value): by key alone when the
 // keys are distinct, by both otherwise.
 __device__ void block_sort_chunk(uint64_t *k, uint32_t *v, int m, uint64_t *sk, uint32_t *sv) {
     if (!sort_chunk_impl<false>(k, v, m, sk, sv)) sort_chunk_impl<true>(k, v, m, sk, sv);
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(NS_THREADS) ns_count_kernel(const uint64_t *__
     }
 }
 
-// 4. Scatter of every key and its index to a slot of its bucket: the tile
+// 4. Scatter of every key and its value to a slot of its bucket: the tile
 // reserves one run of slots per neighbouring bucket, far keys take single
 // slots.  A slot outside the bucket (impossible unless the counts were
 // wrong) is skipped and recorded.
@@ -456,7 +458,7 @@ __global__ void ns_place_kernel(const uint64_t *__restrict__ keys,
     splv[r] = r == 0 ? 0u : (vin ? vin[e] : (uint32_t)e);
 }
 
-// 5. Sort of each bucket by (key, index), in place in (kout, vout); (kscr,
+// 5. Sort of each bucket by (key, value), in place in (kout, vout); (kscr,
 // vscr), the input keys and a free index array, give the merges of a bucket
 // of more than NS_CAP keys their scratch over the same index range.
 __global__ void __launch_bounds__(NSS_THREADS, 4) ns_bucket_kernel(const uint32_t *__restrict__ start,
