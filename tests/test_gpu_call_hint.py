@@ -86,3 +86,31 @@ def test_ties_in_morton_keys_go_by_caller_index():
     finally:
         nb.nbody_destroy(ctx)
     assert _equal(s2, _fresh(s1, 2))
+
+
+@pytest.mark.parametrize("block_levels", [0, 3])
+def test_batched_second_call_equals_a_fresh_context(block_levels):
+    """The same for a forest of systems (the keys carry the system id), with
+    shared steps and with block time steps."""
+    b = ics.batched(24, 5, 8.0, 12.0)
+    off, eps = b["offsets"], b["eps"]
+    s0 = _state(b)
+
+    def step(ctx, s, k):
+        nb.nbody_step_batched(ctx, off, eps, *s, DT, k)
+        torch.cuda.synchronize()
+        return s
+
+    cfg = dict(eps=1.0 / 64, block_levels=block_levels)
+    ctx = nb.nbody_create(nb.nbody_config_default(**cfg))
+    try:
+        s1 = step(ctx, _clone(s0), 1)
+        s2 = step(ctx, _clone(s1), 3)
+    finally:
+        nb.nbody_destroy(ctx)
+    ctx = nb.nbody_create(nb.nbody_config_default(**cfg))
+    try:
+        ref = step(ctx, _clone(s1), 3)
+    finally:
+        nb.nbody_destroy(ctx)
+    assert _equal(s2, ref)
