@@ -1407,10 +1407,14 @@ static nbody_status step_impl(nbody_ctx *ctx, int32_t nsys, const int64_t *offse
     const float hclose = pending_kick ? 0.5f * dt : 0.0f;
     pending_kick = false;
     // the Morton order this call ends in starts the next call's first sort
-    NB_CUDA(ctx, ensure(ctx->last_ids, (size_t)n * 4));
-    NB_CUDA(ctx, cudaMemcpyAsync(ctx->last_ids.p, S[cur].id, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
-    ctx->hint_n = n;
-    ctx->hint_nsys = nsys;
+    // (a call without steps ends in the caller's order: nothing to keep)
+    if (nsteps > 0) {
+        NB_CUDA(ctx, ensure(ctx->last_ids, (size_t)n * 4));
+        NB_CUDA(ctx, cudaMemcpyAsync(ctx->last_ids.p, S[cur].id, (size_t)n * 4,
+                                     cudaMemcpyDeviceToDevice, s));
+        ctx->hint_n = n;
+        ctx->hint_nsys = nsys;
+    }
     // in[] are the device copies (the caller's arrays themselves when on the device)
     launch_store_state(s, n, S[cur], acc, (double *)in[0], (double *)in[1], (double *)in[2],
                        (float *)in[3], (float *)in[4], (float *)in[5], (float *)in[7],
